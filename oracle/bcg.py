@@ -1,0 +1,266 @@
+"""CPU FP64 oracle of the generalized Block Conjugate Gradients method (Dreier & Engwer, arXiv 1912.11930).
+
+TEST INFRASTRUCTURE ONLY. Nothing in the product path may import, call or execute this module: only the
+tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` use it. It shares no code with
+the CUDA library; both are fed from ``paper_1912_11930_gb300.workloads`` (input generation only).
+
+It is deliberately plain and slow: numpy/scipy FP64, every step of Algorithm 1 done in the paper's order,
+no fusion, no blocking, no reordering. Library primitives used as single steps: the sparse product
+``A @ P`` (scipy CSR), dense matmuls, LAPACK's LU with partial pivoting, triangular solves.
+
+Paper passages followed:
+* Section 2, Definition "Relevant *-subalgebras": the block products of the hybrid (S_Hy^p) and global
+  (S_Gl^p) subalgebras; classical = S_Hy^k = S_Gl^k, parallel = S_Hy^1.
+* Section 3, Algorithm 1 (preconditioned, stabilised BCG) with M = I, including the recomputation of
+  rho^{i-1} as <<P^i, R^{i-1}>>_S (the stabilisation of Section 3), and the four kernels BDOT, BAXPY,
+  BOP, BSOLVE listed after it.
+* Section 4, whole-solver experiment: the stopping rule "2-norm of every residual column reduced by the
+  factor tol".
+
+Readings of places where the paper is silent, garbled or inconsistent (each one is also in the design doc):
+* R1 sign of the direction update: Algorithm 1 prints P^{i+1} = Z - P beta. With beta = rho_{i-1}^{-1}
+  rho_i > 0 at k = 1 this contradicts CG, so the oracle uses P^{i+1} = Z + P beta.
+* R2 global product: the printed sum runs from 0 to q; the proof of the global-rate lemma stacks
+  contiguous column blocks, so block j = columns [j p, (j+1) p) for j = 0..q-1 and the global product is
+  sum_j X_j^T Y_j, applied to every block.
+* R3 which rho^{i-1} enters beta: the recomputed one (it overwrites the old value), used both in
+  lambda = alpha^{-1} rho^{i-1} and in beta = (rho^{i-1})^{-1} rho^i.
+* R4 BSOLVE method: alpha (SPD) by Cholesky without pivoting, reading alpha's lower triangle; the
+  recomputed rho (not symmetric in floating point) by LU with partial pivoting; breakdown when a pivot is
+  <= 64 eps max|diag| or not finite.
+* R5 stopping rule: after the residual update, column s has converged when ||R_s|| <= tol ||R_s^0||
+  (recursive residual, 2-norm). Hybrid/parallel blocks freeze once all their columns have converged
+  (their lambda and beta are zero from then on); global/classical stop all columns together. A zero
+  column converges at iteration 0. The iteration count is the number of products Q = A P.
+* R6 no deflation: a breakdown is reported (status BREAKDOWN), never hidden.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+# status codes, numerically identical to the C enum bcg_status
+OK, INVALID_ARG, CUDA_ERR, OOM, BREAKDOWN, NOT_CONVERGED, NUMERIC, TIMEOUT = range(8)
+
+EPS = np.finfo(np.float64).eps
+PIVOT_FACTOR = 64.0
+
+
+def canonical_subalgebra(sub: str, k: int, p: int) -> tuple[str, int]:
+    """Map the four subalgebras of Section 2 onto (kind, p) with kind in {hybrid, global}:
+    parallel = S_Hy^1, classical = S_Hy^k (= S_Gl^k)."""
+    if sub == "parallel":
+        return "hybrid", 1
+    if sub == "classical":
+        return "hybrid", k
+    if sub not in ("hybrid", "global"):
+        raise ValueError(f"unknown subalgebra {sub!r}")
+    if p < 1 or k % p:
+        raise ValueError(f"p={p} must divide k={k}")
+    return sub, p
+
+
+def block_product(X: np.ndarray, Y: np.ndarray, p: int, kind: str) -> np.ndarray:
+    """BDOT, the S-product <<X, Y>>_S of Section 2 (Definition "Relevant *-subalgebras").
+
+    Returns the element of S as its distinct p x p blocks: shape (q, p, p) for hybrid (block j is
+    X_j^T Y_j), shape (1, p, p) for global (sum_j X_j^T Y_j, the same block for every j)."""
+    n, k = X.shape
+    q = k // p
+    blocks = [X[:, j * p:(j + 1) * p].T @ Y[:, j * p:(j + 1) * p] for j in range(q)]
+    if kind == "hybrid":
+        return np.stack(blocks)
+    total = blocks[0].copy()
+    for j in range(1, q):
+        total = total + blocks[j]
+    return total[None]
+
+
+def block_apply(Y: np.ndarray, gamma: np.ndarray) -> np.ndarray:
+    """Y gamma for gamma in S given as its distinct blocks (the product inside BAXPY)."""
+    n, k = Y.shape
+    p = gamma.shape[1]
+    q = k // p
+    out = np.empty_like(Y)
+    for j in range(q):
+        g = gamma[j] if gamma.shape[0] == q else gamma[0]
+        out[:, j * p:(j + 1) * p] = Y[:, j * p:(j + 1) * p] @ g
+    return out
+
+
+def baxpy(X: np.ndarray, Y: np.ndarray, gamma: np.ndarray, sign: float = 1.0) -> np.ndarray:
+    """BAXPY: X + sign * Y gamma (Section 3, kernel list)."""
+    return X + sign * block_apply(Y, gamma)
+
+
+def bop(A: sp.csr_matrix, X: np.ndarray) -> np.ndarray:
+    """BOP: the operator applied to a block of vectors, A X (Section 3, kernel list)."""
+    return np.asarray(A @ X)
+
+
+def cholesky_lower(G: np.ndarray):
+    """Cholesky G = L L^T from G's lower triangle, no pivoting. Returns None on breakdown
+    (a pivot <= 64 eps max|diag(G)| or not finite)."""
+    p = G.shape[0]
+    L = np.zeros_like(G)
+    thresh = PIVOT_FACTOR * EPS * np.max(np.abs(np.diag(G)))
+    for a in range(p):
+        d = G[a, a] - L[a, :a] @ L[a, :a]
+        if not (np.isfinite(d) and d > thresh):
+            return None
+        L[a, a] = np.sqrt(d)
+        L[a + 1:, a] = (G[a + 1:, a] - L[a + 1:, :a] @ L[a, :a]) / L[a, a]
+    return L
+
+
+def bsolve_cholesky(alpha: np.ndarray, delta: np.ndarray, active: np.ndarray):
+    """BSOLVE for lambda = alpha^{-1} delta in S, alpha SPD: one Cholesky per distinct block.
+    Blocks that are not active get a zero result. Returns (result, ok)."""
+    out = np.zeros_like(delta)
+    for j in range(alpha.shape[0]):
+        if not active[j]:
+            continue
+        L = cholesky_lower(alpha[j])
+        if L is None:
+            return out, False
+        y = sla.solve_triangular(L, delta[j], lower=True)
+        out[j] = sla.solve_triangular(L.T, y, lower=False)
+        if not np.all(np.isfinite(out[j])):
+            return out, False
+    return out, True
+
+
+def bsolve_lu(rho: np.ndarray, delta: np.ndarray, active: np.ndarray):
+    """BSOLVE for beta = rho^{-1} delta in S by LU with partial pivoting (rho is not symmetric in
+    floating point). Returns (result, ok)."""
+    out = np.zeros_like(delta)
+    for j in range(rho.shape[0]):
+        if not active[j]:
+            continue
+        G = rho[j]
+        if not np.all(np.isfinite(G)):
+            return out, False
+        thresh = PIVOT_FACTOR * EPS * np.max(np.abs(np.diag(G)))
+        lu, piv = sla.lu_factor(G, check_finite=False)
+        if np.any(np.abs(np.diag(lu)) <= thresh):
+            return out, False
+        out[j] = sla.lu_solve((lu, piv), delta[j], check_finite=False)
+        if not np.all(np.isfinite(out[j])):
+            return out, False
+    return out, True
+
+
+@dataclass
+class Result:
+    X: np.ndarray
+    status: int
+    iters: int                     # number of products Q = A P performed
+    block_iters: np.ndarray        # per distinct block: iteration at which it froze (or the last one)
+    breakdown_iter: int            # -1 if none
+    relres_recursive: np.ndarray   # ||R_s|| / ||R_s^0|| per column (0 where R_s^0 = 0)
+    relres_true: np.ndarray        # ||B_s - A X_s|| / ||B_s - A X_s^0|| per column
+    history: dict = field(default_factory=dict)
+
+
+def solve(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, sub: str = "hybrid",
+          tol: float = 1e-8, maxit: int = 1000, record: bool = False) -> Result:
+    """Algorithm 1 of Section 3 with M = I, FP64, step by step.
+
+    ``A`` is a scipy sparse matrix (or anything supporting ``A @ X``); B and X0 are n x k."""
+    B = np.asarray(B, dtype=np.float64)
+    n, k = B.shape
+    kind, p = canonical_subalgebra(sub, k, p)
+    q = k // p
+    nblk = q if kind == "hybrid" else 1
+    X = np.zeros_like(B) if X0 is None else np.array(X0, dtype=np.float64, copy=True)
+
+    hist = {"X": [], "R": [], "P": [], "Q": [], "alpha": [], "rho_rec": [], "rho": []} if record else {}
+
+    def colnorms(M):
+        return np.sqrt(np.sum(M * M, axis=0))
+
+    # R^0 = B - A X^0
+    R = B - bop(A, X)
+    # P^1 = M^{-1} R^0 with M = I
+    P = R.copy()
+    r0 = colnorms(R)
+    if not (np.all(np.isfinite(r0)) and np.all(np.isfinite(X))):
+        return Result(X, NUMERIC, 0, np.zeros(nblk, dtype=np.int64), -1, r0 * np.nan, r0 * np.nan, hist)
+
+    def block_converged(rn):
+        col_ok = rn <= tol * r0
+        if kind == "hybrid":
+            return np.array([bool(np.all(col_ok[j * p:(j + 1) * p])) for j in range(q)])
+        return np.array([bool(np.all(col_ok))])
+
+    active = ~block_converged(r0)
+    block_iters = np.zeros(nblk, dtype=np.int64)
+    status, brk, it = OK, -1, 0
+    if record:
+        hist["X"].append(X.copy()); hist["R"].append(R.copy()); hist["P"].append(P.copy())
+
+    while np.any(active) and it < maxit:
+        it += 1
+        block_iters[active] = it
+        # Q^i = A P^i
+        Q = bop(A, P)
+        # alpha^i = <<P^i, Q^i>>
+        alpha = block_product(P, Q, p, kind)
+        # rho^{i-1} = <<P^i, R^{i-1}>>  (recomputed)
+        rho_rec = block_product(P, R, p, kind)
+        # lambda^i = (alpha^i)^{-1} rho^{i-1}
+        lam, ok = bsolve_cholesky(alpha, rho_rec, active)
+        if not ok:
+            status, brk = BREAKDOWN, it
+            break
+        # X^i = X^{i-1} + P^i lambda^i ;  R^i = R^{i-1} - Q^i lambda^i
+        X = baxpy(X, P, lam, +1.0)
+        R = baxpy(R, Q, lam, -1.0)
+        rn = colnorms(R)
+        if not np.all(np.isfinite(rn)):
+            status = NUMERIC
+            break
+        active = active & ~block_converged(rn)
+        # Z^{i+1} = M^{-1} R^i = R^i ; rho^i = <<Z^{i+1}, R^i>>
+        rho = block_product(R, R, p, kind)
+        # beta^i = (rho^{i-1})^{-1} rho^i
+        beta, ok = bsolve_lu(rho_rec, rho, active)
+        if record:
+            hist["Q"].append(Q.copy()); hist["alpha"].append(alpha); hist["rho_rec"].append(rho_rec)
+            hist["rho"].append(rho)
+        if not ok:
+            status, brk = BREAKDOWN, it
+            break
+        # P^{i+1} = Z^{i+1} + P^i beta^i   (sign reading R1)
+        P = baxpy(R, P, beta, +1.0)
+        if record:
+            hist["X"].append(X.copy()); hist["R"].append(R.copy()); hist["P"].append(P.copy())
+
+    if status == OK and np.any(active):
+        status = NOT_CONVERGED
+    rn = colnorms(R)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        rel_rec = np.where(r0 > 0, rn / np.where(r0 > 0, r0, 1.0), 0.0)
+        rt = colnorms(B - bop(A, X))
+        rel_true = np.where(r0 > 0, rt / np.where(r0 > 0, r0, 1.0), rt)
+    return Result(X, status, it, block_iters, brk, rel_rec, rel_true, hist)
+
+
+def grad_values(rowptr: np.ndarray, colind: np.ndarray, Lam: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Gradient of a loss L(X), X = A^{-1} B, with respect to the stored CSR values of A:
+    dL/dA_ij = -Lambda_i . X_j (row i of the adjoint solution Lambda = A^{-T} dL/dX dotted with row j of
+    X), one value per stored entry (i, j). Follows from dX = -A^{-1} dA X."""
+    n = rowptr.shape[0] - 1
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    return -np.einsum("ec,ec->e", Lam[rows], X[colind.astype(np.int64)])
+
+
+def solve_and_grad(A, rowptr, colind, B, W, p=1, sub="hybrid", tol=1e-12, maxit=5000):
+    """Forward solve X = A^{-1} B, loss L = sum(W * X), adjoint solve A Lambda = W (A symmetric),
+    dL/dB = Lambda, dL/dvals from ``grad_values``."""
+    fwd = solve(A, B, p=p, sub=sub, tol=tol, maxit=maxit)
+    adj = solve(A, W, p=p, sub=sub, tol=tol, maxit=maxit)
+    return fwd, adj, grad_values(rowptr, colind, adj.X, fwd.X)

@@ -1,0 +1,56 @@
+"""Seeded input generators: closed-form nonzero counts, symmetry, positive definiteness on tiny sizes,
+and platform-independent seeding."""
+import numpy as np
+import pytest
+
+from paper_1912_11930_gb300 import workloads as W
+
+
+def test_poisson_nnz_closed_forms():
+    # 5-point: 5n - 2(nx + ny); 7-point: 7n - 2(nx ny + ny nz + nx nz)
+    assert W.poisson2d(64).nnz == 5 * 4096 - 2 * 128 == 20224
+    m = W.poisson3d(12)
+    assert m.nnz == 7 * 12 ** 3 - 6 * 12 ** 2
+    assert 7 * 128 ** 3 - 6 * 128 ** 2 == 14581760   # the 128^3 workload
+
+
+@pytest.mark.parametrize("make", [lambda: W.poisson2d(5, 4), lambda: W.poisson3d(3, 4, 2),
+                                  lambda: W.varcoef3d(3, 4, 2, seed=1), lambda: W.stencil27(3, 2, 4, seed=2)])
+def test_symmetric_positive_definite(make):
+    M = make()
+    A = M.to_scipy().toarray()
+    assert np.array_equal(A, A.T)
+    assert np.linalg.eigvalsh(A)[0] > 0
+    assert np.all(np.diff(M.rowptr) > 0)
+    for i in range(M.n):   # sorted columns within each row
+        c = M.colind[M.rowptr[i]:M.rowptr[i + 1]]
+        assert np.all(np.diff(c) > 0)
+
+
+def test_poisson_scaling():
+    M = W.poisson2d(64)
+    h = 1.0 / 65
+    A = M.to_scipy()
+    assert A[0, 0] == pytest.approx(4.0 / h ** 2) and A[0, 1] == pytest.approx(-1.0 / h ** 2)
+
+
+def test_varcoef_rows_sum_to_boundary_faces():
+    """Row sums of the variable-coefficient operator equal h^-2 times the cell's boundary-face
+    coefficients (interior faces cancel)."""
+    nx, ny, nz = 3, 4, 2
+    M = W.varcoef3d(nx, ny, nz, seed=3)
+    A = M.to_scipy()
+    fx, fy, fz = W.split_faces(M.stencil["coef"], nx, ny, nz)
+    bnd = np.zeros((nz, ny, nx))
+    bnd[:, :, 0] += fx[:, :, 0]; bnd[:, :, -1] += fx[:, :, -1]
+    bnd[:, 0, :] += fy[:, 0, :]; bnd[:, -1, :] += fy[:, -1, :]
+    bnd[0] += fz[0]; bnd[-1] += fz[-1]
+    assert np.allclose(np.asarray(A.sum(axis=1)).ravel(), M.stencil["scale"] * bnd.ravel(), rtol=1e-12)
+
+
+def test_seeds():
+    a = W.rhs(10, 3, seed=4)
+    assert np.array_equal(a, W.rhs(10, 3, seed=4))
+    assert not np.array_equal(a, W.loss_weights(10, 3, seed=4))
+    # PCG64 standard normals are platform independent; first value for seed 0
+    assert W.rhs(1, 1, seed=0)[0, 0] == pytest.approx(0.12573022, abs=1e-8)
