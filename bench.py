@@ -1,0 +1,345 @@
+#!/usr/bin/env python
+"""Benchmark of the block CG hot path: time-to-tolerance of one solve (a "step" = one full solve from
+X^0 = 0 to every column's relative residual <= 1e-8), per-iteration HBM traffic and the roofline of the
+dominant kernel, measured live with CUDA events on the solver's stream.
+
+Default workload: 3D 7-point Poisson 128^3 (n = 2,097,152, CSR), k = 32 right-hand sides i.i.d. N(0,1),
+hybrid subalgebra p = 8, FP64, tol 1e-8. At N > 1 GPUs every rank solves its own 32 right-hand sides
+(seed + rank; hybrid blocks are independent, so no data-path collective) and the job time is the max over
+ranks.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--no-variants]
+
+--impl reference times the CPU oracle (the only reference this method has) on a bounded sample of the
+same workload and prints the same line with "impl": "reference".
+"""
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BCG time-to-1e-8 rel. residual; HBM GB/s/iter vs roofline; mixed vs FP64"
+NOMINAL_FP64_TFLOPS = 1.25          # GB300 FP64 (vector and tensor) per GPU, nominal
+WORKLOAD = dict(name="poisson3d_128_csr_k32_hybrid_p8_fp64", grid=128, k=32, p=8, sub="hybrid", prec="fp64",
+                tol=1e-8)
+# Iterations the 128^3 / k = 32 / hybrid p = 8 FP64 solve takes to reach 1e-8 (measured on the GPU; the oracle
+# agrees within +-2 on every size it can finish). Used only to extrapolate the oracle's per-iteration time
+# to a time-to-tolerance in the reference arm.
+REF_ITERS = None
+ORACLE_SAMPLE_ITERS = 3
+# DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/k_op_gram_poisson3d_96_*.md,
+# scaled by rows to 128^3), valid only for the kernel source it was taken on (sha256 prefix of the
+# bcg_kernels.cuh text from apply_row to the end of k_op_gram); reported as null once that source changes.
+TRAFFIC = {("op_gram", "poisson3d_128_csr_k32_hybrid_p8_fp64"): ("7908c5fc0ec73b8b", 1.986e9)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6782.1)), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def kernel_model(n, k, p, z, s, a_bytes):
+    """Algorithmic flops and bytes per launch of each iteration kernel (the paper's Table 1 per kernel,
+    fused as the kernels fuse them): K1 = BOP + 2 BDOT, K2 = 2 BAXPY + BDOT + column norms, K3 = BAXPY."""
+    return {
+        "op_gram": dict(flops=2.0 * k * z + 4.0 * n * p * k, bytes=a_bytes + 3.0 * n * k * s),
+        "update_xr": dict(flops=6.0 * n * p * k + 2.0 * n * k, bytes=6.0 * n * k * s),
+        "update_p": dict(flops=2.0 * n * p * k, bytes=3.0 * n * k * s),
+    }
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].replace(".", "").isdigit())
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": float(rows[0][2]),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def oracle_sample(grid, k, p, sub, iters, seed):
+    """Time the CPU oracle on `iters` iterations of the workload in a fresh single-threaded process.
+    Returns (seconds per iteration, seconds of the sample)."""
+    code = f"""
+import json, sys, time
+sys.path.insert(0, {ROOT!r})
+from oracle import bcg as O
+from paper_1912_11930_gb300 import workloads as W
+M = W.poisson3d({grid})
+A = M.to_scipy()
+B = W.rhs(M.n, {k}, seed={seed})
+t0 = time.perf_counter()
+O.solve(A, B, p={p}, sub={sub!r}, tol=0.0, maxit=1)
+t1 = time.perf_counter()
+O.solve(A, B, p={p}, sub={sub!r}, tol=0.0, maxit={1 + iters})
+t2 = time.perf_counter()
+print(json.dumps(dict(per_iter=((t2 - t1) - (t1 - t0)) / {iters}, first=t1 - t0, total=t2 - t0)))
+"""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = WORKLOAD
+    iters_to_tol = REF_ITERS
+    samples = []
+    for _ in range(args.warmup + args.steps):
+        samples.append(oracle_sample(w["grid"], w["k"], w["p"], w["sub"], 1, seed=0))
+    timed = samples[args.warmup:]
+    per_iter = sum(s["per_iter"] for s in timed) / len(timed)
+    first = sum(s["first"] for s in timed) / len(timed)
+    value = first + per_iter * iters_to_tol if iters_to_tol else None
+    line = {"metric": METRIC, "value": value, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": None if value is None else value * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": w["name"], "n": w["grid"] ** 3, "k": w["k"], "p": w["p"],
+                       "subalgebra": w["sub"], "tol": w["tol"]},
+            "cpu_baseline": {"value": value, "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": f"each step: 1 oracle iteration of the full workload (plus the initial "
+                                       f"residual), single-threaded; time-to-tolerance = initial residual + "
+                                       f"per-iteration time x {iters_to_tol} iterations"},
+            "e2e": {"value": value, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--grid", type=int, default=WORKLOAD["grid"],
+                    help="Poisson grid edge (smaller grids only for profiling captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    from paper_1912_11930_gb300 import bcg, workloads as W
+
+    def barrier():
+        if dist:
+            dist.barrier()
+
+    w = dict(WORKLOAD)
+    if args.grid != w["grid"]:
+        w["grid"] = args.grid
+        w["name"] = w["name"].replace("128", str(args.grid))
+    M = W.poisson3d(w["grid"])
+    n, k, p, z = M.n, w["k"], w["p"], M.nnz
+    B_host = W.rhs(n, k, seed=rank)
+    B = torch.from_numpy(B_host).to(dev)
+    X = torch.zeros_like(B)
+    S = bcg.Solver.from_matrix(M, k=k, p=p, sub=w["sub"], prec=w["prec"], device=dev)
+    for _ in range(args.warmup):
+        X.zero_()
+        X, res = S.solve(B, X, tol=w["tol"], maxit=20000)
+        assert res.ok, res
+    S.set_option("profile", 1)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    results = []
+    e0.record(S.stream)
+    for _ in range(args.steps):
+        with torch.cuda.stream(S.stream):
+            X.zero_()
+        X, res = S.solve(B, X, tol=w["tol"], maxit=20000)
+        results.append(res)
+    e1.record(S.stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    if dist:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    prof = S.profile()
+    S.set_option("profile", 0)
+    iters = results[-1].iters
+    ok = all(r.ok and r.max_rel_res_true <= 1.5 * w["tol"] for r in results)
+
+    # roofline of the dominant kernel
+    s_bytes = 8
+    a_bytes = 12.0 * z + 8.0 * (n + 1)
+    model = kernel_model(n, k, p, z, s_bytes, a_bytes)
+    hbm_peak, hbm_src = peaks()
+    per_kernel = {}
+    for name, (tot, cnt) in prof.items():
+        if cnt > 0:
+            entry = {"avg_ms": tot / cnt, "launches": cnt, "share": None}
+            if name in model:
+                mdl = model[name]
+                entry["alg_gflop"] = mdl["flops"] / 1e9
+                entry["alg_gb"] = mdl["bytes"] / 1e9
+                entry["tflops"] = mdl["flops"] / (tot / cnt * 1e-3) / 1e12
+                entry["gbs"] = mdl["bytes"] / (tot / cnt * 1e-3) / 1e9
+            per_kernel[name] = entry
+    total_ms = sum(v["avg_ms"] * v["launches"] for v in per_kernel.values())
+    for v in per_kernel.values():
+        v["share"] = v["avg_ms"] * v["launches"] / total_ms if total_ms else None
+    dom = max((nm for nm in per_kernel if nm in model), key=lambda nm: per_kernel[nm]["share"])
+    d = per_kernel[dom]
+    traffic = None
+    import hashlib
+    src = os.path.join(ROOT, "paper_1912_11930_gb300", "csrc", "bcg_kernels.cuh")
+    text = open(src).read()
+    region = text[text.index("// One row of BOP"):text.index("// K2: X += P lambda")]
+    cur_sha = hashlib.sha256(region.encode()).hexdigest()[:16]
+    ent = TRAFFIC.get((dom, w["name"]))
+    if ent and ent[0] == cur_sha:
+        traffic = ent[1]
+    roofline = {"bound": "alu", "kernel": dom, "achieved": d["tflops"], "peak": NOMINAL_FP64_TFLOPS,
+                "unit": "TFLOP/s", "frac": d["tflops"] / NOMINAL_FP64_TFLOPS, "traffic": traffic,
+                "peak_source": "nominal FP64 (GB300 FP64 vector and tensor rate; the P0 DFMA probe measured 1.19)",
+                "hbm_achieved_gbs": d["gbs"], "hbm_peak_gbs": hbm_peak, "hbm_frac": d["gbs"] / hbm_peak,
+                "hbm_peak_source": hbm_src}
+    iter_bytes = sum(model[nm]["bytes"] for nm in model)
+    iter_ms = sum(per_kernel[nm]["avg_ms"] for nm in per_kernel)
+    launched_iters = int(math.ceil(iters / 8.0) * 8)
+    gpu_launches = args.steps * (4 + 5 * launched_iters)
+
+    line = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"], "n": n, "nnz": z, "k": k, "p": p, "subalgebra": w["sub"],
+                       "tol": w["tol"], "rhs_per_rank": k, "l2": "inputs larger than L2 (537 MB per block vector)",
+                       "parallelism": f"independent right-hand-side blocks per rank x{world}"},
+            "iterations": iters, "converged": ok, "max_rel_res_true": max(r.max_rel_res_true for r in results),
+            "gb_per_iter_model": iter_bytes / 1e9, "gbs_per_iter": iter_bytes / (iter_ms * 1e-3) / 1e9,
+            "hbm_frac_per_iter": iter_bytes / (iter_ms * 1e-3) / 1e9 / hbm_peak,
+            "kernels": per_kernel, "roofline": roofline, "gpu_launches": gpu_launches, "clocks": clk}
+
+    # end-to-end through the public host-buffer entry point: B and X^0 host -> device, X device -> host
+    if rank == 0 or world > 1:
+        Bh = torch.from_numpy(B_host).pin_memory().numpy()
+        Xh = torch.zeros(n, k, dtype=torch.float64).pin_memory().numpy()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Xh[:] = 0.0
+            Xh, rh = S.solve_host(Bh, Xh, tol=w["tol"], maxit=20000)
+        torch.cuda.synchronize()
+        e2e = (time.perf_counter() - t0) / args.steps
+        t = torch.tensor([e2e], dtype=torch.float64, device=dev)
+        if dist:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": float(t.item()), "unit": "s", "h2d_bytes_per_step": 2 * n * k * 8,
+                       "d2h_bytes_per_step": n * k * 8}
+
+    if rank == 0 and world == 1 and not args.no_variants:
+        variants = {}
+        for vname, sub, vp, prec in (("parallel_p1_fp64", "parallel", 1, "fp64"),
+                                     ("global_p32_fp64", "global", 32, "fp64"),
+                                     ("hybrid_p8_fp32_refine", "hybrid", 8, "fp32_refine")):
+            V = bcg.Solver.from_matrix(M, k=k, p=vp, sub=sub, prec=prec, device=dev)
+            Xv = torch.zeros_like(B)
+            V.solve(B, Xv, tol=w["tol"], maxit=20000)
+            Xv.zero_()
+            torch.cuda.synchronize()
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(V.stream)
+            Xv, rv = V.solve(B, Xv, tol=w["tol"], maxit=20000)
+            a1.record(V.stream)
+            torch.cuda.synchronize()
+            variants[vname] = {"s": a0.elapsed_time(a1) / 1e3, "iterations": rv.iters, "outer": rv.outer_iters,
+                               "status": bcg.STATUS_NAMES[rv.status], "max_rel_res_true": rv.max_rel_res_true}
+            V.close()
+        variants["hybrid_p8_fp64"] = {"s": ms_max / 1e3, "iterations": iters}
+        line["variants"] = variants
+        line["mixed_vs_fp64_speedup"] = variants["hybrid_p8_fp64"]["s"] / variants["hybrid_p8_fp32_refine"]["s"]
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        smp = oracle_sample(w["grid"], k, p, w["sub"], ORACLE_SAMPLE_ITERS, seed=0)
+        val = smp["first"] + smp["per_iter"] * iters
+        line["cpu_baseline"] = {"value": val, "unit": "s", "cores": 1, "kind": "oracle",
+                                "sample": f"{ORACLE_SAMPLE_ITERS} oracle iterations of the full workload "
+                                          f"({smp['total']:.1f} s, single-threaded); time-to-tolerance = initial "
+                                          f"residual + per-iteration time x the GPU's {iters} iterations",
+                                "per_iter_s": smp["per_iter"]}
+    S.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,208 @@
+/*
+ * bcg.h -- C ABI of libbcg.so, a GB300 (sm_103a) implementation of the hot path of the generalized
+ * Block Conjugate Gradients method (Dreier & Engwer, "Strategies for the vectorized Block Conjugate
+ * Gradients method", arXiv 1912.11930).
+ *
+ * The library solves A X = B for a sparse symmetric positive definite A (n x n) and n x k blocks B, X
+ * with Algorithm 1 of Section 3 (stabilised block CG, preconditioner M = I). Every block product is
+ * restricted to one *-subalgebra S of R^{k x k} (Section 2, Definition "Relevant *-subalgebras"):
+ *   hybrid    S_Hy^p = diag((R^{p x p})^q), q = k/p: q independent p x p Gram blocks;
+ *   global    S_Gl^p = R^{p x p} (x) I_q: one p x p Gram summed over the q blocks, applied to each;
+ *   parallel  S_Pl   = S_Hy^1: k independent CGs in lockstep;
+ *   classical S_Cl   = S_Hy^k = S_Gl^k: O'Leary's block CG.
+ * Column block j is the contiguous column range [j p, (j+1) p).
+ *
+ * Conventions for every function:
+ *  - Block vectors are row-major n x k with leading dimension k: element (i, c) at i*k + c.
+ *  - "device" pointers must be CUDA device (or managed) memory of the current device; "host" pointers
+ *    ordinary or pinned host memory.
+ *  - The caller owns every array it passes in. A handle BORROWS the matrix arrays given to
+ *    bcg_create_* until bcg_destroy (they must stay valid and unchanged, except through
+ *    bcg_update_values) and OWNS all of its workspace, allocated once at create time.
+ *  - Every function returns a bcg_status and never aborts the process. Argument errors are detected on
+ *    the host before any launch and leave all outputs untouched. bcg_last_error() describes the most
+ *    recent failure of the calling thread.
+ *  - Work is ordered on the handle's CUDA stream; bcg_solve returns after the final status is known.
+ *  - A handle may be used by one thread at a time.
+ */
+#ifndef BCG_H
+#define BCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bcg_ctx *bcg_handle;
+
+typedef enum {
+  BCG_OK = 0,
+  BCG_ERR_INVALID_ARG = 1,   /* bad size, pointer, enum or option; nothing was launched            */
+  BCG_ERR_CUDA = 2,          /* a CUDA runtime call failed                                          */
+  BCG_ERR_OOM = 3,           /* workspace allocation failed; nothing is leaked                      */
+  BCG_ERR_BREAKDOWN = 4,     /* a p x p pivot <= 64 eps max|diag| or not finite (no deflation, the
+                                method of Section 3 has none); X holds the last completed iterate    */
+  BCG_ERR_NOT_CONVERGED = 5, /* maxit reached; X holds the last iterate, info is filled              */
+  BCG_ERR_NUMERIC = 6,       /* a non-finite value in B, X0 or a residual norm                       */
+  BCG_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up                                  */
+} bcg_status;
+
+typedef enum {
+  BCG_SUB_HYBRID = 0,
+  BCG_SUB_GLOBAL = 1,
+  BCG_SUB_PARALLEL = 2,      /* same as hybrid with p = 1 (p is ignored) */
+  BCG_SUB_CLASSICAL = 3      /* same as hybrid with p = k (p is ignored) */
+} bcg_subalgebra;
+
+typedef enum {
+  BCG_FP64 = 0,              /* every step in IEEE FP64                                               */
+  BCG_FP32_REFINE = 1        /* FP64 iterative refinement around an FP32 inner block CG: operator
+                                products and block updates in FP32, Gram matrices accumulated in
+                                FP64, p x p Cholesky/LU solves and the outer residual in FP64       */
+} bcg_precision;
+
+typedef enum {
+  BCG_STENCIL_5PT_2D = 0,         /* scale * (4, -1, -1, -1, -1) on nx x ny, Dirichlet eliminated     */
+  BCG_STENCIL_7PT_3D = 1,         /* scale * (6, -1 x 6) on nx x ny x nz                              */
+  BCG_STENCIL_7PT_3D_VARCOEF = 2  /* scale * face-coefficient diffusion, see bcg_create_stencil       */
+} bcg_stencil_kind;
+
+typedef struct {
+  int32_t status;                 /* bcg_status of the solve                                         */
+  int32_t iters;                  /* FP64: products Q = A P performed (max over blocks);
+                                     FP32_REFINE: total inner iterations over all outer steps         */
+  int32_t outer_iters;            /* FP32_REFINE: refinement steps (0 for FP64)                      */
+  int32_t breakdown_iter;         /* iteration of a breakdown, -1 if none                            */
+  double max_rel_res_recursive;   /* max_s ||R_s|| / ||R_s^0|| of the recursive residual            */
+  double max_rel_res_true;        /* max_s ||B_s - A X_s|| / ||B_s - A X_s^0||, recomputed in FP64   */
+} bcg_info;
+
+/*
+ * bcg_create_csr -- solver for a CSR matrix (Section 3, kernel BOP "Y <- A X" on an assembled matrix).
+ *   n, nnz        matrix order and number of stored entries (n >= 1, nnz >= 1)
+ *   rowptr        device int64[n+1], rowptr[0] = 0, rowptr[n] = nnz
+ *   colind        device int32[nnz], column of each entry, 0 <= colind < n
+ *   vals          device double[nnz]; A must be symmetric positive definite
+ *   k, p, sub     number of right-hand sides (1..256), block size (p divides k, p <= 32 in this
+ *                 version), subalgebra (bcg_subalgebra)
+ *   prec          bcg_precision
+ *   cuda_stream   cudaStream_t to order all work on (NULL = legacy default stream)
+ * Returns INVALID_ARG for bad sizes/pointers/enums, OOM if the workspace (about 4 n k scalars plus
+ * small buffers) cannot be allocated.
+ */
+bcg_status bcg_create_csr(bcg_handle *h, int64_t n, int64_t nnz, const int64_t *rowptr,
+                          const int32_t *colind, const double *vals, int32_t k, int32_t p,
+                          int32_t sub, int32_t prec, void *cuda_stream);
+
+/*
+ * bcg_create_stencil -- matrix-free solver (BOP as a stencil, no assembled matrix).
+ *   kind          bcg_stencil_kind; nz = 1 for the 2D stencil
+ *   coef          NULL for the constant stencils. For BCG_STENCIL_7PT_3D_VARCOEF a device double
+ *                 array of face coefficients: x-faces [nz][ny][nx+1], then y-faces [nz][ny+1][nx],
+ *                 then z-faces [nz+1][ny][nx] (boundary faces included). Row i = x + nx*(y + ny*z) has
+ *                 A_ii = scale * (sum of its six faces) and A_ij = -scale * (shared face).
+ *   scale         multiplies the stencil (e.g. 1/h^2)
+ * Other arguments as for bcg_create_csr. bcg_grad_values is not available on stencil handles.
+ */
+bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t ny, int32_t nz,
+                              const double *coef, double scale, int32_t k, int32_t p, int32_t sub,
+                              int32_t prec, void *cuda_stream);
+
+/*
+ * bcg_set_option -- tune a handle. Keys:
+ *   "inner_tol"    FP32_REFINE: relative residual reduction of each inner solve (default 1e-4)
+ *   "max_outer"    FP32_REFINE: maximum refinement steps (default 30)
+ *   "check_every"  iterations launched between two host reads of the device status word (default 8;
+ *                  converged iterations in between are skipped on the device at launch cost only)
+ *   "graph"        1 = replay the batch of iterations as a captured CUDA graph, 0 = plain launches
+ *                  (default 1; graphs need a non-NULL stream)
+ *   "profile"      1 = time every iteration kernel with CUDA events (see bcg_profile), 0 = off;
+ *                  setting it resets the counters
+ * Unknown keys or out-of-range values return INVALID_ARG.
+ */
+bcg_status bcg_set_option(bcg_handle h, const char *key, double value);
+
+/*
+ * bcg_solve -- Algorithm 1 (Section 3) with M = I from X^0 = X to the stopping rule of Section 4's
+ * whole-solver experiment: every column s with ||R_s|| <= tol ||R_s^0|| (recursive residual, 2-norm).
+ * Hybrid/parallel blocks stop updating once all their columns pass; global/classical stop together.
+ *   B      device double[n*k], row-major, not modified
+ *   X      device double[n*k], row-major; in: X^0, out: the solution (or last iterate on error)
+ *   tol    > 0 (FP32_REFINE: tolerance of the FP64 outer residual)
+ *   maxit  >= 1; FP64: iteration cap; FP32_REFINE: cap on inner iterations per refinement step
+ *   info   host, may be NULL
+ * Returns OK, BREAKDOWN, NOT_CONVERGED, NUMERIC, TIMEOUT, CUDA or INVALID_ARG.
+ */
+bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32_t maxit,
+                     bcg_info *info);
+
+/*
+ * bcg_solve_host -- bcg_solve on HOST arrays: copies B and X^0 to the handle's device staging
+ * buffers (allocated at the first call, 2 n k doubles), solves, and copies X back. Same arguments
+ * and statuses as bcg_solve, with B and X in host memory.
+ */
+bcg_status bcg_solve_host(bcg_handle h, const double *B, double *X, double tol, int32_t maxit,
+                          bcg_info *info);
+
+/*
+ * bcg_block_iters -- per distinct block (q for hybrid/parallel/classical, 1 for global) the
+ * iteration at which it froze in the last solve (or the last iteration if it never did).
+ * out: host int32[cap]; returns INVALID_ARG if cap is smaller than the number of blocks.
+ */
+bcg_status bcg_block_iters(bcg_handle h, int32_t *out, int32_t cap);
+
+/*
+ * bcg_grad_values -- gradient of a loss L(X) with respect to the stored CSR values, for
+ * X = A^{-1} B: grad[e] = -Lambda_i . X_j for stored entry e = (i, j), where Lambda solves
+ * A Lambda = dL/dX (an adjoint solve with the same handle, since A is symmetric).
+ *   Lambda, X  device double[n*k]; grad: device double[nnz] (overwritten)
+ * CSR handles only (INVALID_ARG otherwise). The paper has no differentiation; this is the adjoint
+ * of BOP on the sparsity pattern.
+ */
+bcg_status bcg_grad_values(bcg_handle h, const double *Lambda, const double *X, double *grad);
+
+/*
+ * bcg_update_values -- rebind the CSR values (same pattern) or the varcoef faces: vals is a device
+ * array of the same length as at create time; it is borrowed from now on.
+ */
+bcg_status bcg_update_values(bcg_handle h, const double *vals);
+
+/*
+ * bcg_bdot -- the BDOT kernel alone (Section 3; Section 2, Definition "Relevant *-subalgebras"):
+ * gamma = <<X, Y>>_S for the handle's k, p and subalgebra, accumulated in FP64 with per-CTA partials in
+ * the handle's workspace and summed in a fixed order.
+ *   X, Y   device double[n*k], row-major
+ *   gamma  device double[nblk*p*p], nblk = q (hybrid/parallel/classical) or 1 (global); block jb's entry
+ *          (a, b) = sum_i X[i, jb*p + a] Y[i, jb*p + b] (global: summed over the q blocks) at jb*p*p + a*p + b
+ */
+bcg_status bcg_bdot(bcg_handle h, const double *X, const double *Y, double *gamma);
+
+/*
+ * bcg_bop -- the BOP kernel alone (Section 3): Y = A X in FP64 with the handle's operator.
+ *   X, Y  device double[n*k], row-major, must not overlap.
+ */
+bcg_status bcg_bop(bcg_handle h, const double *X, double *Y);
+
+/*
+ * bcg_profile -- live per-kernel timing. After bcg_set_option(h, "profile", 1) (which also resets the
+ * counters) every iteration kernel of the following solves is bracketed by CUDA events on the handle's
+ * stream (plain launches, no graph replay), counting only iterations that executed. Fills, for
+ *   0 K1 (BOP + alpha + recomputed rho), 1 K4a (Cholesky solve), 2 K2 (X, R update + rho + norms),
+ *   3 K4b (stopping test + LU solve), 4 K3 (P update), 5 reserved,
+ * the total milliseconds ms[i] and the launch count count[i]. ms, count: host arrays of cap >= 6.
+ * Timing instrumentation, not part of the paper's method.
+ */
+bcg_status bcg_profile(bcg_handle h, double *ms, int64_t *count, int32_t cap);
+
+/* bcg_last_error -- message of the calling thread's most recent failure ("" if none). */
+const char *bcg_last_error(void);
+
+/* bcg_destroy -- free the handle's workspace; NULL-safe. */
+void bcg_destroy(bcg_handle h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCG_H */

@@ -1,0 +1,653 @@
+// C ABI of libbcg.so (declared in include/bcg.h) and the host-side iteration driver.
+//
+// One solve is: K0 (R = B - A X, P = R, ||R^0_c||^2) and a status reset, then iterations of
+//   K1  Q = A P, alpha = <<P,Q>>, rho_rec = <<P,R>>        (BOP + 2 BDOT, Algorithm 1)
+//   K4a lambda = alpha^{-1} rho_rec                          (BSOLVE, Cholesky)
+//   K2  X += P lambda, R -= Q lambda, rho = <<R,R>>, ||R_c||  (2 BAXPY + BDOT)
+//   K4b stopping test, beta = rho_rec^{-1} rho                (BSOLVE, LU with partial pivoting)
+//   K3  P = R + P beta                                        (BAXPY)
+// launched in batches of `check_every` iterations (optionally replayed as one CUDA graph) between two
+// host reads of the device status word; once the device has flagged completion the remaining kernels
+// of a batch return immediately.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/bcg.h"
+#include "bcg_launch.h"
+
+using namespace bcgk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+bcg_status fail(bcg_status s, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return s;
+}
+
+#define CK(call)                                                                                  \
+  do {                                                                                            \
+    cudaError_t e_ = (call);                                                                      \
+    if (e_ != cudaSuccess)                                                                        \
+      return fail(e_ == cudaErrorMemoryAllocation ? BCG_ERR_OOM : BCG_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                             \
+  } while (0)
+
+#define CKS(expr)                        \
+  do {                                   \
+    bcg_status s_ = (expr);              \
+    if (s_ != BCG_OK) return s_;         \
+  } while (0)
+
+bool is_device_ptr(const void *p) {
+  if (p == nullptr) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct bcg_ctx {
+  // problem
+  int64_t n = 0, nnz = 0;
+  int k = 0, p = 0, global = 0, nblk = 0, prec = BCG_FP64;
+  int opkind = OP_CSR;
+  OpDesc A64{}, A32{};
+  int64_t ncoef = 0;                   // length of vals (CSR) or faces (varcoef), 0 otherwise
+  cudaStream_t stream = nullptr;
+  int nsm = 0;
+  StreamGrids g64{}, g32{};
+  int nparts = 0;                      // partial-buffer rows (max CTAs of K0/K1/K2)
+  // options
+  double inner_tol = 1e-4;
+  int max_outer = 30;
+  int check_every = 8;
+  int use_graph = 1;
+  int profile = 0;
+  // live per-kernel timing (profile = 1): CUDA events around every launch of an executed iteration
+  static constexpr int kKernels = 6;   // K1 op_gram, K4a solve_lambda, K2 update_xr, K4b solve_beta, K3 update_p, K0 residual
+  double prof_ms[kKernels] = {0, 0, 0, 0, 0, 0};
+  int64_t prof_count[kKernels] = {0, 0, 0, 0, 0, 0};
+  std::vector<cudaEvent_t> ev;         // 2 * 5 * check_every events, reused per batch
+  // workspace (owned)
+  std::vector<void *> allocs;
+  double *R = nullptr, *P = nullptr, *Q = nullptr;           // FP64 iteration vectors
+  float *R32 = nullptr, *P32 = nullptr, *Q32 = nullptr, *D32 = nullptr;
+  void *vals32 = nullptr;              // FP32 copy of CSR values or faces
+  double *partA = nullptr, *partR = nullptr, *partRho = nullptr, *partN = nullptr;
+  double *lam = nullptr, *beta = nullptr, *rho_rec = nullptr;
+  double *r0n2 = nullptr, *rn2 = nullptr, *rtn2 = nullptr, *outer0 = nullptr;
+  int *active = nullptr, *block_iters = nullptr;
+  int32_t *rowidx = nullptr;           // CSR row of each entry (gradient)
+  DevStatus *st = nullptr;
+  DevStatus *h_st = nullptr;           // pinned
+  double *h_vec = nullptr;             // pinned, 3k doubles
+  int *h_iters = nullptr;              // pinned, nblk ints
+  double *stageB = nullptr, *stageX = nullptr;  // bcg_solve_host staging
+  // graph of one batch of inner FP32 iterations (workspace pointers only, so reusable)
+  cudaGraphExec_t graph32 = nullptr;
+  int graph32_batch = 0;
+  std::vector<int> last_block_iters;
+
+  template <typename U>
+  bcg_status alloc(U **ptr, size_t count) {
+    void *p_ = nullptr;
+    cudaError_t e = cudaMalloc(&p_, count * sizeof(U) + 16);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      return fail(BCG_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(U), cudaGetErrorString(e));
+    }
+    allocs.push_back(p_);
+    *ptr = static_cast<U *>(p_);
+    return BCG_OK;
+  }
+
+  ~bcg_ctx() {
+    for (cudaEvent_t e : ev) cudaEventDestroy(e);
+    if (graph32) cudaGraphExecDestroy(graph32);
+    for (void *a : allocs) cudaFree(a);
+    if (h_st) cudaFreeHost(h_st);
+    if (h_vec) cudaFreeHost(h_vec);
+    if (h_iters) cudaFreeHost(h_iters);
+  }
+};
+
+namespace {
+
+bcg_status validate_common(int32_t k, int32_t *p, int32_t sub, int32_t prec, int *global) {
+  if (k < 1 || k > kNT) return fail(BCG_ERR_INVALID_ARG, "k=%d out of range 1..%d", k, kNT);
+  switch (sub) {
+    case BCG_SUB_HYBRID: *global = 0; break;
+    case BCG_SUB_GLOBAL: *global = 1; break;
+    case BCG_SUB_PARALLEL: *global = 0; *p = 1; break;
+    case BCG_SUB_CLASSICAL: *global = 0; *p = k; break;
+    default: return fail(BCG_ERR_INVALID_ARG, "unknown subalgebra %d", sub);
+  }
+  if (*p < 1 || k % *p != 0) return fail(BCG_ERR_INVALID_ARG, "p=%d must divide k=%d", *p, k);
+  if (*p > kMaxP) return fail(BCG_ERR_INVALID_ARG, "p=%d > %d is not supported by this build", *p, kMaxP);
+  if (prec != BCG_FP64 && prec != BCG_FP32_REFINE) return fail(BCG_ERR_INVALID_ARG, "unknown precision %d", prec);
+  return BCG_OK;
+}
+
+// Workspace common to both matrix forms; called once A64 is filled in.
+bcg_status setup_workspace(bcg_ctx *h) {
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
+  CK(small_prepare(h->p));
+  CK(stream_grids<double>(h->opkind, h->n, h->k, h->p, h->global, h->nsm, &h->g64));
+  int np = std::max(h->g64.op, std::max(h->g64.upd, h->g64.res));
+  if (h->prec == BCG_FP32_REFINE) {
+    CK(stream_grids<float>(h->opkind, h->n, h->k, h->p, h->global, h->nsm, &h->g32));
+    np = std::max(np, std::max(h->g32.op, std::max(h->g32.upd, h->g32.res)));
+  }
+  h->nparts = np;
+  const size_t nk = (size_t)h->n * h->k;
+  const size_t E = (size_t)h->k * h->p;
+  const size_t pp = (size_t)h->nblk * h->p * h->p;
+  if (h->prec == BCG_FP64) {
+    CKS(h->alloc(&h->R, nk));
+    CKS(h->alloc(&h->P, nk));
+    CKS(h->alloc(&h->Q, nk));
+  } else {
+    CKS(h->alloc(&h->Q, nk));   // FP64 outer residual / true-residual scratch
+    CKS(h->alloc(&h->R32, nk));
+    CKS(h->alloc(&h->P32, nk));
+    CKS(h->alloc(&h->Q32, nk));
+    CKS(h->alloc(&h->D32, nk));
+  }
+  CKS(h->alloc(&h->partA, (size_t)np * E));
+  CKS(h->alloc(&h->partR, (size_t)np * E));
+  CKS(h->alloc(&h->partRho, (size_t)np * E));
+  CKS(h->alloc(&h->partN, (size_t)np * h->k));
+  CKS(h->alloc(&h->lam, pp));
+  CKS(h->alloc(&h->beta, pp));
+  CKS(h->alloc(&h->rho_rec, pp));
+  CKS(h->alloc(&h->r0n2, h->k));
+  CKS(h->alloc(&h->rn2, h->k));
+  CKS(h->alloc(&h->rtn2, h->k));
+  CKS(h->alloc(&h->outer0, h->k));
+  CKS(h->alloc(&h->active, h->nblk));
+  CKS(h->alloc(&h->block_iters, h->nblk));
+  CKS(h->alloc(&h->st, 1));
+  CK(cudaMallocHost(&h->h_st, sizeof(DevStatus)));
+  CK(cudaMallocHost(&h->h_vec, 3 * sizeof(double) * h->k));
+  CK(cudaMallocHost(&h->h_iters, sizeof(int) * h->nblk));
+  h->last_block_iters.assign(h->nblk, 0);
+  return BCG_OK;
+}
+
+bcg_status make_fp32_copy(bcg_ctx *h) {
+  if (h->prec != BCG_FP32_REFINE) return BCG_OK;
+  h->A32 = h->A64;
+  if (h->ncoef > 0) {
+    if (h->vals32 == nullptr) {
+      float *v = nullptr;
+      CKS(h->alloc(&v, h->ncoef));
+      h->vals32 = v;
+    }
+    const double *src = static_cast<const double *>(h->opkind == OP_CSR ? h->A64.vals : h->A64.faces);
+    CK(launch_cast_to_float(src, static_cast<float *>(h->vals32), h->ncoef, h->nsm, h->stream));
+    if (h->opkind == OP_CSR) h->A32.vals = h->vals32;
+    else h->A32.faces = h->vals32;
+  }
+  return BCG_OK;
+}
+
+// ev: NULL, or 10 events recorded around the 5 launches (profiling)
+template <typename T>
+bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g, double tol2,
+                            cudaEvent_t *ev = nullptr) {
+  cudaStream_t s = h->stream;
+#define REC(i) do { if (ev) CK(cudaEventRecord(ev[i], s)); } while (0)
+  REC(0);
+  CK(launch_op_gram<T>(A, P, R, Q, h->n, h->k, h->p, h->global, h->active, h->partA, h->partR, h->st, g.op, s));
+  REC(1); REC(2);
+  CK(launch_solve_lambda(h->partA, h->partR, g.op, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st, s));
+  REC(3); REC(4);
+  CK(launch_update_xr<T>(X, R, P, Q, h->n, h->k, h->p, h->global, h->lam, h->active, h->partRho, h->partN, h->st,
+                         g.upd, s));
+  REC(5); REC(6);
+  CK(launch_solve_beta(h->partRho, h->partN, g.upd, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
+                       h->block_iters, h->rho_rec, h->beta, h->st, s));
+  REC(7); REC(8);
+  CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, g.pup, s));
+  REC(9);
+#undef REC
+  return BCG_OK;
+}
+
+bcg_status ensure_events(bcg_ctx *h, int count) {
+  while ((int)h->ev.size() < count) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    h->ev.push_back(e);
+  }
+  return BCG_OK;
+}
+
+// Accumulate the event timings of the first `executed` iterations of a profiled batch.
+bcg_status collect_events(bcg_ctx *h, int executed) {
+  for (int i = 0; i < executed; ++i) {
+    for (int kk = 0; kk < 5; ++kk) {
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, h->ev[10 * i + 2 * kk], h->ev[10 * i + 2 * kk + 1]));
+      h->prof_ms[kk] += ms;
+      h->prof_count[kk] += 1;
+    }
+  }
+  return BCG_OK;
+}
+
+bcg_status read_status(bcg_ctx *h) {
+  CK(cudaMemcpyAsync(h->h_st, h->st, sizeof(DevStatus), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BCG_OK;
+}
+
+// Run iterations until the device flags completion or `maxit` iterations were launched.
+// On return h->h_st holds the final status word.
+template <typename T>
+bcg_status run_iterations(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g, double tol2,
+                          int maxit, cudaGraphExec_t *cached, int *cached_batch) {
+  CKS(read_status(h));
+  int launched = 0;
+  const int batch = h->check_every;
+  struct Guard {   // a graph built for this call only is destroyed on every exit path
+    cudaGraphExec_t exec = nullptr;
+    bool own = false;
+    ~Guard() { if (own && exec) cudaGraphExecDestroy(exec); }
+  } gd;
+  gd.exec = cached ? *cached : nullptr;
+  cudaGraphExec_t &exec = gd.exec;
+  bool &own_exec = gd.own;
+  // stream capture is impossible on the legacy default stream: plain launches there
+  const bool graphs = h->use_graph && h->stream != nullptr && !h->profile;
+  if (h->profile) CKS(ensure_events(h, 10 * batch));
+  while (h->h_st->flags == 0 && launched < maxit) {
+    const int nb = std::min(batch, maxit - launched);
+    if (graphs && nb == batch) {
+      if (exec == nullptr || (cached && *cached_batch != batch)) {
+        if (exec && (own_exec || cached)) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        if (cached) *cached = nullptr;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        bcg_status sc = BCG_OK;
+        for (int i = 0; i < nb && sc == BCG_OK; ++i) sc = launch_iteration<T>(h, A, X, R, P, Q, g, tol2);
+        cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
+        if (sc != BCG_OK) {
+          if (graph) cudaGraphDestroy(graph);
+          return sc;
+        }
+        if (ec != cudaSuccess) return fail(BCG_ERR_CUDA, "graph capture: %s", cudaGetErrorString(ec));
+        ec = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ec != cudaSuccess) return fail(BCG_ERR_CUDA, "graph instantiate: %s", cudaGetErrorString(ec));
+        if (cached) {
+          *cached = exec;
+          *cached_batch = batch;
+        } else {
+          own_exec = true;
+        }
+      }
+      CK(cudaGraphLaunch(exec, h->stream));
+    } else {
+      for (int i = 0; i < nb; ++i)
+        CKS(launch_iteration<T>(h, A, X, R, P, Q, g, tol2, h->profile ? &h->ev[10 * i] : nullptr));
+    }
+    launched += nb;
+    const int before = h->h_st->iter;
+    CKS(read_status(h));
+    if (h->profile) {
+      // iterations that ran (the rest of the batch returned at entry once the status was set)
+      int executed = h->h_st->iter - before;
+      if (h->h_st->flags & (ST_BREAKDOWN | ST_NUMERIC)) executed += 1;
+      CKS(collect_events(h, std::max(0, std::min(nb, executed))));
+    }
+  }
+  return BCG_OK;
+}
+
+bcg_status fill_block_iters(bcg_ctx *h) {
+  CK(cudaMemcpyAsync(h->h_iters, h->block_iters, sizeof(int) * h->nblk, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  for (int j = 0; j < h->nblk; ++j) h->last_block_iters[j] = h->h_iters[j];
+  return BCG_OK;
+}
+
+// copy k doubles from device to h->h_vec + off*k
+bcg_status fetch_vec(bcg_ctx *h, const double *src, int off) {
+  CK(cudaMemcpyAsync(h->h_vec + (size_t)off * h->k, src, sizeof(double) * h->k, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BCG_OK;
+}
+
+double max_ratio(const double *num2, const double *den2, int k) {
+  double m = 0.0;
+  for (int c = 0; c < k; ++c) {
+    const double r = den2[c] > 0 ? std::sqrt(num2[c] / den2[c]) : std::sqrt(num2[c]);
+    if (!(r <= m)) m = r;   // propagates NaN
+  }
+  return m;
+}
+
+bcg_status status_from_flags(int flags, bool all_done) {
+  if (flags & ST_NUMERIC) return BCG_ERR_NUMERIC;
+  if (flags & ST_BREAKDOWN) return BCG_ERR_BREAKDOWN;
+  if (!all_done) return BCG_ERR_NOT_CONVERGED;
+  return BCG_OK;
+}
+
+bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int maxit, bcg_info *info) {
+  cudaStream_t s = h->stream;
+  const double tol2 = tol * tol;
+  CK(launch_residual<double>(h->A64, X, B, h->R, h->P, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, s));
+  CK(launch_init_status(h->partN, h->g64.res, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters,
+                        h->lam, h->beta, h->st, s));
+  CKS(run_iterations<double>(h, h->A64, X, h->R, h->P, h->Q, h->g64, tol2, maxit, nullptr, nullptr));
+  const DevStatus fin = *h->h_st;
+  CKS(fill_block_iters(h));
+  // true residual B - A X, recomputed
+  CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, s));
+  CK(launch_reduce_norms(h->partN, h->g64.res, h->k, h->rtn2, s));
+  CKS(fetch_vec(h, h->r0n2, 0));
+  CKS(fetch_vec(h, h->rn2, 1));
+  CKS(fetch_vec(h, h->rtn2, 2));
+  const double *r0 = h->h_vec, *rn = h->h_vec + h->k, *rt = h->h_vec + 2 * h->k;
+  const bcg_status st = status_from_flags(fin.flags, (fin.flags & ST_DONE) != 0);
+  if (info) {
+    info->status = st;
+    info->iters = fin.iter;
+    info->outer_iters = 0;
+    info->breakdown_iter = (fin.flags & ST_BREAKDOWN) ? fin.breakdown_iter : -1;
+    info->max_rel_res_recursive = max_ratio(rn, r0, h->k);
+    info->max_rel_res_true = max_ratio(rt, r0, h->k);
+  }
+  if (st != BCG_OK) {
+    const char *what = st == BCG_ERR_NUMERIC ? "non-finite value" : st == BCG_ERR_BREAKDOWN ? "breakdown" : "maxit reached";
+    fail(st, "solve stopped: %s after %d iterations", what, fin.iter);
+  }
+  return st;
+}
+
+// FP64 iterative refinement around FP32 inner block-CG solves.
+bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int maxit, bcg_info *info) {
+  cudaStream_t s = h->stream;
+  const int64_t nk = h->n * h->k;
+  const double itol2 = h->inner_tol * h->inner_tol;
+  int outer = 0, inner_total = 0, brk = -1;
+  bcg_status st = BCG_ERR_NOT_CONVERGED;
+  double last_max = INFINITY;
+  int stalls = 0;
+  for (;;) {
+    // outer residual in FP64, rounded to FP32 as the inner right-hand side (R32 = P32 = fl(R))
+    CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, h->R32, h->P32, h->n, h->k, h->partN, h->g64.res, s));
+    CK(launch_reduce_norms(h->partN, h->g64.res, h->k, h->rtn2, s));
+    if (outer == 0) CK(cudaMemcpyAsync(h->outer0, h->rtn2, sizeof(double) * h->k, cudaMemcpyDeviceToDevice, s));
+    CKS(fetch_vec(h, h->outer0, 0));
+    CKS(fetch_vec(h, h->rtn2, 2));
+    const double *r0 = h->h_vec, *rt = h->h_vec + 2 * h->k;
+    const double m = max_ratio(rt, r0, h->k);
+    if (!std::isfinite(m)) { st = BCG_ERR_NUMERIC; break; }
+    if (m <= tol) { st = BCG_OK; break; }
+    if (outer >= h->max_outer) { st = BCG_ERR_NOT_CONVERGED; break; }
+    if (m >= 0.9 * last_max) {
+      if (++stalls >= 3) { st = BCG_ERR_NOT_CONVERGED; break; }
+    } else {
+      stalls = 0;
+    }
+    last_max = std::min(last_max, m);
+    // inner FP32 solve of A D = fl(R) from D = 0
+    CK(cudaMemsetAsync(h->D32, 0, sizeof(float) * nk, s));
+    CK(launch_init_status(h->partN, h->g64.res, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters,
+                          h->lam, h->beta, h->st, s));
+    CKS(run_iterations<float>(h, h->A32, h->D32, h->R32, h->P32, h->Q32, h->g32, itol2, maxit, &h->graph32,
+                              &h->graph32_batch));
+    const DevStatus fin = *h->h_st;
+    inner_total += fin.iter;
+    if (fin.flags & ST_NUMERIC) { st = BCG_ERR_NUMERIC; break; }
+    if ((fin.flags & ST_BREAKDOWN) && fin.breakdown_iter <= 1) {
+      brk = inner_total;
+      st = BCG_ERR_BREAKDOWN;
+      break;
+    }
+    // a later inner breakdown or maxit still leaves a useful correction: apply it and refine on
+    CK(launch_add_correction(X, h->D32, nk, h->nsm, s));
+    ++outer;
+  }
+  CKS(fill_block_iters(h));
+  CKS(fetch_vec(h, h->outer0, 0));
+  CKS(fetch_vec(h, h->rtn2, 2));
+  const double *r0 = h->h_vec, *rt = h->h_vec + 2 * h->k;
+  if (info) {
+    info->status = st;
+    info->iters = inner_total;
+    info->outer_iters = outer;
+    info->breakdown_iter = brk;
+    info->max_rel_res_recursive = max_ratio(rt, r0, h->k);
+    info->max_rel_res_true = info->max_rel_res_recursive;
+  }
+  if (st != BCG_OK) fail(st, "refinement stopped with status %d after %d outer / %d inner iterations", st, outer, inner_total);
+  return st;
+}
+
+bcg_status finish_create(bcg_ctx *h, bcg_handle *out) {
+  bcg_status s = setup_workspace(h);
+  if (s == BCG_OK) s = make_fp32_copy(h);
+  if (s == BCG_OK && h->opkind == OP_CSR) {
+    s = h->alloc(&h->rowidx, (size_t)h->nnz);
+    if (s == BCG_OK) {
+      cudaError_t e = launch_row_index(h->A64.rowptr, h->n, h->rowidx, h->nsm, h->stream);
+      if (e != cudaSuccess) s = fail(BCG_ERR_CUDA, "row index: %s", cudaGetErrorString(e));
+    }
+  }
+  if (s == BCG_OK) {
+    cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) s = fail(BCG_ERR_CUDA, "create: %s", cudaGetErrorString(e));
+  }
+  if (s != BCG_OK) {
+    delete h;
+    return s;
+  }
+  *out = h;
+  return BCG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bcg_status bcg_create_csr(bcg_handle *out, int64_t n, int64_t nnz, const int64_t *rowptr, const int32_t *colind,
+                          const double *vals, int32_t k, int32_t p, int32_t sub, int32_t prec, void *cuda_stream) {
+  if (out == nullptr) return fail(BCG_ERR_INVALID_ARG, "handle pointer is NULL");
+  *out = nullptr;
+  if (n < 1 || nnz < 1) return fail(BCG_ERR_INVALID_ARG, "n=%lld nnz=%lld must be >= 1", (long long)n, (long long)nnz);
+  if (n > INT32_MAX) return fail(BCG_ERR_INVALID_ARG, "n=%lld exceeds the int32 column index range", (long long)n);
+  int global = 0;
+  CKS(validate_common(k, &p, sub, prec, &global));
+  if (!is_device_ptr(rowptr) || !is_device_ptr(colind) || !is_device_ptr(vals))
+    return fail(BCG_ERR_INVALID_ARG, "rowptr, colind and vals must be device pointers");
+  bcg_ctx *h = new (std::nothrow) bcg_ctx;
+  if (h == nullptr) return fail(BCG_ERR_OOM, "host allocation failed");
+  h->n = n; h->nnz = nnz; h->k = k; h->p = p; h->global = global; h->prec = prec;
+  h->nblk = global ? 1 : k / p;
+  h->opkind = OP_CSR;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->A64.kind = OP_CSR; h->A64.n = n; h->A64.rowptr = rowptr; h->A64.colind = colind; h->A64.vals = vals;
+  h->ncoef = nnz;
+  return finish_create(h, out);
+}
+
+bcg_status bcg_create_stencil(bcg_handle *out, int32_t kind, int32_t nx, int32_t ny, int32_t nz, const double *coef,
+                              double scale, int32_t k, int32_t p, int32_t sub, int32_t prec, void *cuda_stream) {
+  if (out == nullptr) return fail(BCG_ERR_INVALID_ARG, "handle pointer is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1) return fail(BCG_ERR_INVALID_ARG, "grid %d x %d x %d invalid", nx, ny, nz);
+  if (!(scale > 0.0) || !std::isfinite(scale)) return fail(BCG_ERR_INVALID_ARG, "scale must be finite and > 0");
+  int opk;
+  switch (kind) {
+    case BCG_STENCIL_5PT_2D: opk = OP_ST5; if (nz != 1) return fail(BCG_ERR_INVALID_ARG, "2D stencil needs nz = 1"); break;
+    case BCG_STENCIL_7PT_3D: opk = OP_ST7; break;
+    case BCG_STENCIL_7PT_3D_VARCOEF: opk = OP_ST7VC; break;
+    default: return fail(BCG_ERR_INVALID_ARG, "unknown stencil kind %d", kind);
+  }
+  if (opk == OP_ST7VC && !is_device_ptr(coef)) return fail(BCG_ERR_INVALID_ARG, "varcoef stencil needs device faces");
+  if (opk != OP_ST7VC && coef != nullptr) return fail(BCG_ERR_INVALID_ARG, "constant stencils take coef = NULL");
+  const int64_t n = (int64_t)nx * ny * nz;
+  int global = 0;
+  CKS(validate_common(k, &p, sub, prec, &global));
+  bcg_ctx *h = new (std::nothrow) bcg_ctx;
+  if (h == nullptr) return fail(BCG_ERR_OOM, "host allocation failed");
+  h->n = n; h->k = k; h->p = p; h->global = global; h->prec = prec;
+  h->nblk = global ? 1 : k / p;
+  h->opkind = opk;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->A64.kind = opk; h->A64.n = n; h->A64.nx = nx; h->A64.ny = ny; h->A64.nz = nz; h->A64.scale = scale;
+  h->A64.faces = coef;
+  h->ncoef = opk == OP_ST7VC ? (int64_t)nz * ny * (nx + 1) + (int64_t)nz * (ny + 1) * nx + (int64_t)(nz + 1) * ny * nx : 0;
+  return finish_create(h, out);
+}
+
+bcg_status bcg_set_option(bcg_handle h, const char *key, double value) {
+  if (h == nullptr || key == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle or key");
+  if (!std::isfinite(value)) return fail(BCG_ERR_INVALID_ARG, "option value must be finite");
+  if (!strcmp(key, "inner_tol")) {
+    if (!(value > 0.0 && value < 1.0)) return fail(BCG_ERR_INVALID_ARG, "inner_tol must lie in (0, 1)");
+    h->inner_tol = value;
+  } else if (!strcmp(key, "max_outer")) {
+    if (value < 1 || value > 1000) return fail(BCG_ERR_INVALID_ARG, "max_outer must lie in 1..1000");
+    h->max_outer = (int)value;
+  } else if (!strcmp(key, "check_every")) {
+    if (value < 1 || value > 4096) return fail(BCG_ERR_INVALID_ARG, "check_every must lie in 1..4096");
+    h->check_every = (int)value;
+  } else if (!strcmp(key, "profile")) {
+    if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "profile must be 0 or 1");
+    h->profile = (int)value;
+    for (int i = 0; i < bcg_ctx::kKernels; ++i) { h->prof_ms[i] = 0.0; h->prof_count[i] = 0; }
+  } else if (!strcmp(key, "graph")) {
+    if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "graph must be 0 or 1");
+    h->use_graph = (int)value;
+  } else {
+    return fail(BCG_ERR_INVALID_ARG, "unknown option '%s'", key);
+  }
+  return BCG_OK;
+}
+
+bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32_t maxit, bcg_info *info) {
+  if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (!is_device_ptr(B) || !is_device_ptr(X)) return fail(BCG_ERR_INVALID_ARG, "B and X must be device pointers");
+  if (B == X) return fail(BCG_ERR_INVALID_ARG, "B and X must not alias");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(BCG_ERR_INVALID_ARG, "tol must be finite and > 0");
+  if (maxit < 1) return fail(BCG_ERR_INVALID_ARG, "maxit must be >= 1");
+  g_last_error.clear();
+  return h->prec == BCG_FP64 ? solve_fp64(h, B, X, tol, maxit, info) : solve_refine(h, B, X, tol, maxit, info);
+}
+
+bcg_status bcg_solve_host(bcg_handle h, const double *B, double *X, double tol, int32_t maxit, bcg_info *info) {
+  if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (B == nullptr || X == nullptr) return fail(BCG_ERR_INVALID_ARG, "B and X must not be NULL");
+  if (!(tol > 0.0) || !std::isfinite(tol)) return fail(BCG_ERR_INVALID_ARG, "tol must be finite and > 0");
+  if (maxit < 1) return fail(BCG_ERR_INVALID_ARG, "maxit must be >= 1");
+  const size_t bytes = sizeof(double) * (size_t)h->n * h->k;
+  if (h->stageB == nullptr) {
+    CKS(h->alloc(&h->stageB, (size_t)h->n * h->k));
+    CKS(h->alloc(&h->stageX, (size_t)h->n * h->k));
+  }
+  CK(cudaMemcpyAsync(h->stageB, B, bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->stageX, X, bytes, cudaMemcpyHostToDevice, h->stream));
+  const bcg_status st = bcg_solve(h, h->stageB, h->stageX, tol, maxit, info);
+  if (st == BCG_ERR_INVALID_ARG || st == BCG_ERR_CUDA || st == BCG_ERR_OOM) return st;
+  const std::string msg = g_last_error;
+  CK(cudaMemcpyAsync(X, h->stageX, bytes, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  g_last_error = msg;
+  return st;
+}
+
+bcg_status bcg_block_iters(bcg_handle h, int32_t *out, int32_t cap) {
+  if (h == nullptr || out == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL argument");
+  if (cap < h->nblk) return fail(BCG_ERR_INVALID_ARG, "cap=%d < number of blocks %d", cap, h->nblk);
+  for (int j = 0; j < h->nblk; ++j) out[j] = h->last_block_iters[j];
+  return BCG_OK;
+}
+
+bcg_status bcg_grad_values(bcg_handle h, const double *Lambda, const double *X, double *grad) {
+  if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (h->opkind != OP_CSR) return fail(BCG_ERR_INVALID_ARG, "gradient needs a CSR handle");
+  if (!is_device_ptr(Lambda) || !is_device_ptr(X) || !is_device_ptr(grad))
+    return fail(BCG_ERR_INVALID_ARG, "Lambda, X and grad must be device pointers");
+  CK(launch_grad_values(h->rowidx, h->A64.colind, Lambda, X, h->nnz, h->k, grad, h->nsm, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BCG_OK;
+}
+
+bcg_status bcg_update_values(bcg_handle h, const double *vals) {
+  if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (h->ncoef == 0) return fail(BCG_ERR_INVALID_ARG, "constant stencils have no values");
+  if (!is_device_ptr(vals)) return fail(BCG_ERR_INVALID_ARG, "vals must be a device pointer");
+  if (h->opkind == OP_CSR) h->A64.vals = vals;
+  else h->A64.faces = vals;
+  CKS(make_fp32_copy(h));
+  if (h->graph32) {   // captured graphs hold the old operator descriptor
+    cudaGraphExecDestroy(h->graph32);
+    h->graph32 = nullptr;
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  return BCG_OK;
+}
+
+bcg_status bcg_bdot(bcg_handle h, const double *X, const double *Y, double *gamma) {
+  if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (!is_device_ptr(X) || !is_device_ptr(Y) || !is_device_ptr(gamma))
+    return fail(BCG_ERR_INVALID_ARG, "X, Y and gamma must be device pointers");
+  const int grid = std::min(h->nparts, bdot_grid<double>(h->n, h->k, h->p, h->nsm));
+  CK(launch_bdot<double>(X, Y, h->n, h->k, h->p, h->partA, grid, h->stream));
+  CK(launch_finish_gram(h->partA, grid, h->k, h->p, h->global, gamma, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BCG_OK;
+}
+
+bcg_status bcg_bop(bcg_handle h, const double *X, double *Y) {
+  if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (!is_device_ptr(X) || !is_device_ptr(Y) || X == Y) return fail(BCG_ERR_INVALID_ARG, "X, Y: distinct device pointers");
+  CK(launch_bop<double>(h->A64, X, Y, h->n, h->k, h->g64.res, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BCG_OK;
+}
+
+bcg_status bcg_profile(bcg_handle h, double *ms, int64_t *count, int32_t cap) {
+  if (h == nullptr || ms == nullptr || count == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL argument");
+  if (cap < bcg_ctx::kKernels) return fail(BCG_ERR_INVALID_ARG, "cap=%d < %d", cap, bcg_ctx::kKernels);
+  for (int i = 0; i < bcg_ctx::kKernels; ++i) { ms[i] = h->prof_ms[i]; count[i] = h->prof_count[i]; }
+  return BCG_OK;
+}
+
+const char *bcg_last_error(void) { return g_last_error.c_str(); }
+
+void bcg_destroy(bcg_handle h) {
+  if (h == nullptr) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  else cudaDeviceSynchronize();
+  delete h;
+}
+
+}  // extern "C"

@@ -1,0 +1,65 @@
+// Host-side launchers of the device kernels (one translation unit per precision plus the small-solve
+// unit); the C ABI in bcg_capi.cu only talks to these.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "bcg_kernels.cuh"
+
+namespace bcgk {
+
+// Largest p handled by the streaming kernels (per-thread Gram accumulators live in registers).
+constexpr int kMaxP = 32;
+
+struct StreamGrids {
+  int op;        // K1 CTAs
+  int upd;       // K2 CTAs
+  int pup;       // K3 CTAs
+  int res;       // K0 CTAs
+};
+
+// Sizes the grids for n rows from the occupancy of each kernel variant (capped to whole waves of SMs).
+template <typename T>
+cudaError_t stream_grids(int opkind, int64_t n, int k, int p, int global, int nsm, StreamGrids *out);
+
+template <typename T>
+cudaError_t launch_op_gram(const OpDesc &A, const T *P, const T *R, T *Q, int64_t n, int k, int p, int global,
+                           const int *active, double *partA, double *partR, const DevStatus *st, int grid,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_xr(T *X, T *R, const T *P, const T *Q, int64_t n, int k, int p, int global,
+                             const double *lam, const int *active, double *partRho, double *partN,
+                             const DevStatus *st, int grid, cudaStream_t s);
+template <typename T>
+cudaError_t launch_update_p(T *P, const T *R, int64_t n, int k, int p, int global, const double *beta,
+                            const int *active, DevStatus *st, int grid, cudaStream_t s);
+template <typename T>
+cudaError_t launch_residual(const OpDesc &A, const T *X, const T *B, T *R, T *P, float *R32, float *P32, int64_t n,
+                            int k, double *partN, int grid, cudaStream_t s);
+
+template <typename T>
+cudaError_t launch_bdot(const T *X, const T *Y, int64_t n, int k, int p, double *part, int grid, cudaStream_t s);
+template <typename T>
+int bdot_grid(int64_t n, int k, int p, int nsm);
+cudaError_t launch_finish_gram(const double *part, int nparts, int k, int p, int global, double *gamma, cudaStream_t s);
+template <typename T>
+cudaError_t launch_bop(const OpDesc &A, const T *X, T *Y, int64_t n, int k, int grid, cudaStream_t s);
+
+cudaError_t small_prepare(int p);
+cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int k, int p, int global,
+                                const int *active, double *lam, double *rho_rec, DevStatus *st, cudaStream_t s);
+cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int k, int p, int global,
+                              double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
+                              const double *rho_rec, double *beta, DevStatus *st, cudaStream_t s);
+cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, int global, double *r0n2, double *rn2,
+                               int *active, int *block_iters, double *lam, double *beta, DevStatus *st,
+                               cudaStream_t s);
+cudaError_t launch_reduce_norms(const double *partN, int nparts, int k, double *out, cudaStream_t s);
+cudaError_t launch_add_correction(double *X, const float *D, int64_t len, int nsm, cudaStream_t s);
+cudaError_t launch_cast_to_float(const double *src, float *dst, int64_t len, int nsm, cudaStream_t s);
+cudaError_t launch_grad_values(const int32_t *rowidx, const int32_t *colind, const double *Lam, const double *X,
+                               int64_t nnz, int k, double *grad, int nsm, cudaStream_t s);
+cudaError_t launch_row_index(const int64_t *rowptr, int64_t n, int32_t *rowidx, int nsm, cudaStream_t s);
+
+}  // namespace bcgk

@@ -1,0 +1,428 @@
+// BSOLVE kernels (Section 3, "solve a block system in the *-subalgebra"), the stopping test and the
+// status bookkeeping. One CTA per distinct block of the subalgebra (q for hybrid, 1 for global), FP64.
+//
+// Each CTA first sums the per-CTA partials of its block in CTA order (deterministic), then factors:
+//   lambda = alpha^{-1} rho_rec  by Cholesky of alpha (SPD), reading alpha's lower triangle;
+//   beta   = rho_rec^{-1} rho    by LU with partial pivoting of the recomputed rho (not symmetric in
+//                                floating point).
+// A pivot <= 64 eps max|diag| or a non-finite value is a breakdown: the method has no deflation, so
+// the solve stops and reports it.
+#include <cfloat>
+#include <cmath>
+
+#include "bcg_launch.h"
+
+namespace bcgk {
+
+constexpr int kSmallNT = 256;
+constexpr double kPivotFactor = 64.0;
+
+// Sum the partials of distinct block jb into dst[b*p + a] (the partial layout).
+__device__ void reduce_block(const double *__restrict__ part, int nparts, int k, int p, int global, int jb,
+                             double *dst, double *scratch) {
+  const int NT = blockDim.x;
+  const int Eb = p * p;
+  const int S = Eb >= NT ? 1 : NT / Eb;
+  const int64_t E = (int64_t)k * p;
+  const int q = k / p;
+  for (int t = threadIdx.x; t < Eb * S; t += NT) {
+    const int el = t % Eb, sub = t / Eb;
+    double s = 0.0;
+    for (int pi = sub; pi < nparts; pi += S) {
+      const double *base = part + pi * E + el;
+      if (!global) {
+        s += base[(int64_t)jb * Eb];
+      } else {
+        for (int j = 0; j < q; ++j) s += base[(int64_t)j * Eb];
+      }
+    }
+    scratch[t] = s;
+  }
+  __syncthreads();
+  for (int el = threadIdx.x; el < Eb; el += NT) {
+    double s = 0.0;
+    for (int sub = 0; sub < S; ++sub) s += scratch[sub * Eb + el];
+    dst[el] = s;
+  }
+  __syncthreads();
+}
+
+// dst[a*p + b] = src[b*p + a]
+__device__ void transpose_into(const double *src, double *dst, int p) {
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int b = e / p, a = e - b * p;
+    dst[a * p + b] = src[e];
+  }
+  __syncthreads();
+}
+
+__device__ void flag_breakdown(DevStatus *st) {
+  atomicOr(&st->flags, ST_BREAKDOWN);
+  atomicCAS(&st->breakdown_iter, 0, st->cur);
+}
+
+// K4a: lambda_j = alpha_j^{-1} rho_rec_j; also stores rho_rec_j (row-major a*p + b) for K4b.
+__global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restrict__ partA,
+                                                           const double *__restrict__ partR, int nparts, int k,
+                                                           int p, int global, const int *__restrict__ active,
+                                                           double *__restrict__ lam, double *__restrict__ rho_rec,
+                                                           DevStatus *st) {
+  if (st->flags != 0) return;
+  const int jb = blockIdx.x;
+  const int pp = p * p;
+  double *lj = lam + (int64_t)jb * pp;
+  if (!active[jb]) {
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) lj[e] = 0.0;
+    return;
+  }
+  extern __shared__ __align__(16) double sm[];
+  double *sA = sm;            // alpha, row-major, factored in place into L (lower)
+  double *sR = sA + pp;       // rho_rec, row-major; overwritten by Y then lambda
+  double *tmp = sR + pp;      // p*p
+  double *scr = tmp + pp;     // max(NT, p*p)
+  __shared__ int bad;
+  __shared__ double thresh;
+  reduce_block(partA, nparts, k, p, global, jb, tmp, scr);
+  transpose_into(tmp, sA, p);
+  reduce_block(partR, nparts, k, p, global, jb, tmp, scr);
+  transpose_into(tmp, sR, p);
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) rho_rec[(int64_t)jb * pp + e] = sR[e];
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    for (int a = 0; a < p; ++a) m = fmax(m, fabs(sA[a * p + a]));
+    thresh = kPivotFactor * DBL_EPSILON * m;
+    bad = 0;
+  }
+  __syncthreads();
+  // right-looking Cholesky on the lower triangle
+  for (int a = 0; a < p; ++a) {
+    if (threadIdx.x == 0) {
+      const double d = sA[a * p + a];
+      if (!(isfinite(d) && d > thresh)) bad = 1;
+      else sA[a * p + a] = sqrt(d);
+    }
+    __syncthreads();
+    if (bad) break;
+    const double la = sA[a * p + a];
+    for (int i = a + 1 + threadIdx.x; i < p; i += blockDim.x) sA[i * p + a] /= la;
+    __syncthreads();
+    const int m = p - a - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = a + 1 + e / m, jj = a + 1 + e % m;
+      if (jj <= i) sA[i * p + jj] -= sA[i * p + a] * sA[jj * p + a];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) flag_breakdown(st);
+    return;
+  }
+  // L Y = rho_rec, then L^T lambda = Y; one thread per right-hand-side column b
+  for (int b = threadIdx.x; b < p; b += blockDim.x) {
+    for (int a = 0; a < p; ++a) {
+      double s = sR[a * p + b];
+      for (int m2 = 0; m2 < a; ++m2) s -= sA[a * p + m2] * sR[m2 * p + b];
+      sR[a * p + b] = s / sA[a * p + a];
+    }
+    for (int a = p - 1; a >= 0; --a) {
+      double s = sR[a * p + b];
+      for (int m2 = a + 1; m2 < p; ++m2) s -= sA[m2 * p + a] * sR[m2 * p + b];
+      sR[a * p + b] = s / sA[a * p + a];
+    }
+  }
+  __syncthreads();
+  bool finite = true;
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+    lj[e] = sR[e];
+    if (!isfinite(sR[e])) finite = false;
+  }
+  if (!__syncthreads_and(finite) && threadIdx.x == 0) flag_breakdown(st);
+}
+
+// K4b: per-column norms, stopping test, beta_j = rho_rec_j^{-1} rho_j by LU with partial pivoting.
+__global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restrict__ partRho,
+                                                         const double *__restrict__ partN, int nparts, int k, int p,
+                                                         int global, double tol2, const double *__restrict__ r0n2,
+                                                         double *__restrict__ rn2, int *__restrict__ active,
+                                                         int *__restrict__ block_iters,
+                                                         const double *__restrict__ rho_rec,
+                                                         double *__restrict__ beta, DevStatus *st) {
+  if (st->flags != 0) return;
+  const int jb = blockIdx.x;
+  if (!active[jb]) return;
+  const int pp = p * p;
+  const int it = st->cur;
+  const int c0 = global ? 0 : jb * p, c1 = global ? k : c0 + p;
+  bool conv = true, finite = true;
+  for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+    double s = 0.0;
+    for (int pi = 0; pi < nparts; ++pi) s += partN[(int64_t)pi * k + c];
+    rn2[c] = s;
+    if (!isfinite(s)) finite = false;
+    if (!(s <= tol2 * r0n2[c])) conv = false;
+  }
+  finite = __syncthreads_and(finite);
+  conv = __syncthreads_and(conv);
+  double *bj = beta + (int64_t)jb * pp;
+  if (!finite) {
+    if (threadIdx.x == 0) atomicOr(&st->flags, ST_NUMERIC);
+    return;
+  }
+  if (conv) {
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) bj[e] = 0.0;
+    if (threadIdx.x == 0) {
+      active[jb] = 0;
+      block_iters[jb] = it;
+      atomicMax(&st->iter, it);
+      if (atomicSub(&st->n_active, 1) == 1) atomicOr(&st->flags, ST_DONE);
+    }
+    return;
+  }
+  extern __shared__ __align__(16) double sm[];
+  double *sM = sm;          // rho_rec (row-major), LU-factored in place
+  double *sB = sM + pp;     // right-hand sides rho (row-major), become beta
+  double *tmp = sB + pp;
+  double *scr = tmp + pp;
+  __shared__ int bad, piv;
+  __shared__ double thresh;
+  reduce_block(partRho, nparts, k, p, global, jb, tmp, scr);
+  transpose_into(tmp, sB, p);
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) sM[e] = rho_rec[(int64_t)jb * pp + e];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0.0;
+    bool fin = true;
+    for (int a = 0; a < p; ++a) m = fmax(m, fabs(sM[a * p + a]));
+    for (int e = 0; e < pp; ++e) fin = fin && isfinite(sM[e]);
+    thresh = kPivotFactor * DBL_EPSILON * m;
+    bad = fin ? 0 : 1;
+  }
+  __syncthreads();
+  for (int a = 0; a < p && !bad; ++a) {
+    if (threadIdx.x == 0) {
+      int best = a;
+      double bv = fabs(sM[a * p + a]);
+      for (int i = a + 1; i < p; ++i) {
+        const double v = fabs(sM[i * p + a]);
+        if (v > bv) { bv = v; best = i; }
+      }
+      piv = best;
+      if (!(bv > thresh)) bad = 1;
+    }
+    __syncthreads();
+    if (bad) break;
+    if (piv != a) {
+      for (int col = threadIdx.x; col < p; col += blockDim.x) {
+        double t = sM[a * p + col]; sM[a * p + col] = sM[piv * p + col]; sM[piv * p + col] = t;
+        t = sB[a * p + col]; sB[a * p + col] = sB[piv * p + col]; sB[piv * p + col] = t;
+      }
+    }
+    __syncthreads();
+    const double ua = sM[a * p + a];
+    for (int i = a + 1 + threadIdx.x; i < p; i += blockDim.x) sM[i * p + a] /= ua;   // multipliers
+    __syncthreads();
+    const int m = p - a - 1;
+    for (int e = threadIdx.x; e < m * (m + p); e += blockDim.x) {
+      const int i = a + 1 + e / (m + p), col = e % (m + p);
+      const double l = sM[i * p + a];
+      if (col < m) sM[i * p + a + 1 + col] -= l * sM[a * p + a + 1 + col];
+      else sB[i * p + (col - m)] -= l * sB[a * p + (col - m)];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) flag_breakdown(st);
+    return;
+  }
+  for (int b = threadIdx.x; b < p; b += blockDim.x) {
+    for (int a = p - 1; a >= 0; --a) {
+      double s = sB[a * p + b];
+      for (int m2 = a + 1; m2 < p; ++m2) s -= sM[a * p + m2] * sB[m2 * p + b];
+      sB[a * p + b] = s / sM[a * p + a];
+    }
+  }
+  __syncthreads();
+  bool fin = true;
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+    bj[e] = sB[e];
+    if (!isfinite(sB[e])) fin = false;
+  }
+  if (!__syncthreads_and(fin)) {
+    if (threadIdx.x == 0) flag_breakdown(st);
+    return;
+  }
+  if (threadIdx.x == 0) atomicMax(&st->iter, it);
+}
+
+// Start of a solve: reduce the initial residual norms, mark zero columns converged, reset the status.
+__global__ void k_init_status(const double *__restrict__ partN, int nparts, int k, int p, int global,
+                              double *__restrict__ r0n2, double *__restrict__ rn2, int *__restrict__ active,
+                              int *__restrict__ block_iters, double *__restrict__ lam, double *__restrict__ beta,
+                              DevStatus *st) {
+  const int nblk = global ? 1 : k / p;
+  __shared__ int nact, nonfinite;
+  if (threadIdx.x == 0) { nact = 0; nonfinite = 0; }
+  __syncthreads();
+  for (int c = threadIdx.x; c < k; c += blockDim.x) {
+    double s = 0.0;
+    for (int pi = 0; pi < nparts; ++pi) s += partN[(int64_t)pi * k + c];
+    r0n2[c] = s;
+    rn2[c] = s;
+    if (!isfinite(s)) atomicOr(&nonfinite, 1);
+  }
+  __syncthreads();
+  for (int jb = threadIdx.x; jb < nblk; jb += blockDim.x) {
+    const int c0 = global ? 0 : jb * p, c1 = global ? k : c0 + p;
+    bool all_zero = true;   // ||R_c^0|| <= tol ||R_c^0|| holds for tol < 1 only when R_c^0 = 0
+    for (int c = c0; c < c1; ++c) all_zero = all_zero && (r0n2[c] == 0.0);
+    active[jb] = all_zero ? 0 : 1;
+    block_iters[jb] = 0;
+    if (!all_zero) atomicAdd(&nact, 1);
+  }
+  const int pp = p * p;
+  for (int e = threadIdx.x; e < nblk * pp; e += blockDim.x) { lam[e] = 0.0; beta[e] = 0.0; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    st->n_active = nact;
+    st->iter = 0;
+    st->cur = 1;
+    st->breakdown_iter = 0;
+    st->flags = nonfinite ? ST_NUMERIC : (nact == 0 ? ST_DONE : 0);
+  }
+}
+
+// Sum BDOT partials in CTA order into gamma (per distinct block p*p, row-major a*p + b).
+__global__ void __launch_bounds__(kSmallNT) k_finish_gram(const double *__restrict__ part, int nparts, int k, int p,
+                                                          int global, double *__restrict__ gamma) {
+  extern __shared__ __align__(16) double sm[];
+  const int pp = p * p;
+  double *tmp = sm, *scr = sm + pp;
+  const int jb = blockIdx.x;
+  reduce_block(part, nparts, k, p, global, jb, tmp, scr);
+  for (int e = threadIdx.x; e < pp; e += blockDim.x) {
+    const int b = e / p, a = e - b * p;
+    gamma[(int64_t)jb * pp + a * p + b] = tmp[e];
+  }
+}
+
+__global__ void k_reduce_norms(const double *__restrict__ partN, int nparts, int k, double *__restrict__ out) {
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < k; c += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int pi = 0; pi < nparts; ++pi) s += partN[(int64_t)pi * k + c];
+    out[c] = s;
+  }
+}
+
+// X64 += D32 (the refinement update of the mixed-precision form)
+__global__ void k_add_correction(double *__restrict__ X, const float *__restrict__ D, int64_t len) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    X[i] += (double)D[i];
+}
+
+__global__ void k_cast_to_float(const double *__restrict__ src, float *__restrict__ dst, int64_t len) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (float)src[i];
+}
+
+// Gradient with respect to the stored CSR values: grad[e] = -Lambda_row(e) . X_col(e).
+__global__ void k_grad_values(const int32_t *__restrict__ rowidx, const int32_t *__restrict__ colind,
+                              const double *__restrict__ Lam, const double *__restrict__ X, int64_t nnz, int k,
+                              double *__restrict__ grad) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x) {
+    const double *l = Lam + (int64_t)rowidx[e] * k;
+    const double *x = X + (int64_t)colind[e] * k;
+    double s = 0.0;
+    for (int c = 0; c < k; ++c) s = fma(l[c], x[c], s);
+    grad[e] = -s;
+  }
+}
+
+__global__ void k_row_index(const int64_t *__restrict__ rowptr, int64_t n, int32_t *__restrict__ rowidx) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    for (int64_t e = rowptr[r]; e < rowptr[r + 1]; ++e) rowidx[e] = (int32_t)r;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// host launchers
+
+static size_t small_smem(int p) {
+  const int pp = p * p;
+  return (size_t)(3 * pp + (pp > kSmallNT ? pp : kSmallNT)) * sizeof(double);
+}
+
+cudaError_t small_prepare(int p) {
+  const size_t sm = small_smem(p);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_solve_lambda, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(k_solve_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int k, int p, int global,
+                                const int *active, double *lam, double *rho_rec, DevStatus *st, cudaStream_t s) {
+  const int nblk = global ? 1 : k / p;
+  k_solve_lambda<<<nblk, kSmallNT, small_smem(p), s>>>(partA, partR, nparts, k, p, global, active, lam, rho_rec, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int k, int p, int global,
+                              double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
+                              const double *rho_rec, double *beta, DevStatus *st, cudaStream_t s) {
+  const int nblk = global ? 1 : k / p;
+  k_solve_beta<<<nblk, kSmallNT, small_smem(p), s>>>(partRho, partN, nparts, k, p, global, tol2, r0n2, rn2, active,
+                                                     block_iters, rho_rec, beta, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, int global, double *r0n2, double *rn2,
+                               int *active, int *block_iters, double *lam, double *beta, DevStatus *st,
+                               cudaStream_t s) {
+  k_init_status<<<1, kSmallNT, 0, s>>>(partN, nparts, k, p, global, r0n2, rn2, active, block_iters, lam, beta, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_finish_gram(const double *part, int nparts, int k, int p, int global, double *gamma,
+                               cudaStream_t s) {
+  const int nblk = global ? 1 : k / p;
+  const int pp = p * p;
+  const size_t sm = (size_t)(pp + (pp > kSmallNT ? pp : kSmallNT)) * sizeof(double);
+  k_finish_gram<<<nblk, kSmallNT, sm, s>>>(part, nparts, k, p, global, gamma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_norms(const double *partN, int nparts, int k, double *out, cudaStream_t s) {
+  k_reduce_norms<<<(k + 255) / 256, 256, 0, s>>>(partN, nparts, k, out);
+  return cudaGetLastError();
+}
+
+static int stream_grid(int64_t len, int nsm) {
+  int64_t g = (len + 255) / 256;
+  const int64_t cap = (int64_t)nsm * 8;
+  return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+cudaError_t launch_add_correction(double *X, const float *D, int64_t len, int nsm, cudaStream_t s) {
+  k_add_correction<<<stream_grid(len, nsm), 256, 0, s>>>(X, D, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_to_float(const double *src, float *dst, int64_t len, int nsm, cudaStream_t s) {
+  k_cast_to_float<<<stream_grid(len, nsm), 256, 0, s>>>(src, dst, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_values(const int32_t *rowidx, const int32_t *colind, const double *Lam, const double *X,
+                               int64_t nnz, int k, double *grad, int nsm, cudaStream_t s) {
+  k_grad_values<<<stream_grid(nnz, nsm), 256, 0, s>>>(rowidx, colind, Lam, X, nnz, k, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_row_index(const int64_t *rowptr, int64_t n, int32_t *rowidx, int nsm, cudaStream_t s) {
+  k_row_index<<<stream_grid(n, nsm), 256, 0, s>>>(rowptr, n, rowidx);
+  return cudaGetLastError();
+}
+
+}  // namespace bcgk

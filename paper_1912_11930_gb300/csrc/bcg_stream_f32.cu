@@ -1,0 +1,3 @@
+#include <type_traits>
+#define BCG_T float
+#include "bcg_stream.inc"

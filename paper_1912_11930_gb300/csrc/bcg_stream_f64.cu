@@ -1,0 +1,3 @@
+#include <type_traits>
+#define BCG_T double
+#include "bcg_stream.inc"
