@@ -273,3 +273,22 @@ def test_full_size_poisson128_k32(torch_dev, sub, p):
             yi += M.vals[e] * B[M.colind[e]]
         assert np.allclose(Y[i], yi, rtol=1e-13, atol=1e-9)
     S.close()
+
+
+@pytest.mark.parametrize("sub,k,p", [("hybrid", 8, 4), ("global", 8, 4), ("parallel", 12, 1), ("classical", 16, 16),
+                                     ("hybrid", 64, 16), ("global", 96, 32), ("hybrid", 256, 8), ("hybrid", 1, 1)])
+def test_bdot_matches_block_product(torch_dev, sub, k, p):
+    """The BDOT kernel alone against the oracle's block product (Section 2 definition)."""
+    torch, dev = torch_dev
+    from paper_1912_11930_gb300 import bcg
+    M = mat("p3d_30")
+    X = W.rhs(M.n, k, seed=20)
+    Y = W.rhs(M.n, k, seed=21)
+    S = bcg.Solver.from_matrix(M, k=k, p=p, sub=sub, device=dev)
+    g = S.bdot(torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)).cpu().numpy()
+    S.close()
+    kind, pp = O.canonical_subalgebra(sub, k, p)
+    ref = O.block_product(X, Y, pp, kind)
+    assert g.shape == ref.shape
+    scale = np.linalg.norm(X) * np.linalg.norm(Y) / k
+    assert np.max(np.abs(g - ref)) <= 1e-13 * scale
