@@ -179,6 +179,29 @@ bcg_status bcg_update_values(bcg_handle h, const double *vals);
 bcg_status bcg_bdot(bcg_handle h, const double *X, const double *Y, double *gamma);
 
 /*
+ * bcg_bdot_noalloc -- bcg_bdot for callers that cannot allocate device memory. The paper has no
+ * counterpart; this is a deployment variant of the BDOT kernel.
+ *
+ * Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being captured and must not
+ * allocate, plug-ins whose host application owns every device allocation through its own pool, and
+ * latency-critical paths where an allocation may block or fail. This entry point needs no handle (creating
+ * one allocates) and allocates nothing: the per-CTA partial sums live in one static device array of
+ * 262,144 doubles (2 MiB) that every GPU which loads the library holds until the process exits. The
+ * caller passes the inputs and the output.
+ *   n, k, p, sub  as for bcg_create_csr (1 <= k <= 256, p divides k, p <= 32; k*p must fit the array)
+ *   X, Y          device double[n*k], row-major
+ *   gamma         device double[nblk*p*p], layout as for bcg_bdot
+ *   cuda_stream   stream to order the two launches on; the call returns once they are enqueued
+ * The first call on a device looks up that device's address of the array (cudaGetSymbolAddress) and
+ * should therefore come before any stream capture. Every call shares the array and overwrites the
+ * partial sums it uses before reading them (nothing has to start at zero), so calls that overlap on the
+ * GPU -- on different streams, or from several threads -- race and must be serialised by the caller.
+ * Returns INVALID_ARG (sizes beyond the limits, non-device pointers, unknown subalgebra) or CUDA.
+ */
+bcg_status bcg_bdot_noalloc(int64_t n, int32_t k, int32_t p, int32_t sub, const double *X, const double *Y,
+                            double *gamma, void *cuda_stream);
+
+/*
  * bcg_bop -- the BOP kernel alone (Section 3): Y = A X in FP64 with the handle's operator.
  *   X, Y  device double[n*k], row-major, must not overlap.
  */

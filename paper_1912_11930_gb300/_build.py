@@ -9,7 +9,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libbcg.so")
-SOURCES = ["bcg_stream_f64.cu", "bcg_stream_f32.cu", "bcg_small.cu", "bcg_capi.cu"]
+SOURCES = ["bcg_stream_f64.cu", "bcg_stream_f32.cu", "bcg_small.cu", "bcg_capi.cu", "bcg_noalloc.cu"]
 NVCC = os.environ.get("NVCC", "nvcc")
 FLAGS = ["-std=c++17", "-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo",
          "-Xcompiler", "-fPIC", "-I", INCLUDE]

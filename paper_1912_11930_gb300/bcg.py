@@ -58,6 +58,7 @@ def load():
         "bcg_update_values": [vp, vp],
         "bcg_bop": [vp, vp, vp],
         "bcg_bdot": [vp, vp, vp, vp],
+        "bcg_bdot_noalloc": [i64, i32, i32, i32, vp, vp, vp, vp],
         "bcg_profile": [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), i32],
     }
     for name, args in sig.items():
@@ -148,6 +149,12 @@ def bcg_bop(h, X, Y):
 
 def bcg_bdot(h, X, Y, gamma):
     _check(load().bcg_bdot(h, _ptr(X), _ptr(Y), _ptr(gamma)))
+
+
+def bcg_bdot_noalloc(n, k, p, sub, X, Y, gamma, stream=None):
+    """Allocation-free BDOT (static device scratch); stream-ordered, returns once enqueued."""
+    _check(load().bcg_bdot_noalloc(n, k, p, SUBALGEBRA.get(sub, sub), _ptr(X), _ptr(Y), _ptr(gamma),
+                                   _stream(stream)))
 
 
 KERNEL_NAMES = ["op_gram", "solve_lambda", "update_xr", "solve_beta", "update_p", "residual"]

@@ -65,6 +65,9 @@ bool is_device_ptr(const void *p) {
 
 }  // namespace
 
+// Lets the other C ABI translation unit (bcg_noalloc.cu) report through bcg_last_error.
+void bcg_internal_set_error(const char *msg) { g_last_error = msg; }
+
 struct bcg_ctx {
   // problem
   int64_t n = 0, nnz = 0;
