@@ -165,6 +165,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=WORKLOAD["grid"],
                     help="Poisson grid edge (smaller grids only for profiling captures)")
+    ap.add_argument("--prec", default=WORKLOAD["prec"], choices=["fp64", "fp32_refine"],
+                    help="precision of the timed solve (profiling captures of the mixed form)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -199,6 +201,9 @@ def main():
     if args.grid != w["grid"]:
         w["grid"] = args.grid
         w["name"] = w["name"].replace("128", str(args.grid))
+    if args.prec != w["prec"]:
+        w["prec"] = args.prec
+        w["name"] = w["name"].replace("fp64", args.prec)
     M = W.poisson3d(w["grid"])
     n, k, p, z = M.n, w["k"], w["p"], M.nnz
     B_host = W.rhs(n, k, seed=rank)
@@ -278,7 +283,8 @@ def main():
 
     line = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f64" if w["prec"] == "fp64" else "f32 inner, f64 refinement",
+            "data": "synthetic",
             "config": {"workload": w["name"], "n": n, "nnz": z, "k": k, "p": p, "subalgebra": w["sub"],
                        "tol": w["tol"], "rhs_per_rank": k, "l2": "inputs larger than L2 (537 MB per block vector)",
                        "parallelism": f"independent right-hand-side blocks per rank x{world}"},

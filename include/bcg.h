@@ -179,6 +179,13 @@ bcg_status bcg_update_values(bcg_handle h, const double *vals);
 bcg_status bcg_bdot(bcg_handle h, const double *X, const double *Y, double *gamma);
 
 /*
+ * bcg_bdot_f32 -- BDOT on FP32 block vectors with FP64-accurate accumulation: the block product exactly as
+ * the FP32_REFINE inner solve forms it (products of FP32 values are exact in FP64; the sums carry FP64-class
+ * accuracy). X, Y: device float[n*k]; gamma as for bcg_bdot (double).
+ */
+bcg_status bcg_bdot_f32(bcg_handle h, const float *X, const float *Y, double *gamma);
+
+/*
  * bcg_bdot_noalloc -- bcg_bdot for callers that cannot allocate device memory. The paper has no
  * counterpart; this is a deployment variant of the BDOT kernel.
  *

@@ -58,6 +58,7 @@ def load():
         "bcg_update_values": [vp, vp],
         "bcg_bop": [vp, vp, vp],
         "bcg_bdot": [vp, vp, vp, vp],
+        "bcg_bdot_f32": [vp, vp, vp, vp],
         "bcg_bdot_noalloc": [i64, i32, i32, i32, vp, vp, vp, vp],
         "bcg_profile": [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), i32],
     }
@@ -149,6 +150,10 @@ def bcg_bop(h, X, Y):
 
 def bcg_bdot(h, X, Y, gamma):
     _check(load().bcg_bdot(h, _ptr(X), _ptr(Y), _ptr(gamma)))
+
+
+def bcg_bdot_f32(h, X, Y, gamma):
+    _check(load().bcg_bdot_f32(h, _ptr(X), _ptr(Y), _ptr(gamma)))
 
 
 def bcg_bdot_noalloc(n, k, p, sub, X, Y, gamma, stream=None):
@@ -275,7 +280,7 @@ class Solver:
         """gamma = <<X, Y>>_S as a (nblk, p, p) float64 tensor."""
         g = self.torch.empty(self.nblk, self.p, self.p, dtype=self.torch.float64, device=self.device)
         self._enter()
-        bcg_bdot(self.h, X, Y, g)
+        (bcg_bdot_f32 if X.dtype == self.torch.float32 else bcg_bdot)(self.h, X, Y, g)
         self._leave()
         return g
 

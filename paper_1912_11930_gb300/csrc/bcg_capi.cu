@@ -629,6 +629,17 @@ bcg_status bcg_bdot(bcg_handle h, const double *X, const double *Y, double *gamm
   return BCG_OK;
 }
 
+bcg_status bcg_bdot_f32(bcg_handle h, const float *X, const float *Y, double *gamma) {
+  if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (!is_device_ptr(X) || !is_device_ptr(Y) || !is_device_ptr(gamma))
+    return fail(BCG_ERR_INVALID_ARG, "X, Y and gamma must be device pointers");
+  const int grid = std::min(h->nparts, bdot_grid<float>(h->n, h->k, h->p, h->nsm));
+  CK(launch_bdot<float>(X, Y, h->n, h->k, h->p, h->partA, grid, h->stream));
+  CK(launch_finish_gram(h->partA, grid, h->k, h->p, h->global, gamma, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return BCG_OK;
+}
+
 bcg_status bcg_bop(bcg_handle h, const double *X, double *Y) {
   if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
   if (!is_device_ptr(X) || !is_device_ptr(Y) || X == Y) return fail(BCG_ERR_INVALID_ARG, "X, Y: distinct device pointers");

@@ -47,12 +47,15 @@ constexpr int kNT = 256;   // threads per CTA of the streaming kernels (k <= 256
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 // dynamic shared memory layouts (bytes), shared by kernels and launchers
-__host__ __device__ constexpr size_t op_gram_smem(int p) { return kNT * sizeof(double) + (size_t)kNT * p * sizeof(double); }
+// K1: broadcast tile + FP64 slot sums of alpha and of the recomputed rho
+__host__ __device__ constexpr size_t op_gram_smem(int p) { return kNT * sizeof(double) + 2 * (size_t)kNT * p * sizeof(double); }
+__host__ __device__ constexpr size_t bdot_smem(int p) { return kNT * sizeof(double) + (size_t)kNT * p * sizeof(double); }
 __host__ __device__ constexpr size_t update_xr_red_offset(int k, int p, int global, size_t tsize) {
   return align16((2 * kNT + (size_t)(global ? 1 : k / p) * p * p) * tsize);
 }
+// K2: P, Q tiles, lambda, then FP64 slot sums of rho and of the column norms
 __host__ __device__ constexpr size_t update_xr_smem(int k, int p, int global, size_t tsize) {
-  return update_xr_red_offset(k, p, global, tsize) + (size_t)kNT * p * sizeof(double);
+  return update_xr_red_offset(k, p, global, tsize) + (size_t)kNT * (p + 1) * sizeof(double);
 }
 __host__ __device__ constexpr size_t update_p_smem(int k, int p, int global, size_t tsize) {
   return (kNT + (size_t)(global ? 1 : k / p) * p * p) * tsize;
@@ -61,6 +64,97 @@ __host__ __device__ constexpr size_t residual_smem() { return kNT * sizeof(doubl
 
 __device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
 __device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+// ---- Gram accumulation off the FP64 pipe ----------------------------------------------------------------
+// GB300 executes FP64 at 1/61 of its FP32 rate, so block-product entries are accumulated as unevaluated float
+// pairs (s, c) with error-free transformations -- TwoProd by FMA and TwoSum, i.e. algorithm Dot2 of Ogita, Rump
+// & Oishi, "Accurate sum and dot product", SIAM J. Sci. Comput. 26(6), 2005 -- and added into per-thread FP64
+// sums in shared memory every kFlushPasses rows (which bounds the pair's own error growth). FP64 inputs are
+// first split into hi + lo floats (48 significant bits) with integer operations only. The per-CTA and grid
+// reductions stay in FP64.
+constexpr int kFlushPasses = 128;
+
+__device__ __forceinline__ void two_sum_acc(float &s, float &c, float p, float e) {
+  const float t = __fadd_rn(s, p);
+  const float z = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(p, z));   // s + p = t + err exactly
+  s = t;
+  c = __fadd_rn(c, __fadd_rn(err, e));
+}
+
+// x = hi + lo with hi = x truncated to 24 significant bits, lo = the remaining 29 bits rounded to 24: the
+// bits are moved with integer operations (no FP64 instruction) whenever both halves are normal floats.
+__device__ __forceinline__ float2 split_f64(double x) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi32 = (unsigned)(u >> 32);
+  const int e = (int)((hi32 >> 20) & 0x7FFu);
+  if (e >= 949 && e <= 1150) {
+    const unsigned sign = hi32 & 0x80000000u;
+    const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((u >> 29) & 0x7FFFFFu));
+    const float scale = __uint_as_float((unsigned)(e - 948) << 23);              // 2^(e - 1075)
+    const float lo = __fmul_rn(__uint2float_rn((unsigned)(u & 0x1FFFFFFFu)), scale);
+    return make_float2(hi, sign ? -lo : lo);
+  }
+  const float hi = (float)x;   // zero, tiny, huge or non-finite: plain conversions
+  return make_float2(hi, isfinite(x) ? (float)(x - (double)hi) : 0.0f);
+}
+
+template <typename T>
+struct Gram;
+template <>
+struct Gram<float> {
+  using B = float;   // broadcast / operand representation
+  __device__ static B conv(float v) { return v; }
+  __device__ static B zero() { return 0.0f; }
+  __device__ static void add(float &s, float &c, B x, B y) {
+    const float p = __fmul_rn(x, y);
+    two_sum_acc(s, c, p, __fmaf_rn(x, y, -p));   // x*y = p + e exactly
+  }
+};
+template <>
+struct Gram<double> {
+  using B = float2;
+  __device__ static B conv(double v) { return split_f64(v); }
+  __device__ static B zero() { return make_float2(0.0f, 0.0f); }
+  __device__ static void add(float &s, float &c, B x, B y) {
+    const float p = __fmul_rn(x.x, y.x);
+    float e = __fmaf_rn(x.x, y.x, -p);   // exact error of hi*hi
+    e = __fmaf_rn(x.x, y.y, e);          // cross terms, relative weight 2^-24
+    e = __fmaf_rn(x.y, y.x, e);
+    two_sum_acc(s, c, p, e);
+  }
+};
+
+template <int PM>
+struct GramAcc {
+  float s[PM], c[PM];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int a = 0; a < PM; ++a) { s[a] = 0.0f; c[a] = 0.0f; }
+  }
+  // move the pairs into the thread's FP64 sums and restart
+  __device__ __forceinline__ void flush(double *slot, int p) {
+#pragma unroll
+    for (int a = 0; a < PM; ++a)
+      if (a < p) {
+        slot[a] += (double)s[a];
+        slot[a] += (double)c[a];
+        s[a] = 0.0f;
+        c[a] = 0.0f;
+      }
+  }
+};
+
+// Sum the FP64 slots of all row slots of the CTA in fixed order: out[e] = sum_g red[g*E + e].
+__device__ __forceinline__ void cta_sum_slots(const double *red, int E, int rpp, double *__restrict__ out) {
+  __syncthreads();
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    double v = 0.0;
+    for (int gg = 0; gg < rpp; ++gg) v += red[(int64_t)gg * E + e];
+    out[e] = v;
+  }
+  __syncthreads();
+}
 
 // One row of BOP: (A X)_{r,c}.
 template <typename T, int OPK>
@@ -154,48 +248,60 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
                                                  T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                  const int *__restrict__ active, double *__restrict__ partA,
                                                  double *__restrict__ partR, const DevStatus *__restrict__ st) {
+  using G = Gram<T>;
+  using BT = typename G::B;
   if (st != nullptr && st->flags != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  T *sP = reinterpret_cast<T *>(smem);
-  double *red = reinterpret_cast<double *>(smem + kNT * sizeof(double));
+  BT *sP = reinterpret_cast<BT *>(smem);
+  double *redA = reinterpret_cast<double *>(smem + kNT * sizeof(double));
+  double *redR = redA + kNT * p;
   const int rpp = kNT / k;
   const int g = threadIdx.x / k, c = threadIdx.x - g * k;
   const bool slot = g < rpp;
-  const int j = c / p, b = c - j * p;
+  const int j = c / p;
   const bool act = slot && block_active(active, global, j);
-  double accA[PM], accR[PM];
-#pragma unroll
-  for (int a = 0; a < PM; ++a) { accA[a] = 0.0; accR[a] = 0.0; }
+  double *slotA = redA + ((int64_t)g * k + c) * p, *slotR = redR + ((int64_t)g * k + c) * p;
+  if (slot)
+    for (int a = 0; a < p; ++a) { slotA[a] = 0.0; slotR[a] = 0.0; }
+  GramAcc<PM> accA, accR;
+  accA.zero();
+  accR.zero();
+  int pass = 0;
   const int64_t stride = (int64_t)gridDim.x * rpp;
   for (int64_t row0 = (int64_t)blockIdx.x * rpp; row0 < n; row0 += stride) {
     const int64_t r = row0 + g;
-    T pv = T(0), qv = T(0), rv = T(0);
+    BT pb = G::zero(), qb = G::zero(), rb = G::zero();
     if (act && r < n) {
       const int64_t o = r * k + c;
-      qv = apply_row<T, OPK>(A, P, r, k, c);
-      pv = P[o];
-      rv = R[o];
+      const T qv = apply_row<T, OPK>(A, P, r, k, c);
       Q[o] = qv;
+      pb = G::conv(P[o]);
+      qb = G::conv(qv);
+      rb = G::conv(R[o]);
     }
-    if (slot) sP[g * k + c] = pv;
+    if (slot) sP[g * k + c] = pb;
     __syncthreads();
     if (act) {
-      const T *prow = sP + g * k + j * p;
+      const BT *prow = sP + g * k + j * p;
 #pragma unroll
       for (int a = 0; a < PM; ++a) {
         if (a < p) {
-          const double pa = (double)prow[a];
-          accA[a] = fma(pa, (double)qv, accA[a]);
-          accR[a] = fma(pa, (double)rv, accR[a]);
+          const BT pa = prow[a];
+          G::add(accA.s[a], accA.c[a], pa, qb);
+          G::add(accR.s[a], accR.c[a], pa, rb);
         }
       }
     }
     __syncthreads();
+    if (++pass == kFlushPasses) {
+      pass = 0;
+      if (slot) { accA.flush(slotA, p); accR.flush(slotR, p); }
+    }
   }
-  (void)b;
-  const int64_t E = (int64_t)k * p;
-  cta_reduce_partial<PM>(accA, red, k, p, g, c, rpp, partA + blockIdx.x * E);
-  cta_reduce_partial<PM>(accR, red, k, p, g, c, rpp, partR + blockIdx.x * E);
+  if (slot) { accA.flush(slotA, p); accR.flush(slotR, p); }
+  const int E = k * p;
+  cta_sum_slots(redA, E, rpp, partA + (int64_t)blockIdx.x * E);
+  cta_sum_slots(redR, E, rpp, partR + (int64_t)blockIdx.x * E);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -206,13 +312,18 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
                                                    const double *__restrict__ lam, const int *__restrict__ active,
                                                    double *__restrict__ partRho, double *__restrict__ partN,
                                                    const DevStatus *__restrict__ st) {
+  using G = Gram<T>;
+  using BT = typename G::B;
+  static_assert(sizeof(BT) <= sizeof(T), "broadcast tile reuses the P tile");
   if (st != nullptr && st->flags != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
   T *sP = reinterpret_cast<T *>(smem);
   T *sQ = sP + kNT;
   T *sL = sQ + kNT;                       // lambda in T, [nblk][p][p]
+  BT *sRb = reinterpret_cast<BT *>(smem);  // new residual row, broadcast (reuses the P tile)
   const int nblk = global ? 1 : k / p;
   double *red = reinterpret_cast<double *>(smem + update_xr_red_offset(k, p, global, sizeof(T)));
+  double *nred = red + kNT * p;
   for (int e = threadIdx.x; e < nblk * p * p; e += blockDim.x) sL[e] = (T)lam[e];
   const int rpp = kNT / k;
   const int g = threadIdx.x / k, c = threadIdx.x - g * k;
@@ -220,10 +331,16 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
   const int j = c / p, b = c - j * p;
   const bool act = slot && block_active(active, global, j);
   const T *lj = sL + (global ? 0 : j) * p * p + b;   // lj[a*p] = lambda_j(a, b)
-  double accRho[PM];
-  double accN = 0.0;
-#pragma unroll
-  for (int a = 0; a < PM; ++a) accRho[a] = 0.0;
+  double *slotRho = red + ((int64_t)g * k + c) * p;
+  double *slotN = nred + (int64_t)g * k + c;
+  if (slot) {
+    for (int a = 0; a < p; ++a) slotRho[a] = 0.0;
+    *slotN = 0.0;
+  }
+  GramAcc<PM> acc;
+  acc.zero();
+  float ns = 0.0f, nc = 0.0f;
+  int pass = 0;
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * rpp;
   for (int64_t row0 = (int64_t)blockIdx.x * rpp; row0 < n; row0 += stride) {
@@ -249,22 +366,35 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
       R[o] = rv;
     }
     __syncthreads();
-    if (slot) sP[g * k + c] = live ? rv : T(0);
+    const BT rb = live ? G::conv(rv) : G::zero();
+    if (slot) sRb[g * k + c] = rb;
     __syncthreads();
     if (live) {
-      const T *rrow = sP + g * k + j * p;
-      const double rd = (double)rv;
+      const BT *rrow = sRb + g * k + j * p;
 #pragma unroll
       for (int a = 0; a < PM; ++a)
-        if (a < p) accRho[a] = fma((double)rrow[a], rd, accRho[a]);
-      accN = fma(rd, rd, accN);
+        if (a < p) G::add(acc.s[a], acc.c[a], rrow[a], rb);
+      G::add(ns, nc, rb, rb);
     }
     __syncthreads();
+    if (++pass == kFlushPasses) {
+      pass = 0;
+      if (slot) {
+        acc.flush(slotRho, p);
+        *slotN += (double)ns;
+        *slotN += (double)nc;
+        ns = nc = 0.0f;
+      }
+    }
   }
-  const int64_t E = (int64_t)k * p;
-  cta_reduce_partial<PM>(accRho, red, k, p, g, c, rpp, partRho + blockIdx.x * E);
-  double an[1] = {accN};
-  cta_reduce_partial<1>(an, red, k, 1, g, c, rpp, partN + (int64_t)blockIdx.x * k);
+  if (slot) {
+    acc.flush(slotRho, p);
+    *slotN += (double)ns;
+    *slotN += (double)nc;
+  }
+  const int E = k * p;
+  cta_sum_slots(red, E, rpp, partRho + (int64_t)blockIdx.x * E);
+  cta_sum_slots(nred, k, rpp, partN + (int64_t)blockIdx.x * k);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -344,32 +474,42 @@ __global__ void __launch_bounds__(kNT) k_residual(OpDesc A, const T *__restrict_
 template <typename T, int PM>
 __global__ void __launch_bounds__(kNT) k_bdot(const T *__restrict__ X, const T *__restrict__ Y, int64_t n, int k,
                                               int p, double *__restrict__ part) {
+  using G = Gram<T>;
+  using BT = typename G::B;
   extern __shared__ __align__(16) unsigned char smem[];
-  T *sX = reinterpret_cast<T *>(smem);
+  BT *sX = reinterpret_cast<BT *>(smem);
   double *red = reinterpret_cast<double *>(smem + kNT * sizeof(double));
   const int rpp = kNT / k;
   const int g = threadIdx.x / k, c = threadIdx.x - g * k;
   const bool slot = g < rpp;
   const int j = c / p;
-  double acc[PM];
-#pragma unroll
-  for (int a = 0; a < PM; ++a) acc[a] = 0.0;
+  double *sl = red + ((int64_t)g * k + c) * p;
+  if (slot)
+    for (int a = 0; a < p; ++a) sl[a] = 0.0;
+  GramAcc<PM> acc;
+  acc.zero();
+  int pass = 0;
   const int64_t stride = (int64_t)gridDim.x * rpp;
   for (int64_t row0 = (int64_t)blockIdx.x * rpp; row0 < n; row0 += stride) {
     const int64_t r = row0 + g;
-    T xv = T(0), yv = T(0);
-    if (slot && r < n) { xv = X[r * k + c]; yv = Y[r * k + c]; }
-    if (slot) sX[g * k + c] = xv;
+    BT xb = G::zero(), yb = G::zero();
+    if (slot && r < n) { xb = G::conv(X[r * k + c]); yb = G::conv(Y[r * k + c]); }
+    if (slot) sX[g * k + c] = xb;
     __syncthreads();
     if (slot) {
-      const T *xrow = sX + g * k + j * p;
+      const BT *xrow = sX + g * k + j * p;
 #pragma unroll
       for (int a = 0; a < PM; ++a)
-        if (a < p) acc[a] = fma((double)xrow[a], (double)yv, acc[a]);
+        if (a < p) G::add(acc.s[a], acc.c[a], xrow[a], yb);
     }
     __syncthreads();
+    if (++pass == kFlushPasses) {
+      pass = 0;
+      if (slot) acc.flush(sl, p);
+    }
   }
-  cta_reduce_partial<PM>(acc, red, k, p, g, c, rpp, part + (int64_t)blockIdx.x * k * p);
+  if (slot) acc.flush(sl, p);
+  cta_sum_slots(red, k * p, rpp, part + (int64_t)blockIdx.x * k * p);
 }
 
 // BOP alone: Y = A X.

@@ -14,37 +14,55 @@
 
 namespace bcgk {
 
-constexpr int kSmallNT = 256;
+constexpr int kSmallNT = 512;
 constexpr double kPivotFactor = 64.0;
+
+// Deterministic reduction out[e] = sum over pi < nparts of load(pi, e), e < E: each entry's sum is split
+// over S = blockDim/E thread subsets (pi = sub, sub + S, ...) with 4 independent accumulators per thread
+// (several loads in flight), then the subsets are added in a fixed order. scratch: >= max(E, blockDim)
+// doubles. The order is fixed by (E, nparts, blockDim), so results repeat bitwise.
+template <typename F>
+__device__ void det_reduce(int E, int nparts, F load, double *out, double *scratch) {
+  const int NT = blockDim.x;
+  const int S = E >= NT ? 1 : NT / E;
+  for (int t = threadIdx.x; t < E * S; t += NT) {
+    const int el = t % E, sub = t / E;
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int pi = sub;
+    for (; pi + 3 * S < nparts; pi += 4 * S) {
+      a0 += load(pi, el);
+      a1 += load(pi + S, el);
+      a2 += load(pi + 2 * S, el);
+      a3 += load(pi + 3 * S, el);
+    }
+    for (; pi < nparts; pi += S) a0 += load(pi, el);
+    scratch[t] = (a0 + a1) + (a2 + a3);
+  }
+  __syncthreads();
+  for (int el = threadIdx.x; el < E; el += NT) {
+    double v = 0.0;
+    for (int sub = 0; sub < S; ++sub) v += scratch[sub * E + el];
+    out[el] = v;
+  }
+  __syncthreads();
+}
 
 // Sum the partials of distinct block jb into dst[b*p + a] (the partial layout).
 __device__ void reduce_block(const double *__restrict__ part, int nparts, int k, int p, int global, int jb,
                              double *dst, double *scratch) {
-  const int NT = blockDim.x;
   const int Eb = p * p;
-  const int S = Eb >= NT ? 1 : NT / Eb;
   const int64_t E = (int64_t)k * p;
   const int q = k / p;
-  for (int t = threadIdx.x; t < Eb * S; t += NT) {
-    const int el = t % Eb, sub = t / Eb;
-    double s = 0.0;
-    for (int pi = sub; pi < nparts; pi += S) {
-      const double *base = part + pi * E + el;
-      if (!global) {
-        s += base[(int64_t)jb * Eb];
-      } else {
-        for (int j = 0; j < q; ++j) s += base[(int64_t)j * Eb];
-      }
-    }
-    scratch[t] = s;
+  if (!global) {
+    const double *base = part + (int64_t)jb * Eb;
+    det_reduce(Eb, nparts, [&](int pi, int el) { return base[pi * E + el]; }, dst, scratch);
+  } else {
+    det_reduce(Eb, nparts, [&](int pi, int el) {
+      double v = 0.0;
+      for (int j = 0; j < q; ++j) v += part[pi * E + (int64_t)j * Eb + el];
+      return v;
+    }, dst, scratch);
   }
-  __syncthreads();
-  for (int el = threadIdx.x; el < Eb; el += NT) {
-    double s = 0.0;
-    for (int sub = 0; sub < S; ++sub) s += scratch[sub * Eb + el];
-    dst[el] = s;
-  }
-  __syncthreads();
 }
 
 // dst[a*p + b] = src[b*p + a]
@@ -153,10 +171,14 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
   const int pp = p * p;
   const int it = st->cur;
   const int c0 = global ? 0 : jb * p, c1 = global ? k : c0 + p;
+  extern __shared__ __align__(16) double sm[];
+  {
+    double *ncol = sm, *nscr = sm + kNT;   // column norms of this block, scratch
+    det_reduce(c1 - c0, nparts, [&](int pi, int c) { return partN[(int64_t)pi * k + c0 + c]; }, ncol, nscr);
+  }
   bool conv = true, finite = true;
   for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-    double s = 0.0;
-    for (int pi = 0; pi < nparts; ++pi) s += partN[(int64_t)pi * k + c];
+    const double s = sm[c - c0];
     rn2[c] = s;
     if (!isfinite(s)) finite = false;
     if (!(s <= tol2 * r0n2[c])) conv = false;
@@ -178,7 +200,6 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
     }
     return;
   }
-  extern __shared__ __align__(16) double sm[];
   double *sM = sm;          // rho_rec (row-major), LU-factored in place
   double *sB = sM + pp;     // right-hand sides rho (row-major), become beta
   double *tmp = sB + pp;
@@ -263,9 +284,10 @@ __global__ void k_init_status(const double *__restrict__ partN, int nparts, int 
   __shared__ int nact, nonfinite;
   if (threadIdx.x == 0) { nact = 0; nonfinite = 0; }
   __syncthreads();
+  __shared__ double ncol[kNT], nscr[kSmallNT > kNT ? kSmallNT : kNT];
+  det_reduce(k, nparts, [&](int pi, int c) { return partN[(int64_t)pi * k + c]; }, ncol, nscr);
   for (int c = threadIdx.x; c < k; c += blockDim.x) {
-    double s = 0.0;
-    for (int pi = 0; pi < nparts; ++pi) s += partN[(int64_t)pi * k + c];
+    const double s = ncol[c];
     r0n2[c] = s;
     rn2[c] = s;
     if (!isfinite(s)) atomicOr(&nonfinite, 1);
@@ -306,11 +328,9 @@ __global__ void __launch_bounds__(kSmallNT) k_finish_gram(const double *__restri
 }
 
 __global__ void k_reduce_norms(const double *__restrict__ partN, int nparts, int k, double *__restrict__ out) {
-  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < k; c += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int pi = 0; pi < nparts; ++pi) s += partN[(int64_t)pi * k + c];
-    out[c] = s;
-  }
+  __shared__ double ncol[kNT], nscr[kSmallNT > kNT ? kSmallNT : kNT];
+  det_reduce(k, nparts, [&](int pi, int c) { return partN[(int64_t)pi * k + c]; }, ncol, nscr);
+  for (int c = threadIdx.x; c < k; c += blockDim.x) out[c] = ncol[c];
 }
 
 // X64 += D32 (the refinement update of the mixed-precision form)
@@ -347,7 +367,9 @@ __global__ void k_row_index(const int64_t *__restrict__ rowptr, int64_t n, int32
 
 static size_t small_smem(int p) {
   const int pp = p * p;
-  return (size_t)(3 * pp + (pp > kSmallNT ? pp : kSmallNT)) * sizeof(double);
+  const size_t solve = (size_t)(3 * pp + (pp > kSmallNT ? pp : kSmallNT));
+  const size_t norms = (size_t)(kNT + kSmallNT);   // column norms + reduction scratch in k_solve_beta
+  return (solve > norms ? solve : norms) * sizeof(double);
 }
 
 cudaError_t small_prepare(int p) {
@@ -394,7 +416,7 @@ cudaError_t launch_finish_gram(const double *part, int nparts, int k, int p, int
 }
 
 cudaError_t launch_reduce_norms(const double *partN, int nparts, int k, double *out, cudaStream_t s) {
-  k_reduce_norms<<<(k + 255) / 256, 256, 0, s>>>(partN, nparts, k, out);
+  k_reduce_norms<<<1, kSmallNT, 0, s>>>(partN, nparts, k, out);
   return cudaGetLastError();
 }
 

@@ -292,3 +292,22 @@ def test_bdot_matches_block_product(torch_dev, sub, k, p):
     assert g.shape == ref.shape
     scale = np.linalg.norm(X) * np.linalg.norm(Y) / k
     assert np.max(np.abs(g - ref)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("sub,k,p", [("hybrid", 8, 4), ("global", 32, 8), ("hybrid", 64, 16), ("classical", 32, 32)])
+def test_bdot_f32_is_fp64_accurate(torch_dev, sub, k, p):
+    """The mixed form's Gram: FP32 block vectors, products and sums carried to FP64-class accuracy (error-free
+    transformations on the FP32 pipes). Reference: the same FP32 values multiplied and summed in FP64."""
+    torch, dev = torch_dev
+    M = mat("p3d_30")
+    X = W.rhs(M.n, k, seed=22).astype(np.float32)
+    Y = (W.rhs(M.n, k, seed=23) * np.exp(W.rhs(M.n, k, seed=24))).astype(np.float32)   # wide dynamic range
+    from paper_1912_11930_gb300 import bcg
+    S = bcg.Solver.from_matrix(M, k=k, p=p, sub=sub, device=dev)
+    g = S.bdot(torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)).cpu().numpy()
+    S.close()
+    kind, pp = O.canonical_subalgebra(sub, k, p)
+    ref = O.block_product(X.astype(np.float64), Y.astype(np.float64), pp, kind)
+    absdot = O.block_product(np.abs(X.astype(np.float64)), np.abs(Y.astype(np.float64)), pp, kind)
+    # FP64-class: error far below FP32 accumulation (which would be ~1e-7 relative to sum |x y|)
+    assert np.max(np.abs(g - ref) / absdot) <= 1e-13
