@@ -111,7 +111,9 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
 
 /*
  * bcg_set_option -- tune a handle. Keys:
- *   "inner_tol"    FP32_REFINE: relative residual reduction of each inner solve (default 1e-4)
+ *   "inner_tol"    FP32_REFINE: smallest relative residual reduction an inner solve is asked for
+ *                  (default 1e-5); each inner solve targets the reduction still needed by the outer
+ *                  tolerance (times 0.5), but not less than this
  *   "max_outer"    FP32_REFINE: maximum refinement steps (default 30)
  *   "check_every"  iterations launched between two host reads of the device status word (default 8;
  *                  converged iterations in between are skipped on the device at launch cost only)

@@ -80,7 +80,7 @@ struct bcg_ctx {
   StreamGrids g64{}, g32{};
   int nparts = 0;                      // partial-buffer rows (max CTAs of K0/K1/K2)
   // options
-  double inner_tol = 1e-4;
+  double inner_tol = 1e-5;
   int max_outer = 30;
   int check_every = 8;
   int use_graph = 1;
@@ -396,7 +396,6 @@ bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int ma
 bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int maxit, bcg_info *info) {
   cudaStream_t s = h->stream;
   const int64_t nk = h->n * h->k;
-  const double itol2 = h->inner_tol * h->inner_tol;
   int outer = 0, inner_total = 0, brk = -1;
   bcg_status st = BCG_ERR_NOT_CONVERGED;
   double last_max = INFINITY;
@@ -419,7 +418,10 @@ bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int 
       stalls = 0;
     }
     last_max = std::min(last_max, m);
-    // inner FP32 solve of A D = fl(R) from D = 0
+    // inner FP32 solve of A D = fl(R) from D = 0, asked for the reduction still needed (with a factor-2
+    // margin), but never for less than inner_tol (what FP32 block vectors can be trusted to deliver)
+    const double itol = std::min(0.5, std::max(h->inner_tol, 0.5 * tol / m));
+    const double itol2 = itol * itol;
     CK(cudaMemsetAsync(h->D32, 0, sizeof(float) * nk, s));
     CK(launch_init_status(h->partN, h->g64.res, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters,
                           h->lam, h->beta, h->st, s));

@@ -47,18 +47,29 @@ constexpr int kNT = 256;   // threads per CTA of the streaming kernels (k <= 256
 
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
 // dynamic shared memory layouts (bytes), shared by kernels and launchers
-// K1: broadcast tile + FP64 slot sums of alpha and of the recomputed rho
-__host__ __device__ constexpr size_t op_gram_smem(int p) { return kNT * sizeof(double) + 2 * (size_t)kNT * p * sizeof(double); }
+// Rows per thread per pass: every load of a pass is issued before its arithmetic, so RPT rows' worth of
+// memory requests are in flight per thread (the row loops are otherwise latency-bound on GB300).
+// (measured on GB300: FP64 kernels are bound by the FP64 pipe and lose occupancy with RPT > 1; the FP32
+// updates gain a little from RPT = 4; K1 is register heavy and keeps RPT = 1)
+template <typename T>
+__host__ __device__ constexpr int rpt_stream() { return sizeof(T) == 4 ? 4 : 1; }   // K2, K3
+template <typename T>
+__host__ __device__ constexpr int rpt_op() { return 1; }                              // K1
+
+// K1: broadcast tile (RPT rows per slot) + FP64 slot sums of alpha and of the recomputed rho
+__host__ __device__ constexpr size_t op_gram_smem(int p, int rpt) {
+  return (size_t)rpt * kNT * sizeof(double) + 2 * (size_t)kNT * p * sizeof(double);
+}
 __host__ __device__ constexpr size_t bdot_smem(int p) { return kNT * sizeof(double) + (size_t)kNT * p * sizeof(double); }
-__host__ __device__ constexpr size_t update_xr_red_offset(int k, int p, int global, size_t tsize) {
-  return align16((2 * kNT + (size_t)(global ? 1 : k / p) * p * p) * tsize);
+__host__ __device__ constexpr size_t update_xr_red_offset(int k, int p, int global, size_t tsize, int rpt) {
+  return align16((2 * (size_t)rpt * kNT + (size_t)(global ? 1 : k / p) * p * p) * tsize);
 }
 // K2: P, Q tiles, lambda, then FP64 slot sums of rho and of the column norms
-__host__ __device__ constexpr size_t update_xr_smem(int k, int p, int global, size_t tsize) {
-  return update_xr_red_offset(k, p, global, tsize) + (size_t)kNT * (p + 1) * sizeof(double);
+__host__ __device__ constexpr size_t update_xr_smem(int k, int p, int global, size_t tsize, int rpt) {
+  return update_xr_red_offset(k, p, global, tsize, rpt) + (size_t)kNT * (p + 1) * sizeof(double);
 }
-__host__ __device__ constexpr size_t update_p_smem(int k, int p, int global, size_t tsize) {
-  return (kNT + (size_t)(global ? 1 : k / p) * p * p) * tsize;
+__host__ __device__ constexpr size_t update_p_smem(int k, int p, int global, size_t tsize, int rpt) {
+  return ((size_t)rpt * kNT + (size_t)(global ? 1 : k / p) * p * p) * tsize;
 }
 __host__ __device__ constexpr size_t residual_smem() { return kNT * sizeof(double); }
 
@@ -125,6 +136,28 @@ struct Gram<double> {
   }
 };
 
+// Read row[a] for a < PM from shared memory, 16 bytes at a time when the row start is aligned.
+template <typename E, int PM>
+__device__ __forceinline__ void load_row(const E *row, E (&out)[PM], int p) {
+  constexpr int V = 16 / sizeof(E);   // elements per 16-byte load
+  if (PM >= V && p == PM && (reinterpret_cast<uintptr_t>(row) & 15) == 0) {
+#pragma unroll
+    for (int a = 0; a < PM; a += V) {
+      if constexpr (V == 4) {
+        const float4 t = *reinterpret_cast<const float4 *>(row + a);
+        out[a] = t.x; out[a + 1] = t.y; out[a + 2] = t.z; out[a + 3] = t.w;
+      } else {   // 8-byte elements (double, or a float2 hi/lo pair)
+        const double2 t = *reinterpret_cast<const double2 *>(row + a);
+        out[a] = *reinterpret_cast<const E *>(&t.x);
+        out[a + 1] = *reinterpret_cast<const E *>(&t.y);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int a = 0; a < PM; ++a) out[a] = a < p ? row[a] : E{};
+  }
+}
+
 template <int PM>
 struct GramAcc {
   float s[PM], c[PM];
@@ -160,11 +193,25 @@ __device__ __forceinline__ void cta_sum_slots(const double *red, int E, int rpp,
 template <typename T, int OPK>
 __device__ __forceinline__ T apply_row(const OpDesc &A, const T *__restrict__ X, int64_t r, int k, int c) {
   if constexpr (OPK == OP_CSR) {
+    // batches of 8 entries: all column indices and values first, then all gathered X loads, then the FMAs,
+    // so a row costs ~2 dependent memory round trips instead of one per entry
     const T *__restrict__ v = static_cast<const T *>(A.vals);
     const int64_t e0 = __ldg(A.rowptr + r), e1 = __ldg(A.rowptr + r + 1);
     T s = T(0);
-    for (int64_t e = e0; e < e1; ++e)
-      s = fma_t(__ldg(v + e), __ldg(X + (int64_t)__ldg(A.colind + e) * k + c), s);
+    for (int64_t e = e0; e < e1; e += 8) {
+      int col[8];
+      T w[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool in = e + u < e1;
+        col[u] = in ? __ldg(A.colind + e + u) : 0;
+        w[u] = in ? __ldg(v + e + u) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = (e + u < e1) ? __ldg(X + (int64_t)col[u] * k + c) : T(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s = fma_t(w[u], xv[u], s);
+    }
     return s;
   } else if constexpr (OPK == OP_ST5) {
     const int nx = A.nx, ny = A.ny;
@@ -236,13 +283,26 @@ __device__ __forceinline__ void cta_reduce_partial(const double (&acc)[PM], doub
   __syncthreads();
 }
 
+// The shared-memory row tiles are indexed by thread (tile element t = g*k + c). When no block of p columns
+// straddles a warp -- k divides 32, or 32 divides k and p divides 32 -- every broadcast read stays inside the
+// writing warp, so a warp barrier orders it and the warps of a CTA run their row passes independently
+// (better latency hiding than CTA-wide barriers, which make all warps load together and compute together).
+__host__ __device__ __forceinline__ bool warp_local_rows(int k, int p) {
+  return (32 % k == 0) || (k % 32 == 0 && 32 % p == 0);
+}
+__device__ __forceinline__ void row_sync(bool warp_local) {
+  if (warp_local) __syncwarp();
+  else __syncthreads();
+}
+
 __device__ __forceinline__ bool block_active(const int *__restrict__ active, int global, int j) {
   return active == nullptr || active[global ? 0 : j] != 0;
 }
 
 // ---------------------------------------------------------------------------------------------------
 // K1: Q = A P (BOP), alpha = <<P, Q>>_S, and the recomputed rho^{i-1} = <<P, R^{i-1}>>_S (BDOT x 2),
-// one pass over the rows.
+// one pass over the rows. A CTA pass covers RPT * rpp consecutive rows; slot g handles rows
+// row0 + u*rpp + g, u < RPT.
 template <typename T, int OPK, int PM>
 __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
                                                  T *__restrict__ Q, int64_t n, int k, int p, int global,
@@ -250,12 +310,14 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
                                                  double *__restrict__ partR, const DevStatus *__restrict__ st) {
   using G = Gram<T>;
   using BT = typename G::B;
+  constexpr int RPT = rpt_op<T>();
   if (st != nullptr && st->flags != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  BT *sP = reinterpret_cast<BT *>(smem);
-  double *redA = reinterpret_cast<double *>(smem + kNT * sizeof(double));
+  BT *sP = reinterpret_cast<BT *>(smem);   // [RPT][kNT]
+  double *redA = reinterpret_cast<double *>(smem + (size_t)RPT * kNT * sizeof(double));
   double *redR = redA + kNT * p;
   const int rpp = kNT / k;
+  const bool wl = warp_local_rows(k, p);
   const int g = threadIdx.x / k, c = threadIdx.x - g * k;
   const bool slot = g < rpp;
   const int j = c / p;
@@ -267,33 +329,47 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
   accA.zero();
   accR.zero();
   int pass = 0;
-  const int64_t stride = (int64_t)gridDim.x * rpp;
-  for (int64_t row0 = (int64_t)blockIdx.x * rpp; row0 < n; row0 += stride) {
-    const int64_t r = row0 + g;
-    BT pb = G::zero(), qb = G::zero(), rb = G::zero();
-    if (act && r < n) {
-      const int64_t o = r * k + c;
-      const T qv = apply_row<T, OPK>(A, P, r, k, c);
-      Q[o] = qv;
-      pb = G::conv(P[o]);
-      qb = G::conv(qv);
-      rb = G::conv(R[o]);
-    }
-    if (slot) sP[g * k + c] = pb;
-    __syncthreads();
-    if (act) {
-      const BT *prow = sP + g * k + j * p;
+  const int64_t span = (int64_t)rpp * RPT;
+  const int64_t stride = (int64_t)gridDim.x * span;
+  for (int64_t row0 = (int64_t)blockIdx.x * span; row0 < n; row0 += stride) {
+    BT qb[RPT], rb[RPT];
+    T qv[RPT], pv[RPT], rv[RPT];
 #pragma unroll
-      for (int a = 0; a < PM; ++a) {
-        if (a < p) {
-          const BT pa = prow[a];
-          G::add(accA.s[a], accA.c[a], pa, qb);
-          G::add(accR.s[a], accR.c[a], pa, rb);
+    for (int u = 0; u < RPT; ++u) {
+      const int64_t r = row0 + u * rpp + g;
+      qv[u] = pv[u] = rv[u] = T(0);
+      if (act && r < n) {
+        const int64_t o = r * k + c;
+        pv[u] = P[o];
+        rv[u] = R[o];
+        qv[u] = apply_row<T, OPK>(A, P, r, k, c);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int64_t r = row0 + u * rpp + g;
+      if (act && r < n) Q[r * k + c] = qv[u];
+      qb[u] = G::conv(qv[u]);
+      rb[u] = G::conv(rv[u]);
+      if (slot) sP[u * kNT + g * k + c] = G::conv(pv[u]);
+    }
+    row_sync(wl);
+    if (act) {
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        BT prow[PM];
+        load_row<BT, PM>(sP + u * kNT + g * k + j * p, prow, p);
+#pragma unroll
+        for (int a = 0; a < PM; ++a) {
+          if (a < p) {
+            G::add(accA.s[a], accA.c[a], prow[a], qb[u]);
+            G::add(accR.s[a], accR.c[a], prow[a], rb[u]);
+          }
         }
       }
     }
-    __syncthreads();
-    if (++pass == kFlushPasses) {
+    row_sync(wl);
+    if (++pass == kFlushPasses / RPT) {
       pass = 0;
       if (slot) { accA.flush(slotA, p); accR.flush(slotR, p); }
     }
@@ -314,23 +390,24 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
                                                    const DevStatus *__restrict__ st) {
   using G = Gram<T>;
   using BT = typename G::B;
+  constexpr int RPT = rpt_stream<T>();
   static_assert(sizeof(BT) <= sizeof(T), "broadcast tile reuses the P tile");
   if (st != nullptr && st->flags != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  T *sP = reinterpret_cast<T *>(smem);
-  T *sQ = sP + kNT;
-  T *sL = sQ + kNT;                       // lambda in T, [nblk][p][p]
-  BT *sRb = reinterpret_cast<BT *>(smem);  // new residual row, broadcast (reuses the P tile)
+  T *sP = reinterpret_cast<T *>(smem);     // [RPT][kNT]
+  T *sQ = sP + RPT * kNT;                  // [RPT][kNT]
+  T *sL = sQ + RPT * kNT;                  // lambda in T, [nblk][p][p]
+  BT *sRb = reinterpret_cast<BT *>(smem);  // new residual rows, broadcast (reuses the P tile)
   const int nblk = global ? 1 : k / p;
-  double *red = reinterpret_cast<double *>(smem + update_xr_red_offset(k, p, global, sizeof(T)));
+  double *red = reinterpret_cast<double *>(smem + update_xr_red_offset(k, p, global, sizeof(T), RPT));
   double *nred = red + kNT * p;
   for (int e = threadIdx.x; e < nblk * p * p; e += blockDim.x) sL[e] = (T)lam[e];
   const int rpp = kNT / k;
+  const bool wl = warp_local_rows(k, p);
   const int g = threadIdx.x / k, c = threadIdx.x - g * k;
   const bool slot = g < rpp;
   const int j = c / p, b = c - j * p;
   const bool act = slot && block_active(active, global, j);
-  const T *lj = sL + (global ? 0 : j) * p * p + b;   // lj[a*p] = lambda_j(a, b)
   double *slotRho = red + ((int64_t)g * k + c) * p;
   double *slotN = nred + (int64_t)g * k + c;
   if (slot) {
@@ -342,42 +419,71 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
   float ns = 0.0f, nc = 0.0f;
   int pass = 0;
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * rpp;
-  for (int64_t row0 = (int64_t)blockIdx.x * rpp; row0 < n; row0 += stride) {
-    const int64_t r = row0 + g;
-    const bool live = act && r < n;
-    const int64_t o = r * k + c;
-    T xv = T(0), rv = T(0), pv = T(0), qv = T(0);
-    if (live) { xv = X[o]; rv = R[o]; pv = P[o]; qv = Q[o]; }
-    if (slot) { sP[g * k + c] = pv; sQ[g * k + c] = qv; }
-    __syncthreads();
-    if (live) {
-      const T *prow = sP + g * k + j * p;
-      const T *qrow = sQ + g * k + j * p;
+  T lcol[PM];   // column b of lambda_j: the same for every row this thread updates
+  {
+    const T *lj = sL + (global ? 0 : j) * p * p + b;
 #pragma unroll
-      for (int a = 0; a < PM; ++a) {
-        if (a < p) {
-          const T l = lj[a * p];
-          xv = fma_t(prow[a], l, xv);
-          rv = fma_t(-qrow[a], l, rv);
+    for (int a = 0; a < PM; ++a) lcol[a] = (slot && a < p) ? lj[a * p] : T(0);
+  }
+  const int64_t span = (int64_t)rpp * RPT;
+  const int64_t stride = (int64_t)gridDim.x * span;
+  for (int64_t row0 = (int64_t)blockIdx.x * span; row0 < n; row0 += stride) {
+    T xv[RPT], rv[RPT], pv[RPT], qv[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int64_t r = row0 + u * rpp + g;
+      xv[u] = rv[u] = pv[u] = qv[u] = T(0);
+      if (act && r < n) {
+        const int64_t o = r * k + c;
+        xv[u] = X[o]; rv[u] = R[o]; pv[u] = P[o]; qv[u] = Q[o];
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < RPT; ++u)
+      if (slot) { sP[u * kNT + g * k + c] = pv[u]; sQ[u * kNT + g * k + c] = qv[u]; }
+    row_sync(wl);
+    if (act) {
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        T prow[PM], qrow[PM];
+        load_row<T, PM>(sP + u * kNT + g * k + j * p, prow, p);
+        load_row<T, PM>(sQ + u * kNT + g * k + j * p, qrow, p);
+#pragma unroll
+        for (int a = 0; a < PM; ++a) {
+          if (a < p) {
+            xv[u] = fma_t(prow[a], lcol[a], xv[u]);
+            rv[u] = fma_t(-qrow[a], lcol[a], rv[u]);
+          }
+        }
+        const int64_t r = row0 + u * rpp + g;
+        if (r < n) {
+          X[r * k + c] = xv[u];
+          R[r * k + c] = rv[u];
         }
       }
-      X[o] = xv;
-      R[o] = rv;
     }
-    __syncthreads();
-    const BT rb = live ? G::conv(rv) : G::zero();
-    if (slot) sRb[g * k + c] = rb;
-    __syncthreads();
-    if (live) {
-      const BT *rrow = sRb + g * k + j * p;
+    row_sync(wl);
+    BT rb[RPT];
 #pragma unroll
-      for (int a = 0; a < PM; ++a)
-        if (a < p) G::add(acc.s[a], acc.c[a], rrow[a], rb);
-      G::add(ns, nc, rb, rb);
+    for (int u = 0; u < RPT; ++u) {
+      const int64_t r = row0 + u * rpp + g;
+      rb[u] = (act && r < n) ? G::conv(rv[u]) : G::zero();
+      if (slot) sRb[u * kNT + g * k + c] = rb[u];
     }
-    __syncthreads();
-    if (++pass == kFlushPasses) {
+    row_sync(wl);
+    if (act) {
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        BT rrow[PM];
+        load_row<BT, PM>(sRb + u * kNT + g * k + j * p, rrow, p);
+#pragma unroll
+        for (int a = 0; a < PM; ++a)
+          if (a < p) G::add(acc.s[a], acc.c[a], rrow[a], rb[u]);
+        G::add(ns, nc, rb[u], rb[u]);
+      }
+    }
+    row_sync(wl);
+    if (++pass == kFlushPasses / RPT) {
       pass = 0;
       if (slot) {
         acc.flush(slotRho, p);
@@ -403,38 +509,53 @@ template <typename T, int PM>
 __global__ void __launch_bounds__(kNT) k_update_p(T *__restrict__ P, const T *__restrict__ R, int64_t n, int k,
                                                   int p, int global, const double *__restrict__ beta,
                                                   const int *__restrict__ active, DevStatus *__restrict__ st) {
+  constexpr int RPT = rpt_stream<T>();
   if (st->flags != 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) st->cur += 1;   // no other kernel of this launch reads it
   extern __shared__ __align__(16) unsigned char smem[];
-  T *sP = reinterpret_cast<T *>(smem);
-  T *sB = sP + kNT;
+  T *sP = reinterpret_cast<T *>(smem);   // [RPT][kNT]
+  T *sB = sP + RPT * kNT;
   const int nblk = global ? 1 : k / p;
   for (int e = threadIdx.x; e < nblk * p * p; e += blockDim.x) sB[e] = (T)beta[e];
   const int rpp = kNT / k;
+  const bool wl = warp_local_rows(k, p);
   const int g = threadIdx.x / k, c = threadIdx.x - g * k;
   const bool slot = g < rpp;
   const int j = c / p, b = c - j * p;
   const bool act = slot && block_active(active, global, j);
-  const T *bj = sB + (global ? 0 : j) * p * p + b;
   __syncthreads();
-  const int64_t stride = (int64_t)gridDim.x * rpp;
-  for (int64_t row0 = (int64_t)blockIdx.x * rpp; row0 < n; row0 += stride) {
-    const int64_t r = row0 + g;
-    const bool live = act && r < n;
-    const int64_t o = r * k + c;
-    T pv = T(0), rv = T(0);
-    if (live) { pv = P[o]; rv = R[o]; }
-    if (slot) sP[g * k + c] = pv;
-    __syncthreads();
-    if (live) {
-      const T *prow = sP + g * k + j * p;
-      T s = rv;
+  T bcol[PM];   // column b of beta_j
+  {
+    const T *bj = sB + (global ? 0 : j) * p * p + b;
 #pragma unroll
-      for (int a = 0; a < PM; ++a)
-        if (a < p) s = fma_t(prow[a], bj[a * p], s);
-      P[o] = s;
+    for (int a = 0; a < PM; ++a) bcol[a] = (slot && a < p) ? bj[a * p] : T(0);
+  }
+  const int64_t span = (int64_t)rpp * RPT;
+  const int64_t stride = (int64_t)gridDim.x * span;
+  for (int64_t row0 = (int64_t)blockIdx.x * span; row0 < n; row0 += stride) {
+    T pv[RPT], rv[RPT];
+#pragma unroll
+    for (int u = 0; u < RPT; ++u) {
+      const int64_t r = row0 + u * rpp + g;
+      pv[u] = rv[u] = T(0);
+      if (act && r < n) { pv[u] = P[r * k + c]; rv[u] = R[r * k + c]; }
+      if (slot) sP[u * kNT + g * k + c] = pv[u];
     }
-    __syncthreads();
+    row_sync(wl);
+    if (act) {
+#pragma unroll
+      for (int u = 0; u < RPT; ++u) {
+        const int64_t r = row0 + u * rpp + g;
+        T prow[PM];
+        load_row<T, PM>(sP + u * kNT + g * k + j * p, prow, p);
+        T s = rv[u];
+#pragma unroll
+        for (int a = 0; a < PM; ++a)
+          if (a < p) s = fma_t(prow[a], bcol[a], s);
+        if (r < n) P[r * k + c] = s;
+      }
+    }
+    row_sync(wl);
   }
 }
 
@@ -480,6 +601,7 @@ __global__ void __launch_bounds__(kNT) k_bdot(const T *__restrict__ X, const T *
   BT *sX = reinterpret_cast<BT *>(smem);
   double *red = reinterpret_cast<double *>(smem + kNT * sizeof(double));
   const int rpp = kNT / k;
+  const bool wl = warp_local_rows(k, p);
   const int g = threadIdx.x / k, c = threadIdx.x - g * k;
   const bool slot = g < rpp;
   const int j = c / p;
@@ -495,14 +617,15 @@ __global__ void __launch_bounds__(kNT) k_bdot(const T *__restrict__ X, const T *
     BT xb = G::zero(), yb = G::zero();
     if (slot && r < n) { xb = G::conv(X[r * k + c]); yb = G::conv(Y[r * k + c]); }
     if (slot) sX[g * k + c] = xb;
-    __syncthreads();
+    row_sync(wl);
     if (slot) {
-      const BT *xrow = sX + g * k + j * p;
+      BT xrow[PM];
+      load_row<BT, PM>(sX + g * k + j * p, xrow, p);
 #pragma unroll
       for (int a = 0; a < PM; ++a)
         if (a < p) G::add(acc.s[a], acc.c[a], xrow[a], yb);
     }
-    __syncthreads();
+    row_sync(wl);
     if (++pass == kFlushPasses) {
       pass = 0;
       if (slot) acc.flush(sl, p);
