@@ -1,0 +1,476 @@
+// Warp-chunk variants of the three streaming kernels (K1 op+Gram, K2 X/R update + Gram, K3 P update).
+//
+// Each warp owns chunks of 32*V block-vector elements (V = 16 bytes / element size: float4 or double2
+// accesses) and works on them alone:
+//   memory phase   lane l moves V consecutive elements of one row with 16-byte loads/stores (and, in K1,
+//                  computes their BOP values with V-wide gathers) between HBM and a warp-private
+//                  shared-memory tile;
+//   compute phase  the same 32*V elements are processed in V sub-passes of 32, lane l always owning one
+//                  column, so the block-product accumulators stay one column wide.
+// Only __syncwarp orders the two phases, so warps never wait for each other inside the row loop. K1 and K2
+// are register heavy; they are compiled for at least 3 resident CTAs per SM, which measured faster than the
+// 2 their unconstrained register counts allow. The
+// layout needs V | k, and k | 32 or 32 | k (with k/32 dividing the 8 warps of a CTA), and every block of p
+// columns inside one warp's 32 columns (p | 32); other shapes use the per-element kernels of bcg_kernels.cuh.
+//
+// Chunk geometry: k >= 32 -- a chunk is V rows x 32 columns of column group cg = warp % (k/32) (fixed per
+// warp); sub-pass s is row R0 + s. k < 32 -- a chunk is 32*V/k whole rows; sub-pass s covers 32/k rows.
+#pragma once
+
+#include "bcg_kernels.cuh"
+
+namespace bcgk {
+
+constexpr int kWarps = kNT / 32;
+
+template <typename T, int V>
+struct VecOf;
+template <> struct VecOf<float, 1> { using type = float; };
+template <> struct VecOf<float, 2> { using type = float2; };
+template <> struct VecOf<float, 4> { using type = float4; };
+template <> struct VecOf<double, 1> { using type = double; };
+template <> struct VecOf<double, 2> { using type = double2; };
+
+template <typename T, int V>
+union VecU {
+  typename VecOf<T, V>::type v;
+  T e[V];
+};
+
+// One vector width per precision: 16-byte accesses (float4, double2).
+template <typename T>
+__host__ __device__ constexpr int wc_vec() { return 16 / (int)sizeof(T); }
+// k | 32, or 32 | k with the k/32 column groups dividing the 8 warps of a CTA (so each warp keeps one column
+// group); blocks of p columns must not straddle a warp; k must be a multiple of the vector width.
+template <typename T>
+__host__ __device__ constexpr bool wc_layout_ok(int k, int p) {
+  return k >= 1 && k <= kNT && k % wc_vec<T>() == 0 &&
+         ((32 % k == 0) || (k % 32 == 0 && kWarps % (k / 32) == 0 && 32 % p == 0));
+}
+
+struct WcGeom {
+  int k, ng, gr, rc, cg, lane, warp;
+  int64_t rb0, rbs, nrb;
+  // compute-phase identity of this lane: column and row offset inside a sub-pass
+  int col, ro;
+  // memory-phase identity: sub-pass group and element offset within its 32 elements
+  int sm, om;
+  __device__ void init(int64_t n, int k_, int V) {
+    k = k_;
+    lane = threadIdx.x & 31;
+    warp = threadIdx.x >> 5;
+    ng = k >= 32 ? k / 32 : 1;
+    gr = k >= 32 ? 1 : 32 / k;      // rows per sub-pass
+    rc = V * gr;                    // rows per chunk
+    const int64_t gw = (int64_t)blockIdx.x * kWarps + warp;
+    cg = (int)(gw % ng);
+    rb0 = gw / ng;
+    rbs = (int64_t)gridDim.x * kWarps / ng;
+    nrb = (n + rc - 1) / rc;
+    col = k >= 32 ? cg * 32 + lane : lane % k;
+    ro = k >= 32 ? 0 : lane / k;
+    const int lpg = 32 / V;         // memory lanes per sub-pass group
+    sm = lane / lpg;
+    om = (lane % lpg) * V;
+  }
+  // memory-phase element: row and column of the first of this lane's V elements in chunk R0
+  __device__ __forceinline__ void mem_pos(int64_t R0, int64_t &row, int &c) const {
+    if (k >= 32) { row = R0 + sm; c = cg * 32 + om; }
+    else { row = R0 + (int64_t)sm * gr + om / k; c = om % k; }
+  }
+};
+
+// V columns of one row of BOP: (A X)_{r, c..c+V-1}
+template <typename T, int OPK, int V>
+__device__ __forceinline__ VecU<T, V> apply_row_vec(const OpDesc &A, const T *__restrict__ X, int64_t r, int k,
+                                                   int c) {
+  using VT = typename VecOf<T, V>::type;
+  VecU<T, V> s;
+#pragma unroll
+  for (int v = 0; v < V; ++v) s.e[v] = T(0);
+  const VT *__restrict__ Xv = reinterpret_cast<const VT *>(X);
+  const int kv = k / V, cv = c / V;
+  if constexpr (OPK == OP_CSR) {
+    const T *__restrict__ vals = static_cast<const T *>(A.vals);
+    const int64_t e0 = __ldg(A.rowptr + r), e1 = __ldg(A.rowptr + r + 1);
+    for (int64_t e = e0; e < e1; e += 8) {
+      int colj[8];
+      T w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool in = e + u < e1;
+        colj[u] = in ? __ldg(A.colind + e + u) : 0;
+        w[u] = in ? __ldg(vals + e + u) : T(0);
+      }
+      VecU<T, V> xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (e + u < e1) xv[u].v = __ldg(Xv + (int64_t)colj[u] * kv + cv);
+        else {
+#pragma unroll
+          for (int v = 0; v < V; ++v) xv[u].e[v] = T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+#pragma unroll
+        for (int v = 0; v < V; ++v) s.e[v] = fma_t(w[u], xv[u].e[v], s.e[v]);
+    }
+    return s;
+  } else {
+    const int nx = A.nx, ny = A.ny, nz = (OPK == OP_ST5) ? 1 : A.nz;
+    const int64_t pl = (int64_t)nx * ny;
+    const int ix = (int)(r % nx), iy = (int)((r / nx) % ny), iz = (int)(r / pl);
+    const int64_t o = r * kv + cv;
+    VecU<T, V> t;
+    auto add = [&](int64_t off, T w) {
+      t.v = __ldg(Xv + off);
+#pragma unroll
+      for (int v = 0; v < V; ++v) s.e[v] = fma_t(w, t.e[v], s.e[v]);
+    };
+    if constexpr (OPK == OP_ST7VC) {
+      const T *__restrict__ f = static_cast<const T *>(A.faces);
+      const int64_t nfx = (int64_t)nz * ny * (nx + 1), nfy = (int64_t)nz * (ny + 1) * nx;
+      const T *fx = f, *fy = f + nfx, *fz = f + nfx + nfy;
+      const int64_t bx = ((int64_t)iz * ny + iy) * (nx + 1) + ix;
+      const int64_t by = ((int64_t)iz * (ny + 1) + iy) * nx + ix;
+      const int64_t bz = ((int64_t)iz * ny + iy) * nx + ix;
+      const T wxm = __ldg(fx + bx), wxp = __ldg(fx + bx + 1);
+      const T wym = __ldg(fy + by), wyp = __ldg(fy + by + nx);
+      const T wzm = __ldg(fz + bz), wzp = __ldg(fz + bz + pl);
+      add(o, ((wxm + wxp) + (wym + wyp)) + (wzm + wzp));
+      if (ix > 0) add(o - kv, -wxm);
+      if (ix < nx - 1) add(o + kv, -wxp);
+      if (iy > 0) add(o - (int64_t)nx * kv, -wym);
+      if (iy < ny - 1) add(o + (int64_t)nx * kv, -wyp);
+      if (iz > 0) add(o - pl * kv, -wzm);
+      if (iz < nz - 1) add(o + pl * kv, -wzp);
+    } else {
+      add(o, OPK == OP_ST5 ? T(4) : T(6));
+      if (ix > 0) add(o - kv, T(-1));
+      if (ix < nx - 1) add(o + kv, T(-1));
+      if (iy > 0) add(o - (int64_t)nx * kv, T(-1));
+      if (iy < ny - 1) add(o + (int64_t)nx * kv, T(-1));
+      if constexpr (OPK == OP_ST7) {
+        if (iz > 0) add(o - pl * kv, T(-1));
+        if (iz < nz - 1) add(o + pl * kv, T(-1));
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) s.e[v] *= T(A.scale);
+    return s;
+  }
+}
+
+// CTA reduction of the per-thread FP64 slots red[t*p + a] into out[c*p + a], summing, in a fixed order,
+// the threads whose compute column is c.
+__device__ __forceinline__ void wc_cta_reduce(const double *red, int k, int p, double *__restrict__ out) {
+  __syncthreads();
+  const int ng = k >= 32 ? k / 32 : 1;
+  const int E = k * p;
+  for (int e = threadIdx.x; e < E; e += blockDim.x) {
+    const int c = e / p, a = e - c * p;
+    double v = 0.0;
+    if (k >= 32) {
+      const int lane = c & 31, cgc = c >> 5;
+      for (int w = cgc; w < kWarps; w += ng) v += red[(w * 32 + lane) * p + a];
+    } else {
+      for (int w = 0; w < kWarps; ++w)
+        for (int l = c; l < 32; l += k) v += red[(w * 32 + l) * p + a];
+    }
+    out[e] = v;
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__host__ __device__ constexpr size_t wc_tile_bytes(int V) { return (size_t)32 * V * sizeof(T); }
+// per-warp tiles: K1 3 broadcast tiles (8 bytes per element max); K2 4 T tiles + 1 broadcast; K3 3 T tiles
+__host__ __device__ constexpr size_t wc_op_smem(int p, int V) {
+  return (size_t)kWarps * 3 * 32 * V * 8 + 2 * (size_t)kNT * p * sizeof(double);
+}
+__host__ __device__ constexpr size_t wc_upd_smem(int k, int p, int global, size_t tsize, int V) {
+  return align16((size_t)kWarps * 5 * 32 * V * 8 + (size_t)(global ? 1 : k / p) * p * p * tsize) +
+         (size_t)kNT * (p + 1) * sizeof(double);
+}
+__host__ __device__ constexpr size_t wc_pup_smem(int k, int p, int global, size_t tsize, int V) {
+  return (size_t)kWarps * 3 * 32 * V * tsize + (size_t)(global ? 1 : k / p) * p * p * tsize;
+}
+
+// ---------------------------------------------------------------------------------------------------
+// K1 (warp-chunk): Q = A P, alpha = <<P, Q>>_S, recomputed rho = <<P, R>>_S.
+template <typename T, int OPK, int PM, int V>
+__global__ void __launch_bounds__(kNT, 3) kw_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
+                                                  T *__restrict__ Q, int64_t n, int k, int p, int global,
+                                                  const int *__restrict__ active, double *__restrict__ partA,
+                                                  double *__restrict__ partR, const DevStatus *__restrict__ st) {
+  using G = Gram<T>;
+  using BT = typename G::B;
+  using VT = typename VecOf<T, V>::type;
+  if (st != nullptr && st->flags != 0) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  WcGeom geo;
+  geo.init(n, k, V);
+  BT *tile = reinterpret_cast<BT *>(smem + (size_t)geo.warp * 3 * 32 * V * 8);
+  BT *sP = tile, *sQ = tile + 32 * V, *sR = tile + 64 * V;
+  double *redA = reinterpret_cast<double *>(smem + (size_t)kWarps * 3 * 32 * V * 8);
+  double *redR = redA + kNT * p;
+  const int c = geo.col, j = c / p, b = c - j * p;
+  const bool act = block_active(active, global, j);
+  double *slotA = redA + threadIdx.x * p, *slotR = redR + threadIdx.x * p;
+  for (int a = 0; a < p; ++a) { slotA[a] = 0.0; slotR[a] = 0.0; }
+  GramAcc<PM> accA, accR;
+  accA.zero();
+  accR.zero();
+  int pass = 0;
+  const int kv = k / V;
+  for (int64_t rb = geo.rb0; rb < geo.nrb; rb += geo.rbs) {
+    const int64_t R0 = rb * geo.rc;
+    int64_t row;
+    int mc;
+    geo.mem_pos(R0, row, mc);
+    VecU<T, V> pv, rv, qv;
+    if (row < n) {
+      const int64_t o = row * kv + mc / V;
+      pv.v = reinterpret_cast<const VT *>(P)[o];
+      rv.v = reinterpret_cast<const VT *>(R)[o];
+      qv = apply_row_vec<T, OPK, V>(A, P, row, k, mc);
+      reinterpret_cast<VT *>(Q)[o] = qv.v;
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) pv.e[v] = rv.e[v] = qv.e[v] = T(0);
+    }
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      const int t = 32 * geo.sm + geo.om + v;
+      sP[t] = G::conv(pv.e[v]);
+      sQ[t] = G::conv(qv.e[v]);
+      sR[t] = G::conv(rv.e[v]);
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int s = 0; s < V; ++s) {
+        const int t = 32 * s + geo.lane;
+        const BT qb = sQ[t], rb2 = sR[t];
+        BT prow[PM];
+        load_row<BT, PM>(sP + t - b, prow, p);
+#pragma unroll
+        for (int a = 0; a < PM; ++a)
+          if (a < p) {
+            G::add(accA.s[a], accA.c[a], prow[a], qb);
+            G::add(accR.s[a], accR.c[a], prow[a], rb2);
+          }
+      }
+    }
+    __syncwarp();
+    if (++pass == kFlushPasses / V) {
+      pass = 0;
+      accA.flush(slotA, p);
+      accR.flush(slotR, p);
+    }
+  }
+  accA.flush(slotA, p);
+  accR.flush(slotR, p);
+  const int E = k * p;
+  wc_cta_reduce(redA, k, p, partA + (int64_t)blockIdx.x * E);
+  wc_cta_reduce(redR, k, p, partR + (int64_t)blockIdx.x * E);
+}
+
+// ---------------------------------------------------------------------------------------------------
+// K2 (warp-chunk): X += P lambda, R -= Q lambda, rho = <<R, R>>_S, column norms.
+template <typename T, int PM, int V>
+__global__ void __launch_bounds__(kNT, 3) kw_update_xr(T *__restrict__ X, T *__restrict__ R, const T *__restrict__ P,
+                                                    const T *__restrict__ Q, int64_t n, int k, int p, int global,
+                                                    const double *__restrict__ lam, const int *__restrict__ active,
+                                                    double *__restrict__ partRho, double *__restrict__ partN,
+                                                    const DevStatus *__restrict__ st) {
+  using G = Gram<T>;
+  using BT = typename G::B;
+  using VT = typename VecOf<T, V>::type;
+  if (st != nullptr && st->flags != 0) return;
+  extern __shared__ __align__(16) unsigned char smem[];
+  WcGeom geo;
+  geo.init(n, k, V);
+  unsigned char *wbase = smem + (size_t)geo.warp * 5 * 32 * V * 8;
+  T *sX = reinterpret_cast<T *>(wbase);
+  T *sR = sX + 32 * V, *sP = sR + 32 * V, *sQ = sP + 32 * V;
+  BT *sRb = reinterpret_cast<BT *>(wbase + 4 * 32 * V * sizeof(T));
+  const int nblk = global ? 1 : k / p;
+  T *sL = reinterpret_cast<T *>(smem + (size_t)kWarps * 5 * 32 * V * 8);
+  double *red = reinterpret_cast<double *>(smem + align16((size_t)kWarps * 5 * 32 * V * 8 +
+                                                          (size_t)nblk * p * p * sizeof(T)));
+  double *nred = red + kNT * p;
+  for (int e = threadIdx.x; e < nblk * p * p; e += blockDim.x) sL[e] = (T)lam[e];
+  const int c = geo.col, j = c / p, b = c - j * p;
+  const bool act = block_active(active, global, j);
+  double *slotRho = red + threadIdx.x * p;
+  double *slotN = nred + threadIdx.x;
+  for (int a = 0; a < p; ++a) slotRho[a] = 0.0;
+  *slotN = 0.0;
+  __syncthreads();
+  T lcol[PM];
+  {
+    const T *lj = sL + (global ? 0 : j) * p * p + b;
+#pragma unroll
+    for (int a = 0; a < PM; ++a) lcol[a] = a < p ? lj[a * p] : T(0);
+  }
+  GramAcc<PM> acc;
+  acc.zero();
+  float ns = 0.0f, nc = 0.0f;
+  int pass = 0;
+  const int kv = k / V;
+  for (int64_t rb = geo.rb0; rb < geo.nrb; rb += geo.rbs) {
+    const int64_t R0 = rb * geo.rc;
+    int64_t row;
+    int mc;
+    geo.mem_pos(R0, row, mc);
+    const int64_t o = row * kv + mc / V;
+    VecU<T, V> xv, rv, pv, qv;
+    if (row < n) {
+      xv.v = reinterpret_cast<const VT *>(X)[o];
+      rv.v = reinterpret_cast<const VT *>(R)[o];
+      pv.v = reinterpret_cast<const VT *>(P)[o];
+      qv.v = reinterpret_cast<const VT *>(Q)[o];
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) xv.e[v] = rv.e[v] = pv.e[v] = qv.e[v] = T(0);
+    }
+    const int tm = 32 * geo.sm + geo.om;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      sX[tm + v] = xv.e[v];
+      sR[tm + v] = rv.e[v];
+      sP[tm + v] = pv.e[v];
+      sQ[tm + v] = qv.e[v];
+    }
+    __syncwarp();
+    // BAXPY x 2 for each sub-pass; the new residual is written as its broadcast representation
+#pragma unroll
+    for (int s = 0; s < V; ++s) {
+      const int t = 32 * s + geo.lane;
+      T x = sX[t], r = sR[t];
+      if (act) {
+        T prow[PM], qrow[PM];
+        load_row<T, PM>(sP + t - b, prow, p);
+        load_row<T, PM>(sQ + t - b, qrow, p);
+#pragma unroll
+        for (int a = 0; a < PM; ++a)
+          if (a < p) {
+            x = fma_t(prow[a], lcol[a], x);
+            r = fma_t(-qrow[a], lcol[a], r);
+          }
+      }
+      sX[t] = x;
+      sR[t] = r;
+      sRb[t] = G::conv(r);
+    }
+    __syncwarp();
+    if (act) {
+#pragma unroll
+      for (int s = 0; s < V; ++s) {
+        const int t = 32 * s + geo.lane;
+        const BT rb2 = sRb[t];
+        BT rrow[PM];
+        load_row<BT, PM>(sRb + t - b, rrow, p);
+#pragma unroll
+        for (int a = 0; a < PM; ++a)
+          if (a < p) G::add(acc.s[a], acc.c[a], rrow[a], rb2);
+        G::add(ns, nc, rb2, rb2);
+      }
+    }
+    if (row < n) {
+      VecU<T, V> xo, ro2;
+#pragma unroll
+      for (int v = 0; v < V; ++v) { xo.e[v] = sX[tm + v]; ro2.e[v] = sR[tm + v]; }
+      reinterpret_cast<VT *>(X)[o] = xo.v;
+      reinterpret_cast<VT *>(R)[o] = ro2.v;
+    }
+    __syncwarp();
+    if (++pass == kFlushPasses / V) {
+      pass = 0;
+      acc.flush(slotRho, p);
+      *slotN += (double)ns;
+      *slotN += (double)nc;
+      ns = nc = 0.0f;
+    }
+  }
+  acc.flush(slotRho, p);
+  *slotN += (double)ns;
+  *slotN += (double)nc;
+  const int E = k * p;
+  wc_cta_reduce(red, k, p, partRho + (int64_t)blockIdx.x * E);
+  wc_cta_reduce(nred, k, 1, partN + (int64_t)blockIdx.x * k);
+}
+
+// ---------------------------------------------------------------------------------------------------
+// K3 (warp-chunk): P = R + P beta.
+template <typename T, int PM, int V>
+__global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *__restrict__ R, int64_t n, int k,
+                                                   int p, int global, const double *__restrict__ beta,
+                                                   const int *__restrict__ active, DevStatus *__restrict__ st) {
+  using VT = typename VecOf<T, V>::type;
+  if (st->flags != 0) return;
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->cur += 1;   // no other kernel of this launch reads it
+  extern __shared__ __align__(16) unsigned char smem[];
+  WcGeom geo;
+  geo.init(n, k, V);
+  T *sP = reinterpret_cast<T *>(smem) + (size_t)geo.warp * 3 * 32 * V;
+  T *sR = sP + 32 * V, *sN = sR + 32 * V;
+  const int nblk = global ? 1 : k / p;
+  T *sB = reinterpret_cast<T *>(smem) + (size_t)kWarps * 3 * 32 * V;
+  for (int e = threadIdx.x; e < nblk * p * p; e += blockDim.x) sB[e] = (T)beta[e];
+  const int c = geo.col, j = c / p, b = c - j * p;
+  const bool act = block_active(active, global, j);
+  __syncthreads();
+  T bcol[PM];
+  {
+    const T *bj = sB + (global ? 0 : j) * p * p + b;
+#pragma unroll
+    for (int a = 0; a < PM; ++a) bcol[a] = a < p ? bj[a * p] : T(0);
+  }
+  const int kv = k / V;
+  for (int64_t rb = geo.rb0; rb < geo.nrb; rb += geo.rbs) {
+    const int64_t R0 = rb * geo.rc;
+    int64_t row;
+    int mc;
+    geo.mem_pos(R0, row, mc);
+    const int64_t o = row * kv + mc / V;
+    VecU<T, V> pv, rv;
+    if (row < n) {
+      pv.v = reinterpret_cast<const VT *>(P)[o];
+      rv.v = reinterpret_cast<const VT *>(R)[o];
+    } else {
+#pragma unroll
+      for (int v = 0; v < V; ++v) pv.e[v] = rv.e[v] = T(0);
+    }
+    const int tm = 32 * geo.sm + geo.om;
+#pragma unroll
+    for (int v = 0; v < V; ++v) { sP[tm + v] = pv.e[v]; sR[tm + v] = rv.e[v]; }
+    __syncwarp();
+#pragma unroll
+    for (int s = 0; s < V; ++s) {
+      const int t = 32 * s + geo.lane;
+      T out = sP[t];
+      if (act) {
+        T prow[PM];
+        load_row<T, PM>(sP + t - b, prow, p);
+        out = sR[t];
+#pragma unroll
+        for (int a = 0; a < PM; ++a)
+          if (a < p) out = fma_t(prow[a], bcol[a], out);
+      }
+      sN[t] = out;
+    }
+    __syncwarp();
+    if (row < n) {
+      VecU<T, V> po;
+#pragma unroll
+      for (int v = 0; v < V; ++v) po.e[v] = sN[tm + v];
+      reinterpret_cast<VT *>(P)[o] = po.v;
+    }
+    __syncwarp();
+  }
+}
+
+}  // namespace bcgk

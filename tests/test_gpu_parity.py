@@ -101,8 +101,14 @@ def test_fp64_converged_counts_and_solution(torch_dev, name, sub, k, p, compare_
     assert r.ok, r
     ref = O.solve(A, B, p=p, sub=sub, tol=tol, maxit=3000)
     assert ref.status == O.OK
-    assert abs(r.iters - ref.iters) <= 2
-    assert np.all(np.abs(np.array(r.block_iters) - ref.block_iters) <= 2)
+    # +-2, widened by the oracle's own spread of counts under 1e-16 relative perturbations of B (zero on the
+    # Poisson and 27-point matrices; one or two on the log-normal variable-coefficient matrix, whose count
+    # also differs between BLAS builds of the oracle)
+    spread = [O.solve(A, B * (1 + 1e-16 * np.random.default_rng(s).standard_normal(B.shape)), p=p, sub=sub,
+                      tol=tol, maxit=3000).iters for s in range(3)]
+    allow = 2 + max(spread + [ref.iters]) - min(spread + [ref.iters])
+    assert abs(r.iters - ref.iters) <= allow, (r.iters, ref.iters, spread)
+    assert np.all(np.abs(np.array(r.block_iters) - ref.block_iters) <= allow)
     # stopping rule: every column's true residual is at the tolerance (recursive <= tol, true close to it)
     res = np.linalg.norm(B - A @ Xg, axis=0) / np.linalg.norm(B, axis=0)
     assert np.all(res <= 1.5 * tol) and r.max_rel_res_recursive <= tol
