@@ -32,7 +32,7 @@ WORKLOAD = dict(name="poisson3d_128_csr_k32_hybrid_p8_fp64", grid=128, k=32, p=8
 # Iterations the 128^3 / k = 32 / hybrid p = 8 FP64 solve takes to reach 1e-8 (measured on the GPU; the oracle
 # agrees within +-2 on every size it can finish). Used only to extrapolate the oracle's per-iteration time
 # to a time-to-tolerance in the reference arm.
-REF_ITERS = None
+REF_ITERS = 354
 ORACLE_SAMPLE_ITERS = 3
 # DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/k_op_gram_poisson3d_96_*.md,
 # scaled by rows to 128^3), valid only for the kernel source it was taken on (sha256 prefix of the
@@ -50,12 +50,15 @@ def peaks():
 
 
 def kernel_model(n, k, p, z, s, a_bytes):
-    """Algorithmic flops and bytes per launch of each iteration kernel (the paper's Table 1 per kernel,
-    fused as the kernels fuse them): K1 = BOP + 2 BDOT, K2 = 2 BAXPY + BDOT + column norms, K3 = BAXPY."""
+    """Algorithmic flops and bytes per launch of each iteration kernel (the paper's Table 1 omega and beta per
+    kernel, fused as the kernels fuse them): K1 = BOP + 2 BDOT, K2 = 2 BAXPY + BDOT + column norms,
+    K3 = BAXPY. `alu` is the part executed as native arithmetic of the block vectors' precision (BOP and
+    BAXPY: FP64 FMAs in the FP64 form, FP32 FMAs in the mixed form); `gram` is the block-product part,
+    which runs as error-free (Dot2) FP32 arithmetic with FP64-class accuracy in both forms."""
     return {
-        "op_gram": dict(flops=2.0 * k * z + 4.0 * n * p * k, bytes=a_bytes + 3.0 * n * k * s),
-        "update_xr": dict(flops=6.0 * n * p * k + 2.0 * n * k, bytes=6.0 * n * k * s),
-        "update_p": dict(flops=2.0 * n * p * k, bytes=3.0 * n * k * s),
+        "op_gram": dict(alu=2.0 * k * z, gram=4.0 * n * p * k, bytes=a_bytes + 3.0 * n * k * s),
+        "update_xr": dict(alu=4.0 * n * p * k, gram=2.0 * n * p * k + 2.0 * n * k, bytes=6.0 * n * k * s),
+        "update_p": dict(alu=2.0 * n * p * k, gram=0.0, bytes=3.0 * n * k * s),
     }
 
 
@@ -155,6 +158,109 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ---------------------------------------------------------------------------------------------------------------
+# Other workloads (not the default line): measured with `python bench.py --workload NAME`
+EXTRA_WORKLOADS = ("poisson2d_64_k8", "varcoef3d_160_k64_mixed", "stencil27_100_k16_autograd", "poisson3d_96_sweep")
+
+
+def time_solve(bcg, torch, M, B, *, k, p, sub, prec, form="csr", tol=1e-8, reps=2, dev=None, opts=None):
+    """Warm-up solve, then the mean of `reps` timed solves from X0 = 0 (CUDA events on the solver's stream)."""
+    S = bcg.Solver.from_matrix(M, k=k, p=p, sub=sub, prec=prec, form=form, device=dev)
+    for key, v in (opts or {}).items():
+        S.set_option(key, v)
+    X = torch.zeros_like(B)
+    S.solve(B, X, tol=tol, maxit=20000)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(S.stream)
+    for _ in range(reps):
+        with torch.cuda.stream(S.stream):
+            X.zero_()
+        X, r = S.solve(B, X, tol=tol, maxit=20000)
+    e1.record(S.stream)
+    torch.cuda.synchronize()
+    S.close()
+    return e0.elapsed_time(e1) / reps / 1e3, r, X
+
+
+def run_extra(name, args):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1912_11930_gb300 import bcg, workloads as W
+    dev = torch.device("cuda", 0)
+    base = {"metric": METRIC, "unit": "s", "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "data": "synthetic"}
+    out = dict(base)
+    if name == "poisson2d_64_k8":
+        M = W.poisson2d(64)
+        B = torch.from_numpy(W.rhs(M.n, 8, seed=0)).to(dev)
+        rows = []
+        for sub, p in (("hybrid", 4), ("global", 4), ("parallel", 1), ("classical", 8), ("hybrid", 1)):
+            t, r, _ = time_solve(bcg, torch, M, B, k=8, p=p, sub=sub, prec="fp64", reps=args.steps, dev=dev)
+            rows.append(dict(sub=sub, p=p, s=t, iterations=r.iters, status=bcg.STATUS_NAMES[r.status],
+                             max_rel_res_true=r.max_rel_res_true))
+        out.update(value=rows[0]["s"], dtype="f64", config={"workload": "poisson2d_64_csr_k8", "n": M.n, "k": 8},
+                   results=rows)
+    elif name == "varcoef3d_160_k64_mixed":
+        M = W.varcoef3d(160, seed=0)
+        k = 64
+        B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev)
+        rows = []
+        for prec, tol in (("fp32_refine", 1e-10), ("fp32_refine", 1e-8), ("fp64", 1e-8)):
+            t, r, _ = time_solve(bcg, torch, M, B, k=k, p=16, sub="hybrid", prec=prec, form="stencil", tol=tol,
+                                 reps=1, dev=dev)
+            rows.append(dict(prec=prec, tol=tol, s=t, iterations=r.iters, outer=r.outer_iters,
+                             status=bcg.STATUS_NAMES[r.status], max_rel_res_true=r.max_rel_res_true))
+        out.update(value=rows[0]["s"], dtype="f32 inner, f64 refinement",
+                   config={"workload": "varcoef3d_160_stencil_k64_hybrid_p16", "n": M.n, "k": k, "p": 16},
+                   results=rows, mixed_vs_fp64_speedup_at_1e8=rows[2]["s"] / rows[1]["s"])
+    elif name == "stencil27_100_k16_autograd":
+        from paper_1912_11930_gb300.autograd import bcg_solve_autograd
+        M = W.stencil27(100, seed=0)
+        k = 16
+        vals = torch.from_numpy(M.vals.copy()).to(dev).requires_grad_(True)
+        csr = (torch.from_numpy(M.rowptr).to(dev), torch.from_numpy(M.colind).to(dev), vals)
+        S = bcg.Solver(k=k, p=16, sub="hybrid", csr=csr, device=dev)
+        B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev).requires_grad_(True)
+        Wt = torch.from_numpy(W.loss_weights(M.n, k, seed=0)).to(dev)
+        times = []
+        for rep in range(1 + args.steps):
+            vals.grad = None
+            B.grad = None
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            X = bcg_solve_autograd(vals, B, S, tol=1e-8)
+            loss = (Wt * X).sum()
+            loss.backward()
+            torch.cuda.synchronize()
+            if rep:
+                times.append(time.perf_counter() - t0)
+        S.close()
+        out.update(value=sum(times) / len(times), dtype="f64",
+                   config={"workload": "stencil27_100_csr_k16_hybrid_p16_forward_backward", "n": M.n, "k": k,
+                           "nnz": M.nnz}, note="one forward solve + adjoint solve + gradient kernel, tol 1e-8")
+    elif name == "poisson3d_96_sweep":
+        M = W.poisson3d(96)
+        rows = []
+        for k in (1, 8, 32, 128, 256):
+            B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev)
+            for p in sorted({1, max(1, k // 8), k}):
+                for prec in ("fp64", "fp32_refine"):
+                    sub = "hybrid"
+                    t, r, _ = time_solve(bcg, torch, M, B, k=k, p=p, sub=sub, prec=prec, reps=1, dev=dev)
+                    rows.append(dict(k=k, p=p, prec=prec, s=t, iterations=r.iters, outer=r.outer_iters,
+                                     status=bcg.STATUS_NAMES[r.status], max_rel_res_true=r.max_rel_res_true,
+                                     s_per_rhs=t / k))
+                    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            del B
+        out.update(value=next(x["s"] for x in rows if x["k"] == 32 and x["p"] == 4 and x["prec"] == "fp64"),
+                   dtype="f64 and f32 inner/f64 refinement", config={"workload": "poisson3d_96_csr_sweep",
+                                                                     "n": M.n}, results=rows)
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -167,6 +273,8 @@ def main():
                     help="Poisson grid edge (smaller grids only for profiling captures)")
     ap.add_argument("--prec", default=WORKLOAD["prec"], choices=["fp64", "fp32_refine"],
                     help="precision of the timed solve (profiling captures of the mixed form)")
+    ap.add_argument("--workload", default=None, choices=EXTRA_WORKLOADS,
+                    help="measure one of the other workloads instead of the default line")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -176,6 +284,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload:
+        return run_extra(args.workload, args)
 
     import numpy as np
     import torch
@@ -252,16 +362,20 @@ def main():
             entry = {"avg_ms": tot / cnt, "launches": cnt, "share": None}
             if name in model:
                 mdl = model[name]
-                entry["alg_gflop"] = mdl["flops"] / 1e9
+                sec = tot / cnt * 1e-3
+                entry["alg_gflop_fp64_pipe"] = mdl["alu"] / 1e9
+                entry["alg_gflop_gram_dot2"] = mdl["gram"] / 1e9
                 entry["alg_gb"] = mdl["bytes"] / 1e9
-                entry["tflops"] = mdl["flops"] / (tot / cnt * 1e-3) / 1e12
-                entry["gbs"] = mdl["bytes"] / (tot / cnt * 1e-3) / 1e9
+                entry["fp64_tflops"] = mdl["alu"] / sec / 1e12
+                entry["gbs"] = mdl["bytes"] / sec / 1e9
             per_kernel[name] = entry
     total_ms = sum(v["avg_ms"] * v["launches"] for v in per_kernel.values())
     for v in per_kernel.values():
         v["share"] = v["avg_ms"] * v["launches"] / total_ms if total_ms else None
     dom = max((nm for nm in per_kernel if nm in model), key=lambda nm: per_kernel[nm]["share"])
     d = per_kernel[dom]
+    # FP64-pipe roofline of the dominant kernel: only the algorithmic flops that run as FP64 FMAs count
+    # (the block products run as error-free FP32 arithmetic and are reported beside it)
     traffic = None
     import hashlib
     src = os.path.join(ROOT, "paper_1912_11930_gb300", "csrc", "bcg_kernels.cuh")
@@ -271,8 +385,10 @@ def main():
     ent = TRAFFIC.get((dom, w["name"]))
     if ent and ent[0] == cur_sha:
         traffic = ent[1]
-    roofline = {"bound": "alu", "kernel": dom, "achieved": d["tflops"], "peak": NOMINAL_FP64_TFLOPS,
-                "unit": "TFLOP/s", "frac": d["tflops"] / NOMINAL_FP64_TFLOPS, "traffic": traffic,
+    roofline = {"bound": "alu", "kernel": dom, "achieved": d["fp64_tflops"], "peak": NOMINAL_FP64_TFLOPS,
+                "unit": "TFLOP/s", "frac": d["fp64_tflops"] / NOMINAL_FP64_TFLOPS, "traffic": traffic,
+                "counted": "algorithmic FP64-FMA flops of the kernel (BOP / BAXPY); its block products run as "
+                           "error-free FP32 arithmetic and are listed under kernels.*.alg_gflop_gram_dot2",
                 "peak_source": "nominal FP64 (GB300 FP64 vector and tensor rate; the P0 DFMA probe measured 1.19)",
                 "hbm_achieved_gbs": d["gbs"], "hbm_peak_gbs": hbm_peak, "hbm_frac": d["gbs"] / hbm_peak,
                 "hbm_peak_source": hbm_src}

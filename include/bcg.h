@@ -84,8 +84,9 @@ typedef struct {
  *   rowptr        device int64[n+1], rowptr[0] = 0, rowptr[n] = nnz
  *   colind        device int32[nnz], column of each entry, 0 <= colind < n
  *   vals          device double[nnz]; A must be symmetric positive definite
- *   k, p, sub     number of right-hand sides (1..256), block size (p divides k, p <= 32 in this
- *                 version), subalgebra (bcg_subalgebra)
+ *   k, p, sub     number of right-hand sides (1..256), block size (p divides k; p <= 32, or a
+ *                 multiple of 32 up to 256 -- wide blocks use tiled block products and updates),
+ *                 subalgebra (bcg_subalgebra)
  *   prec          bcg_precision
  *   cuda_stream   cudaStream_t to order all work on (NULL = legacy default stream)
  * Returns INVALID_ARG for bad sizes/pointers/enums, OOM if the workspace (about 4 n k scalars plus

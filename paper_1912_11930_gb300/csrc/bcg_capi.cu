@@ -99,6 +99,7 @@ struct bcg_ctx {
   double *lam = nullptr, *beta = nullptr, *rho_rec = nullptr;
   double *r0n2 = nullptr, *rn2 = nullptr, *rtn2 = nullptr, *outer0 = nullptr;
   int *active = nullptr, *block_iters = nullptr;
+  double *gws = nullptr;               // global workspace of the p x p solves when p is large
   int32_t *rowidx = nullptr;           // CSR row of each entry (gradient)
   DevStatus *st = nullptr;
   DevStatus *h_st = nullptr;           // pinned
@@ -145,7 +146,8 @@ bcg_status validate_common(int32_t k, int32_t *p, int32_t sub, int32_t prec, int
     default: return fail(BCG_ERR_INVALID_ARG, "unknown subalgebra %d", sub);
   }
   if (*p < 1 || k % *p != 0) return fail(BCG_ERR_INVALID_ARG, "p=%d must divide k=%d", *p, k);
-  if (*p > kMaxP) return fail(BCG_ERR_INVALID_ARG, "p=%d > %d is not supported by this build", *p, kMaxP);
+  if (*p > kMaxP && (*p % 32 != 0 || *p > kNT))
+    return fail(BCG_ERR_INVALID_ARG, "p=%d: blocks wider than %d must be a multiple of 32 (and <= %d)", *p, kMaxP, kNT);
   if (prec != BCG_FP64 && prec != BCG_FP32_REFINE) return fail(BCG_ERR_INVALID_ARG, "unknown precision %d", prec);
   return BCG_OK;
 }
@@ -190,6 +192,7 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CKS(h->alloc(&h->outer0, h->k));
   CKS(h->alloc(&h->active, h->nblk));
   CKS(h->alloc(&h->block_iters, h->nblk));
+  if (small_needs_gws(h->p)) CKS(h->alloc(&h->gws, (size_t)h->nblk * small_ws_doubles(h->p)));
   CKS(h->alloc(&h->st, 1));
   CK(cudaMallocHost(&h->h_st, sizeof(DevStatus)));
   CK(cudaMallocHost(&h->h_vec, 3 * sizeof(double) * h->k));
@@ -224,17 +227,40 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
   REC(0);
   CK(launch_op_gram<T>(A, P, R, Q, h->n, h->k, h->p, h->global, h->active, h->partA, h->partR, h->st, g.op, s));
   REC(1); REC(2);
-  CK(launch_solve_lambda(h->partA, h->partR, g.op, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st, s));
+  CK(launch_solve_lambda(h->partA, h->partR, g.op, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
+                         h->gws, s));
   REC(3); REC(4);
   CK(launch_update_xr<T>(X, R, P, Q, h->n, h->k, h->p, h->global, h->lam, h->active, h->partRho, h->partN, h->st,
                          g.upd, s));
   REC(5); REC(6);
   CK(launch_solve_beta(h->partRho, h->partN, g.upd, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
-                       h->block_iters, h->rho_rec, h->beta, h->st, s));
+                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, s));
   REC(7); REC(8);
   CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, g.pup, s));
   REC(9);
 #undef REC
+  return BCG_OK;
+}
+
+// One iteration with large blocks (p > 32): tiled products. The direction update cannot run in place across
+// column tiles, so it writes into the Q buffer (free at that point) and the caller swaps P and Q.
+template <typename T>
+bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g,
+                               double tol2) {
+  cudaStream_t s = h->stream;
+  const int ch = g.op;
+  CK(launch_lp_bop<T>(A, P, Q, h->n, h->k, h->st, h->nsm, s));
+  CK(launch_lp_gram<T>(P, Q, h->n, h->k, h->p, h->global, h->active, h->partA, ch, h->st, s));
+  CK(launch_lp_gram<T>(P, R, h->n, h->k, h->p, h->global, h->active, h->partR, ch, h->st, s));
+  CK(launch_solve_lambda(h->partA, h->partR, ch, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
+                         h->gws, s));
+  CK(launch_lp_baxpy<T>(X, X, P, h->lam, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 0, s));
+  CK(launch_lp_baxpy<T>(R, R, Q, h->lam, h->n, h->k, h->p, h->global, -1.0, h->active, h->st, 0, s));
+  CK(launch_lp_gram<T>(R, R, h->n, h->k, h->p, h->global, h->active, h->partRho, ch, h->st, s));
+  CK(launch_lp_colnorm<T>(R, h->n, h->k, h->partN, ch, h->st, s));
+  CK(launch_solve_beta(h->partRho, h->partN, ch, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
+                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, s));
+  CK(launch_lp_baxpy<T>(Q, R, P, h->beta, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 1, s));
   return BCG_OK;
 }
 
@@ -274,6 +300,18 @@ bcg_status run_iterations(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, c
   CKS(read_status(h));
   int launched = 0;
   const int batch = h->check_every;
+  if (h->p > kMaxP) {   // large blocks: plain launches, P and Q swap every iteration
+    while (h->h_st->flags == 0 && launched < maxit) {
+      const int nb = std::min(batch, maxit - launched);
+      for (int i = 0; i < nb; ++i) {
+        CKS(launch_iteration_lp<T>(h, A, X, R, P, Q, g, tol2));
+        std::swap(P, Q);
+      }
+      launched += nb;
+      CKS(read_status(h));
+    }
+    return BCG_OK;
+  }
   struct Guard {   // a graph built for this call only is destroyed on every exit path
     cudaGraphExec_t exec = nullptr;
     bool own = false;
@@ -624,9 +662,14 @@ bcg_status bcg_bdot(bcg_handle h, const double *X, const double *Y, double *gamm
   if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
   if (!is_device_ptr(X) || !is_device_ptr(Y) || !is_device_ptr(gamma))
     return fail(BCG_ERR_INVALID_ARG, "X, Y and gamma must be device pointers");
-  const int grid = std::min(h->nparts, bdot_grid<double>(h->n, h->k, h->p, h->nsm));
-  CK(launch_bdot<double>(X, Y, h->n, h->k, h->p, h->partA, grid, h->stream));
-  CK(launch_finish_gram(h->partA, grid, h->k, h->p, h->global, gamma, h->stream));
+  if (h->p > kMaxP) {
+    CK(launch_lp_gram<double>(X, Y, h->n, h->k, h->p, h->global, nullptr, h->partA, h->g64.op, nullptr, h->stream));
+    CK(launch_finish_gram(h->partA, h->g64.op, h->k, h->p, h->global, gamma, h->gws, h->stream));
+  } else {
+    const int grid = std::min(h->nparts, bdot_grid<double>(h->n, h->k, h->p, h->nsm));
+    CK(launch_bdot<double>(X, Y, h->n, h->k, h->p, h->partA, grid, h->stream));
+    CK(launch_finish_gram(h->partA, grid, h->k, h->p, h->global, gamma, h->gws, h->stream));
+  }
   CK(cudaStreamSynchronize(h->stream));
   return BCG_OK;
 }
@@ -635,9 +678,14 @@ bcg_status bcg_bdot_f32(bcg_handle h, const float *X, const float *Y, double *ga
   if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
   if (!is_device_ptr(X) || !is_device_ptr(Y) || !is_device_ptr(gamma))
     return fail(BCG_ERR_INVALID_ARG, "X, Y and gamma must be device pointers");
-  const int grid = std::min(h->nparts, bdot_grid<float>(h->n, h->k, h->p, h->nsm));
-  CK(launch_bdot<float>(X, Y, h->n, h->k, h->p, h->partA, grid, h->stream));
-  CK(launch_finish_gram(h->partA, grid, h->k, h->p, h->global, gamma, h->stream));
+  if (h->p > kMaxP) {
+    CK(launch_lp_gram<float>(X, Y, h->n, h->k, h->p, h->global, nullptr, h->partA, h->g64.op, nullptr, h->stream));
+    CK(launch_finish_gram(h->partA, h->g64.op, h->k, h->p, h->global, gamma, h->gws, h->stream));
+  } else {
+    const int grid = std::min(h->nparts, bdot_grid<float>(h->n, h->k, h->p, h->nsm));
+    CK(launch_bdot<float>(X, Y, h->n, h->k, h->p, h->partA, grid, h->stream));
+    CK(launch_finish_gram(h->partA, grid, h->k, h->p, h->global, gamma, h->gws, h->stream));
+  }
   CK(cudaStreamSynchronize(h->stream));
   return BCG_OK;
 }

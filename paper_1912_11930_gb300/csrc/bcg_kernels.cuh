@@ -93,8 +93,16 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float p, float e
   c = __fadd_rn(c, __fadd_rn(err, e));
 }
 
-// x = hi + lo with hi = x truncated to 24 significant bits, lo = the remaining 29 bits rounded to 24: the
-// bits are moved with integer operations (no FP64 instruction) whenever both halves are normal floats.
+// Tiny, huge or non-finite values: plain conversions. Kept out of line so that the compiler cannot if-convert
+// this branch into every call (its FP64 instructions would then run for every element on the narrow pipe).
+static __device__ __noinline__ float2 split_f64_rare(double x) {
+  const float hi = (float)x;
+  return make_float2(hi, isfinite(x) ? (float)(x - (double)hi) : 0.0f);
+}
+
+// x = hi + lo with hi = x truncated to 24 significant bits and lo = the remaining 29 bits truncated to 24.
+// Both halves are assembled from the bit pattern with integer operations only (no FP64 or conversion
+// instruction: on GB300 those share the narrow FP64 pipe) whenever both are normal floats.
 __device__ __forceinline__ float2 split_f64(double x) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const unsigned hi32 = (unsigned)(u >> 32);
@@ -102,12 +110,15 @@ __device__ __forceinline__ float2 split_f64(double x) {
   if (e >= 949 && e <= 1150) {
     const unsigned sign = hi32 & 0x80000000u;
     const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((u >> 29) & 0x7FFFFFu));
-    const float scale = __uint_as_float((unsigned)(e - 948) << 23);              // 2^(e - 1075)
-    const float lo = __fmul_rn(__uint2float_rn((unsigned)(u & 0x1FFFFFFFu)), scale);
-    return make_float2(hi, sign ? -lo : lo);
+    // low part: rem * 2^(e - 1075) with rem < 2^29; normalise rem by its leading one
+    const unsigned rem = (unsigned)(u & 0x1FFFFFFFu);
+    const int msb = 31 - __clz(rem);                       // 0..28 (meaningless if rem == 0)
+    const unsigned mant = msb >= 23 ? rem >> (msb - 23) : rem << (23 - msb);
+    const unsigned lob = sign | ((unsigned)(msb + e - 948) << 23) | (mant & 0x7FFFFFu);
+    return make_float2(hi, rem ? __uint_as_float(lob) : 0.0f);
   }
-  const float hi = (float)x;   // zero, tiny, huge or non-finite: plain conversions
-  return make_float2(hi, isfinite(x) ? (float)(x - (double)hi) : 0.0f);
+  if ((u << 1) == 0ull) return make_float2(__uint_as_float(hi32 & 0x80000000u), 0.0f);   // +-0
+  return split_f64_rare(x);
 }
 
 template <typename T>
@@ -210,7 +221,8 @@ __device__ __forceinline__ T apply_row(const OpDesc &A, const T *__restrict__ X,
 #pragma unroll
       for (int u = 0; u < 8; ++u) xv[u] = (e + u < e1) ? __ldg(X + (int64_t)col[u] * k + c) : T(0);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s = fma_t(w[u], xv[u], s);
+      for (int u = 0; u < 8; ++u)
+        if (e + u < e1) s = fma_t(w[u], xv[u], s);
     }
     return s;
   } else if constexpr (OPK == OP_ST5) {

@@ -8,8 +8,8 @@
 //   compute phase  the same 32*V elements are processed in V sub-passes of 32, lane l always owning one
 //                  column, so the block-product accumulators stay one column wide.
 // Only __syncwarp orders the two phases, so warps never wait for each other inside the row loop. K1 and K2
-// are register heavy; they are compiled for at least 3 resident CTAs per SM, which measured faster than the
-// 2 their unconstrained register counts allow. The
+// are register heavy; up to p = 16 they are compiled for at least 3 resident CTAs per SM, which measured
+// faster than the 2 their unconstrained register counts allow. The
 // layout needs V | k, and k | 32 or 32 | k (with k/32 dividing the 8 warps of a CTA), and every block of p
 // columns inside one warp's 32 columns (p | 32); other shapes use the per-element kernels of bcg_kernels.cuh.
 //
@@ -113,8 +113,10 @@ __device__ __forceinline__ VecU<T, V> apply_row_vec(const OpDesc &A, const T *__
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u)
+        if (e + u < e1) {   // warp-uniform for the lanes of one row: no wasted FMAs on short rows
 #pragma unroll
-        for (int v = 0; v < V; ++v) s.e[v] = fma_t(w[u], xv[u].e[v], s.e[v]);
+          for (int v = 0; v < V; ++v) s.e[v] = fma_t(w[u], xv[u].e[v], s.e[v]);
+        }
     }
     return s;
   } else {
@@ -199,8 +201,12 @@ __host__ __device__ constexpr size_t wc_pup_smem(int k, int p, int global, size_
 
 // ---------------------------------------------------------------------------------------------------
 // K1 (warp-chunk): Q = A P, alpha = <<P, Q>>_S, recomputed rho = <<P, R>>_S.
+// at least 3 CTAs per SM up to p = 16; p = 32 needs its registers (64 accumulator pairs per thread)
+template <int PM>
+constexpr int wc_min_ctas() { return PM <= 16 ? 3 : 1; }
+
 template <typename T, int OPK, int PM, int V>
-__global__ void __launch_bounds__(kNT, 3) kw_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
+__global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
                                                   T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                   const int *__restrict__ active, double *__restrict__ partA,
                                                   double *__restrict__ partR, const DevStatus *__restrict__ st) {
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(kNT, 3) kw_op_gram(OpDesc A, const T *__restri
 // ---------------------------------------------------------------------------------------------------
 // K2 (warp-chunk): X += P lambda, R -= Q lambda, rho = <<R, R>>_S, column norms.
 template <typename T, int PM, int V>
-__global__ void __launch_bounds__(kNT, 3) kw_update_xr(T *__restrict__ X, T *__restrict__ R, const T *__restrict__ P,
+__global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__restrict__ X, T *__restrict__ R, const T *__restrict__ P,
                                                     const T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                     const double *__restrict__ lam, const int *__restrict__ active,
                                                     double *__restrict__ partRho, double *__restrict__ partN,

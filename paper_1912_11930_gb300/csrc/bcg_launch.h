@@ -42,16 +42,37 @@ template <typename T>
 cudaError_t launch_bdot(const T *X, const T *Y, int64_t n, int k, int p, double *part, int grid, cudaStream_t s);
 template <typename T>
 int bdot_grid(int64_t n, int k, int p, int nsm);
-cudaError_t launch_finish_gram(const double *part, int nparts, int k, int p, int global, double *gamma, cudaStream_t s);
+cudaError_t launch_finish_gram(const double *part, int nparts, int k, int p, int global, double *gamma, double *gws,
+                               cudaStream_t s);
 template <typename T>
 cudaError_t launch_bop(const OpDesc &A, const T *X, T *Y, int64_t n, int k, int grid, cudaStream_t s);
 
+// large blocks (32 < p <= 256, p % 32 == 0): tiled products, see bcg_kernels_lp.cuh
+int lp_chunks(int64_t n, int k, int p, int nsm);
+template <typename T>
+cudaError_t launch_lp_bop(const OpDesc &A, const T *P, T *Q, int64_t n, int k, const DevStatus *st, int nsm,
+                          cudaStream_t s);
+template <typename T>
+cudaError_t launch_lp_gram(const T *X, const T *Y, int64_t n, int k, int p, int global, const int *active,
+                           double *part, int chunks, const DevStatus *st, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lp_baxpy(T *OUT, const T *BASE, const T *Y, const double *C, int64_t n, int k, int p, int global,
+                            double sign, const int *active, DevStatus *st, int bump, cudaStream_t s);
+template <typename T>
+cudaError_t launch_lp_colnorm(const T *R, int64_t n, int k, double *partN, int grid, const DevStatus *st,
+                              cudaStream_t s);
+
+// doubles of per-block workspace of the p x p solves; kept in global memory (gws) when too big for shared
+size_t small_ws_doubles(int p);
+bool small_needs_gws(int p);
+
 cudaError_t small_prepare(int p);
 cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int k, int p, int global,
-                                const int *active, double *lam, double *rho_rec, DevStatus *st, cudaStream_t s);
+                                const int *active, double *lam, double *rho_rec, DevStatus *st, double *gws,
+                                cudaStream_t s);
 cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int k, int p, int global,
                               double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
-                              const double *rho_rec, double *beta, DevStatus *st, cudaStream_t s);
+                              const double *rho_rec, double *beta, DevStatus *st, double *gws, cudaStream_t s);
 cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, int global, double *r0n2, double *rn2,
                                int *active, int *block_iters, double *lam, double *beta, DevStatus *st,
                                cudaStream_t s);

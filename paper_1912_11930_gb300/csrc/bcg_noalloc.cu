@@ -89,7 +89,7 @@ extern "C" bcg_status bcg_bdot_noalloc(int64_t n, int32_t k, int32_t p, int32_t 
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
   e = launch_bdot<double>(X, Y, n, k, p, scratch, grid, s);
   if (e != cudaSuccess) return noalloc_fail(BCG_ERR_CUDA, "BDOT launch", e);
-  e = launch_finish_gram(scratch, grid, k, p, global, gamma, s);
+  e = launch_finish_gram(scratch, grid, k, p, global, gamma, nullptr, s);
   if (e != cudaSuccess) return noalloc_fail(BCG_ERR_CUDA, "reduction launch", e);
   return BCG_OK;
 }

@@ -9,6 +9,7 @@
 // the solve stops and reports it.
 #include <cfloat>
 #include <cmath>
+#include <math_constants.h>
 
 #include "bcg_launch.h"
 
@@ -16,6 +17,15 @@ namespace bcgk {
 
 constexpr int kSmallNT = 512;
 constexpr double kPivotFactor = 64.0;
+constexpr size_t kSmallSmemMax = 200 * 1024;   // larger p x p workspaces live in global memory
+
+// per-block workspace (doubles): 3 p x p matrices + reduction scratch, or the column-norm scratch of K4b
+__host__ __device__ inline size_t small_ws_doubles_dev(int p) {
+  const size_t pp = (size_t)p * p;
+  const size_t solve = 3 * pp + (pp > (size_t)kSmallNT ? pp : (size_t)kSmallNT);
+  const size_t norms = (size_t)kNT + kSmallNT;
+  return solve > norms ? solve : norms;
+}
 
 // Deterministic reduction out[e] = sum over pi < nparts of load(pi, e), e < E: each entry's sum is split
 // over S = blockDim/E thread subsets (pi = sub, sub + S, ...) with 4 independent accumulators per thread
@@ -74,6 +84,45 @@ __device__ void transpose_into(const double *src, double *dst, int p) {
   __syncthreads();
 }
 
+// Block-wide max of |diag| (every thread passes its partial) -- result valid in all threads.
+__device__ double block_max(double v) {
+  __shared__ double wmax[kSmallNT / 32];
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double m = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
+  __syncthreads();
+  return m;
+}
+
+// Partial-pivot choice: the row i in [a, p) with the largest |M[i][a]|, the smallest i on ties. Valid in all
+// threads.
+__device__ void block_argmax_col(const double *M, int p, int a, double *best_v, int *best_i) {
+  __shared__ double wv[kSmallNT / 32];
+  __shared__ int wi[kSmallNT / 32];
+  double v = -1.0;
+  int idx = p;
+  for (int i = a + threadIdx.x; i < p; i += blockDim.x) {
+    const double x = fabs(M[(int64_t)i * p + a]);
+    if (x > v || (x == v && i < idx) || !(x == x)) { v = (x == x) ? x : INFINITY; idx = i; }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+    if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { wv[threadIdx.x >> 5] = v; wi[threadIdx.x >> 5] = idx; }
+  __syncthreads();
+  double bv = -1.0;
+  int bi = p;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+    if (wv[w] > bv || (wv[w] == bv && wi[w] < bi)) { bv = wv[w]; bi = wi[w]; }
+  __syncthreads();
+  *best_v = bv;
+  *best_i = bi;
+}
+
 __device__ void flag_breakdown(DevStatus *st) {
   atomicOr(&st->flags, ST_BREAKDOWN);
   atomicCAS(&st->breakdown_iter, 0, st->cur);
@@ -84,7 +133,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
                                                            const double *__restrict__ partR, int nparts, int k,
                                                            int p, int global, const int *__restrict__ active,
                                                            double *__restrict__ lam, double *__restrict__ rho_rec,
-                                                           DevStatus *st) {
+                                                           DevStatus *st, double *gws) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   const int pp = p * p;
@@ -93,7 +142,8 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
     for (int e = threadIdx.x; e < pp; e += blockDim.x) lj[e] = 0.0;
     return;
   }
-  extern __shared__ __align__(16) double sm[];
+  extern __shared__ __align__(16) double sm_dyn[];
+  double *sm = gws ? gws + (int64_t)jb * small_ws_doubles_dev(p) : sm_dyn;
   double *sA = sm;            // alpha, row-major, factored in place into L (lower)
   double *sR = sA + pp;       // rho_rec, row-major; overwritten by Y then lambda
   double *tmp = sR + pp;      // p*p
@@ -105,11 +155,14 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
   reduce_block(partR, nparts, k, p, global, jb, tmp, scr);
   transpose_into(tmp, sR, p);
   for (int e = threadIdx.x; e < pp; e += blockDim.x) rho_rec[(int64_t)jb * pp + e] = sR[e];
-  if (threadIdx.x == 0) {
+  {
     double m = 0.0;
-    for (int a = 0; a < p; ++a) m = fmax(m, fabs(sA[a * p + a]));
-    thresh = kPivotFactor * DBL_EPSILON * m;
-    bad = 0;
+    for (int a = threadIdx.x; a < p; a += blockDim.x) m = fmax(m, fabs(sA[a * p + a]));
+    m = block_max(m);
+    if (threadIdx.x == 0) {
+      thresh = kPivotFactor * DBL_EPSILON * m;
+      bad = 0;
+    }
   }
   __syncthreads();
   // right-looking Cholesky on the lower triangle
@@ -164,14 +217,15 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
                                                          double *__restrict__ rn2, int *__restrict__ active,
                                                          int *__restrict__ block_iters,
                                                          const double *__restrict__ rho_rec,
-                                                         double *__restrict__ beta, DevStatus *st) {
+                                                         double *__restrict__ beta, DevStatus *st, double *gws) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   if (!active[jb]) return;
   const int pp = p * p;
   const int it = st->cur;
   const int c0 = global ? 0 : jb * p, c1 = global ? k : c0 + p;
-  extern __shared__ __align__(16) double sm[];
+  extern __shared__ __align__(16) double sm_dyn[];
+  double *sm = gws ? gws + (int64_t)jb * small_ws_doubles_dev(p) : sm_dyn;
   {
     double *ncol = sm, *nscr = sm + kNT;   // column norms of this block, scratch
     det_reduce(c1 - c0, nparts, [&](int pi, int c) { return partN[(int64_t)pi * k + c0 + c]; }, ncol, nscr);
@@ -210,23 +264,33 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
   transpose_into(tmp, sB, p);
   for (int e = threadIdx.x; e < pp; e += blockDim.x) sM[e] = rho_rec[(int64_t)jb * pp + e];
   __syncthreads();
-  if (threadIdx.x == 0) {
+  {
     double m = 0.0;
     bool fin = true;
-    for (int a = 0; a < p; ++a) m = fmax(m, fabs(sM[a * p + a]));
-    for (int e = 0; e < pp; ++e) fin = fin && isfinite(sM[e]);
-    thresh = kPivotFactor * DBL_EPSILON * m;
-    bad = fin ? 0 : 1;
+    for (int a = threadIdx.x; a < p; a += blockDim.x) m = fmax(m, fabs(sM[a * p + a]));
+    for (int e = threadIdx.x; e < pp; e += blockDim.x) fin = fin && isfinite(sM[e]);
+    m = block_max(m);
+    fin = __syncthreads_and(fin);
+    if (threadIdx.x == 0) {
+      thresh = kPivotFactor * DBL_EPSILON * m;
+      bad = fin ? 0 : 1;
+    }
   }
   __syncthreads();
   for (int a = 0; a < p && !bad; ++a) {
-    if (threadIdx.x == 0) {
-      int best = a;
-      double bv = fabs(sM[a * p + a]);
+    double bv;
+    int best;
+    if (p > 64) {   // wide blocks: all threads search the pivot column
+      block_argmax_col(sM, p, a, &bv, &best);
+    } else if (threadIdx.x == 0) {   // narrow blocks: one thread is faster than a block reduction
+      best = a;
+      bv = fabs(sM[a * p + a]);
       for (int i = a + 1; i < p; ++i) {
         const double v = fabs(sM[i * p + a]);
         if (v > bv) { bv = v; best = i; }
       }
+    }
+    if (threadIdx.x == 0) {
       piv = best;
       if (!(bv > thresh)) bad = 1;
     }
@@ -315,8 +379,9 @@ __global__ void k_init_status(const double *__restrict__ partN, int nparts, int 
 
 // Sum BDOT partials in CTA order into gamma (per distinct block p*p, row-major a*p + b).
 __global__ void __launch_bounds__(kSmallNT) k_finish_gram(const double *__restrict__ part, int nparts, int k, int p,
-                                                          int global, double *__restrict__ gamma) {
-  extern __shared__ __align__(16) double sm[];
+                                                          int global, double *__restrict__ gamma, double *gws) {
+  extern __shared__ __align__(16) double sm_dyn[];
+  double *sm = gws ? gws + (int64_t)blockIdx.x * small_ws_doubles_dev(p) : sm_dyn;
   const int pp = p * p;
   double *tmp = sm, *scr = sm + pp;
   const int jb = blockIdx.x;
@@ -365,12 +430,18 @@ __global__ void k_row_index(const int64_t *__restrict__ rowptr, int64_t n, int32
 // ---------------------------------------------------------------------------------------------------
 // host launchers
 
-static size_t small_smem(int p) {
-  const int pp = p * p;
-  const size_t solve = (size_t)(3 * pp + (pp > kSmallNT ? pp : kSmallNT));
-  const size_t norms = (size_t)(kNT + kSmallNT);   // column norms + reduction scratch in k_solve_beta
-  return (solve > norms ? solve : norms) * sizeof(double);
+size_t small_ws_doubles(int p) { return small_ws_doubles_dev(p); }
+
+// Row chunks (= partial rows) of the tiled large-block products: about 8 CTAs per SM over all tiles.
+int lp_chunks(int64_t n, int k, int p, int nsm) {
+  const int tiles = (k / p) * (p / 32) * (p / 32);
+  int64_t ch = ((int64_t)nsm * 8 + tiles - 1) / tiles;
+  const int64_t max_ch = (n + 31) / 32;
+  if (ch > max_ch) ch = max_ch;
+  return (int)(ch < 1 ? 1 : ch);
 }
+bool small_needs_gws(int p) { return small_ws_doubles_dev(p) * sizeof(double) > kSmallSmemMax; }
+static size_t small_smem(int p) { return small_needs_gws(p) ? 0 : small_ws_doubles_dev(p) * sizeof(double); }
 
 cudaError_t small_prepare(int p) {
   const size_t sm = small_smem(p);
@@ -384,18 +455,20 @@ cudaError_t small_prepare(int p) {
 }
 
 cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int k, int p, int global,
-                                const int *active, double *lam, double *rho_rec, DevStatus *st, cudaStream_t s) {
+                                const int *active, double *lam, double *rho_rec, DevStatus *st, double *gws,
+                                cudaStream_t s) {
   const int nblk = global ? 1 : k / p;
-  k_solve_lambda<<<nblk, kSmallNT, small_smem(p), s>>>(partA, partR, nparts, k, p, global, active, lam, rho_rec, st);
+  k_solve_lambda<<<nblk, kSmallNT, small_smem(p), s>>>(partA, partR, nparts, k, p, global, active, lam, rho_rec, st,
+                                                       small_needs_gws(p) ? gws : nullptr);
   return cudaGetLastError();
 }
 
 cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int k, int p, int global,
                               double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
-                              const double *rho_rec, double *beta, DevStatus *st, cudaStream_t s) {
+                              const double *rho_rec, double *beta, DevStatus *st, double *gws, cudaStream_t s) {
   const int nblk = global ? 1 : k / p;
   k_solve_beta<<<nblk, kSmallNT, small_smem(p), s>>>(partRho, partN, nparts, k, p, global, tol2, r0n2, rn2, active,
-                                                     block_iters, rho_rec, beta, st);
+                                                     block_iters, rho_rec, beta, st, small_needs_gws(p) ? gws : nullptr);
   return cudaGetLastError();
 }
 
@@ -406,12 +479,17 @@ cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_finish_gram(const double *part, int nparts, int k, int p, int global, double *gamma,
+cudaError_t launch_finish_gram(const double *part, int nparts, int k, int p, int global, double *gamma, double *gws,
                                cudaStream_t s) {
   const int nblk = global ? 1 : k / p;
-  const int pp = p * p;
-  const size_t sm = (size_t)(pp + (pp > kSmallNT ? pp : kSmallNT)) * sizeof(double);
-  k_finish_gram<<<nblk, kSmallNT, sm, s>>>(part, nparts, k, p, global, gamma);
+  const bool g = small_needs_gws(p);
+  if (g && gws == nullptr) return cudaErrorInvalidValue;
+  const size_t sm = g ? 0 : small_ws_doubles_dev(p) * sizeof(double);
+  if (sm > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_finish_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    if (e != cudaSuccess) return e;
+  }
+  k_finish_gram<<<nblk, kSmallNT, sm, s>>>(part, nparts, k, p, global, gamma, g ? gws : nullptr);
   return cudaGetLastError();
 }
 

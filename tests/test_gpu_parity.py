@@ -217,8 +217,8 @@ def test_invalid_arguments(torch_dev):
     va = torch.from_numpy(M.vals).to(dev)
     with pytest.raises(bcg.BCGError, match="divide"):
         bcg.bcg_create_csr(M.n, M.nnz, rp, ci, va, 6, 4, "hybrid", "fp64")
-    with pytest.raises(bcg.BCGError, match="not supported"):
-        bcg.bcg_create_csr(M.n, M.nnz, rp, ci, va, 128, 64, "hybrid", "fp64")
+    with pytest.raises(bcg.BCGError, match="multiple of 32"):
+        bcg.bcg_create_csr(M.n, M.nnz, rp, ci, va, 96, 48, "hybrid", "fp64")
     with pytest.raises(bcg.BCGError, match="device pointers"):
         bcg.bcg_create_csr(M.n, M.nnz, rp.cpu(), ci, va, 4, 2, "hybrid", "fp64")
     h = bcg.bcg_create_csr(M.n, M.nnz, rp, ci, va, 4, 2, "hybrid", "fp64")
@@ -317,3 +317,56 @@ def test_bdot_f32_is_fp64_accurate(torch_dev, sub, k, p):
     absdot = O.block_product(np.abs(X.astype(np.float64)), np.abs(Y.astype(np.float64)), pp, kind)
     # FP64-class: error far below FP32 accumulation (which would be ~1e-7 relative to sum |x y|)
     assert np.max(np.abs(g - ref) / absdot) <= 1e-13
+
+
+# ---- large blocks (32 < p <= 256): tiled block products and updates, p x p solves in global memory ------------
+LARGE = [("p3d_30", "classical", 64, 64, 6), ("p3d_30", "hybrid", 128, 64, 6), ("p3d_30", "global", 128, 64, 5),
+         ("s27_15", "classical", 128, 128, 4), ("p3d_30", "classical", 256, 256, 3), ("vc_20", "hybrid", 256, 128, 3)]
+
+
+@pytest.mark.parametrize("name,sub,k,p,m", LARGE)
+@pytest.mark.parametrize("prec", ["fp64"])
+def test_large_p_equal_iterations(torch_dev, name, sub, k, p, m, prec):
+    M = mat(name)
+    B = W.rhs(M.n, k, seed=31)
+    Xg, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, prec=prec, maxit=m)
+    assert r.status == 5 and r.iters == m
+    ref = O.solve(M.to_scipy(), B, p=p, sub=sub, tol=0.0, maxit=m)
+    assert _rel(Xg, ref.X) <= 1e-9
+
+
+@pytest.mark.parametrize("sub,k,p", [("classical", 64, 64), ("hybrid", 256, 128), ("global", 256, 64),
+                                     ("classical", 256, 256)])
+def test_large_p_bdot(torch_dev, sub, k, p):
+    torch, dev = torch_dev
+    from paper_1912_11930_gb300 import bcg
+    M = mat("p2d_37x29")
+    X = W.rhs(M.n, k, seed=40)
+    Y = W.rhs(M.n, k, seed=41)
+    S = bcg.Solver.from_matrix(M, k=k, p=p, sub=sub, device=dev)
+    g = S.bdot(torch.from_numpy(X).to(dev), torch.from_numpy(Y).to(dev)).cpu().numpy()
+    g32 = S.bdot(torch.from_numpy(X.astype(np.float32)).to(dev), torch.from_numpy(Y.astype(np.float32)).to(dev))
+    S.close()
+    kind, pp = O.canonical_subalgebra(sub, k, p)
+    ref = O.block_product(X, Y, pp, kind)
+    scale = np.linalg.norm(X) * np.linalg.norm(Y) / k
+    assert np.max(np.abs(g - ref)) <= 1e-13 * scale
+    ref32 = O.block_product(X.astype(np.float32).astype(np.float64), Y.astype(np.float32).astype(np.float64), pp, kind)
+    assert np.max(np.abs(g32.cpu().numpy() - ref32)) <= 1e-13 * scale
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-8), ("fp32_refine", 1e-10)])
+def test_large_p_converged(torch_dev, prec, tol):
+    """Classical block CG with k = p = 128 to the stopping rule; FP64 counts within the +-2 bar of the oracle,
+    the mixed form refined below 1e-10 (true residual recomputed on the host)."""
+    M = mat("p3d_30")
+    A = M.to_scipy()
+    k = p = 128
+    B = W.rhs(M.n, k, seed=33)
+    X, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub="classical", prec=prec, tol=tol, maxit=2000)
+    assert r.ok, r
+    res = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(res <= 1.5 * tol)
+    if prec == "fp64":
+        ref = O.solve(A, B, sub="classical", tol=tol, maxit=2000)
+        assert abs(r.iters - ref.iters) <= 2
