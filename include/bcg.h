@@ -4,8 +4,8 @@
  * Gradients method", arXiv 1912.11930).
  *
  * The library solves A X = B for a sparse symmetric positive definite A (n x n) and n x k blocks B, X
- * with Algorithm 1 of Section 3 (stabilised block CG, preconditioner M = I). Every block product is
- * restricted to one *-subalgebra S of R^{k x k} (Section 2, Definition "Relevant *-subalgebras"):
+ * with Algorithm 1 of Section 3 (stabilised block CG, preconditioner M = I or Jacobi). Every block
+ * product is restricted to one *-subalgebra S of R^{k x k} (Section 2, Definition "Relevant *-subalgebras"):
  *   hybrid    S_Hy^p = diag((R^{p x p})^q), q = k/p: q independent p x p Gram blocks;
  *   global    S_Gl^p = R^{p x p} (x) I_q: one p x p Gram summed over the q blocks, applied to each;
  *   parallel  S_Pl   = S_Hy^1: k independent CGs in lockstep;
@@ -122,13 +122,17 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
  *                  (default 1; graphs need a non-NULL stream)
  *   "profile"      1 = time every iteration kernel with CUDA events (see bcg_profile), 0 = off;
  *                  setting it resets the counters
+ *   "precond"      preconditioner M of Algorithm 1: 0 = identity (default), 1 = Jacobi, M = diag(A)
+ *                  (Section 3 allows any SPD M; Z = M^{-1} R is formed on the fly by the kernels that
+ *                  read R, from 1/diag(A) computed at create time and by bcg_update_values; the mixed
+ *                  form uses an FP32 copy). Every diagonal entry must be positive.
  * Unknown keys or out-of-range values return INVALID_ARG.
  */
 bcg_status bcg_set_option(bcg_handle h, const char *key, double value);
 
 /*
- * bcg_solve -- Algorithm 1 (Section 3) with M = I from X^0 = X to the stopping rule of Section 4's
- * whole-solver experiment: every column s with ||R_s|| <= tol ||R_s^0|| (recursive residual, 2-norm).
+ * bcg_solve -- Algorithm 1 (Section 3) with M = I (or Jacobi, option "precond") from X^0 = X to the
+ * stopping rule of Section 4's whole-solver experiment: every column s with ||R_s|| <= tol ||R_s^0|| (recursive residual, 2-norm).
  * Hybrid/parallel blocks stop updating once all their columns pass; global/classical stop together.
  *   B      device double[n*k], row-major, not modified
  *   X      device double[n*k], row-major; in: X^0, out: the solution (or last iterate on error)

@@ -11,9 +11,9 @@ no fusion, no blocking, no reordering. Library primitives used as single steps: 
 Paper passages followed:
 * Section 2, Definition "Relevant *-subalgebras": the block products of the hybrid (S_Hy^p) and global
   (S_Gl^p) subalgebras; classical = S_Hy^k = S_Gl^k, parallel = S_Hy^1.
-* Section 3, Algorithm 1 (preconditioned, stabilised BCG) with M = I, including the recomputation of
-  rho^{i-1} as <<P^i, R^{i-1}>>_S (the stabilisation of Section 3), and the four kernels BDOT, BAXPY,
-  BOP, BSOLVE listed after it.
+* Section 3, Algorithm 1 (preconditioned, stabilised BCG) with M = I or the Jacobi preconditioner
+  M = diag(A), including the recomputation of rho^{i-1} as <<P^i, R^{i-1}>>_S (the stabilisation of
+  Section 3), and the four kernels BDOT, BAXPY, BOP, BSOLVE listed after it.
 * Section 4, whole-solver experiment: the stopping rule "2-norm of every residual column reduced by the
   factor tol".
 
@@ -166,10 +166,11 @@ class Result:
 
 
 def solve(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, sub: str = "hybrid",
-          tol: float = 1e-8, maxit: int = 1000, record: bool = False) -> Result:
-    """Algorithm 1 of Section 3 with M = I, FP64, step by step.
+          tol: float = 1e-8, maxit: int = 1000, record: bool = False, precond: str = "none") -> Result:
+    """Algorithm 1 of Section 3, FP64, step by step.
 
-    ``A`` is a scipy sparse matrix (or anything supporting ``A @ X``); B and X0 are n x k."""
+    ``A`` is a scipy sparse matrix (or anything supporting ``A @ X``); B and X0 are n x k.
+    ``precond``: "none" (M = I) or "jacobi" (M = diag(A), applied as Z = M^{-1} R)."""
     B = np.asarray(B, dtype=np.float64)
     n, k = B.shape
     kind, p = canonical_subalgebra(sub, k, p)
@@ -182,10 +183,21 @@ def solve(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, sub: str =
     def colnorms(M):
         return np.sqrt(np.sum(M * M, axis=0))
 
+    if precond == "jacobi":
+        dinv = 1.0 / np.asarray(A.diagonal(), dtype=np.float64)
+
+        def apply_minv(M_):
+            return M_ * dinv[:, None]
+    elif precond == "none":
+        def apply_minv(M_):
+            return M_.copy()
+    else:
+        raise ValueError(f"unknown preconditioner {precond!r}")
+
     # R^0 = B - A X^0
     R = B - bop(A, X)
-    # P^1 = M^{-1} R^0 with M = I
-    P = R.copy()
+    # P^1 = M^{-1} R^0
+    P = apply_minv(R)
     r0 = colnorms(R)
     if not (np.all(np.isfinite(r0)) and np.all(np.isfinite(X))):
         return Result(X, NUMERIC, 0, np.zeros(nblk, dtype=np.int64), -1, r0 * np.nan, r0 * np.nan, hist)
@@ -224,8 +236,9 @@ def solve(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, sub: str =
             status = NUMERIC
             break
         active = active & ~block_converged(rn)
-        # Z^{i+1} = M^{-1} R^i = R^i ; rho^i = <<Z^{i+1}, R^i>>
-        rho = block_product(R, R, p, kind)
+        # Z^{i+1} = M^{-1} R^i ; rho^i = <<Z^{i+1}, R^i>>
+        Z = apply_minv(R)
+        rho = block_product(Z, R, p, kind)
         # beta^i = (rho^{i-1})^{-1} rho^i
         beta, ok = bsolve_lu(rho_rec, rho, active)
         if record:
@@ -235,7 +248,7 @@ def solve(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, sub: str =
             status, brk = BREAKDOWN, it
             break
         # P^{i+1} = Z^{i+1} + P^i beta^i   (sign reading R1)
-        P = baxpy(R, P, beta, +1.0)
+        P = baxpy(Z, P, beta, +1.0)
         if record:
             hist["X"].append(X.copy()); hist["R"].append(R.copy()); hist["P"].append(P.copy())
 

@@ -85,6 +85,7 @@ struct bcg_ctx {
   int check_every = 8;
   int use_graph = 1;
   int profile = 0;
+  int precond = 0;                     // 0: M = I; 1: Jacobi, M = diag(A)
   // live per-kernel timing (profile = 1): CUDA events around every launch of an executed iteration
   static constexpr int kKernels = 6;   // K1 op_gram, K4a solve_lambda, K2 update_xr, K4b solve_beta, K3 update_p, K0 residual
   double prof_ms[kKernels] = {0, 0, 0, 0, 0, 0};
@@ -100,6 +101,8 @@ struct bcg_ctx {
   double *r0n2 = nullptr, *rn2 = nullptr, *rtn2 = nullptr, *outer0 = nullptr;
   int *active = nullptr, *block_iters = nullptr;
   double *gws = nullptr;               // global workspace of the p x p solves when p is large
+  double *dinv64 = nullptr;            // 1 / diag(A) (Jacobi preconditioner)
+  float *dinv32 = nullptr;             // its FP32 copy for the mixed form's inner solve
   int32_t *rowidx = nullptr;           // CSR row of each entry (gradient)
   DevStatus *st = nullptr;
   DevStatus *h_st = nullptr;           // pinned
@@ -193,6 +196,8 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CKS(h->alloc(&h->active, h->nblk));
   CKS(h->alloc(&h->block_iters, h->nblk));
   if (small_needs_gws(h->p)) CKS(h->alloc(&h->gws, (size_t)h->nblk * small_ws_doubles(h->p)));
+  CKS(h->alloc(&h->dinv64, (size_t)h->n));
+  if (h->prec == BCG_FP32_REFINE) CKS(h->alloc(&h->dinv32, (size_t)h->n));
   CKS(h->alloc(&h->st, 1));
   CK(cudaMallocHost(&h->h_st, sizeof(DevStatus)));
   CK(cudaMallocHost(&h->h_vec, 3 * sizeof(double) * h->k));
@@ -202,6 +207,8 @@ bcg_status setup_workspace(bcg_ctx *h) {
 }
 
 bcg_status make_fp32_copy(bcg_ctx *h) {
+  CK(launch_inv_diag(h->A64, h->n, h->dinv64, h->nsm, h->stream));
+  if (h->dinv32) CK(launch_cast_to_float(h->dinv64, h->dinv32, h->n, h->nsm, h->stream));
   if (h->prec != BCG_FP32_REFINE) return BCG_OK;
   h->A32 = h->A64;
   if (h->ncoef > 0) {
@@ -218,6 +225,13 @@ bcg_status make_fp32_copy(bcg_ctx *h) {
   return BCG_OK;
 }
 
+template <typename T>
+const T *dinv_of(const bcg_ctx *h);
+template <>
+const double *dinv_of<double>(const bcg_ctx *h) { return h->precond ? h->dinv64 : nullptr; }
+template <>
+const float *dinv_of<float>(const bcg_ctx *h) { return h->precond ? h->dinv32 : nullptr; }
+
 // ev: NULL, or 10 events recorded around the 5 launches (profiling)
 template <typename T>
 bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g, double tol2,
@@ -228,15 +242,15 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
   CK(launch_op_gram<T>(A, P, R, Q, h->n, h->k, h->p, h->global, h->active, h->partA, h->partR, h->st, g.op, s));
   REC(1); REC(2);
   CK(launch_solve_lambda(h->partA, h->partR, g.op, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
-                         h->gws, s));
+                         h->gws, g.alpha_circ, s));
   REC(3); REC(4);
   CK(launch_update_xr<T>(X, R, P, Q, h->n, h->k, h->p, h->global, h->lam, h->active, h->partRho, h->partN, h->st,
-                         g.upd, s));
+                         g.upd, s, dinv_of<T>(h)));
   REC(5); REC(6);
   CK(launch_solve_beta(h->partRho, h->partN, g.upd, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
-                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, s));
+                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, g.rho_circ, s));
   REC(7); REC(8);
-  CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, g.pup, s));
+  CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, g.pup, s, dinv_of<T>(h)));
   REC(9);
 #undef REC
   return BCG_OK;
@@ -250,17 +264,18 @@ bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T 
   cudaStream_t s = h->stream;
   const int ch = g.op;
   CK(launch_lp_bop<T>(A, P, Q, h->n, h->k, h->st, h->nsm, s));
-  CK(launch_lp_gram<T>(P, Q, h->n, h->k, h->p, h->global, h->active, h->partA, ch, h->st, s));
-  CK(launch_lp_gram<T>(P, R, h->n, h->k, h->p, h->global, h->active, h->partR, ch, h->st, s));
+  CK(launch_lp_gram<T>(P, Q, h->n, h->k, h->p, h->global, h->active, h->partA, ch, h->st, s, nullptr));
+  CK(launch_lp_gram<T>(P, R, h->n, h->k, h->p, h->global, h->active, h->partR, ch, h->st, s, nullptr));
   CK(launch_solve_lambda(h->partA, h->partR, ch, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
-                         h->gws, s));
-  CK(launch_lp_baxpy<T>(X, X, P, h->lam, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 0, s));
-  CK(launch_lp_baxpy<T>(R, R, Q, h->lam, h->n, h->k, h->p, h->global, -1.0, h->active, h->st, 0, s));
-  CK(launch_lp_gram<T>(R, R, h->n, h->k, h->p, h->global, h->active, h->partRho, ch, h->st, s));
+                         h->gws, 0, s));
+  CK(launch_lp_baxpy<T>(X, X, P, h->lam, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 0, s, nullptr));
+  CK(launch_lp_baxpy<T>(R, R, Q, h->lam, h->n, h->k, h->p, h->global, -1.0, h->active, h->st, 0, s, nullptr));
+  // rho = <<Z, R>> with Z = M^{-1} R formed on the fly
+  CK(launch_lp_gram<T>(R, R, h->n, h->k, h->p, h->global, h->active, h->partRho, ch, h->st, s, dinv_of<T>(h)));
   CK(launch_lp_colnorm<T>(R, h->n, h->k, h->partN, ch, h->st, s));
   CK(launch_solve_beta(h->partRho, h->partN, ch, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
-                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, s));
-  CK(launch_lp_baxpy<T>(Q, R, P, h->beta, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 1, s));
+                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s));
+  CK(launch_lp_baxpy<T>(Q, R, P, h->beta, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 1, s, dinv_of<T>(h)));
   return BCG_OK;
 }
 
@@ -401,14 +416,16 @@ bcg_status status_from_flags(int flags, bool all_done) {
 bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int maxit, bcg_info *info) {
   cudaStream_t s = h->stream;
   const double tol2 = tol * tol;
-  CK(launch_residual<double>(h->A64, X, B, h->R, h->P, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, s));
+  CK(launch_residual<double>(h->A64, X, B, h->R, h->P, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, s,
+                             dinv_of<double>(h)));
   CK(launch_init_status(h->partN, h->g64.res, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters,
                         h->lam, h->beta, h->st, s));
   CKS(run_iterations<double>(h, h->A64, X, h->R, h->P, h->Q, h->g64, tol2, maxit, nullptr, nullptr));
   const DevStatus fin = *h->h_st;
   CKS(fill_block_iters(h));
   // true residual B - A X, recomputed
-  CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, s));
+  CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, s,
+                             nullptr));
   CK(launch_reduce_norms(h->partN, h->g64.res, h->k, h->rtn2, s));
   CKS(fetch_vec(h, h->r0n2, 0));
   CKS(fetch_vec(h, h->rn2, 1));
@@ -440,7 +457,8 @@ bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int 
   int stalls = 0;
   for (;;) {
     // outer residual in FP64, rounded to FP32 as the inner right-hand side (R32 = P32 = fl(R))
-    CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, h->R32, h->P32, h->n, h->k, h->partN, h->g64.res, s));
+    CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, h->R32, h->P32, h->n, h->k, h->partN, h->g64.res, s,
+                               dinv_of<double>(h)));
     CK(launch_reduce_norms(h->partN, h->g64.res, h->k, h->rtn2, s));
     if (outer == 0) CK(cudaMemcpyAsync(h->outer0, h->rtn2, sizeof(double) * h->k, cudaMemcpyDeviceToDevice, s));
     CKS(fetch_vec(h, h->outer0, 0));
@@ -586,6 +604,13 @@ bcg_status bcg_set_option(bcg_handle h, const char *key, double value) {
     if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "profile must be 0 or 1");
     h->profile = (int)value;
     for (int i = 0; i < bcg_ctx::kKernels; ++i) { h->prof_ms[i] = 0.0; h->prof_count[i] = 0; }
+  } else if (!strcmp(key, "precond")) {
+    if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "precond must be 0 (none) or 1 (Jacobi)");
+    h->precond = (int)value;
+    if (h->graph32) {   // captured graphs hold the preconditioner pointer
+      cudaGraphExecDestroy(h->graph32);
+      h->graph32 = nullptr;
+    }
   } else if (!strcmp(key, "graph")) {
     if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "graph must be 0 or 1");
     h->use_graph = (int)value;
@@ -663,7 +688,8 @@ bcg_status bcg_bdot(bcg_handle h, const double *X, const double *Y, double *gamm
   if (!is_device_ptr(X) || !is_device_ptr(Y) || !is_device_ptr(gamma))
     return fail(BCG_ERR_INVALID_ARG, "X, Y and gamma must be device pointers");
   if (h->p > kMaxP) {
-    CK(launch_lp_gram<double>(X, Y, h->n, h->k, h->p, h->global, nullptr, h->partA, h->g64.op, nullptr, h->stream));
+    CK(launch_lp_gram<double>(X, Y, h->n, h->k, h->p, h->global, nullptr, h->partA, h->g64.op, nullptr, h->stream,
+                              nullptr));
     CK(launch_finish_gram(h->partA, h->g64.op, h->k, h->p, h->global, gamma, h->gws, h->stream));
   } else {
     const int grid = std::min(h->nparts, bdot_grid<double>(h->n, h->k, h->p, h->nsm));
@@ -679,7 +705,8 @@ bcg_status bcg_bdot_f32(bcg_handle h, const float *X, const float *Y, double *ga
   if (!is_device_ptr(X) || !is_device_ptr(Y) || !is_device_ptr(gamma))
     return fail(BCG_ERR_INVALID_ARG, "X, Y and gamma must be device pointers");
   if (h->p > kMaxP) {
-    CK(launch_lp_gram<float>(X, Y, h->n, h->k, h->p, h->global, nullptr, h->partA, h->g64.op, nullptr, h->stream));
+    CK(launch_lp_gram<float>(X, Y, h->n, h->k, h->p, h->global, nullptr, h->partA, h->g64.op, nullptr, h->stream,
+                             nullptr));
     CK(launch_finish_gram(h->partA, h->g64.op, h->k, h->p, h->global, gamma, h->gws, h->stream));
   } else {
     const int grid = std::min(h->nparts, bdot_grid<float>(h->n, h->k, h->p, h->nsm));

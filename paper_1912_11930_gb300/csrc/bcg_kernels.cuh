@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
                                                    const T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                    const double *__restrict__ lam, const int *__restrict__ active,
                                                    double *__restrict__ partRho, double *__restrict__ partN,
-                                                   const DevStatus *__restrict__ st) {
+                                                   const DevStatus *__restrict__ st, const T *__restrict__ dinv) {
   using G = Gram<T>;
   using BT = typename G::B;
   constexpr int RPT = rpt_stream<T>();
@@ -475,12 +475,13 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
       }
     }
     row_sync(wl);
-    BT rb[RPT];
+    BT rb[RPT];   // own operand R; the broadcast row is Z = M^{-1} R (Z = R without a preconditioner)
 #pragma unroll
     for (int u = 0; u < RPT; ++u) {
       const int64_t r = row0 + u * rpp + g;
-      rb[u] = (act && r < n) ? G::conv(rv[u]) : G::zero();
-      if (slot) sRb[u * kNT + g * k + c] = rb[u];
+      const bool live = act && r < n;
+      rb[u] = live ? G::conv(rv[u]) : G::zero();
+      if (slot) sRb[u * kNT + g * k + c] = live ? (dinv ? G::conv(rv[u] * dinv[r]) : rb[u]) : G::zero();
     }
     row_sync(wl);
     if (act) {
@@ -491,7 +492,7 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
 #pragma unroll
         for (int a = 0; a < PM; ++a)
           if (a < p) G::add(acc.s[a], acc.c[a], rrow[a], rb[u]);
-        G::add(ns, nc, rb[u], rb[u]);
+        G::add(ns, nc, rb[u], rb[u]);   // ||R_c||^2 for the stopping test
       }
     }
     row_sync(wl);
@@ -520,7 +521,8 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
 template <typename T, int PM>
 __global__ void __launch_bounds__(kNT) k_update_p(T *__restrict__ P, const T *__restrict__ R, int64_t n, int k,
                                                   int p, int global, const double *__restrict__ beta,
-                                                  const int *__restrict__ active, DevStatus *__restrict__ st) {
+                                                  const int *__restrict__ active, DevStatus *__restrict__ st,
+                                                  const T *__restrict__ dinv) {
   constexpr int RPT = rpt_stream<T>();
   if (st->flags != 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) st->cur += 1;   // no other kernel of this launch reads it
@@ -550,7 +552,10 @@ __global__ void __launch_bounds__(kNT) k_update_p(T *__restrict__ P, const T *__
     for (int u = 0; u < RPT; ++u) {
       const int64_t r = row0 + u * rpp + g;
       pv[u] = rv[u] = T(0);
-      if (act && r < n) { pv[u] = P[r * k + c]; rv[u] = R[r * k + c]; }
+      if (act && r < n) {
+        pv[u] = P[r * k + c];
+        rv[u] = dinv ? R[r * k + c] * dinv[r] : R[r * k + c];   // Z = M^{-1} R
+      }
       if (slot) sP[u * kNT + g * k + c] = pv[u];
     }
     row_sync(wl);
@@ -573,12 +578,13 @@ __global__ void __launch_bounds__(kNT) k_update_p(T *__restrict__ P, const T *__
 
 // ---------------------------------------------------------------------------------------------------
 // K0: R = B - A X (and optionally P = R), per-column ||R_c||^2 partials. T is the precision of X, B, R;
-// R32/P32 (optional) receive a float copy of R (the mixed-precision inner right-hand side).
+// R32/P32 (optional) receive a float copy of R and of P (the mixed-precision inner right-hand side).
+// dinv (optional): P = M^{-1} R with the Jacobi preconditioner M = diag(A).
 template <typename T, int OPK>
 __global__ void __launch_bounds__(kNT) k_residual(OpDesc A, const T *__restrict__ X, const T *__restrict__ B,
                                                   T *__restrict__ R, T *__restrict__ P, float *__restrict__ R32,
                                                   float *__restrict__ P32, int64_t n, int k,
-                                                  double *__restrict__ partN) {
+                                                  double *__restrict__ partN, const T *__restrict__ dinv) {
   extern __shared__ __align__(16) unsigned char smem[];
   double *red = reinterpret_cast<double *>(smem);
   const int rpp = kNT / k;
@@ -591,10 +597,11 @@ __global__ void __launch_bounds__(kNT) k_residual(OpDesc A, const T *__restrict_
     if (slot && r < n) {
       const int64_t o = r * k + c;
       const T rv = B[o] - apply_row<T, OPK>(A, X, r, k, c);
+      const T zv = dinv ? rv * dinv[r] : rv;   // P^1 = M^{-1} R^0
       if (R) R[o] = rv;
-      if (P) P[o] = rv;
+      if (P) P[o] = zv;
       if (R32) { R32[o] = (float)rv; }
-      if (P32) { P32[o] = (float)rv; }
+      if (P32) { P32[o] = (float)zv; }
       const double rd = (double)rv;
       accN = fma(rd, rd, accN);
     }
@@ -645,6 +652,35 @@ __global__ void __launch_bounds__(kNT) k_bdot(const T *__restrict__ X, const T *
   }
   if (slot) acc.flush(sl, p);
   cta_sum_slots(red, k * p, rpp, part + (int64_t)blockIdx.x * k * p);
+}
+
+// Inverse diagonal of the operator (Jacobi preconditioner M = diag(A)): one value per row.
+template <typename T, int OPK>
+__global__ void k_inv_diag(OpDesc A, int64_t n, T *__restrict__ dinv) {
+  for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    double d = 0.0;
+    if constexpr (OPK == OP_CSR) {
+      const double *v = static_cast<const double *>(A.vals);
+      for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e)
+        if (A.colind[e] == r) d += v[e];
+    } else if constexpr (OPK == OP_ST5) {
+      d = 4.0 * A.scale;
+    } else if constexpr (OPK == OP_ST7) {
+      d = 6.0 * A.scale;
+    } else {
+      const int nx = A.nx, ny = A.ny, nz = A.nz;
+      const int64_t pl = (int64_t)nx * ny;
+      const int ix = (int)(r % nx), iy = (int)((r / nx) % ny), iz = (int)(r / pl);
+      const double *f = static_cast<const double *>(A.faces);
+      const int64_t nfx = (int64_t)nz * ny * (nx + 1), nfy = (int64_t)nz * (ny + 1) * nx;
+      const double *fx = f, *fy = f + nfx, *fz = f + nfx + nfy;
+      const int64_t bx = ((int64_t)iz * ny + iy) * (nx + 1) + ix;
+      const int64_t by = ((int64_t)iz * (ny + 1) + iy) * nx + ix;
+      const int64_t bz = ((int64_t)iz * ny + iy) * nx + ix;
+      d = A.scale * (((fx[bx] + fx[bx + 1]) + (fy[by] + fy[by + nx])) + (fz[bz] + fz[bz + pl]));
+    }
+    dinv[r] = (T)(1.0 / d);
+  }
 }
 
 // BOP alone: Y = A X.

@@ -36,10 +36,12 @@ __global__ void __launch_bounds__(kNT) kl_bop(OpDesc A, const T *__restrict__ P,
 
 // Partials of gamma = <<X, Y>>_S: grid.x = 32 x 32 tiles (block j, a-tile, b-tile), grid.y = row chunks.
 // Partial row blockIdx.y holds entry (a, b) of block j at j*p*p + b*p + a (the layout of the small path).
+// xscale (optional): X's row r is multiplied by xscale[r] (forms Z = M^{-1} R on the fly).
 template <typename T>
 __global__ void __launch_bounds__(kNT) kl_gram(const T *__restrict__ X, const T *__restrict__ Y, int64_t n, int k,
                                                int p, int global, const int *__restrict__ active,
-                                               double *__restrict__ part, const DevStatus *__restrict__ st) {
+                                               double *__restrict__ part, const DevStatus *__restrict__ st,
+                                               const T *__restrict__ xscale) {
   using G = Gram<T>;
   using BT = typename G::B;
   if (st != nullptr && st->flags != 0) return;
@@ -69,7 +71,8 @@ __global__ void __launch_bounds__(kNT) kl_gram(const T *__restrict__ X, const T 
         const int64_t r = r0 + rr;
         BT xb = G::zero(), yb = G::zero();
         if (r < r_end) {
-          xb = G::conv(X[r * k + (int64_t)j * p + a0 + cc]);
+          const T xv = X[r * k + (int64_t)j * p + a0 + cc];
+          xb = G::conv(xscale ? xv * xscale[r] : xv);
           yb = G::conv(Y[r * k + (int64_t)j * p + b0 + cc]);
         }
         Xs[rr][cc] = xb;
@@ -114,11 +117,12 @@ __global__ void __launch_bounds__(kNT) kl_gram(const T *__restrict__ X, const T 
 // OUT_j = BASE_j + sign * Y_j C_j (C_j row-major p x p per distinct block, FP64 in memory). grid.x = column
 // tiles (k/32), grid.y = row tiles of 64. OUT may equal BASE; Y must not alias OUT. bump != 0: CTA (0,0)
 // advances the iteration counter (this launch then plays the role of K3).
+// bscale (optional): BASE's row r is multiplied by bscale[r] (P = M^{-1} R + P beta).
 template <typename T>
 __global__ void __launch_bounds__(kNT) kl_baxpy(T *OUT, const T *BASE, const T *__restrict__ Y,
                                                 const double *__restrict__ C, int64_t n, int k, int p, int global,
                                                 T sign, const int *__restrict__ active, DevStatus *__restrict__ st,
-                                                int bump) {
+                                                int bump, const T *__restrict__ bscale) {
   if (st->flags != 0) return;
   if (bump && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->cur += 1;
   __shared__ T Ys[kLRows][kLT + 1];
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(kNT) kl_baxpy(T *OUT, const T *BASE, const T *
 #pragma unroll
   for (int m = 0; m < kLRows / 8; ++m) {
     const int64_t r = r0 + ty + 8 * m;
-    acc[m] = r < n ? BASE[r * k + c0 + tx] : T(0);
+    acc[m] = r < n ? (bscale ? BASE[r * k + c0 + tx] * bscale[r] : BASE[r * k + c0 + tx]) : T(0);
   }
   if (act) {
     for (int a0 = 0; a0 < p; a0 += kLT) {

@@ -225,7 +225,11 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_op_gram(OpDesc A, c
   const bool act = block_active(active, global, j);
   double *slotA = redA + threadIdx.x * p, *slotR = redR + threadIdx.x * p;
   for (int a = 0; a < p; ++a) { slotA[a] = 0.0; slotR[a] = 0.0; }
-  GramAcc<PM> accA, accR;
+  // alpha is symmetric: lane b accumulates only its circulant diagonals d = 0..p/2, entry ((b + d) mod p, b)
+  // (d = p/2 only for b < p/2); the recomputed rho stays a full product. p == PM here (p divides 32).
+  constexpr int PMH = PM == 1 ? 1 : PM / 2 + 1;
+  GramAcc<PMH> accA;
+  GramAcc<PM> accR;
   accA.zero();
   accR.zero();
   int pass = 0;
@@ -259,24 +263,24 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_op_gram(OpDesc A, c
       for (int s = 0; s < V; ++s) {
         const int t = 32 * s + geo.lane;
         const BT qb = sQ[t], rb2 = sR[t];
+        const BT *rowp = sP + t - b;
         BT prow[PM];
-        load_row<BT, PM>(sP + t - b, prow, p);
+        load_row<BT, PM>(rowp, prow, p);
 #pragma unroll
-        for (int a = 0; a < PM; ++a)
-          if (a < p) {
-            G::add(accA.s[a], accA.c[a], prow[a], qb);
-            G::add(accR.s[a], accR.c[a], prow[a], rb2);
-          }
+        for (int a = 0; a < PM; ++a) G::add(accR.s[a], accR.c[a], prow[a], rb2);
+#pragma unroll
+        for (int d = 0; d < PMH; ++d)
+          if (PM == 1 || d < PM / 2 || b < PM / 2) G::add(accA.s[d], accA.c[d], rowp[(b + d) & (PM - 1)], qb);
       }
     }
     __syncwarp();
     if (++pass == kFlushPasses / V) {
       pass = 0;
-      accA.flush(slotA, p);
+      accA.flush(slotA, PMH);
       accR.flush(slotR, p);
     }
   }
-  accA.flush(slotA, p);
+  accA.flush(slotA, PMH);
   accR.flush(slotR, p);
   const int E = k * p;
   wc_cta_reduce(redA, k, p, partA + (int64_t)blockIdx.x * E);
@@ -290,7 +294,7 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__rest
                                                     const T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                     const double *__restrict__ lam, const int *__restrict__ active,
                                                     double *__restrict__ partRho, double *__restrict__ partN,
-                                                    const DevStatus *__restrict__ st) {
+                                                    const DevStatus *__restrict__ st, const T *__restrict__ dinv) {
   using G = Gram<T>;
   using BT = typename G::B;
   using VT = typename VecOf<T, V>::type;
@@ -315,13 +319,14 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__rest
   for (int a = 0; a < p; ++a) slotRho[a] = 0.0;
   *slotN = 0.0;
   __syncthreads();
+  constexpr int PMH = PM == 1 ? 1 : PM / 2 + 1;   // rho = R^T R is symmetric: circulant diagonals only
   T lcol[PM];
   {
     const T *lj = sL + (global ? 0 : j) * p * p + b;
 #pragma unroll
     for (int a = 0; a < PM; ++a) lcol[a] = a < p ? lj[a * p] : T(0);
   }
-  GramAcc<PM> acc;
+  GramAcc<PMH> acc;
   acc.zero();
   float ns = 0.0f, nc = 0.0f;
   int pass = 0;
@@ -369,20 +374,25 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__rest
       }
       sX[t] = x;
       sR[t] = r;
-      sRb[t] = G::conv(r);
+      // broadcast Z = M^{-1} R (R without a preconditioner); the own operand R is re-read from sR below
+      if (dinv) {
+        const int64_t rw = R0 + (int64_t)s * geo.gr + geo.ro;
+        sRb[t] = G::conv(rw < n ? r * dinv[rw] : T(0));
+      } else {
+        sRb[t] = G::conv(r);
+      }
     }
     __syncwarp();
     if (act) {
 #pragma unroll
       for (int s = 0; s < V; ++s) {
         const int t = 32 * s + geo.lane;
-        const BT rb2 = sRb[t];
-        BT rrow[PM];
-        load_row<BT, PM>(sRb + t - b, rrow, p);
+        const BT rb2 = dinv ? G::conv(sR[t]) : sRb[t];   // own operand: R
+        const BT *rowr = sRb + t - b;                      // broadcast: Z
 #pragma unroll
-        for (int a = 0; a < PM; ++a)
-          if (a < p) G::add(acc.s[a], acc.c[a], rrow[a], rb2);
-        G::add(ns, nc, rb2, rb2);
+        for (int d = 0; d < PMH; ++d)
+          if (PM == 1 || d < PM / 2 || b < PM / 2) G::add(acc.s[d], acc.c[d], rowr[(b + d) & (PM - 1)], rb2);
+        G::add(ns, nc, rb2, rb2);   // ||R_c||^2 for the stopping test
       }
     }
     if (row < n) {
@@ -395,13 +405,13 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__rest
     __syncwarp();
     if (++pass == kFlushPasses / V) {
       pass = 0;
-      acc.flush(slotRho, p);
+      acc.flush(slotRho, PMH);
       *slotN += (double)ns;
       *slotN += (double)nc;
       ns = nc = 0.0f;
     }
   }
-  acc.flush(slotRho, p);
+  acc.flush(slotRho, PMH);
   *slotN += (double)ns;
   *slotN += (double)nc;
   const int E = k * p;
@@ -414,7 +424,8 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__rest
 template <typename T, int PM, int V>
 __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *__restrict__ R, int64_t n, int k,
                                                    int p, int global, const double *__restrict__ beta,
-                                                   const int *__restrict__ active, DevStatus *__restrict__ st) {
+                                                   const int *__restrict__ active, DevStatus *__restrict__ st,
+                                                   const T *__restrict__ dinv) {
   using VT = typename VecOf<T, V>::type;
   if (st->flags != 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) st->cur += 1;   // no other kernel of this launch reads it
@@ -446,6 +457,11 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
     if (row < n) {
       pv.v = reinterpret_cast<const VT *>(P)[o];
       rv.v = reinterpret_cast<const VT *>(R)[o];
+      if (dinv) {   // Z = M^{-1} R
+        const T di = dinv[row];
+#pragma unroll
+        for (int v = 0; v < V; ++v) rv.e[v] *= di;
+      }
     } else {
 #pragma unroll
       for (int v = 0; v < V; ++v) pv.e[v] = rv.e[v] = T(0);

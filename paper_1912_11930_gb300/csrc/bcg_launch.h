@@ -17,6 +17,8 @@ struct StreamGrids {
   int upd;       // K2 CTAs
   int pup;       // K3 CTAs
   int res;       // K0 CTAs
+  int alpha_circ;   // K1 stores alpha by circulant diagonals (symmetric product, half the terms)
+  int rho_circ;     // K2 stores rho by circulant diagonals
 };
 
 // Sizes the grids for n rows from the occupancy of each kernel variant (capped to whole waves of SMs).
@@ -27,16 +29,19 @@ template <typename T>
 cudaError_t launch_op_gram(const OpDesc &A, const T *P, const T *R, T *Q, int64_t n, int k, int p, int global,
                            const int *active, double *partA, double *partR, const DevStatus *st, int grid,
                            cudaStream_t s);
+// dinv (optional, n values): inverse diagonal of the Jacobi preconditioner; Z = M^{-1} R is formed on the
+// fly where Algorithm 1 needs it (NULL: M = I).
 template <typename T>
 cudaError_t launch_update_xr(T *X, T *R, const T *P, const T *Q, int64_t n, int k, int p, int global,
                              const double *lam, const int *active, double *partRho, double *partN,
-                             const DevStatus *st, int grid, cudaStream_t s);
+                             const DevStatus *st, int grid, cudaStream_t s, const T *dinv);
 template <typename T>
 cudaError_t launch_update_p(T *P, const T *R, int64_t n, int k, int p, int global, const double *beta,
-                            const int *active, DevStatus *st, int grid, cudaStream_t s);
+                            const int *active, DevStatus *st, int grid, cudaStream_t s, const T *dinv);
 template <typename T>
 cudaError_t launch_residual(const OpDesc &A, const T *X, const T *B, T *R, T *P, float *R32, float *P32, int64_t n,
-                            int k, double *partN, int grid, cudaStream_t s);
+                            int k, double *partN, int grid, cudaStream_t s, const T *dinv);
+cudaError_t launch_inv_diag(const OpDesc &A, int64_t n, double *dinv, int nsm, cudaStream_t s);
 
 template <typename T>
 cudaError_t launch_bdot(const T *X, const T *Y, int64_t n, int k, int p, double *part, int grid, cudaStream_t s);
@@ -54,10 +59,11 @@ cudaError_t launch_lp_bop(const OpDesc &A, const T *P, T *Q, int64_t n, int k, c
                           cudaStream_t s);
 template <typename T>
 cudaError_t launch_lp_gram(const T *X, const T *Y, int64_t n, int k, int p, int global, const int *active,
-                           double *part, int chunks, const DevStatus *st, cudaStream_t s);
+                           double *part, int chunks, const DevStatus *st, cudaStream_t s, const T *xscale);
 template <typename T>
 cudaError_t launch_lp_baxpy(T *OUT, const T *BASE, const T *Y, const double *C, int64_t n, int k, int p, int global,
-                            double sign, const int *active, DevStatus *st, int bump, cudaStream_t s);
+                            double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
+                            const T *bscale);
 template <typename T>
 cudaError_t launch_lp_colnorm(const T *R, int64_t n, int k, double *partN, int grid, const DevStatus *st,
                               cudaStream_t s);
@@ -69,10 +75,11 @@ bool small_needs_gws(int p);
 cudaError_t small_prepare(int p);
 cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int k, int p, int global,
                                 const int *active, double *lam, double *rho_rec, DevStatus *st, double *gws,
-                                cudaStream_t s);
+                                int alpha_circ, cudaStream_t s);
 cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int k, int p, int global,
                               double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
-                              const double *rho_rec, double *beta, DevStatus *st, double *gws, cudaStream_t s);
+                              const double *rho_rec, double *beta, DevStatus *st, double *gws, int rho_circ,
+                              cudaStream_t s);
 cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, int global, double *r0n2, double *rn2,
                                int *active, int *block_iters, double *lam, double *beta, DevStatus *st,
                                cudaStream_t s);

@@ -84,6 +84,22 @@ __device__ void transpose_into(const double *src, double *dst, int p) {
   __syncthreads();
 }
 
+// Symmetric product stored by circulant diagonals (p a power of two): src[b*p + d] = entry ((b + d) mod p, b)
+// for d < p/2, and for d = p/2 when b < p/2. dst[a*p + b] receives the full symmetric matrix.
+__device__ void unpack_circulant(const double *src, double *dst, int p) {
+  const int h = p / 2;
+  for (int e = threadIdx.x; e < p * p; e += blockDim.x) {
+    const int a = e / p, b = e - a * p;
+    const int d = (a - b) & (p - 1);
+    double v;
+    if (p == 1) v = src[0];
+    else if (d < h || (d == h && b < h)) v = src[b * p + d];
+    else v = src[a * p + ((b - a) & (p - 1))];
+    dst[e] = v;
+  }
+  __syncthreads();
+}
+
 // Block-wide max of |diag| (every thread passes its partial) -- result valid in all threads.
 __device__ double block_max(double v) {
   __shared__ double wmax[kSmallNT / 32];
@@ -133,7 +149,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
                                                            const double *__restrict__ partR, int nparts, int k,
                                                            int p, int global, const int *__restrict__ active,
                                                            double *__restrict__ lam, double *__restrict__ rho_rec,
-                                                           DevStatus *st, double *gws) {
+                                                           DevStatus *st, double *gws, int alpha_circ) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   const int pp = p * p;
@@ -151,7 +167,8 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
   __shared__ int bad;
   __shared__ double thresh;
   reduce_block(partA, nparts, k, p, global, jb, tmp, scr);
-  transpose_into(tmp, sA, p);
+  if (alpha_circ) unpack_circulant(tmp, sA, p);
+  else transpose_into(tmp, sA, p);
   reduce_block(partR, nparts, k, p, global, jb, tmp, scr);
   transpose_into(tmp, sR, p);
   for (int e = threadIdx.x; e < pp; e += blockDim.x) rho_rec[(int64_t)jb * pp + e] = sR[e];
@@ -217,7 +234,8 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
                                                          double *__restrict__ rn2, int *__restrict__ active,
                                                          int *__restrict__ block_iters,
                                                          const double *__restrict__ rho_rec,
-                                                         double *__restrict__ beta, DevStatus *st, double *gws) {
+                                                         double *__restrict__ beta, DevStatus *st, double *gws,
+                                                         int rho_circ) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   if (!active[jb]) return;
@@ -261,7 +279,8 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
   __shared__ int bad, piv;
   __shared__ double thresh;
   reduce_block(partRho, nparts, k, p, global, jb, tmp, scr);
-  transpose_into(tmp, sB, p);
+  if (rho_circ) unpack_circulant(tmp, sB, p);
+  else transpose_into(tmp, sB, p);
   for (int e = threadIdx.x; e < pp; e += blockDim.x) sM[e] = rho_rec[(int64_t)jb * pp + e];
   __syncthreads();
   {
@@ -456,19 +475,21 @@ cudaError_t small_prepare(int p) {
 
 cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int k, int p, int global,
                                 const int *active, double *lam, double *rho_rec, DevStatus *st, double *gws,
-                                cudaStream_t s) {
+                                int alpha_circ, cudaStream_t s) {
   const int nblk = global ? 1 : k / p;
   k_solve_lambda<<<nblk, kSmallNT, small_smem(p), s>>>(partA, partR, nparts, k, p, global, active, lam, rho_rec, st,
-                                                       small_needs_gws(p) ? gws : nullptr);
+                                                       small_needs_gws(p) ? gws : nullptr, alpha_circ);
   return cudaGetLastError();
 }
 
 cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int k, int p, int global,
                               double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
-                              const double *rho_rec, double *beta, DevStatus *st, double *gws, cudaStream_t s) {
+                              const double *rho_rec, double *beta, DevStatus *st, double *gws, int rho_circ,
+                              cudaStream_t s) {
   const int nblk = global ? 1 : k / p;
   k_solve_beta<<<nblk, kSmallNT, small_smem(p), s>>>(partRho, partN, nparts, k, p, global, tol2, r0n2, rn2, active,
-                                                     block_iters, rho_rec, beta, st, small_needs_gws(p) ? gws : nullptr);
+                                                     block_iters, rho_rec, beta, st, small_needs_gws(p) ? gws : nullptr,
+                                                     rho_circ);
   return cudaGetLastError();
 }
 

@@ -2,3 +2,14 @@
 #include <type_traits>
 #define BCG_T double
 #include "bcg_stream.inc"
+
+namespace bcgk {
+cudaError_t launch_inv_diag(const OpDesc &A, int64_t n, double *dinv, int nsm, cudaStream_t s) {
+  return with_op(A.kind, [&](auto ok) -> cudaError_t {
+    constexpr int OPK = decltype(ok)::value;
+    const int grid = (int)std::min<int64_t>((n + 255) / 256, (int64_t)nsm * 8);
+    k_inv_diag<double, OPK><<<grid, 256, 0, s>>>(A, n, dinv);
+    return cudaGetLastError();
+  });
+}
+}  // namespace bcgk

@@ -346,3 +346,58 @@ def test_gradient_dense_and_finite_differences():
         fd = (np.sum(Wt * np.linalg.solve(Ap, B)) - np.sum(Wt * np.linalg.solve(Am, B))) / (2 * h)
         an = g[e] + (g[pos[(j, i)]] if i != j else 0.0)
         assert abs(fd - an) <= 1e-6 * max(abs(an), 1e-3), (i, j, fd, an)
+
+
+# ---- Jacobi preconditioner (Algorithm 1 with M = diag(A)) --------------------------------------------------
+def test_jacobi_k1_is_scipy_pcg():
+    M = W.varcoef3d(6, 5, 4, seed=2)
+    A = M.to_scipy()
+    b = W.rhs(M.n, 1, seed=5)[:, 0]
+    import scipy.sparse as sps
+    Minv = sps.diags(1.0 / A.diagonal())
+    xs = []
+    cg(A, b, x0=np.zeros(M.n), rtol=0.0, atol=0.0, maxiter=20, M=Minv, callback=lambda x: xs.append(x.copy()))
+    for m in (1, 3, 8, 15):
+        res = O.solve(A, b[:, None], p=1, sub="hybrid", tol=0.0, maxit=m, precond="jacobi")
+        assert _rel(res.X[:, 0], xs[m - 1]) < 1e-10, m
+
+
+@pytest.mark.parametrize("sub,k,p", [("hybrid", 8, 4), ("global", 8, 4), ("classical", 4, 4)])
+@pytest.mark.parametrize("m", [1, 2, 3])
+def test_jacobi_galerkin_closed_form(sub, k, p, m):
+    """Preconditioned block CG: X^m - X^0 is the A-norm-optimal correction in the block Krylov space of
+    M^{-1} A and M^{-1} R^0 (the subalgebra's space)."""
+    Mx = W.varcoef3d(5, 4, 3, seed=3)
+    A = Mx.to_scipy()
+    Ad = A.toarray()
+    dinv = 1.0 / np.diag(Ad)
+    B = W.rhs(Mx.n, k, seed=6)
+    kind, pp = O.canonical_subalgebra(sub, k, p)
+    res = O.solve(A, B, p=p, sub=sub, tol=0.0, maxit=m, precond="jacobi")
+    q = k // pp
+    Xg = np.zeros_like(B)
+    if kind == "hybrid":
+        for j in range(q):
+            blk = slice(j * pp, (j + 1) * pp)
+            V = _block_krylov_basis(dinv[:, None] * Ad, dinv[:, None] * B[:, blk], m)
+            Xg[:, blk] = V @ np.linalg.solve(V.T @ Ad @ V, V.T @ B[:, blk])
+    else:
+        Ahat = sla.block_diag(*([Ad] * q))
+        Dhat = np.concatenate([dinv] * q)
+        Bhat = np.vstack([B[:, j * pp:(j + 1) * pp] for j in range(q)])
+        V = _block_krylov_basis(Dhat[:, None] * Ahat, Dhat[:, None] * Bhat, m)
+        C = V @ np.linalg.solve(V.T @ Ahat @ V, V.T @ Bhat)
+        for j in range(q):
+            Xg[:, j * pp:(j + 1) * pp] = C[j * Mx.n:(j + 1) * Mx.n]
+    assert _rel(res.X, Xg) < 1e-9
+
+
+def test_jacobi_converges_to_dense_solution():
+    Mx = W.stencil27(6, seed=4)
+    A = Mx.to_scipy()
+    B = W.rhs(Mx.n, 8, seed=7)
+    res = O.solve(A, B, p=4, sub="hybrid", tol=1e-11, maxit=500, precond="jacobi")
+    assert res.status == O.OK
+    assert _rel(res.X, np.linalg.solve(A.toarray(), B)) < 1e-8
+    plain = O.solve(A, B, p=4, sub="hybrid", tol=1e-11, maxit=500)
+    assert res.iters <= plain.iters + 2
