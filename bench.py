@@ -34,10 +34,21 @@ WORKLOAD = dict(name="poisson3d_128_csr_k32_hybrid_p8_fp64", grid=128, k=32, p=8
 # to a time-to-tolerance in the reference arm.
 REF_ITERS = 354
 ORACLE_SAMPLE_ITERS = 3
-# DRAM bytes per launch of the dominant kernel from an ncu capture (profiles/k_op_gram_poisson3d_96_*.md,
-# scaled by rows to 128^3), valid only for the kernel source it was taken on (sha256 prefix of the
-# bcg_kernels.cuh text from apply_row to the end of k_op_gram); reported as null once that source changes.
-TRAFFIC = {("op_gram", "poisson3d_128_csr_k32_hybrid_p8_fp64"): ("7908c5fc0ec73b8b", 1.986e9)}
+# DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
+# capture at 96^3 (profiles/<kernel>_poisson3d_96_*.md), scaled by rows to the 128^3 launch. Valid only for the
+# device source the capture was taken on: sha256 prefix of KERNEL_SOURCES concatenated; reported as null once
+# that source changes.
+KERNEL_SOURCES = ["bcg_kernels.cuh", "bcg_kernels_wc.cuh", "bcg_kernels_lp.cuh", "bcg_stream.inc"]
+TRAFFIC = {}
+
+
+def kernel_source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1912_11930_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def peaks():
@@ -160,7 +171,8 @@ def run_reference(args, rank, world):
 
 # ---------------------------------------------------------------------------------------------------------------
 # Other workloads (not the default line): measured with `python bench.py --workload NAME`
-EXTRA_WORKLOADS = ("poisson2d_64_k8", "varcoef3d_160_k64_mixed", "stencil27_100_k16_autograd", "poisson3d_96_sweep")
+EXTRA_WORKLOADS = ("poisson2d_64_k8", "varcoef3d_160_k64_mixed", "varcoef3d_160_k64_jacobi", "stencil27_100_k16_autograd",
+                   "poisson3d_96_sweep")
 
 
 def time_solve(bcg, torch, M, B, *, k, p, sub, prec, form="csr", tol=1e-8, reps=2, dev=None, opts=None, warm=True):
@@ -218,6 +230,25 @@ def run_extra(name, args):
         out.update(value=rows[0]["s"], dtype="f32 inner, f64 refinement",
                    config={"workload": "varcoef3d_160_stencil_k64_hybrid_p16", "n": M.n, "k": k, "p": 16},
                    results=rows, mixed_vs_fp64_speedup_at_1e8=rows[2]["s"] / rows[1]["s"])
+    elif name == "varcoef3d_160_k64_jacobi":
+        # the log-normal coefficients' contrast is what a diagonal preconditioner removes: M = I against
+        # M = diag(A), FP64 and the mixed form, time to 1e-8
+        M = W.varcoef3d(160, seed=0)
+        k = 64
+        B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev)
+        rows = []
+        for prec in ("fp64", "fp32_refine"):
+            for pre in (0, 1):
+                t, r, _ = time_solve(bcg, torch, M, B, k=k, p=16, sub="hybrid", prec=prec, form="stencil", tol=1e-8,
+                                     reps=1, dev=dev, opts={"precond": pre})
+                rows.append(dict(prec=prec, precond="jacobi" if pre else "none", s=t, iterations=r.iters,
+                                 outer=r.outer_iters, status=bcg.STATUS_NAMES[r.status],
+                                 max_rel_res_true=r.max_rel_res_true))
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        out.update(value=rows[1]["s"], dtype="f64 (and f32 inner, f64 refinement)",
+                   config={"workload": "varcoef3d_160_stencil_k64_hybrid_p16_jacobi", "n": M.n, "k": k, "p": 16},
+                   results=rows, jacobi_speedup_fp64=rows[0]["s"] / rows[1]["s"],
+                   jacobi_speedup_mixed=rows[2]["s"] / rows[3]["s"])
     elif name == "stencil27_100_k16_autograd":
         from paper_1912_11930_gb300.autograd import bcg_solve_autograd
         M = W.stencil27(100, seed=0)
@@ -377,13 +408,8 @@ def main():
     # FP64-pipe roofline of the dominant kernel: only the algorithmic flops that run as FP64 FMAs count
     # (the block products run as error-free FP32 arithmetic and are reported beside it)
     traffic = None
-    import hashlib
-    src = os.path.join(ROOT, "paper_1912_11930_gb300", "csrc", "bcg_kernels.cuh")
-    text = open(src).read()
-    region = text[text.index("// One row of BOP"):text.index("// K2: X += P lambda")]
-    cur_sha = hashlib.sha256(region.encode()).hexdigest()[:16]
     ent = TRAFFIC.get((dom, w["name"]))
-    if ent and ent[0] == cur_sha:
+    if ent and ent[0] == kernel_source_sha():
         traffic = ent[1]
     roofline = {"bound": "alu", "kernel": dom, "achieved": d["fp64_tflops"], "peak": NOMINAL_FP64_TFLOPS,
                 "unit": "TFLOP/s", "frac": d["fp64_tflops"] / NOMINAL_FP64_TFLOPS, "traffic": traffic,

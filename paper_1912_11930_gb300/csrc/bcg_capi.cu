@@ -162,10 +162,10 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
   CK(small_prepare(h->p));
   CK(stream_grids<double>(h->opkind, h->n, h->k, h->p, h->global, h->nsm, &h->g64));
-  int np = std::max(h->g64.op, std::max(h->g64.upd, h->g64.res));
+  int np = std::max(std::max(h->g64.op, h->g64.upd_zs), std::max(h->g64.upd, h->g64.res));
   if (h->prec == BCG_FP32_REFINE) {
     CK(stream_grids<float>(h->opkind, h->n, h->k, h->p, h->global, h->nsm, &h->g32));
-    np = std::max(np, std::max(h->g32.op, std::max(h->g32.upd, h->g32.res)));
+    np = std::max(np, std::max(std::max(h->g32.op, h->g32.upd_zs), std::max(h->g32.upd, h->g32.res)));
   }
   h->nparts = np;
   const size_t nk = (size_t)h->n * h->k;
@@ -238,6 +238,7 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
                             cudaEvent_t *ev = nullptr) {
   cudaStream_t s = h->stream;
 #define REC(i) do { if (ev) CK(cudaEventRecord(ev[i], s)); } while (0)
+  const int gu = h->precond ? g.upd_zs : g.upd, gp = h->precond ? g.pup_zs : g.pup;
   REC(0);
   CK(launch_op_gram<T>(A, P, R, Q, h->n, h->k, h->p, h->global, h->active, h->partA, h->partR, h->st, g.op, s));
   REC(1); REC(2);
@@ -245,12 +246,12 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
                          h->gws, g.alpha_circ, s));
   REC(3); REC(4);
   CK(launch_update_xr<T>(X, R, P, Q, h->n, h->k, h->p, h->global, h->lam, h->active, h->partRho, h->partN, h->st,
-                         g.upd, s, dinv_of<T>(h)));
+                         gu, s, dinv_of<T>(h)));
   REC(5); REC(6);
-  CK(launch_solve_beta(h->partRho, h->partN, g.upd, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
+  CK(launch_solve_beta(h->partRho, h->partN, gu, gu, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
                        h->block_iters, h->rho_rec, h->beta, h->st, h->gws, g.rho_circ, s));
   REC(7); REC(8);
-  CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, g.pup, s, dinv_of<T>(h)));
+  CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv_of<T>(h)));
   REC(9);
 #undef REC
   return BCG_OK;
@@ -272,8 +273,8 @@ bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T 
   CK(launch_lp_baxpy<T>(R, R, Q, h->lam, h->n, h->k, h->p, h->global, -1.0, h->active, h->st, 0, s, nullptr));
   // rho = <<Z, R>> with Z = M^{-1} R formed on the fly
   CK(launch_lp_gram<T>(R, R, h->n, h->k, h->p, h->global, h->active, h->partRho, ch, h->st, s, dinv_of<T>(h)));
-  CK(launch_lp_colnorm<T>(R, h->n, h->k, h->partN, ch, h->st, s));
-  CK(launch_solve_beta(h->partRho, h->partN, ch, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
+  CK(launch_lp_colnorm<T>(R, h->n, h->k, h->partN, g.res, h->st, s));   // a full-GPU grid, like K0's
+  CK(launch_solve_beta(h->partRho, h->partN, ch, g.res, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
                        h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s));
   CK(launch_lp_baxpy<T>(Q, R, P, h->beta, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 1, s, dinv_of<T>(h)));
   return BCG_OK;

@@ -393,8 +393,9 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
 }
 
 // ---------------------------------------------------------------------------------------------------
-// K2: X += P lambda, R -= Q lambda (BAXPY x 2), then rho^i = <<R, R>>_S and the per-column ||R_c||^2.
-template <typename T, int PM>
+// K2: X += P lambda, R -= Q lambda (BAXPY x 2), then rho^i = <<Z, R>>_S and the per-column ||R_c||^2.
+// ZS: Z = M^{-1} R with the Jacobi preconditioner (dinv = 1 / diag(A)); otherwise Z = R and dinv is unused.
+template <typename T, int PM, bool ZS>
 __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restrict__ R, const T *__restrict__ P,
                                                    const T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                    const double *__restrict__ lam, const int *__restrict__ active,
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
       const int64_t r = row0 + u * rpp + g;
       const bool live = act && r < n;
       rb[u] = live ? G::conv(rv[u]) : G::zero();
-      if (slot) sRb[u * kNT + g * k + c] = live ? (dinv ? G::conv(rv[u] * dinv[r]) : rb[u]) : G::zero();
+      if (slot) sRb[u * kNT + g * k + c] = live ? (ZS ? G::conv(rv[u] * dinv[r]) : rb[u]) : G::zero();
     }
     row_sync(wl);
     if (act) {
@@ -517,8 +518,8 @@ __global__ void __launch_bounds__(kNT) k_update_xr(T *__restrict__ X, T *__restr
 }
 
 // ---------------------------------------------------------------------------------------------------
-// K3: P = R + P beta (BAXPY with the direction-update sign read as "+").
-template <typename T, int PM>
+// K3: P = Z + P beta (BAXPY with the direction-update sign read as "+"); ZS as in K2.
+template <typename T, int PM, bool ZS>
 __global__ void __launch_bounds__(kNT) k_update_p(T *__restrict__ P, const T *__restrict__ R, int64_t n, int k,
                                                   int p, int global, const double *__restrict__ beta,
                                                   const int *__restrict__ active, DevStatus *__restrict__ st,
@@ -554,7 +555,7 @@ __global__ void __launch_bounds__(kNT) k_update_p(T *__restrict__ P, const T *__
       pv[u] = rv[u] = T(0);
       if (act && r < n) {
         pv[u] = P[r * k + c];
-        rv[u] = dinv ? R[r * k + c] * dinv[r] : R[r * k + c];   // Z = M^{-1} R
+        rv[u] = ZS ? R[r * k + c] * dinv[r] : R[r * k + c];   // Z = M^{-1} R
       }
       if (slot) sP[u * kNT + g * k + c] = pv[u];
     }

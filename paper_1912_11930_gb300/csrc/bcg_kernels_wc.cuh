@@ -187,12 +187,23 @@ __device__ __forceinline__ void wc_cta_reduce(const double *red, int k, int p, d
 
 template <typename T>
 __host__ __device__ constexpr size_t wc_tile_bytes(int V) { return (size_t)32 * V * sizeof(T); }
-// per-warp tiles: K1 3 broadcast tiles (8 bytes per element max); K2 4 T tiles + 1 broadcast; K3 3 T tiles
-__host__ __device__ constexpr size_t wc_op_smem(int p, int V) {
-  return (size_t)kWarps * 3 * 32 * V * 8 + 2 * (size_t)kNT * p * sizeof(double);
+// Per-warp tiles: K1 3 broadcast tiles (P, Q, R as Dot2 operands); K2 4 T tiles (X, R, P, Q) + 1 broadcast
+// tile; K3 3 T tiles. A broadcast element is a float for FP32 data and a float pair for FP64 data.
+template <typename T>
+__host__ __device__ constexpr size_t wc_bt_size() { return sizeof(T) == 4 ? 4 : 8; }
+template <typename T>
+__host__ __device__ constexpr size_t wc_op_warp_bytes(int V) { return (size_t)3 * 32 * V * wc_bt_size<T>(); }
+template <typename T>
+__host__ __device__ constexpr size_t wc_upd_warp_bytes(int V) {
+  return (size_t)32 * V * (4 * sizeof(T) + wc_bt_size<T>());
 }
-__host__ __device__ constexpr size_t wc_upd_smem(int k, int p, int global, size_t tsize, int V) {
-  return align16((size_t)kWarps * 5 * 32 * V * 8 + (size_t)(global ? 1 : k / p) * p * p * tsize) +
+template <typename T>
+__host__ __device__ constexpr size_t wc_op_smem(int p, int V) {
+  return (size_t)kWarps * wc_op_warp_bytes<T>(V) + 2 * (size_t)kNT * p * sizeof(double);
+}
+template <typename T>
+__host__ __device__ constexpr size_t wc_upd_smem(int k, int p, int global, int V) {
+  return align16((size_t)kWarps * wc_upd_warp_bytes<T>(V) + (size_t)(global ? 1 : k / p) * p * p * sizeof(T)) +
          (size_t)kNT * (p + 1) * sizeof(double);
 }
 __host__ __device__ constexpr size_t wc_pup_smem(int k, int p, int global, size_t tsize, int V) {
@@ -217,9 +228,10 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_op_gram(OpDesc A, c
   extern __shared__ __align__(16) unsigned char smem[];
   WcGeom geo;
   geo.init(n, k, V);
-  BT *tile = reinterpret_cast<BT *>(smem + (size_t)geo.warp * 3 * 32 * V * 8);
+  static_assert(sizeof(BT) == wc_bt_size<T>(), "broadcast tile element");
+  BT *tile = reinterpret_cast<BT *>(smem + (size_t)geo.warp * wc_op_warp_bytes<T>(V));
   BT *sP = tile, *sQ = tile + 32 * V, *sR = tile + 64 * V;
-  double *redA = reinterpret_cast<double *>(smem + (size_t)kWarps * 3 * 32 * V * 8);
+  double *redA = reinterpret_cast<double *>(smem + (size_t)kWarps * wc_op_warp_bytes<T>(V));
   double *redR = redA + kNT * p;
   const int c = geo.col, j = c / p, b = c - j * p;
   const bool act = block_active(active, global, j);
@@ -288,9 +300,14 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_op_gram(OpDesc A, c
 }
 
 // ---------------------------------------------------------------------------------------------------
-// K2 (warp-chunk): X += P lambda, R -= Q lambda, rho = <<R, R>>_S, column norms.
-template <typename T, int PM, int V>
-__global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__restrict__ X, T *__restrict__ R, const T *__restrict__ P,
+// K2 (warp-chunk): X += P lambda, R -= Q lambda, rho = <<Z, R>>_S, column norms (ZS: Z = M^{-1} R).
+// K2 keeps fewer live values than K1: its unpreconditioned FP32 instantiations up to p = 8 fit 64 registers
+// (4 CTAs per SM)
+template <typename T, int PM, bool ZS>
+constexpr int wc_min_ctas_upd() { return (sizeof(T) == 4 && PM <= 8 && !ZS) ? 4 : wc_min_ctas<PM>(); }
+
+template <typename T, int PM, int V, bool ZS>
+__global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_xr(T *__restrict__ X, T *__restrict__ R, const T *__restrict__ P,
                                                     const T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                     const double *__restrict__ lam, const int *__restrict__ active,
                                                     double *__restrict__ partRho, double *__restrict__ partN,
@@ -302,13 +319,14 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__rest
   extern __shared__ __align__(16) unsigned char smem[];
   WcGeom geo;
   geo.init(n, k, V);
-  unsigned char *wbase = smem + (size_t)geo.warp * 5 * 32 * V * 8;
+  static_assert(sizeof(BT) == wc_bt_size<T>(), "broadcast tile element");
+  unsigned char *wbase = smem + (size_t)geo.warp * wc_upd_warp_bytes<T>(V);
   T *sX = reinterpret_cast<T *>(wbase);
   T *sR = sX + 32 * V, *sP = sR + 32 * V, *sQ = sP + 32 * V;
   BT *sRb = reinterpret_cast<BT *>(wbase + 4 * 32 * V * sizeof(T));
   const int nblk = global ? 1 : k / p;
-  T *sL = reinterpret_cast<T *>(smem + (size_t)kWarps * 5 * 32 * V * 8);
-  double *red = reinterpret_cast<double *>(smem + align16((size_t)kWarps * 5 * 32 * V * 8 +
+  T *sL = reinterpret_cast<T *>(smem + (size_t)kWarps * wc_upd_warp_bytes<T>(V));
+  double *red = reinterpret_cast<double *>(smem + align16((size_t)kWarps * wc_upd_warp_bytes<T>(V) +
                                                           (size_t)nblk * p * p * sizeof(T)));
   double *nred = red + kNT * p;
   for (int e = threadIdx.x; e < nblk * p * p; e += blockDim.x) sL[e] = (T)lam[e];
@@ -375,7 +393,7 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__rest
       sX[t] = x;
       sR[t] = r;
       // broadcast Z = M^{-1} R (R without a preconditioner); the own operand R is re-read from sR below
-      if (dinv) {
+      if constexpr (ZS) {
         const int64_t rw = R0 + (int64_t)s * geo.gr + geo.ro;
         sRb[t] = G::conv(rw < n ? r * dinv[rw] : T(0));
       } else {
@@ -387,7 +405,7 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__rest
 #pragma unroll
       for (int s = 0; s < V; ++s) {
         const int t = 32 * s + geo.lane;
-        const BT rb2 = dinv ? G::conv(sR[t]) : sRb[t];   // own operand: R
+        const BT rb2 = ZS ? G::conv(sR[t]) : sRb[t];   // own operand: R
         const BT *rowr = sRb + t - b;                      // broadcast: Z
 #pragma unroll
         for (int d = 0; d < PMH; ++d)
@@ -420,8 +438,8 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_update_xr(T *__rest
 }
 
 // ---------------------------------------------------------------------------------------------------
-// K3 (warp-chunk): P = R + P beta.
-template <typename T, int PM, int V>
+// K3 (warp-chunk): P = Z + P beta (ZS: Z = M^{-1} R, else Z = R).
+template <typename T, int PM, int V, bool ZS>
 __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *__restrict__ R, int64_t n, int k,
                                                    int p, int global, const double *__restrict__ beta,
                                                    const int *__restrict__ active, DevStatus *__restrict__ st,
@@ -457,7 +475,7 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
     if (row < n) {
       pv.v = reinterpret_cast<const VT *>(P)[o];
       rv.v = reinterpret_cast<const VT *>(R)[o];
-      if (dinv) {   // Z = M^{-1} R
+      if constexpr (ZS) {   // Z = M^{-1} R
         const T di = dinv[row];
 #pragma unroll
         for (int v = 0; v < V; ++v) rv.e[v] *= di;

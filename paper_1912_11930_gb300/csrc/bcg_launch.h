@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "bcg_kernels.cuh"
@@ -16,6 +17,8 @@ struct StreamGrids {
   int op;        // K1 CTAs
   int upd;       // K2 CTAs
   int pup;       // K3 CTAs
+  int upd_zs;    // K2 CTAs, Jacobi-preconditioned instantiation
+  int pup_zs;    // K3 CTAs, Jacobi-preconditioned instantiation
   int res;       // K0 CTAs
   int alpha_circ;   // K1 stores alpha by circulant diagonals (symmetric product, half the terms)
   int rho_circ;     // K2 stores rho by circulant diagonals
@@ -76,8 +79,9 @@ cudaError_t small_prepare(int p);
 cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int k, int p, int global,
                                 const int *active, double *lam, double *rho_rec, DevStatus *st, double *gws,
                                 int alpha_circ, cudaStream_t s);
-cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int k, int p, int global,
-                              double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
+// nparts: partial rows of rho; nparts_n: partial rows of the column norms
+cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int nparts_n, int k, int p,
+                              int global, double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
                               const double *rho_rec, double *beta, DevStatus *st, double *gws, int rho_circ,
                               cudaStream_t s);
 cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, int global, double *r0n2, double *rn2,

@@ -149,7 +149,8 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
                                                            const double *__restrict__ partR, int nparts, int k,
                                                            int p, int global, const int *__restrict__ active,
                                                            double *__restrict__ lam, double *__restrict__ rho_rec,
-                                                           DevStatus *st, double *gws, int alpha_circ) {
+                                                           DevStatus *st, double *gws, int alpha_circ,
+                                                           int split) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   const int pp = p * p;
@@ -205,6 +206,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
     if (threadIdx.x == 0) flag_breakdown(st);
     return;
   }
+  if (split) return;   // k_trsm_cols solves for the columns of lambda from L and rho_rec (both in gws)
   // L Y = rho_rec, then L^T lambda = Y; one thread per right-hand-side column b
   for (int b = threadIdx.x; b < p; b += blockDim.x) {
     for (int a = 0; a < p; ++a) {
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
                                                          int *__restrict__ block_iters,
                                                          const double *__restrict__ rho_rec,
                                                          double *__restrict__ beta, DevStatus *st, double *gws,
-                                                         int rho_circ) {
+                                                         int rho_circ, int nparts_n, int split) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   if (!active[jb]) return;
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
   double *sm = gws ? gws + (int64_t)jb * small_ws_doubles_dev(p) : sm_dyn;
   {
     double *ncol = sm, *nscr = sm + kNT;   // column norms of this block, scratch
-    det_reduce(c1 - c0, nparts, [&](int pi, int c) { return partN[(int64_t)pi * k + c0 + c]; }, ncol, nscr);
+    det_reduce(c1 - c0, nparts_n, [&](int pi, int c) { return partN[(int64_t)pi * k + c0 + c]; }, ncol, nscr);
   }
   bool conv = true, finite = true;
   for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
@@ -274,8 +276,9 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
   }
   double *sM = sm;          // rho_rec (row-major), LU-factored in place
   double *sB = sM + pp;     // right-hand sides rho (row-major), become beta
-  double *tmp = sB + pp;
+  double *tmp = sB + pp;    // reduction output, then (split) the pivot rows as ints
   double *scr = tmp + pp;
+  int *pivots = reinterpret_cast<int *>(tmp);
   __shared__ int bad, piv;
   __shared__ double thresh;
   reduce_block(partRho, nparts, k, p, global, jb, tmp, scr);
@@ -311,6 +314,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
     }
     if (threadIdx.x == 0) {
       piv = best;
+      if (split) pivots[a] = best;
       if (!(bv > thresh)) bad = 1;
     }
     __syncthreads();
@@ -318,7 +322,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
     if (piv != a) {
       for (int col = threadIdx.x; col < p; col += blockDim.x) {
         double t = sM[a * p + col]; sM[a * p + col] = sM[piv * p + col]; sM[piv * p + col] = t;
-        t = sB[a * p + col]; sB[a * p + col] = sB[piv * p + col]; sB[piv * p + col] = t;
+        if (!split) { t = sB[a * p + col]; sB[a * p + col] = sB[piv * p + col]; sB[piv * p + col] = t; }
       }
     }
     __syncthreads();
@@ -326,8 +330,9 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
     for (int i = a + 1 + threadIdx.x; i < p; i += blockDim.x) sM[i * p + a] /= ua;   // multipliers
     __syncthreads();
     const int m = p - a - 1;
-    for (int e = threadIdx.x; e < m * (m + p); e += blockDim.x) {
-      const int i = a + 1 + e / (m + p), col = e % (m + p);
+    const int w = split ? m : m + p;   // split: the right-hand sides are left to k_trsm_cols
+    for (int e = threadIdx.x; e < m * w; e += blockDim.x) {
+      const int i = a + 1 + e / w, col = e % w;
       const double l = sM[i * p + a];
       if (col < m) sM[i * p + a + 1 + col] -= l * sM[a * p + a + 1 + col];
       else sB[i * p + (col - m)] -= l * sB[a * p + (col - m)];
@@ -336,6 +341,10 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
   }
   if (bad) {
     if (threadIdx.x == 0) flag_breakdown(st);
+    return;
+  }
+  if (split) {   // k_trsm_cols applies the pivots and both substitutions
+    if (threadIdx.x == 0) atomicMax(&st->iter, it);
     return;
   }
   for (int b = threadIdx.x; b < p; b += blockDim.x) {
@@ -356,6 +365,112 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
     return;
   }
   if (threadIdx.x == 0) atomicMax(&st->iter, it);
+}
+
+// Triangular solves of the large-block BSOLVEs, spread over the right-hand-side columns: CTA (jb, g) solves
+// columns [8g, 8g + 8) of block jb. The factors come from k_solve_lambda / k_solve_beta (split mode) in the
+// block's global workspace ws = gws + jb * small_ws_doubles(p): M = ws (p x p row-major), B = ws + p*p
+// (right-hand sides, row-major), pivots (LU) as ints at ws + 2*p*p.
+//   chol = 1: M holds L (lower) of alpha = L L^T; out = L^{-T} L^{-1} B  (lambda)
+//   chol = 0: M holds P rho_rec = L U (unit L below the diagonal, U on and above it) with the row
+//             interchanges `pivots`; out = U^{-1} L^{-1} P B  (beta)
+// Each substitution is column oriented (B[i] -= M[i][a] B[a] after B[a] is final) and walks the factor in
+// panels of 32 columns (or rows) staged in shared memory with coalesced loads.
+constexpr int kTrsmCols = 8;
+constexpr int kTrsmPanel = 32;
+__host__ __device__ inline size_t trsm_smem(int p) {
+  return ((size_t)p * kTrsmPanel + (size_t)p * kTrsmCols) * sizeof(double);
+}
+
+__global__ void __launch_bounds__(256) k_trsm_cols(int p, int chol, const double *__restrict__ gws,
+                                                   const int *__restrict__ active, double *__restrict__ out,
+                                                   DevStatus *st) {
+  if (st->flags != 0) return;
+  const int jb = blockIdx.x;
+  if (!active[jb]) return;   // frozen block: its lambda / beta were zeroed by the factorization kernel
+  const int pp = p * p;
+  const double *M = gws + (int64_t)jb * small_ws_doubles_dev(p);
+  const double *Bg = M + pp;
+  const int *pivots = reinterpret_cast<const int *>(M + 2 * pp);
+  const int c0 = blockIdx.y * kTrsmCols;
+  extern __shared__ __align__(16) double sm_dyn[];
+  double *pan = sm_dyn;                          // panel: up to p x 32
+  double *bs = pan + (size_t)p * kTrsmPanel;     // bs[i * 8 + cc] = B[i][c0 + cc]
+  const int NT = blockDim.x;
+  for (int e = threadIdx.x; e < p * kTrsmCols; e += NT) {
+    const int i = e / kTrsmCols, cc = e % kTrsmCols;
+    bs[e] = Bg[(int64_t)i * p + c0 + cc];
+  }
+  __syncthreads();
+  if (!chol) {   // row interchanges in factorization order
+    if (threadIdx.x < kTrsmCols)
+      for (int a = 0; a < p; ++a) {
+        const int r = pivots[a];
+        if (r != a) {
+          const double t = bs[a * kTrsmCols + threadIdx.x];
+          bs[a * kTrsmCols + threadIdx.x] = bs[r * kTrsmCols + threadIdx.x];
+          bs[r * kTrsmCols + threadIdx.x] = t;
+        }
+      }
+    __syncthreads();
+  }
+  // forward: column panels pan[(i - a0) * 32 + j] = M[i][a0 + j], rows i >= a0
+  for (int a0 = 0; a0 < p; a0 += kTrsmPanel) {
+    const int rows = p - a0;
+    for (int e = threadIdx.x; e < rows * kTrsmPanel; e += NT) {
+      const int r = e / kTrsmPanel, j = e % kTrsmPanel;
+      pan[e] = M[(int64_t)(a0 + r) * p + a0 + j];
+    }
+    __syncthreads();
+    for (int j = 0; j < kTrsmPanel; ++j) {
+      const int a = a0 + j;
+      if (chol) {
+        if (threadIdx.x < kTrsmCols) bs[a * kTrsmCols + threadIdx.x] /= pan[j * kTrsmPanel + j];
+        __syncthreads();
+      }
+      for (int e = threadIdx.x; e < (p - a - 1) * kTrsmCols; e += NT) {
+        const int i = a + 1 + e / kTrsmCols, cc = e % kTrsmCols;
+        bs[i * kTrsmCols + cc] -= pan[(i - a0) * kTrsmPanel + j] * bs[a * kTrsmCols + cc];
+      }
+      __syncthreads();
+    }
+  }
+  // backward, a = p-1 .. 0
+  for (int a1 = p; a1 > 0; a1 -= kTrsmPanel) {
+    const int a0 = a1 - kTrsmPanel;
+    if (chol) {   // row panel of L: pan[j * a1 + i] = L[a0 + j][i], i < a1 (L^T[i][a] = L[a][i])
+      for (int e = threadIdx.x; e < kTrsmPanel * a1; e += NT) {
+        const int j = e / a1, i = e % a1;
+        pan[e] = M[(int64_t)(a0 + j) * p + i];
+      }
+    } else {      // column panel of U: pan[i * 32 + j] = U[i][a0 + j], i < a1
+      for (int e = threadIdx.x; e < a1 * kTrsmPanel; e += NT) {
+        const int i = e / kTrsmPanel, j = e % kTrsmPanel;
+        pan[e] = M[(int64_t)i * p + a0 + j];
+      }
+    }
+    __syncthreads();
+    for (int j = kTrsmPanel - 1; j >= 0; --j) {
+      const int a = a0 + j;
+      const double d = chol ? pan[j * a1 + a] : pan[a * kTrsmPanel + j];
+      if (threadIdx.x < kTrsmCols) bs[a * kTrsmCols + threadIdx.x] /= d;
+      __syncthreads();
+      for (int e = threadIdx.x; e < a * kTrsmCols; e += NT) {
+        const int i = e / kTrsmCols, cc = e % kTrsmCols;
+        const double m = chol ? pan[j * a1 + i] : pan[i * kTrsmPanel + j];
+        bs[i * kTrsmCols + cc] -= m * bs[a * kTrsmCols + cc];
+      }
+      __syncthreads();
+    }
+  }
+  bool fin = true;
+  double *oj = out + (int64_t)jb * pp;
+  for (int e = threadIdx.x; e < p * kTrsmCols; e += NT) {
+    const int i = e / kTrsmCols, cc = e % kTrsmCols;
+    oj[(int64_t)i * p + c0 + cc] = bs[e];
+    if (!isfinite(bs[e])) fin = false;
+  }
+  if (!__syncthreads_and(fin) && threadIdx.x == 0) flag_breakdown(st);
 }
 
 // Start of a solve: reduce the initial residual norms, mark zero columns converged, reset the status.
@@ -459,8 +574,11 @@ int lp_chunks(int64_t n, int k, int p, int nsm) {
   if (ch > max_ch) ch = max_ch;
   return (int)(ch < 1 ? 1 : ch);
 }
-bool small_needs_gws(int p) { return small_ws_doubles_dev(p) * sizeof(double) > kSmallSmemMax; }
+// Large blocks keep the p x p matrices in global memory (the column-parallel triangular solves read them
+// there); smaller ones in shared memory unless they do not fit.
+bool small_needs_gws(int p) { return p > kMaxP || small_ws_doubles_dev(p) * sizeof(double) > kSmallSmemMax; }
 static size_t small_smem(int p) { return small_needs_gws(p) ? 0 : small_ws_doubles_dev(p) * sizeof(double); }
+static bool small_split(int p) { return p > kMaxP; }
 
 cudaError_t small_prepare(int p) {
   const size_t sm = small_smem(p);
@@ -470,27 +588,44 @@ cudaError_t small_prepare(int p) {
     e = cudaFuncSetAttribute(k_solve_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
+  if (small_split(p) && trsm_smem(p) > 48 * 1024)
+    return cudaFuncSetAttribute(k_trsm_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem(p));
   return cudaSuccess;
+}
+
+static cudaError_t launch_trsm(int p, int nblk, int chol, const double *gws, const int *active, double *out,
+                               DevStatus *st, cudaStream_t s) {
+  dim3 grid((unsigned)nblk, (unsigned)(p / kTrsmCols));
+  k_trsm_cols<<<grid, 256, trsm_smem(p), s>>>(p, chol, gws, active, out, st);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int k, int p, int global,
                                 const int *active, double *lam, double *rho_rec, DevStatus *st, double *gws,
                                 int alpha_circ, cudaStream_t s) {
   const int nblk = global ? 1 : k / p;
+  if (small_needs_gws(p) && gws == nullptr) return cudaErrorInvalidValue;
+  const int split = small_split(p) ? 1 : 0;
   k_solve_lambda<<<nblk, kSmallNT, small_smem(p), s>>>(partA, partR, nparts, k, p, global, active, lam, rho_rec, st,
-                                                       small_needs_gws(p) ? gws : nullptr, alpha_circ);
-  return cudaGetLastError();
+                                                       small_needs_gws(p) ? gws : nullptr, alpha_circ, split);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !split) return e;
+  return launch_trsm(p, nblk, 1, gws, active, lam, st, s);
 }
 
-cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int k, int p, int global,
-                              double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
+cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int nparts_n, int k, int p,
+                              int global, double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
                               const double *rho_rec, double *beta, DevStatus *st, double *gws, int rho_circ,
                               cudaStream_t s) {
   const int nblk = global ? 1 : k / p;
+  if (small_needs_gws(p) && gws == nullptr) return cudaErrorInvalidValue;
+  const int split = small_split(p) ? 1 : 0;
   k_solve_beta<<<nblk, kSmallNT, small_smem(p), s>>>(partRho, partN, nparts, k, p, global, tol2, r0n2, rn2, active,
                                                      block_iters, rho_rec, beta, st, small_needs_gws(p) ? gws : nullptr,
-                                                     rho_circ);
-  return cudaGetLastError();
+                                                     rho_circ, nparts_n, split);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || !split) return e;
+  return launch_trsm(p, nblk, 0, gws, active, beta, st, s);
 }
 
 cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, int global, double *r0n2, double *rn2,

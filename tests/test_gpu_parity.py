@@ -370,3 +370,22 @@ def test_large_p_converged(torch_dev, prec, tol):
     if prec == "fp64":
         ref = O.solve(A, B, sub="classical", tol=tol, maxit=2000)
         assert abs(r.iters - ref.iters) <= 2
+
+
+def test_large_p_breakdown_and_frozen_blocks(torch_dev):
+    """Large blocks: a rank-deficient block breaks down at the first Cholesky (the column-parallel triangular
+    solves must then leave lambda alone), and a hybrid block whose columns are zero stays frozen while the
+    other block iterates to the oracle's iterate."""
+    from paper_1912_11930_gb300 import bcg
+    M = mat("p3d_30")
+    B = W.rhs(M.n, 64, seed=51)
+    B[:, 7] = B[:, 3]
+    X, r = gpu_solve(torch_dev, M, B, k=64, p=64, sub="classical", tol=1e-8)
+    assert r.status == bcg.BREAKDOWN and r.breakdown_iter == 1
+    B = W.rhs(M.n, 128, seed=52)
+    B[:, :64] = 0.0
+    m = 6
+    X, r = gpu_solve(torch_dev, M, B, k=128, p=64, sub="hybrid", maxit=m)
+    assert r.block_iters[0] == 0 and np.all(X[:, :64] == 0.0)
+    ref = O.solve(M.to_scipy(), B[:, 64:], p=64, sub="classical", tol=0.0, maxit=m)
+    assert _rel(X[:, 64:], ref.X) <= 1e-9
