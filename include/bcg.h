@@ -232,6 +232,66 @@ bcg_status bcg_bop(bcg_handle h, const double *X, double *Y);
  */
 bcg_status bcg_profile(bcg_handle h, double *ms, int64_t *count, int32_t cap);
 
+/*
+ * Row-sharded solves (several GPUs, one rank per GPU). The rows of A are split into contiguous ranges, one
+ * per rank; a rank's handle holds its rows and iterates Algorithm 1 on them. Every block product is a sum
+ * over rows, so a rank's share of alpha, the recomputed rho, rho and the column norms is a partial sum
+ * that the ranks add up (an allreduce) before the p x p solves, which every rank then runs on identical
+ * data (Section 3 notes that the reduction of one block product can travel with the previous one; here the
+ * two products of K1 travel in one message, rho and the column norms in another). BOP needs the rows of P
+ * that other ranks own and A references (the halo), refreshed before every phase 1. FP64 and CSR only.
+ * The caller drives the iteration:
+ *
+ *   bcg_create_csr_rows(&h, n_local, n_cols, nnz, rowptr, colind, vals, k, p, sub, stream)
+ *   bcg_rows_bind(h, sums1, sums2)      the caller's buffers of the sums exchanged between ranks
+ *   bcg_rows_start(h, B, X, tol)        R = B - A X, P = M^{-1} R; norm partials -> sums2[k*p ..]
+ *   allreduce(sums2[k*p .. k*p + k))    then bcg_rows_start_status(h)
+ *   loop:  halo of P: bcg_rows_pack for every rank that needs rows of this one, exchange,
+ *          bcg_rows_unpack of the received rows
+ *          bcg_rows_phase(h, 1)         K1: Q = A P, alpha, rho_rec -> sums1
+ *          allreduce(sums1)
+ *          bcg_rows_phase(h, 2)         lambda, X += P lambda, R -= Q lambda, rho, norms -> sums2
+ *          allreduce(sums2)
+ *          bcg_rows_phase(h, 3)         stopping test, beta, P = Z + P beta
+ *          every few iterations: bcg_rows_poll(h, &done)
+ *   bcg_rows_finish(h, &info)
+ *
+ * Local numbering: rows 0..n_local-1 are this rank's rows; columns n_local..n_cols-1 are halo rows (other
+ * ranks' rows that A references), so colind (int32, device) holds local indices < n_cols and the diagonal
+ * entry of row r is column r. B is n_local x k; X has n_cols rows, the last n_cols - n_local being halo
+ * rows (read once, by bcg_rows_start; only the first n_local rows are updated). All calls enqueue on the
+ * handle's stream and return without waiting, except bcg_rows_poll and bcg_rows_finish. Options
+ * (bcg_set_option) apply, including "precond".
+ *
+ * bcg_create_csr_rows   -- as bcg_create_csr for this rank's rows (FP64); n_cols >= n_local.
+ * bcg_rows_bind         -- sums1 (2 k p doubles) and sums2 (k p + k doubles): device buffers owned by the
+ *                          caller, written by the phases and summed over ranks by the caller.
+ * bcg_rows_start        -- begin a solve from X towards the per-column stopping rule of bcg_solve (tol >= 0).
+ * bcg_rows_start_status -- after the norm partials were summed over ranks: initial norms and status.
+ * bcg_rows_phase        -- phase 1, 2 or 3 of one iteration (see above). After convergence, breakdown or a
+ *                          non-finite value the kernels return at entry, so surplus phases are harmless.
+ * bcg_rows_pack         -- buf[i*k + c] = P[rows[i]*k + c] for i < nrows (rows int32, buf: device): the
+ *                          rows another rank needs.
+ * bcg_rows_unpack       -- copy nrows = n_cols - n_local received rows (device, row-major, in local halo
+ *                          order) into P's halo rows.
+ * bcg_rows_poll         -- *done = 1 once the solve has stopped (converged, breakdown or non-finite);
+ *                          waits for the stream.
+ * bcg_rows_finish       -- status and iteration counts of the solve (info->max_rel_res_true is NaN: it needs
+ *                          the other ranks' rows of X).
+ * On a row-sharded handle bcg_solve and bcg_solve_host return INVALID_ARG.
+ */
+bcg_status bcg_create_csr_rows(bcg_handle *h, int64_t n_local, int64_t n_cols, int64_t nnz,
+                               const int64_t *rowptr, const int32_t *colind, const double *vals, int32_t k,
+                               int32_t p, int32_t sub, void *cuda_stream);
+bcg_status bcg_rows_bind(bcg_handle h, double *sums1, double *sums2);
+bcg_status bcg_rows_start(bcg_handle h, const double *B, double *X, double tol);
+bcg_status bcg_rows_start_status(bcg_handle h);
+bcg_status bcg_rows_phase(bcg_handle h, int32_t phase);
+bcg_status bcg_rows_pack(bcg_handle h, const int32_t *rows, int64_t nrows, double *buf);
+bcg_status bcg_rows_unpack(bcg_handle h, const double *halo, int64_t nrows);
+bcg_status bcg_rows_poll(bcg_handle h, int32_t *done);
+bcg_status bcg_rows_finish(bcg_handle h, bcg_info *info);
+
 /* bcg_last_error -- message of the calling thread's most recent failure ("" if none). */
 const char *bcg_last_error(void);
 

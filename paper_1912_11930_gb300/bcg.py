@@ -61,6 +61,15 @@ def load():
         "bcg_bdot_f32": [vp, vp, vp, vp],
         "bcg_bdot_noalloc": [i64, i32, i32, i32, vp, vp, vp, vp],
         "bcg_profile": [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), i32],
+        "bcg_create_csr_rows": [ctypes.POINTER(vp), i64, i64, i64, vp, vp, vp, i32, i32, i32, vp],
+        "bcg_rows_bind": [vp, vp, vp],
+        "bcg_rows_unpack": [vp, vp, i64],
+        "bcg_rows_start": [vp, vp, vp, dbl],
+        "bcg_rows_start_status": [vp],
+        "bcg_rows_phase": [vp, i32],
+        "bcg_rows_pack": [vp, vp, i64, vp],
+        "bcg_rows_poll": [vp, ctypes.POINTER(i32)],
+        "bcg_rows_finish": [vp, ctypes.POINTER(bcg_info)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -108,6 +117,49 @@ def bcg_create_stencil(kind, nx, ny, nz, coef, scale, k, p, sub, prec, stream=No
     _check(load().bcg_create_stencil(ctypes.byref(h), STENCIL.get(kind, kind), nx, ny, nz, _ptr(coef), scale, k, p,
                                      SUBALGEBRA.get(sub, sub), PRECISION.get(prec, prec), _stream(stream)))
     return h
+
+
+def bcg_create_csr_rows(n_local, n_cols, nnz, rowptr, colind, vals, k, p, sub, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().bcg_create_csr_rows(ctypes.byref(h), n_local, n_cols, nnz, _ptr(rowptr), _ptr(colind), _ptr(vals),
+                                      k, p, SUBALGEBRA.get(sub, sub), _stream(stream)))
+    return h
+
+
+def bcg_rows_bind(h, sums1, sums2):
+    _check(load().bcg_rows_bind(h, _ptr(sums1), _ptr(sums2)))
+
+
+def bcg_rows_unpack(h, halo, nrows):
+    _check(load().bcg_rows_unpack(h, _ptr(halo), nrows))
+
+
+def bcg_rows_start(h, B, X, tol):
+    _check(load().bcg_rows_start(h, _ptr(B), _ptr(X), tol))
+
+
+def bcg_rows_start_status(h):
+    _check(load().bcg_rows_start_status(h))
+
+
+def bcg_rows_phase(h, phase):
+    _check(load().bcg_rows_phase(h, phase))
+
+
+def bcg_rows_pack(h, rows, nrows, buf):
+    _check(load().bcg_rows_pack(h, _ptr(rows), nrows, _ptr(buf)))
+
+
+def bcg_rows_poll(h):
+    done = ctypes.c_int32()
+    _check(load().bcg_rows_poll(h, ctypes.byref(done)))
+    return bool(done.value)
+
+
+def bcg_rows_finish(h):
+    info = bcg_info()
+    st = _check(load().bcg_rows_finish(h, ctypes.byref(info)), allow=(BREAKDOWN, NOT_CONVERGED, NUMERIC, TIMEOUT))
+    return st, info
 
 
 def bcg_set_option(h, key: str, value: float):

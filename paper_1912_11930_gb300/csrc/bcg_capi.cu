@@ -71,6 +71,11 @@ void bcg_internal_set_error(const char *msg) { g_last_error = msg; }
 struct bcg_ctx {
   // problem
   int64_t n = 0, nnz = 0;
+  int64_t ncols = 0;                   // operator columns: n, or own + halo rows of a row-sharded handle
+  int rows_mode = 0;                   // 1: row-sharded handle (bcg_create_csr_rows), driven by bcg_rows_*
+  double *sums1 = nullptr, *sums2 = nullptr;   // row-sharded: caller's buffers of the sums exchanged between ranks
+  double *X_rows = nullptr;            // row-sharded: the caller's X of the current solve (borrowed)
+  double tol2_rows = 0.0;              // row-sharded: squared tolerance of the current solve
   int k = 0, p = 0, global = 0, nblk = 0, prec = BCG_FP64;
   int opkind = OP_CSR;
   OpDesc A64{}, A32{};
@@ -172,9 +177,11 @@ bcg_status setup_workspace(bcg_ctx *h) {
   const size_t E = (size_t)h->k * h->p;
   const size_t pp = (size_t)h->nblk * h->p * h->p;
   if (h->prec == BCG_FP64) {
+    // P (and Q, which trades places with P for p > 32) also hold the halo rows of a row-sharded handle
+    const size_t nck = (size_t)std::max(h->ncols, h->n) * h->k;
     CKS(h->alloc(&h->R, nk));
-    CKS(h->alloc(&h->P, nk));
-    CKS(h->alloc(&h->Q, nk));
+    CKS(h->alloc(&h->P, nck));
+    CKS(h->alloc(&h->Q, nck));
   } else {
     CKS(h->alloc(&h->Q, nk));   // FP64 outer residual / true-residual scratch
     CKS(h->alloc(&h->R32, nk));
@@ -512,6 +519,64 @@ bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int 
   return st;
 }
 
+// ---------------------------------------------------------------------------------------------------
+// Row-sharded iteration (one rank's rows). Each product's per-CTA partials collapse into one partial row
+// (sums1 = [alpha | rho_rec] after phase 1, sums2 = [rho | column norms] after phase 2); the caller sums
+// these over ranks (an allreduce) between the phases, so every rank runs the p x p solves on the same data.
+// The caller also refreshes the halo rows of P before every phase 1.
+bcg_status rows_phase(bcg_ctx *h, int phase, double tol2) {
+  cudaStream_t s = h->stream;
+  const StreamGrids &g = h->g64;
+  const int64_t E = (int64_t)h->k * h->p;
+  const bool lp = h->p > kMaxP;
+  const int gu = h->precond ? g.upd_zs : g.upd, gp = h->precond ? g.pup_zs : g.pup;
+  const double *dinv = dinv_of<double>(h);
+  if (phase == 1) {
+    if (lp) {
+      CK(launch_lp_bop<double>(h->A64, h->P, h->Q, h->n, h->k, h->st, h->nsm, s));
+      CK(launch_lp_gram<double>(h->P, h->Q, h->n, h->k, h->p, h->global, h->active, h->partA, g.op, h->st, s,
+                                nullptr));
+      CK(launch_lp_gram<double>(h->P, h->R, h->n, h->k, h->p, h->global, h->active, h->partR, g.op, h->st, s,
+                                nullptr));
+    } else {
+      CK(launch_op_gram<double>(h->A64, h->P, h->R, h->Q, h->n, h->k, h->p, h->global, h->active, h->partA,
+                                h->partR, h->st, g.op, s));
+    }
+    CK(launch_sum_partials(h->partA, g.op, E, h->sums1, h->nsm, s));
+    CK(launch_sum_partials(h->partR, g.op, E, h->sums1 + E, h->nsm, s));
+  } else if (phase == 2) {
+    CK(launch_solve_lambda(h->sums1, h->sums1 + E, 1, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
+                           h->gws, lp ? 0 : g.alpha_circ, s));
+    if (lp) {
+      CK(launch_lp_baxpy<double>(h->X_rows, h->X_rows, h->P, h->lam, h->n, h->k, h->p, h->global, 1.0, h->active,
+                                 h->st, 0, s, nullptr));
+      CK(launch_lp_baxpy<double>(h->R, h->R, h->Q, h->lam, h->n, h->k, h->p, h->global, -1.0, h->active, h->st, 0, s,
+                                 nullptr));
+      CK(launch_lp_gram<double>(h->R, h->R, h->n, h->k, h->p, h->global, h->active, h->partRho, g.op, h->st, s,
+                                dinv));
+      CK(launch_lp_colnorm<double>(h->R, h->n, h->k, h->partN, g.res, h->st, s));
+      CK(launch_sum_partials(h->partRho, g.op, E, h->sums2, h->nsm, s));
+      CK(launch_sum_partials(h->partN, g.res, h->k, h->sums2 + E, h->nsm, s));
+    } else {
+      CK(launch_update_xr<double>(h->X_rows, h->R, h->P, h->Q, h->n, h->k, h->p, h->global, h->lam, h->active,
+                                  h->partRho, h->partN, h->st, gu, s, dinv));
+      CK(launch_sum_partials(h->partRho, gu, E, h->sums2, h->nsm, s));
+      CK(launch_sum_partials(h->partN, gu, h->k, h->sums2 + E, h->nsm, s));
+    }
+  } else {
+    CK(launch_solve_beta(h->sums2, h->sums2 + E, 1, 1, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
+                         h->block_iters, h->rho_rec, h->beta, h->st, h->gws, lp ? 0 : g.rho_circ, s));
+    if (lp) {
+      CK(launch_lp_baxpy<double>(h->Q, h->R, h->P, h->beta, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 1, s,
+                                 dinv));
+      std::swap(h->P, h->Q);   // the new P was written into Q's buffer
+    } else {
+      CK(launch_update_p<double>(h->P, h->R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv));
+    }
+  }
+  return BCG_OK;
+}
+
 bcg_status finish_create(bcg_ctx *h, bcg_handle *out) {
   bcg_status s = setup_workspace(h);
   if (s == BCG_OK) s = make_fp32_copy(h);
@@ -623,6 +688,7 @@ bcg_status bcg_set_option(bcg_handle h, const char *key, double value) {
 
 bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32_t maxit, bcg_info *info) {
   if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (h->rows_mode) return fail(BCG_ERR_INVALID_ARG, "row-sharded handle: drive it with the bcg_rows_* calls");
   if (!is_device_ptr(B) || !is_device_ptr(X)) return fail(BCG_ERR_INVALID_ARG, "B and X must be device pointers");
   if (B == X) return fail(BCG_ERR_INVALID_ARG, "B and X must not alias");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(BCG_ERR_INVALID_ARG, "tol must be finite and > 0");
@@ -633,6 +699,7 @@ bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32
 
 bcg_status bcg_solve_host(bcg_handle h, const double *B, double *X, double tol, int32_t maxit, bcg_info *info) {
   if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (h->rows_mode) return fail(BCG_ERR_INVALID_ARG, "row-sharded handle: drive it with the bcg_rows_* calls");
   if (B == nullptr || X == nullptr) return fail(BCG_ERR_INVALID_ARG, "B and X must not be NULL");
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(BCG_ERR_INVALID_ARG, "tol must be finite and > 0");
   if (maxit < 1) return fail(BCG_ERR_INVALID_ARG, "maxit must be >= 1");
@@ -731,6 +798,123 @@ bcg_status bcg_profile(bcg_handle h, double *ms, int64_t *count, int32_t cap) {
   if (cap < bcg_ctx::kKernels) return fail(BCG_ERR_INVALID_ARG, "cap=%d < %d", cap, bcg_ctx::kKernels);
   for (int i = 0; i < bcg_ctx::kKernels; ++i) { ms[i] = h->prof_ms[i]; count[i] = h->prof_count[i]; }
   return BCG_OK;
+}
+
+bcg_status bcg_create_csr_rows(bcg_handle *out, int64_t n_local, int64_t n_cols, int64_t nnz, const int64_t *rowptr,
+                               const int32_t *colind, const double *vals, int32_t k, int32_t p, int32_t sub,
+                               void *cuda_stream) {
+  if (out == nullptr) return fail(BCG_ERR_INVALID_ARG, "handle pointer is NULL");
+  *out = nullptr;
+  if (n_local < 1 || nnz < 1 || n_cols < n_local)
+    return fail(BCG_ERR_INVALID_ARG, "n_local=%lld, n_cols=%lld, nnz=%lld: need n_local >= 1, nnz >= 1, "
+                "n_cols >= n_local", (long long)n_local, (long long)n_cols, (long long)nnz);
+  if (n_cols > INT32_MAX) return fail(BCG_ERR_INVALID_ARG, "n_cols exceeds the int32 column index range");
+  int global = 0;
+  CKS(validate_common(k, &p, sub, BCG_FP64, &global));
+  if (!is_device_ptr(rowptr) || !is_device_ptr(colind) || !is_device_ptr(vals))
+    return fail(BCG_ERR_INVALID_ARG, "rowptr, colind and vals must be device pointers");
+  bcg_ctx *h = new (std::nothrow) bcg_ctx;
+  if (h == nullptr) return fail(BCG_ERR_OOM, "host allocation failed");
+  h->n = n_local; h->ncols = n_cols; h->nnz = nnz; h->k = k; h->p = p; h->global = global; h->prec = BCG_FP64;
+  h->rows_mode = 1;
+  h->nblk = global ? 1 : k / p;
+  h->opkind = OP_CSR;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->A64.kind = OP_CSR; h->A64.n = n_local; h->A64.rowptr = rowptr; h->A64.colind = colind; h->A64.vals = vals;
+  h->ncoef = nnz;
+  return finish_create(h, out);
+}
+
+static bcg_status rows_handle(bcg_handle h) {
+  if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (!h->rows_mode) return fail(BCG_ERR_INVALID_ARG, "not a row-sharded handle (bcg_create_csr_rows)");
+  return BCG_OK;
+}
+
+bcg_status bcg_rows_bind(bcg_handle h, double *sums1, double *sums2) {
+  CKS(rows_handle(h));
+  if (!is_device_ptr(sums1) || !is_device_ptr(sums2) || sums1 == sums2)
+    return fail(BCG_ERR_INVALID_ARG, "sums1 and sums2 must be distinct device pointers");
+  h->sums1 = sums1;
+  h->sums2 = sums2;
+  return BCG_OK;
+}
+
+bcg_status bcg_rows_start(bcg_handle h, const double *B, double *X, double tol) {
+  CKS(rows_handle(h));
+  if (!is_device_ptr(B) || !is_device_ptr(X)) return fail(BCG_ERR_INVALID_ARG, "B and X must be device pointers");
+  if (!(tol >= 0.0)) return fail(BCG_ERR_INVALID_ARG, "tol=%g must be >= 0", tol);
+  if (h->sums1 == nullptr) return fail(BCG_ERR_INVALID_ARG, "bcg_rows_bind has not been called");
+  h->X_rows = X;
+  h->tol2_rows = tol * tol;
+  const int64_t E = (int64_t)h->k * h->p;
+  CK(launch_residual<double>(h->A64, X, B, h->R, h->P, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, h->stream,
+                             dinv_of<double>(h)));
+  CK(launch_sum_partials(h->partN, h->g64.res, h->k, h->sums2 + E, h->nsm, h->stream));
+  return BCG_OK;
+}
+
+bcg_status bcg_rows_start_status(bcg_handle h) {
+  CKS(rows_handle(h));
+  const int64_t E = (int64_t)h->k * h->p;
+  CK(launch_init_status(h->sums2 + E, 1, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters, h->lam,
+                        h->beta, h->st, h->stream));
+  return BCG_OK;
+}
+
+bcg_status bcg_rows_phase(bcg_handle h, int32_t phase) {
+  CKS(rows_handle(h));
+  if (phase < 1 || phase > 3) return fail(BCG_ERR_INVALID_ARG, "phase=%d must be 1, 2 or 3", phase);
+  if (h->X_rows == nullptr) return fail(BCG_ERR_INVALID_ARG, "bcg_rows_start has not been called");
+  return rows_phase(h, phase, h->tol2_rows);
+}
+
+bcg_status bcg_rows_pack(bcg_handle h, const int32_t *rows, int64_t nrows, double *buf) {
+  CKS(rows_handle(h));
+  if (nrows < 0) return fail(BCG_ERR_INVALID_ARG, "nrows=%lld < 0", (long long)nrows);
+  if (nrows == 0) return BCG_OK;
+  if (!is_device_ptr(rows) || !is_device_ptr(buf)) return fail(BCG_ERR_INVALID_ARG, "rows and buf must be device pointers");
+  CK(launch_gather_rows(h->P, rows, nrows, h->k, buf, h->nsm, h->stream));
+  return BCG_OK;
+}
+
+bcg_status bcg_rows_unpack(bcg_handle h, const double *halo, int64_t nrows) {
+  CKS(rows_handle(h));
+  if (nrows != h->ncols - h->n)
+    return fail(BCG_ERR_INVALID_ARG, "nrows=%lld, this rank has %lld halo rows", (long long)nrows,
+                (long long)(h->ncols - h->n));
+  if (nrows == 0) return BCG_OK;
+  if (!is_device_ptr(halo)) return fail(BCG_ERR_INVALID_ARG, "halo must be a device pointer");
+  CK(cudaMemcpyAsync(h->P + h->n * h->k, halo, sizeof(double) * nrows * h->k, cudaMemcpyDeviceToDevice, h->stream));
+  return BCG_OK;
+}
+
+bcg_status bcg_rows_poll(bcg_handle h, int32_t *done) {
+  CKS(rows_handle(h));
+  if (!done) return fail(BCG_ERR_INVALID_ARG, "NULL output pointer");
+  CKS(read_status(h));
+  *done = h->h_st->flags != 0 ? 1 : 0;
+  return BCG_OK;
+}
+
+bcg_status bcg_rows_finish(bcg_handle h, bcg_info *info) {
+  CKS(rows_handle(h));
+  CKS(read_status(h));
+  const DevStatus fin = *h->h_st;
+  CKS(fill_block_iters(h));
+  CKS(fetch_vec(h, h->r0n2, 0));
+  CKS(fetch_vec(h, h->rn2, 1));
+  const bcg_status st = status_from_flags(fin.flags, (fin.flags & ST_DONE) != 0);
+  if (info) {
+    info->status = st;
+    info->iters = fin.iter;
+    info->outer_iters = 0;
+    info->breakdown_iter = (fin.flags & ST_BREAKDOWN) ? fin.breakdown_iter : -1;
+    info->max_rel_res_recursive = max_ratio(h->h_vec + h->k, h->h_vec, h->k);
+    info->max_rel_res_true = NAN;   // needs the other ranks' rows of X: the caller recomputes it
+  }
+  h->X_rows = nullptr;
+  return st;
 }
 
 const char *bcg_last_error(void) { return g_last_error.c_str(); }

@@ -532,6 +532,31 @@ __global__ void k_reduce_norms(const double *__restrict__ partN, int nparts, int
   for (int c = threadIdx.x; c < k; c += blockDim.x) out[c] = ncol[c];
 }
 
+// out[e] = sum over pi < nparts of part[pi * E + e], in partial order (one thread per entry): the per-CTA
+// partials of one product collapsed into a single partial row, ready for a sum over ranks.
+__global__ void k_sum_partials(const double *__restrict__ part, int nparts, int64_t E, double *__restrict__ out) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+    double a0 = 0.0, a1 = 0.0;
+    int pi = 0;
+    for (; pi + 1 < nparts; pi += 2) {
+      a0 += part[(int64_t)pi * E + e];
+      a1 += part[(int64_t)(pi + 1) * E + e];
+    }
+    if (pi < nparts) a0 += part[(int64_t)pi * E + e];
+    out[e] = a0 + a1;
+  }
+}
+
+// buf[i * k + c] = P[rows[i] * k + c]: the rows of P another rank needs (halo exchange of the row-sharded solve)
+__global__ void k_gather_rows(const double *__restrict__ P, const int32_t *__restrict__ rows, int64_t nrows, int k,
+                              double *__restrict__ buf) {
+  const int64_t total = nrows * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / k;
+    buf[e] = P[(int64_t)rows[i] * k + (e - i * k)];
+  }
+}
+
 // X64 += D32 (the refinement update of the mixed-precision form)
 __global__ void k_add_correction(double *__restrict__ X, const float *__restrict__ D, int64_t len) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
@@ -658,6 +683,18 @@ static int stream_grid(int64_t len, int nsm) {
   int64_t g = (len + 255) / 256;
   const int64_t cap = (int64_t)nsm * 8;
   return (int)(g < 1 ? 1 : (g > cap ? cap : g));
+}
+
+cudaError_t launch_sum_partials(const double *part, int nparts, int64_t E, double *out, int nsm, cudaStream_t s) {
+  k_sum_partials<<<stream_grid(E, nsm), 256, 0, s>>>(part, nparts, E, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_rows(const double *P, const int32_t *rows, int64_t nrows, int k, double *buf, int nsm,
+                               cudaStream_t s) {
+  if (nrows <= 0) return cudaSuccess;
+  k_gather_rows<<<stream_grid(nrows * k, nsm), 256, 0, s>>>(P, rows, nrows, k, buf);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_add_correction(double *X, const float *D, int64_t len, int nsm, cudaStream_t s) {

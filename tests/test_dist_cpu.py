@@ -61,3 +61,91 @@ def test_two_ranks_solve_their_blocks(tmp_path):
     X = np.hstack([np.load(tmp_path / f"x{r}.npy") for r in range(world)])
     assert np.array_equal(X, full.X)      # independent blocks: bitwise the same iterates
     assert all(np.load(tmp_path / f"t{r}.npy")[0] == 2.0 for r in range(world))
+
+
+# ---- row-sharded solves: the split, its halo plan and the exchanges (host logic; the kernels run on GPUs) ----
+def test_row_plans_reproduce_the_operator():
+    """Every rank's local CSR applied to [own rows; halo rows] gives that rank's rows of A x, bitwise."""
+    from paper_1912_11930_gb300 import workloads as W
+    import scipy.sparse as sp
+    for M in (W.poisson3d(7, 6, 5), W.stencil27(6, 5, 4, seed=1), W.poisson2d(9)):
+        A = M.to_scipy()
+        x = W.rhs(M.n, 3, seed=2)
+        y = A @ x
+        for world in (1, 2, 3, 4):
+            plans = D.make_plans(M, world)
+            assert [pl.n_local for pl in plans] == [b1 - b0 for b0, b1 in zip(plans[0].bounds, plans[0].bounds[1:])]
+            for pl in plans:
+                r0, r1 = pl.bounds[pl.rank], pl.bounds[pl.rank + 1]
+                L = sp.csr_matrix((pl.vals, pl.colind, pl.rowptr), shape=(pl.n_local, pl.n_cols))
+                xl = np.vstack([x[r0:r1], x[pl.halo_gids]])
+                assert np.array_equal(L @ xl, y[r0:r1])
+                assert np.all(np.diff(pl.halo_gids) > 0)                       # sorted, unique
+                assert all(not (r0 <= g < r1) for g in pl.halo_gids)
+                # what a rank sends is exactly what its peers asked for, in their halo order
+                for q, rows in pl.send:
+                    assert np.array_equal(rows + r0, plans[q].requests[pl.rank])
+
+
+def _exchange_round(comm, plan, x, torch):
+    r0 = plan.bounds[plan.rank]
+    sends = {q: torch.from_numpy(x[rows + r0].copy()) for q, rows in plan.send}
+    halo = torch.zeros(len(plan.halo_gids), x.shape[1], dtype=torch.float64)
+    recvs = {q: halo[off:off + cnt] for q, off, cnt in plan.recv}
+    comm.exchange(sends, recvs)
+    t = torch.full((5,), float(plan.rank + 1), dtype=torch.float64)
+    comm.allreduce_(t)
+    return halo.numpy(), t.numpy()
+
+
+def test_thread_comm_halo_and_allreduce():
+    import threading
+    import torch
+    from paper_1912_11930_gb300 import workloads as W
+    M = W.poisson3d(6, 6, 6)
+    x = W.rhs(M.n, 4, seed=5)
+    world = 3
+    plans = D.make_plans(M, world)
+    comms = D.ThreadComm.group(world)
+    out = [None] * world
+    def run(q):
+        out[q] = _exchange_round(comms[q], plans[q], x, torch)
+    ths = [threading.Thread(target=run, args=(q,)) for q in range(world)]
+    for t in ths:
+        t.start()
+    for t in ths:
+        t.join()
+    for q in range(world):
+        halo, s = out[q]
+        assert np.array_equal(halo, x[plans[q].halo_gids])
+        assert np.all(s == sum(range(1, world + 1)))
+
+
+def _rows_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import torch
+    from paper_1912_11930_gb300 import workloads as W
+    M = W.poisson3d(6, 5, 7)
+    x = W.rhs(M.n, 3, seed=6)
+    comm = D.TorchComm(dist)
+    b = D.row_bounds(M.n, world)
+    plan = D.local_plan(M.rowptr, M.colind, M.vals, b, rank)
+    D.fill_sends(plan, comm.all_gather_object(plan.requests))
+    halo, s = _exchange_round(comm, plan, x, torch)
+    ref = D.make_plans(M, world)[rank]
+    ok = (len(plan.send) == len(ref.send) and all(q == qr and np.array_equal(r, rr)
+                                                   for (q, r), (qr, rr) in zip(plan.send, ref.send)))
+    np.save(os.path.join(out, f"r{rank}.npy"), np.array([ok, np.array_equal(halo, x[plan.halo_gids]),
+                                                         bool(np.all(s == world * (world + 1) / 2))]))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_torch_comm_two_ranks_row_split(tmp_path):
+    """The production exchange (torch.distributed; gloo here on host tensors): each rank builds its own plan,
+    learns its sends from an all-gather of the requests, and the halo rows it receives are its peers' rows."""
+    world = 2
+    mp.start_processes(_rows_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, start_method="spawn")
+    for r in range(world):
+        assert np.load(tmp_path / f"r{r}.npy").all()
