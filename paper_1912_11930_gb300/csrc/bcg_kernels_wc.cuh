@@ -215,9 +215,13 @@ __host__ __device__ constexpr size_t wc_pup_smem(int k, int p, int global, size_
 // at least 3 CTAs per SM up to p = 16; p = 32 needs its registers (64 accumulator pairs per thread)
 template <int PM>
 constexpr int wc_min_ctas() { return PM <= 16 ? 3 : 1; }
+// the FP32 CSR K1 up to p = 8 runs faster at 4 CTAs per SM despite a few spilled registers (0.73 -> 0.67 ms,
+// 128^3, k = 32); the stencil and FP64 instantiations measured slower there
+template <typename T, int OPK, int PM>
+constexpr int wc_min_ctas_op() { return (sizeof(T) == 4 && OPK == OP_CSR && PM <= 8) ? 4 : wc_min_ctas<PM>(); }
 
 template <typename T, int OPK, int PM, int V>
-__global__ void __launch_bounds__(kNT, wc_min_ctas<PM>()) kw_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
+__global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM>()) kw_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
                                                   T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                   const int *__restrict__ active, double *__restrict__ partA,
                                                   double *__restrict__ partR, const DevStatus *__restrict__ st) {
