@@ -39,7 +39,7 @@ ORACLE_SAMPLE_ITERS = 3
 # device source the capture was taken on: sha256 prefix of KERNEL_SOURCES concatenated; reported as null once
 # that source changes.
 KERNEL_SOURCES = ["bcg_kernels.cuh", "bcg_kernels_wc.cuh", "bcg_kernels_lp.cuh", "bcg_stream.inc"]
-TRAFFIC = {}
+TRAFFIC = {("update_xr", "poisson3d_128_csr_k32_hybrid_p8_fp64"): ("27ae426cb0ff382a", 1.3191e9 * 2097152 / 884736)}
 
 
 def kernel_source_sha():
@@ -172,7 +172,7 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------------------------------------------
 # Other workloads (not the default line): measured with `python bench.py --workload NAME`
 EXTRA_WORKLOADS = ("poisson2d_64_k8", "varcoef3d_160_k64_mixed", "varcoef3d_160_k64_jacobi", "stencil27_100_k16_autograd",
-                   "poisson3d_96_sweep")
+                   "poisson3d_96_sweep", "sell_vs_csr")
 
 
 def time_solve(bcg, torch, M, B, *, k, p, sub, prec, form="csr", tol=1e-8, reps=2, dev=None, opts=None, warm=True):
@@ -249,6 +249,28 @@ def run_extra(name, args):
                    config={"workload": "varcoef3d_160_stencil_k64_hybrid_p16_jacobi", "n": M.n, "k": k, "p": 16},
                    results=rows, jacobi_speedup_fp64=rows[0]["s"] / rows[1]["s"],
                    jacobi_speedup_mixed=rows[2]["s"] / rows[3]["s"])
+    elif name == "sell_vs_csr":
+        # BOP (inside K1) with the matrix in CSR and in SELL-C-sigma: the 128^3 Poisson matrix and an SPD matrix
+        # with very uneven rows (2M rows, power-law degrees); K1 time per iteration from the live profile
+        rows = []
+        for mname, M in (("poisson3d_128", W.poisson3d(128)), ("powerlaw_2M", W.powerlaw_laplacian(1 << 21))):
+            for k, p, sub in ((1, 1, "parallel"), (8, 8, "hybrid"), (32, 8, "hybrid")):
+                B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev)
+                for form, sigma in (("csr", 1), ("sell", 1), ("sell", 4096)):
+                    S = bcg.Solver.from_matrix(M, k=k, p=p, sub=sub, prec="fp64", form=form, device=dev, sigma=sigma)
+                    X = torch.zeros_like(B)
+                    S.solve(B, X, tol=1e-300, maxit=8)
+                    S.set_option("profile", 1)
+                    X.zero_()
+                    S.solve(B, X, tol=1e-300, maxit=24)
+                    tot, cnt = S.profile()["op_gram"]
+                    S.close()
+                    rows.append(dict(matrix=mname, k=k, p=p, format=form, sigma=sigma, k1_ms=tot / max(cnt, 1)))
+                    print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+                del B
+        out.update(value=rows[0]["k1_ms"] / 1e3, unit="s", dtype="f64",
+                   config={"workload": "sell_vs_csr_k1_time", "iterations_profiled": 24}, results=rows,
+                   note="value: K1 time of the first row (128^3 Poisson, k = 1, CSR), seconds per launch")
     elif name == "stencil27_100_k16_autograd":
         from paper_1912_11930_gb300.autograd import bcg_solve_autograd
         M = W.stencil27(100, seed=0)

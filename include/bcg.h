@@ -97,6 +97,30 @@ bcg_status bcg_create_csr(bcg_handle *h, int64_t n, int64_t nnz, const int64_t *
                           int32_t sub, int32_t prec, void *cuda_stream);
 
 /*
+ * bcg_create_sell -- solver on an SELL-C-sigma matrix (Kreutzer, Hager, Wellein, Fehske, Bishop, SIAM J.
+ * Sci. Comput. 36(5), 2014; the sparse format Section 4 suggests against BOP's cache pressure at large k).
+ * The matrix is stored for the permuted system A' = Pi A Pi^T, (Pi x)[s] = x[perm[s]]: rows sorted by
+ * decreasing length inside windows of sigma rows, columns renumbered with the same permutation. Chunks of
+ * C = 32 consecutive rows are stored column-major: entry j of row s at chunkptr[s / 32] + j*32 + s % 32,
+ * rowlen[s] entries in row s, each chunk padded to its longest row (padding is never read).
+ *   n         rows (>= 1, <= INT32_MAX)
+ *   nent      stored entries including padding (length of colind and vals)
+ *   chunkptr  device int64[ceil(n / 32)]: first entry of each chunk
+ *   rowlen    device int32[n]
+ *   colind    device int32[nent]: permuted column indices
+ *   vals      device double[nent]
+ *   perm      device int32[n]: the original row of permuted row s (a permutation of 0..n-1)
+ * B and X of bcg_solve / bcg_solve_host stay in the original row order: the handle permutes them on entry
+ * and X back on exit (two n x k buffers of workspace). bcg_bop applies A in the original order too.
+ * bcg_update_values takes new values in the same padded layout; bcg_grad_values is not available.
+ * Other arguments and ownership as for bcg_create_csr.
+ */
+bcg_status bcg_create_sell(bcg_handle *h, int64_t n, int64_t nent, const int64_t *chunkptr,
+                           const int32_t *rowlen, const int32_t *colind, const double *vals,
+                           const int32_t *perm, int32_t k, int32_t p, int32_t sub, int32_t prec,
+                           void *cuda_stream);
+
+/*
  * bcg_create_stencil -- matrix-free solver (BOP as a stencil, no assembled matrix).
  *   kind          bcg_stencil_kind; nz = 1 for the 2D stencil
  *   coef          NULL for the constant stencils. For BCG_STENCIL_7PT_3D_VARCOEF a device double

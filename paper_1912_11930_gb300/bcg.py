@@ -61,6 +61,7 @@ def load():
         "bcg_bdot_f32": [vp, vp, vp, vp],
         "bcg_bdot_noalloc": [i64, i32, i32, i32, vp, vp, vp, vp],
         "bcg_profile": [vp, ctypes.POINTER(dbl), ctypes.POINTER(i64), i32],
+        "bcg_create_sell": [ctypes.POINTER(vp), i64, i64, vp, vp, vp, vp, vp, i32, i32, i32, i32, vp],
         "bcg_create_csr_rows": [ctypes.POINTER(vp), i64, i64, i64, vp, vp, vp, i32, i32, i32, vp],
         "bcg_rows_bind": [vp, vp, vp],
         "bcg_rows_unpack": [vp, vp, i64],
@@ -116,6 +117,14 @@ def bcg_create_stencil(kind, nx, ny, nz, coef, scale, k, p, sub, prec, stream=No
     h = ctypes.c_void_p()
     _check(load().bcg_create_stencil(ctypes.byref(h), STENCIL.get(kind, kind), nx, ny, nz, _ptr(coef), scale, k, p,
                                      SUBALGEBRA.get(sub, sub), PRECISION.get(prec, prec), _stream(stream)))
+    return h
+
+
+def bcg_create_sell(n, nent, chunkptr, rowlen, colind, vals, perm, k, p, sub, prec, stream=None):
+    h = ctypes.c_void_p()
+    _check(load().bcg_create_sell(ctypes.byref(h), n, nent, _ptr(chunkptr), _ptr(rowlen), _ptr(colind), _ptr(vals),
+                                  _ptr(perm), k, p, SUBALGEBRA.get(sub, sub), PRECISION.get(prec, prec),
+                                  _stream(stream)))
     return h
 
 
@@ -251,7 +260,7 @@ class Solver:
     replayed as CUDA graphs). Calls are ordered after torch's current stream and torch's current stream
     waits for them."""
 
-    def __init__(self, *, k, p=1, sub="hybrid", prec="fp64", csr=None, stencil=None, device=None):
+    def __init__(self, *, k, p=1, sub="hybrid", prec="fp64", csr=None, stencil=None, sell=None, device=None):
         import torch
         self.torch = torch
         self.device = torch.device(device or "cuda")
@@ -269,6 +278,13 @@ class Solver:
                 self.n = rowptr.numel() - 1
                 self.nnz = colind.numel()
                 self.h = bcg_create_csr(self.n, self.nnz, rowptr, colind, vals, k, p, sub, prec, self.stream)
+            elif sell is not None:   # (chunkptr, rowlen, colind, vals, perm) device tensors
+                chunkptr, rowlen, colind, vals, perm = sell
+                self._keep += list(sell)
+                self.n = rowlen.numel()
+                self.nnz = vals.numel()
+                self.h = bcg_create_sell(self.n, self.nnz, chunkptr, rowlen, colind, vals, perm, k, p, sub, prec,
+                                         self.stream)
             else:
                 kind, nx, ny, nz, coef, scale = stencil
                 if coef is not None:
@@ -278,10 +294,15 @@ class Solver:
                 self.h = bcg_create_stencil(kind, nx, ny, nz, coef, scale, k, p, sub, prec, self.stream)
 
     @classmethod
-    def from_matrix(cls, M, *, k, p=1, sub="hybrid", prec="fp64", form="csr", device=None):
-        """M: a workloads.CSRMatrix; form 'csr' or 'stencil'."""
+    def from_matrix(cls, M, *, k, p=1, sub="hybrid", prec="fp64", form="csr", device=None, sigma=1):
+        """M: a workloads.CSRMatrix; form 'csr', 'stencil' or 'sell' (SELL-C-sigma, sorting window sigma)."""
         import torch
         dev = torch.device(device or "cuda")
+        if form == "sell":
+            from .formats import sell_from_csr
+            S = sell_from_csr(M.rowptr, M.colind, M.vals, sigma)
+            sell = tuple(torch.from_numpy(a).to(dev) for a in (S.chunkptr, S.rowlen, S.colind, S.vals, S.perm))
+            return cls(k=k, p=p, sub=sub, prec=prec, sell=sell, device=dev)
         if form == "csr":
             csr = (torch.from_numpy(M.rowptr).to(dev), torch.from_numpy(M.colind).to(dev),
                    torch.from_numpy(M.vals).to(dev))

@@ -75,6 +75,8 @@ struct bcg_ctx {
   int rows_mode = 0;                   // 1: row-sharded handle (bcg_create_csr_rows), driven by bcg_rows_*
   double *sums1 = nullptr, *sums2 = nullptr;   // row-sharded: caller's buffers of the sums exchanged between ranks
   double *X_rows = nullptr;            // row-sharded: the caller's X of the current solve (borrowed)
+  const int32_t *perm = nullptr;       // SELL: row of the original system held by permuted row s (borrowed)
+  double *Bp = nullptr, *Xp = nullptr; // SELL: B and X in the permuted row order
   double tol2_rows = 0.0;              // row-sharded: squared tolerance of the current solve
   int k = 0, p = 0, global = 0, nblk = 0, prec = BCG_FP64;
   int opkind = OP_CSR;
@@ -224,9 +226,10 @@ bcg_status make_fp32_copy(bcg_ctx *h) {
       CKS(h->alloc(&v, h->ncoef));
       h->vals32 = v;
     }
-    const double *src = static_cast<const double *>(h->opkind == OP_CSR ? h->A64.vals : h->A64.faces);
+    const bool by_entry = h->opkind == OP_CSR || h->opkind == OP_SELL;
+    const double *src = static_cast<const double *>(by_entry ? h->A64.vals : h->A64.faces);
     CK(launch_cast_to_float(src, static_cast<float *>(h->vals32), h->ncoef, h->nsm, h->stream));
-    if (h->opkind == OP_CSR) h->A32.vals = h->vals32;
+    if (by_entry) h->A32.vals = h->vals32;
     else h->A32.faces = h->vals32;
   }
   return BCG_OK;
@@ -624,6 +627,35 @@ bcg_status bcg_create_csr(bcg_handle *out, int64_t n, int64_t nnz, const int64_t
   return finish_create(h, out);
 }
 
+bcg_status bcg_create_sell(bcg_handle *out, int64_t n, int64_t nent, const int64_t *chunkptr, const int32_t *rowlen,
+                           const int32_t *colind, const double *vals, const int32_t *perm, int32_t k, int32_t p,
+                           int32_t sub, int32_t prec, void *cuda_stream) {
+  if (out == nullptr) return fail(BCG_ERR_INVALID_ARG, "handle pointer is NULL");
+  *out = nullptr;
+  if (n < 1 || nent < 1) return fail(BCG_ERR_INVALID_ARG, "n=%lld nent=%lld must be >= 1", (long long)n, (long long)nent);
+  if (n > INT32_MAX) return fail(BCG_ERR_INVALID_ARG, "n=%lld exceeds the int32 column index range", (long long)n);
+  int global = 0;
+  CKS(validate_common(k, &p, sub, prec, &global));
+  if (!is_device_ptr(chunkptr) || !is_device_ptr(rowlen) || !is_device_ptr(colind) || !is_device_ptr(vals) ||
+      !is_device_ptr(perm))
+    return fail(BCG_ERR_INVALID_ARG, "chunkptr, rowlen, colind, vals and perm must be device pointers");
+  bcg_ctx *h = new (std::nothrow) bcg_ctx;
+  if (h == nullptr) return fail(BCG_ERR_OOM, "host allocation failed");
+  h->n = n; h->nnz = nent; h->k = k; h->p = p; h->global = global; h->prec = prec;
+  h->nblk = global ? 1 : k / p;
+  h->opkind = OP_SELL;
+  h->stream = static_cast<cudaStream_t>(cuda_stream);
+  h->A64.kind = OP_SELL; h->A64.n = n; h->A64.rowptr = chunkptr; h->A64.colind = colind; h->A64.vals = vals;
+  h->A64.rowlen = rowlen;
+  h->ncoef = nent;
+  h->perm = perm;
+  if (h->alloc(&h->Bp, (size_t)n * k) != BCG_OK || h->alloc(&h->Xp, (size_t)n * k) != BCG_OK) {
+    delete h;
+    return BCG_ERR_OOM;
+  }
+  return finish_create(h, out);
+}
+
 bcg_status bcg_create_stencil(bcg_handle *out, int32_t kind, int32_t nx, int32_t ny, int32_t nz, const double *coef,
                               double scale, int32_t k, int32_t p, int32_t sub, int32_t prec, void *cuda_stream) {
   if (out == nullptr) return fail(BCG_ERR_INVALID_ARG, "handle pointer is NULL");
@@ -694,7 +726,19 @@ bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(BCG_ERR_INVALID_ARG, "tol must be finite and > 0");
   if (maxit < 1) return fail(BCG_ERR_INVALID_ARG, "maxit must be >= 1");
   g_last_error.clear();
-  return h->prec == BCG_FP64 ? solve_fp64(h, B, X, tol, maxit, info) : solve_refine(h, B, X, tol, maxit, info);
+  if (h->perm == nullptr)
+    return h->prec == BCG_FP64 ? solve_fp64(h, B, X, tol, maxit, info) : solve_refine(h, B, X, tol, maxit, info);
+  // SELL-C-sigma handle: iterate on the permuted system (Pi A Pi^T)(Pi X) = Pi B
+  CK(launch_permute_rows(B, h->perm, h->n, h->k, h->Bp, 0, h->nsm, h->stream));
+  CK(launch_permute_rows(X, h->perm, h->n, h->k, h->Xp, 0, h->nsm, h->stream));
+  const bcg_status st = h->prec == BCG_FP64 ? solve_fp64(h, h->Bp, h->Xp, tol, maxit, info)
+                                            : solve_refine(h, h->Bp, h->Xp, tol, maxit, info);
+  if (st == BCG_ERR_INVALID_ARG || st == BCG_ERR_CUDA || st == BCG_ERR_OOM) return st;
+  const std::string msg = g_last_error;
+  CK(launch_permute_rows(h->Xp, h->perm, h->n, h->k, X, 1, h->nsm, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  g_last_error = msg;
+  return st;
 }
 
 bcg_status bcg_solve_host(bcg_handle h, const double *B, double *X, double tol, int32_t maxit, bcg_info *info) {
@@ -740,7 +784,7 @@ bcg_status bcg_update_values(bcg_handle h, const double *vals) {
   if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
   if (h->ncoef == 0) return fail(BCG_ERR_INVALID_ARG, "constant stencils have no values");
   if (!is_device_ptr(vals)) return fail(BCG_ERR_INVALID_ARG, "vals must be a device pointer");
-  if (h->opkind == OP_CSR) h->A64.vals = vals;
+  if (h->opkind == OP_CSR || h->opkind == OP_SELL) h->A64.vals = vals;
   else h->A64.faces = vals;
   CKS(make_fp32_copy(h));
   if (h->graph32) {   // captured graphs hold the old operator descriptor
@@ -788,7 +832,13 @@ bcg_status bcg_bdot_f32(bcg_handle h, const float *X, const float *Y, double *ga
 bcg_status bcg_bop(bcg_handle h, const double *X, double *Y) {
   if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
   if (!is_device_ptr(X) || !is_device_ptr(Y) || X == Y) return fail(BCG_ERR_INVALID_ARG, "X, Y: distinct device pointers");
-  CK(launch_bop<double>(h->A64, X, Y, h->n, h->k, h->g64.res, h->stream));
+  if (h->perm == nullptr) {
+    CK(launch_bop<double>(h->A64, X, Y, h->n, h->k, h->g64.res, h->stream));
+  } else {   // Y = Pi^T (Pi A Pi^T) Pi X
+    CK(launch_permute_rows(X, h->perm, h->n, h->k, h->Xp, 0, h->nsm, h->stream));
+    CK(launch_bop<double>(h->A64, h->Xp, h->Bp, h->n, h->k, h->g64.res, h->stream));
+    CK(launch_permute_rows(h->Bp, h->perm, h->n, h->k, Y, 1, h->nsm, h->stream));
+  }
   CK(cudaStreamSynchronize(h->stream));
   return BCG_OK;
 }

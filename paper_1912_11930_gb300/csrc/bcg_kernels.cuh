@@ -19,7 +19,14 @@
 
 namespace bcgk {
 
-enum OpKind { OP_CSR = 0, OP_ST5 = 1, OP_ST7 = 2, OP_ST7VC = 3 };
+enum OpKind { OP_CSR = 0, OP_ST5 = 1, OP_ST7 = 2, OP_ST7VC = 3, OP_SELL = 4 };
+
+// SELL-C-sigma (Kreutzer et al., SIAM J. Sci. Comput. 36(5), 2014, the format Section 4 suggests for BOP):
+// rows in chunks of kSellC; entry j of row r is stored at rowptr[r / kSellC] + j * kSellC + r % kSellC
+// (column-major inside a chunk, so lanes holding consecutive rows read consecutive words); rowlen[r] entries
+// per row, the chunk padded to its longest row. The sigma-sorting of rows is a permutation applied outside
+// the operator (the handle iterates on the permuted system).
+constexpr int kSellC = 32;
 
 // Device status word shared by all kernels of one solve.
 struct DevStatus {
@@ -41,6 +48,7 @@ struct OpDesc {
   int nx, ny, nz;
   double scale;
   const void *faces;
+  const int32_t *rowlen;   // SELL: entries per row (rowptr then holds the chunk offsets)
 };
 
 constexpr int kNT = 256;   // threads per CTA of the streaming kernels (k <= 256)
@@ -223,6 +231,28 @@ __device__ __forceinline__ T apply_row(const OpDesc &A, const T *__restrict__ X,
 #pragma unroll
       for (int u = 0; u < 8; ++u)
         if (e + u < e1) s = fma_t(w[u], xv[u], s);
+    }
+    return s;
+  } else if constexpr (OPK == OP_SELL) {
+    const T *__restrict__ v = static_cast<const T *>(A.vals);
+    const int64_t base = __ldg(A.rowptr + r / kSellC) + r % kSellC;
+    const int len = __ldg(A.rowlen + r);
+    T s = T(0);
+    for (int j = 0; j < len; j += 8) {
+      int col[8];
+      T w[8], xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool in = j + u < len;
+        const int64_t e = base + (int64_t)(j + u) * kSellC;
+        col[u] = in ? __ldg(A.colind + e) : 0;
+        w[u] = in ? __ldg(v + e) : T(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) xv[u] = (j + u < len) ? __ldg(X + (int64_t)col[u] * k + c) : T(0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j + u < len) s = fma_t(w[u], xv[u], s);
     }
     return s;
   } else if constexpr (OPK == OP_ST5) {
@@ -669,6 +699,11 @@ __global__ void k_inv_diag(OpDesc A, int64_t n, T *__restrict__ dinv) {
       const double *v = static_cast<const double *>(A.vals);
       for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e)
         if (A.colind[e] == r) d += v[e];
+    } else if constexpr (OPK == OP_SELL) {
+      const double *v = static_cast<const double *>(A.vals);
+      const int64_t base = A.rowptr[r / kSellC] + r % kSellC;
+      for (int j = 0; j < A.rowlen[r]; ++j)
+        if (A.colind[base + (int64_t)j * kSellC] == r) d += v[base + (int64_t)j * kSellC];
     } else if constexpr (OPK == OP_ST5) {
       d = 4.0 * A.scale;
     } else if constexpr (OPK == OP_ST7) {

@@ -119,6 +119,37 @@ __device__ __forceinline__ VecU<T, V> apply_row_vec(const OpDesc &A, const T *__
         }
     }
     return s;
+  } else if constexpr (OPK == OP_SELL) {
+    const T *__restrict__ vals = static_cast<const T *>(A.vals);
+    const int64_t base = __ldg(A.rowptr + r / kSellC) + r % kSellC;
+    const int len = __ldg(A.rowlen + r);
+    for (int j = 0; j < len; j += 8) {
+      int colj[8];
+      T w[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const bool in = j + u < len;
+        const int64_t e = base + (int64_t)(j + u) * kSellC;
+        colj[u] = in ? __ldg(A.colind + e) : 0;
+        w[u] = in ? __ldg(vals + e) : T(0);
+      }
+      VecU<T, V> xv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        if (j + u < len) xv[u].v = __ldg(Xv + (int64_t)colj[u] * kv + cv);
+        else {
+#pragma unroll
+          for (int v = 0; v < V; ++v) xv[u].e[v] = T(0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (j + u < len) {
+#pragma unroll
+          for (int v = 0; v < V; ++v) s.e[v] = fma_t(w[u], xv[u].e[v], s.e[v]);
+        }
+    }
+    return s;
   } else {
     const int nx = A.nx, ny = A.ny, nz = (OPK == OP_ST5) ? 1 : A.nz;
     const int64_t pl = (int64_t)nx * ny;

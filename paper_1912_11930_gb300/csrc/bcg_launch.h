@@ -91,6 +91,8 @@ cudaError_t launch_reduce_norms(const double *partN, int nparts, int k, double *
 cudaError_t launch_sum_partials(const double *part, int nparts, int64_t E, double *out, int nsm, cudaStream_t s);
 cudaError_t launch_gather_rows(const double *P, const int32_t *rows, int64_t nrows, int k, double *buf, int nsm,
                                cudaStream_t s);
+cudaError_t launch_permute_rows(const double *src, const int32_t *perm, int64_t n, int k, double *dst, int scatter,
+                                int nsm, cudaStream_t s);
 cudaError_t launch_add_correction(double *X, const float *D, int64_t len, int nsm, cudaStream_t s);
 cudaError_t launch_cast_to_float(const double *src, float *dst, int64_t len, int nsm, cudaStream_t s);
 cudaError_t launch_grad_values(const int32_t *rowidx, const int32_t *colind, const double *Lam, const double *X,

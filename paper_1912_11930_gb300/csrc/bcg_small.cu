@@ -557,6 +557,18 @@ __global__ void k_gather_rows(const double *__restrict__ P, const int32_t *__res
   }
 }
 
+// Row permutation of an n x k block vector: gather dst[s] = src[perm[s]], or scatter dst[perm[s]] = src[s].
+__global__ void k_permute_rows(const double *__restrict__ src, const int32_t *__restrict__ perm, int64_t n, int k,
+                               double *__restrict__ dst, int scatter) {
+  const int64_t total = n * k;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = e / k, c = e - s * k;
+    const int64_t r = perm[s];
+    if (scatter) dst[r * k + c] = src[e];
+    else dst[e] = src[r * k + c];
+  }
+}
+
 // X64 += D32 (the refinement update of the mixed-precision form)
 __global__ void k_add_correction(double *__restrict__ X, const float *__restrict__ D, int64_t len) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
@@ -694,6 +706,12 @@ cudaError_t launch_gather_rows(const double *P, const int32_t *rows, int64_t nro
                                cudaStream_t s) {
   if (nrows <= 0) return cudaSuccess;
   k_gather_rows<<<stream_grid(nrows * k, nsm), 256, 0, s>>>(P, rows, nrows, k, buf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_rows(const double *src, const int32_t *perm, int64_t n, int k, double *dst, int scatter,
+                                int nsm, cudaStream_t s) {
+  k_permute_rows<<<stream_grid(n * k, nsm), 256, 0, s>>>(src, perm, n, k, dst, scatter);
   return cudaGetLastError();
 }
 

@@ -18,6 +18,9 @@ Workloads (the paper's whole-solver experiment in Section 4 uses a 2D heterogene
                      coefficients, A_ij = -h^-2 * (coefficient of the shared face).
 * ``stencil27``      27-point SPD matrix: one value -U(0.5, 1.5) per unordered neighbour pair (so A is
                      symmetric), diagonal = row sum of |off-diagonals| + 0.1 (strictly diagonally dominant).
+* ``powerlaw_laplacian``  graph Laplacian + I of a random graph whose out-degrees follow a Pareto law
+                     (row lengths from a few to thousands): not one of the paper's problems, only the
+                     irregular-row case the SELL-C-sigma format is meant for.
 * ``rhs``            n x k block, i.i.d. N(0, 1), row-major (element (i, c) at i*k + c).
 
 Seeds: the right-hand side uses ``seed``, the loss weights of the autograd workload ``seed + 1`` and matrix
@@ -192,6 +195,25 @@ def stencil27(nx: int, ny: int | None = None, nz: int | None = None, seed: int =
     rowptr, colind, v = _assemble(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
     return CSRMatrix(n, rowptr, colind, v, stencil=None,
                      meta=dict(name=f"stencil27_{nx}x{ny}x{nz}", seed=seed))
+
+
+def powerlaw_laplacian(n: int, seed: int = 0, shape: float = 1.5, scale: float = 3.0,
+                       max_degree: int = 2000) -> CSRMatrix:
+    """L + I for the symmetrised random graph where node i links to deg_i uniform targets, deg_i =
+    min(max_degree, floor(scale (1 + Pareto(shape)))); SPD (diagonally dominant), rows of very uneven length."""
+    import scipy.sparse as sp
+    rng = np.random.default_rng(seed + 2)
+    deg = np.minimum((rng.pareto(shape, size=n) + 1.0) * scale, max_degree).astype(np.int64)
+    src = np.repeat(np.arange(n, dtype=np.int64), deg)
+    dst = rng.integers(0, n, size=src.size)
+    G = sp.coo_matrix((np.ones(src.size), (src, dst)), shape=(n, n)).tocsr()
+    G = ((G + G.T) > 0).astype(np.float64)
+    G.setdiag(0)
+    G.eliminate_zeros()
+    L = (sp.diags(np.asarray(G.sum(axis=1)).ravel() + 1.0) - G).tocsr()
+    L.sort_indices()
+    return CSRMatrix(n, L.indptr.astype(np.int64), L.indices.astype(np.int32), L.data.astype(np.float64),
+                     stencil=None, meta=dict(name=f"powerlaw_laplacian_{n}", seed=seed))
 
 
 def rhs(n: int, k: int, seed: int = 0) -> np.ndarray:

@@ -54,3 +54,17 @@ def test_seeds():
     assert not np.array_equal(a, W.loss_weights(10, 3, seed=4))
     # PCG64 standard normals are platform independent; first value for seed 0
     assert W.rhs(1, 1, seed=0)[0, 0] == pytest.approx(0.12573022, abs=1e-8)
+
+
+def test_powerlaw_laplacian_is_spd_with_uneven_rows():
+    from paper_1912_11930_gb300 import workloads as W
+    M = W.powerlaw_laplacian(3000, seed=4)
+    A = M.to_scipy()
+    assert abs(A - A.T).max() == 0.0
+    d = A.diagonal()
+    off = np.asarray(abs(A).sum(axis=1)).ravel() - d
+    assert np.all(d >= off + 1.0 - 1e-12)            # L + I: strictly diagonally dominant, so SPD
+    lens = np.diff(M.rowptr)
+    assert lens.max() > 10 * np.median(lens)
+    M2 = W.powerlaw_laplacian(3000, seed=4)
+    assert np.array_equal(M.colind, M2.colind) and np.array_equal(M.vals, M2.vals)
