@@ -153,3 +153,18 @@ def test_jacobi_option_toggles_and_update_values(torch_dev):
     X_n, r_n = S.solve(Bt, tol=1e-10, maxit=5000)
     S.close()
     assert r_g.ok and torch.equal(X_g, X_n) and r_g.iters == r_n.iters
+
+
+def test_jacobi_zero_diagonal_is_reported(torch_dev):
+    """M = diag(A) needs a positive diagonal; a zero diagonal entry makes Z non-finite and the solve stops
+    with NUMERIC (or BREAKDOWN), in both precisions and on large blocks, instead of iterating on garbage."""
+    from paper_1912_11930_gb300 import bcg
+    M = mat("p3d_30")
+    vals = M.vals.copy()
+    diag = np.nonzero(M.colind == np.repeat(np.arange(M.n), np.diff(M.rowptr)))[0]
+    vals[diag[17]] = 0.0
+    Z = W.CSRMatrix(M.n, M.rowptr, M.colind, vals)
+    for prec, k, p in (("fp64", 8, 4), ("fp32_refine", 8, 4), ("fp64", 64, 64)):
+        X, r = gpu_solve(torch_dev, Z, W.rhs(M.n, k, seed=13), k=k, p=p, sub="hybrid" if p < k else "classical",
+                         prec=prec, tol=1e-8, maxit=200)
+        assert r.status in (bcg.NUMERIC, bcg.BREAKDOWN), r
