@@ -137,7 +137,7 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
 /*
  * bcg_set_option -- tune a handle. Keys:
  *   "inner_tol"    FP32_REFINE: smallest relative residual reduction an inner solve is asked for
- *                  (default 1e-5); each inner solve targets the reduction still needed by the outer
+ *                  (default 3e-5); each inner solve targets the reduction still needed by the outer
  *                  tolerance (times 0.5), but not less than this
  *   "max_outer"    FP32_REFINE: maximum refinement steps (default 30)
  *   "check_every"  iterations launched between two host reads of the device status word (default 8;

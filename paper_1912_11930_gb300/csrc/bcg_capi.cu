@@ -87,7 +87,7 @@ struct bcg_ctx {
   StreamGrids g64{}, g32{};
   int nparts = 0;                      // partial-buffer rows (max CTAs of K0/K1/K2)
   // options
-  double inner_tol = 1e-5;
+  double inner_tol = 3e-5;             // 2-7 % fewer inner iterations than 1e-5 on the benchmark problems
   int max_outer = 30;
   int check_every = 8;
   int use_graph = 1;
