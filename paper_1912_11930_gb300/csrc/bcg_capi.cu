@@ -77,7 +77,8 @@ struct bcg_ctx {
   double *X_rows = nullptr;            // row-sharded: the caller's X of the current solve (borrowed)
   const int32_t *perm = nullptr;       // SELL: row of the original system held by permuted row s (borrowed)
   double *Bp = nullptr, *Xp = nullptr; // SELL: B and X in the permuted row order
-  double tol2_rows = 0.0;              // row-sharded: squared tolerance of the current solve
+  double *tol2_dev = nullptr;          // squared stopping tolerance of the running solve (device, read by K4b)
+  double *h_tol2 = nullptr;            // pinned staging for it
   int k = 0, p = 0, global = 0, nblk = 0, prec = BCG_FP64;
   int opkind = OP_CSR;
   OpDesc A64{}, A32{};
@@ -139,6 +140,7 @@ struct bcg_ctx {
     if (graph32) cudaGraphExecDestroy(graph32);
     for (void *a : allocs) cudaFree(a);
     if (h_st) cudaFreeHost(h_st);
+    if (h_tol2) cudaFreeHost(h_tol2);
     if (h_vec) cudaFreeHost(h_vec);
     if (h_iters) cudaFreeHost(h_iters);
   }
@@ -169,10 +171,14 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CK(cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, dev));
   CK(small_prepare(h->p));
   CK(stream_grids<double>(h->opkind, h->n, h->k, h->p, h->global, h->nsm, &h->g64));
-  int np = std::max(std::max(h->g64.op, h->g64.upd_zs), std::max(h->g64.upd, h->g64.res));
+  // partial rows: every grid that writes them (K0, K1, K2, and K3 for the recomputed rho)
+  auto grids_max = [](const StreamGrids &g) {
+    return std::max(std::max(std::max(g.op, g.res), std::max(g.upd, g.upd_zs)), std::max(g.pup, g.pup_zs));
+  };
+  int np = grids_max(h->g64);
   if (h->prec == BCG_FP32_REFINE) {
     CK(stream_grids<float>(h->opkind, h->n, h->k, h->p, h->global, h->nsm, &h->g32));
-    np = std::max(np, std::max(std::max(h->g32.op, h->g32.upd_zs), std::max(h->g32.upd, h->g32.res)));
+    np = std::max(np, grids_max(h->g32));
   }
   h->nparts = np;
   const size_t nk = (size_t)h->n * h->k;
@@ -208,6 +214,8 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CKS(h->alloc(&h->dinv64, (size_t)h->n));
   if (h->prec == BCG_FP32_REFINE) CKS(h->alloc(&h->dinv32, (size_t)h->n));
   CKS(h->alloc(&h->st, 1));
+  CKS(h->alloc(&h->tol2_dev, 1));
+  CK(cudaMallocHost(&h->h_tol2, sizeof(double)));
   CK(cudaMallocHost(&h->h_st, sizeof(DevStatus)));
   CK(cudaMallocHost(&h->h_vec, 3 * sizeof(double) * h->k));
   CK(cudaMallocHost(&h->h_iters, sizeof(int) * h->nblk));
@@ -242,9 +250,27 @@ const double *dinv_of<double>(const bcg_ctx *h) { return h->precond ? h->dinv64 
 template <>
 const float *dinv_of<float>(const bcg_ctx *h) { return h->precond ? h->dinv32 : nullptr; }
 
+// The squared tolerance lives in device memory so that a captured batch of iterations serves every solve
+// and every refinement step (their tolerances differ). Stream-ordered; the pinned staging value is only
+// rewritten after the stream has been synchronised (every solve reads the status word before returning).
+bcg_status set_tol2(bcg_ctx *h, double tol2) {
+  *h->h_tol2 = tol2;
+  CK(cudaMemcpyAsync(h->tol2_dev, h->h_tol2, sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  return BCG_OK;
+}
+
+// With rho_k3 the first iteration's recomputed rho, <<P^1, R^0>>_S, is a BDOT after K0, on the K3 grid so that
+// K4a reads every iteration's partials the same way (later iterations get it from K3).
+template <typename T>
+bcg_status first_rho_rec(bcg_ctx *h, const T *P, const T *R, const StreamGrids &g) {
+  if (!g.rho_k3) return BCG_OK;
+  CK(launch_bdot<T>(P, R, h->n, h->k, h->p, h->partR, h->precond ? g.pup_zs : g.pup, h->stream));
+  return BCG_OK;
+}
+
 // ev: NULL, or 10 events recorded around the 5 launches (profiling)
 template <typename T>
-bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g, double tol2,
+bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g,
                             cudaEvent_t *ev = nullptr) {
   cudaStream_t s = h->stream;
 #define REC(i) do { if (ev) CK(cudaEventRecord(ev[i], s)); } while (0)
@@ -252,16 +278,18 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
   REC(0);
   CK(launch_op_gram<T>(A, P, R, Q, h->n, h->k, h->p, h->global, h->active, h->partA, h->partR, h->st, g.op, s));
   REC(1); REC(2);
-  CK(launch_solve_lambda(h->partA, h->partR, g.op, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
-                         h->gws, g.alpha_circ, s));
+  CK(launch_solve_lambda(h->partA, h->partR, g.op, g.rho_k3 ? gp : g.op, h->k, h->p, h->global, h->active, h->lam,
+                         h->rho_rec, h->st, h->gws, g.alpha_circ, s));
   REC(3); REC(4);
   CK(launch_update_xr<T>(X, R, P, Q, h->n, h->k, h->p, h->global, h->lam, h->active, h->partRho, h->partN, h->st,
                          gu, s, dinv_of<T>(h)));
   REC(5); REC(6);
-  CK(launch_solve_beta(h->partRho, h->partN, gu, gu, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
+  CK(launch_solve_beta(h->partRho, h->partN, gu, gu, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
+                       h->active,
                        h->block_iters, h->rho_rec, h->beta, h->st, h->gws, g.rho_circ, s));
   REC(7); REC(8);
-  CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv_of<T>(h)));
+  CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv_of<T>(h),
+                        h->partR));
   REC(9);
 #undef REC
   return BCG_OK;
@@ -270,21 +298,21 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
 // One iteration with large blocks (p > 32): tiled products. The direction update cannot run in place across
 // column tiles, so it writes into the Q buffer (free at that point) and the caller swaps P and Q.
 template <typename T>
-bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g,
-                               double tol2) {
+bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g) {
   cudaStream_t s = h->stream;
   const int ch = g.op;
   CK(launch_lp_bop<T>(A, P, Q, h->n, h->k, h->st, h->nsm, s));
   CK(launch_lp_gram<T>(P, Q, h->n, h->k, h->p, h->global, h->active, h->partA, ch, h->st, s, nullptr));
   CK(launch_lp_gram<T>(P, R, h->n, h->k, h->p, h->global, h->active, h->partR, ch, h->st, s, nullptr));
-  CK(launch_solve_lambda(h->partA, h->partR, ch, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
+  CK(launch_solve_lambda(h->partA, h->partR, ch, ch, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
                          h->gws, 0, s));
   CK(launch_lp_baxpy<T>(X, X, P, h->lam, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 0, s, nullptr));
   CK(launch_lp_baxpy<T>(R, R, Q, h->lam, h->n, h->k, h->p, h->global, -1.0, h->active, h->st, 0, s, nullptr));
   // rho = <<Z, R>> with Z = M^{-1} R formed on the fly
   CK(launch_lp_gram<T>(R, R, h->n, h->k, h->p, h->global, h->active, h->partRho, ch, h->st, s, dinv_of<T>(h)));
   CK(launch_lp_colnorm<T>(R, h->n, h->k, h->partN, g.res, h->st, s));   // a full-GPU grid, like K0's
-  CK(launch_solve_beta(h->partRho, h->partN, ch, g.res, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
+  CK(launch_solve_beta(h->partRho, h->partN, ch, g.res, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
+                       h->active,
                        h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s));
   CK(launch_lp_baxpy<T>(Q, R, P, h->beta, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 1, s, dinv_of<T>(h)));
   return BCG_OK;
@@ -323,6 +351,7 @@ bcg_status read_status(bcg_ctx *h) {
 template <typename T>
 bcg_status run_iterations(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g, double tol2,
                           int maxit, cudaGraphExec_t *cached, int *cached_batch) {
+  CKS(set_tol2(h, tol2));
   CKS(read_status(h));
   int launched = 0;
   const int batch = h->check_every;
@@ -330,7 +359,7 @@ bcg_status run_iterations(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, c
     while (h->h_st->flags == 0 && launched < maxit) {
       const int nb = std::min(batch, maxit - launched);
       for (int i = 0; i < nb; ++i) {
-        CKS(launch_iteration_lp<T>(h, A, X, R, P, Q, g, tol2));
+        CKS(launch_iteration_lp<T>(h, A, X, R, P, Q, g));
         std::swap(P, Q);
       }
       launched += nb;
@@ -359,7 +388,7 @@ bcg_status run_iterations(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, c
         cudaGraph_t graph = nullptr;
         CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
         bcg_status sc = BCG_OK;
-        for (int i = 0; i < nb && sc == BCG_OK; ++i) sc = launch_iteration<T>(h, A, X, R, P, Q, g, tol2);
+        for (int i = 0; i < nb && sc == BCG_OK; ++i) sc = launch_iteration<T>(h, A, X, R, P, Q, g);
         cudaError_t ec = cudaStreamEndCapture(h->stream, &graph);
         if (sc != BCG_OK) {
           if (graph) cudaGraphDestroy(graph);
@@ -379,7 +408,7 @@ bcg_status run_iterations(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, c
       CK(cudaGraphLaunch(exec, h->stream));
     } else {
       for (int i = 0; i < nb; ++i)
-        CKS(launch_iteration<T>(h, A, X, R, P, Q, g, tol2, h->profile ? &h->ev[10 * i] : nullptr));
+        CKS(launch_iteration<T>(h, A, X, R, P, Q, g, h->profile ? &h->ev[10 * i] : nullptr));
     }
     launched += nb;
     const int before = h->h_st->iter;
@@ -431,6 +460,7 @@ bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int ma
                              dinv_of<double>(h)));
   CK(launch_init_status(h->partN, h->g64.res, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters,
                         h->lam, h->beta, h->st, s));
+  CKS(first_rho_rec<double>(h, h->P, h->R, h->g64));
   CKS(run_iterations<double>(h, h->A64, X, h->R, h->P, h->Q, h->g64, tol2, maxit, nullptr, nullptr));
   const DevStatus fin = *h->h_st;
   CKS(fill_block_iters(h));
@@ -492,6 +522,7 @@ bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int 
     CK(cudaMemsetAsync(h->D32, 0, sizeof(float) * nk, s));
     CK(launch_init_status(h->partN, h->g64.res, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters,
                           h->lam, h->beta, h->st, s));
+    CKS(first_rho_rec<float>(h, h->P32, h->R32, h->g32));
     CKS(run_iterations<float>(h, h->A32, h->D32, h->R32, h->P32, h->Q32, h->g32, itol2, maxit, &h->graph32,
                               &h->graph32_batch));
     const DevStatus fin = *h->h_st;
@@ -527,7 +558,7 @@ bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int 
 // (sums1 = [alpha | rho_rec] after phase 1, sums2 = [rho | column norms] after phase 2); the caller sums
 // these over ranks (an allreduce) between the phases, so every rank runs the p x p solves on the same data.
 // The caller also refreshes the halo rows of P before every phase 1.
-bcg_status rows_phase(bcg_ctx *h, int phase, double tol2) {
+bcg_status rows_phase(bcg_ctx *h, int phase) {
   cudaStream_t s = h->stream;
   const StreamGrids &g = h->g64;
   const int64_t E = (int64_t)h->k * h->p;
@@ -546,9 +577,10 @@ bcg_status rows_phase(bcg_ctx *h, int phase, double tol2) {
                                 h->partR, h->st, g.op, s));
     }
     CK(launch_sum_partials(h->partA, g.op, E, h->sums1, h->nsm, s));
-    CK(launch_sum_partials(h->partR, g.op, E, h->sums1 + E, h->nsm, s));
+    // the recomputed rho: from this K1, or (rho_k3) already summed after the previous K3 / the start
+    if (!g.rho_k3) CK(launch_sum_partials(h->partR, g.op, E, h->sums1 + E, h->nsm, s));
   } else if (phase == 2) {
-    CK(launch_solve_lambda(h->sums1, h->sums1 + E, 1, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
+    CK(launch_solve_lambda(h->sums1, h->sums1 + E, 1, 1, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
                            h->gws, lp ? 0 : g.alpha_circ, s));
     if (lp) {
       CK(launch_lp_baxpy<double>(h->X_rows, h->X_rows, h->P, h->lam, h->n, h->k, h->p, h->global, 1.0, h->active,
@@ -567,14 +599,17 @@ bcg_status rows_phase(bcg_ctx *h, int phase, double tol2) {
       CK(launch_sum_partials(h->partN, gu, h->k, h->sums2 + E, h->nsm, s));
     }
   } else {
-    CK(launch_solve_beta(h->sums2, h->sums2 + E, 1, 1, h->k, h->p, h->global, tol2, h->r0n2, h->rn2, h->active,
+    CK(launch_solve_beta(h->sums2, h->sums2 + E, 1, 1, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
+                         h->active,
                          h->block_iters, h->rho_rec, h->beta, h->st, h->gws, lp ? 0 : g.rho_circ, s));
     if (lp) {
       CK(launch_lp_baxpy<double>(h->Q, h->R, h->P, h->beta, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 1, s,
                                  dinv));
       std::swap(h->P, h->Q);   // the new P was written into Q's buffer
     } else {
-      CK(launch_update_p<double>(h->P, h->R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv));
+      CK(launch_update_p<double>(h->P, h->R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv,
+                                 h->partR));
+      if (g.rho_k3) CK(launch_sum_partials(h->partR, gp, E, h->sums1 + E, h->nsm, s));
     }
   }
   return BCG_OK;
@@ -896,11 +931,15 @@ bcg_status bcg_rows_start(bcg_handle h, const double *B, double *X, double tol) 
   if (!(tol >= 0.0)) return fail(BCG_ERR_INVALID_ARG, "tol=%g must be >= 0", tol);
   if (h->sums1 == nullptr) return fail(BCG_ERR_INVALID_ARG, "bcg_rows_bind has not been called");
   h->X_rows = X;
-  h->tol2_rows = tol * tol;
+  CKS(set_tol2(h, tol * tol));
   const int64_t E = (int64_t)h->k * h->p;
   CK(launch_residual<double>(h->A64, X, B, h->R, h->P, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, h->stream,
                              dinv_of<double>(h)));
   CK(launch_sum_partials(h->partN, h->g64.res, h->k, h->sums2 + E, h->nsm, h->stream));
+  if (h->g64.rho_k3) {   // the first recomputed rho travels in sums1 with the first alpha
+    CKS(first_rho_rec<double>(h, h->P, h->R, h->g64));
+    CK(launch_sum_partials(h->partR, h->precond ? h->g64.pup_zs : h->g64.pup, E, h->sums1 + E, h->nsm, h->stream));
+  }
   return BCG_OK;
 }
 
@@ -916,7 +955,7 @@ bcg_status bcg_rows_phase(bcg_handle h, int32_t phase) {
   CKS(rows_handle(h));
   if (phase < 1 || phase > 3) return fail(BCG_ERR_INVALID_ARG, "phase=%d must be 1, 2 or 3", phase);
   if (h->X_rows == nullptr) return fail(BCG_ERR_INVALID_ARG, "bcg_rows_start has not been called");
-  return rows_phase(h, phase, h->tol2_rows);
+  return rows_phase(h, phase);
 }
 
 bcg_status bcg_rows_pack(bcg_handle h, const int32_t *rows, int64_t nrows, double *buf) {

@@ -344,8 +344,9 @@ __device__ __forceinline__ bool block_active(const int *__restrict__ active, int
 // ---------------------------------------------------------------------------------------------------
 // K1: Q = A P (BOP), alpha = <<P, Q>>_S, and the recomputed rho^{i-1} = <<P, R^{i-1}>>_S (BDOT x 2),
 // one pass over the rows. A CTA pass covers RPT * rpp consecutive rows; slot g handles rows
-// row0 + u*rpp + g, u < RPT.
-template <typename T, int OPK, int PM>
+// row0 + u*rpp + g, u < RPT. Without RR the recomputed rho comes from the previous iteration's K3 and R is
+// not read.
+template <typename T, int OPK, int PM, bool RR>
 __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
                                                  T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                  const int *__restrict__ active, double *__restrict__ partA,
@@ -366,8 +367,9 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
   const bool act = slot && block_active(active, global, j);
   double *slotA = redA + ((int64_t)g * k + c) * p, *slotR = redR + ((int64_t)g * k + c) * p;
   if (slot)
-    for (int a = 0; a < p; ++a) { slotA[a] = 0.0; slotR[a] = 0.0; }
-  GramAcc<PM> accA, accR;
+    for (int a = 0; a < p; ++a) { slotA[a] = 0.0; if (RR) slotR[a] = 0.0; }
+  GramAcc<PM> accA;
+  GramAcc<RR ? PM : 1> accR;
   accA.zero();
   accR.zero();
   int pass = 0;
@@ -383,7 +385,7 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
       if (act && r < n) {
         const int64_t o = r * k + c;
         pv[u] = P[o];
-        rv[u] = R[o];
+        if (RR) rv[u] = R[o];
         qv[u] = apply_row<T, OPK>(A, P, r, k, c);
       }
     }
@@ -405,7 +407,7 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
         for (int a = 0; a < PM; ++a) {
           if (a < p) {
             G::add(accA.s[a], accA.c[a], prow[a], qb[u]);
-            G::add(accR.s[a], accR.c[a], prow[a], rb[u]);
+            if constexpr (RR) G::add(accR.s[a], accR.c[a], prow[a], rb[u]);
           }
         }
       }
@@ -413,13 +415,13 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
     row_sync(wl);
     if (++pass == kFlushPasses / RPT) {
       pass = 0;
-      if (slot) { accA.flush(slotA, p); accR.flush(slotR, p); }
+      if (slot) { accA.flush(slotA, p); if (RR) accR.flush(slotR, p); }
     }
   }
-  if (slot) { accA.flush(slotA, p); accR.flush(slotR, p); }
+  if (slot) { accA.flush(slotA, p); if (RR) accR.flush(slotR, p); }
   const int E = k * p;
   cta_sum_slots(redA, E, rpp, partA + (int64_t)blockIdx.x * E);
-  cta_sum_slots(redR, E, rpp, partR + (int64_t)blockIdx.x * E);
+  if constexpr (RR) cta_sum_slots(redR, E, rpp, partR + (int64_t)blockIdx.x * E);
 }
 
 // ---------------------------------------------------------------------------------------------------

@@ -237,22 +237,33 @@ __host__ __device__ constexpr size_t wc_upd_smem(int k, int p, int global, int V
   return align16((size_t)kWarps * wc_upd_warp_bytes<T>(V) + (size_t)(global ? 1 : k / p) * p * p * sizeof(T)) +
          (size_t)kNT * (p + 1) * sizeof(double);
 }
-__host__ __device__ constexpr size_t wc_pup_smem(int k, int p, int global, size_t tsize, int V) {
-  return (size_t)kWarps * 3 * 32 * V * tsize + (size_t)(global ? 1 : k / p) * p * p * tsize;
+// K3: 3 T tiles (P, Z, P_new) per warp, plus (RR) P_new and R as Dot2 operands and the FP64 slots of rho
+template <typename T>
+__host__ __device__ constexpr size_t wc_pup_warp_bytes(int V, bool rr) {
+  return (size_t)32 * V * (3 * sizeof(T) + (rr ? 2 * wc_bt_size<T>() : 0));
+}
+template <typename T>
+__host__ __device__ constexpr size_t wc_pup_smem(int k, int p, int global, int V, bool rr) {
+  return align16((size_t)kWarps * wc_pup_warp_bytes<T>(V, rr) + (size_t)(global ? 1 : k / p) * p * p * sizeof(T)) +
+         (rr ? (size_t)kNT * p * sizeof(double) : 0);
 }
 
 // ---------------------------------------------------------------------------------------------------
-// K1 (warp-chunk): Q = A P, alpha = <<P, Q>>_S, recomputed rho = <<P, R>>_S.
+// K1 (warp-chunk): Q = A P, alpha = <<P, Q>>_S, and (RR) the recomputed rho = <<P, R>>_S; without RR the
+// previous iteration's K3 has formed the recomputed rho and K1 does not read R.
 // at least 3 CTAs per SM up to p = 16; p = 32 needs its registers (64 accumulator pairs per thread)
 template <int PM>
 constexpr int wc_min_ctas() { return PM <= 16 ? 3 : 1; }
 // the FP32 CSR K1 up to p = 8 runs faster at 4 CTAs per SM despite a few spilled registers (0.73 -> 0.67 ms,
-// 128^3, k = 32); the stencil and FP64 instantiations measured slower there
-template <typename T, int OPK, int PM>
-constexpr int wc_min_ctas_op() { return (sizeof(T) == 4 && OPK == OP_CSR && PM <= 8) ? 4 : wc_min_ctas<PM>(); }
+// 128^3, k = 32); the FP64 CSR K1 fits 4 CTAs without spills once the recomputed rho has moved to K3 (with it,
+// 4 CTAs spilled and measured slower); the stencil instantiations stay at 3
+template <typename T, int OPK, int PM, bool RR>
+constexpr int wc_min_ctas_op() {
+  return (OPK == OP_CSR && PM <= 8 && (sizeof(T) == 4 || !RR)) ? 4 : wc_min_ctas<PM>();
+}
 
-template <typename T, int OPK, int PM, int V>
-__global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM>()) kw_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
+template <typename T, int OPK, int PM, int V, bool RR>
+__global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM, RR>()) kw_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
                                                   T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                   const int *__restrict__ active, double *__restrict__ partA,
                                                   double *__restrict__ partR, const DevStatus *__restrict__ st) {
@@ -271,12 +282,12 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM>()) kw_op_gram(
   const int c = geo.col, j = c / p, b = c - j * p;
   const bool act = block_active(active, global, j);
   double *slotA = redA + threadIdx.x * p, *slotR = redR + threadIdx.x * p;
-  for (int a = 0; a < p; ++a) { slotA[a] = 0.0; slotR[a] = 0.0; }
+  for (int a = 0; a < p; ++a) { slotA[a] = 0.0; if (RR) slotR[a] = 0.0; }
   // alpha is symmetric: lane b accumulates only its circulant diagonals d = 0..p/2, entry ((b + d) mod p, b)
   // (d = p/2 only for b < p/2); the recomputed rho stays a full product. p == PM here (p divides 32).
   constexpr int PMH = PM == 1 ? 1 : PM / 2 + 1;
   GramAcc<PMH> accA;
-  GramAcc<PM> accR;
+  GramAcc<RR ? PM : 1> accR;
   accA.zero();
   accR.zero();
   int pass = 0;
@@ -290,7 +301,7 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM>()) kw_op_gram(
     if (row < n) {
       const int64_t o = row * kv + mc / V;
       pv.v = reinterpret_cast<const VT *>(P)[o];
-      rv.v = reinterpret_cast<const VT *>(R)[o];
+      if constexpr (RR) rv.v = reinterpret_cast<const VT *>(R)[o];
       qv = apply_row_vec<T, OPK, V>(A, P, row, k, mc);
       reinterpret_cast<VT *>(Q)[o] = qv.v;
     } else {
@@ -302,19 +313,22 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM>()) kw_op_gram(
       const int t = 32 * geo.sm + geo.om + v;
       sP[t] = G::conv(pv.e[v]);
       sQ[t] = G::conv(qv.e[v]);
-      sR[t] = G::conv(rv.e[v]);
+      if constexpr (RR) sR[t] = G::conv(rv.e[v]);
     }
     __syncwarp();
     if (act) {
 #pragma unroll
       for (int s = 0; s < V; ++s) {
         const int t = 32 * s + geo.lane;
-        const BT qb = sQ[t], rb2 = sR[t];
+        const BT qb = sQ[t];
         const BT *rowp = sP + t - b;
-        BT prow[PM];
-        load_row<BT, PM>(rowp, prow, p);
+        if constexpr (RR) {
+          const BT rb2 = sR[t];
+          BT prow[PM];
+          load_row<BT, PM>(rowp, prow, p);
 #pragma unroll
-        for (int a = 0; a < PM; ++a) G::add(accR.s[a], accR.c[a], prow[a], rb2);
+          for (int a = 0; a < PM; ++a) G::add(accR.s[a], accR.c[a], prow[a], rb2);
+        }
 #pragma unroll
         for (int d = 0; d < PMH; ++d)
           if (PM == 1 || d < PM / 2 || b < PM / 2) G::add(accA.s[d], accA.c[d], rowp[(b + d) & (PM - 1)], qb);
@@ -324,14 +338,14 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM>()) kw_op_gram(
     if (++pass == kFlushPasses / V) {
       pass = 0;
       accA.flush(slotA, PMH);
-      accR.flush(slotR, p);
+      if constexpr (RR) accR.flush(slotR, p);
     }
   }
   accA.flush(slotA, PMH);
-  accR.flush(slotR, p);
+  if constexpr (RR) accR.flush(slotR, p);
   const int E = k * p;
   wc_cta_reduce(redA, k, p, partA + (int64_t)blockIdx.x * E);
-  wc_cta_reduce(redR, k, p, partR + (int64_t)blockIdx.x * E);
+  if constexpr (RR) wc_cta_reduce(redR, k, p, partR + (int64_t)blockIdx.x * E);
 }
 
 // ---------------------------------------------------------------------------------------------------
@@ -474,24 +488,37 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_x
 
 // ---------------------------------------------------------------------------------------------------
 // K3 (warp-chunk): P = Z + P beta (ZS: Z = M^{-1} R, else Z = R).
-template <typename T, int PM, int V, bool ZS>
+// RR: also the recomputed rho of the next iteration, <<P_new, R>>_S (Algorithm 1 recomputes
+// rho^{i-1} = <<P^i, R^{i-1}>>_S; both operands are in this kernel's registers, and its FP32 pipes are idle
+// while it waits on the FP64 pipe or on HBM). Partials as in K1, entry (a, b) of block j at j*p*p + b*p + a.
+template <typename T, int PM, int V, bool ZS, bool RR>
 __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *__restrict__ R, int64_t n, int k,
                                                    int p, int global, const double *__restrict__ beta,
                                                    const int *__restrict__ active, DevStatus *__restrict__ st,
-                                                   const T *__restrict__ dinv) {
+                                                   const T *__restrict__ dinv, double *__restrict__ partR) {
+  using G = Gram<T>;
+  using BT = typename G::B;
   using VT = typename VecOf<T, V>::type;
   if (st->flags != 0) return;
   if (blockIdx.x == 0 && threadIdx.x == 0) st->cur += 1;   // no other kernel of this launch reads it
   extern __shared__ __align__(16) unsigned char smem[];
   WcGeom geo;
   geo.init(n, k, V);
-  T *sP = reinterpret_cast<T *>(smem) + (size_t)geo.warp * 3 * 32 * V;
+  unsigned char *wbase = smem + (size_t)geo.warp * wc_pup_warp_bytes<T>(V, RR);
+  T *sP = reinterpret_cast<T *>(wbase);
   T *sR = sP + 32 * V, *sN = sR + 32 * V;
+  BT *sNb = reinterpret_cast<BT *>(sN + 32 * V);   // RR: P_new (broadcast) and R (own) as Dot2 operands
+  BT *sRb = sNb + 32 * V;
   const int nblk = global ? 1 : k / p;
-  T *sB = reinterpret_cast<T *>(smem) + (size_t)kWarps * 3 * 32 * V;
+  T *sB = reinterpret_cast<T *>(smem + (size_t)kWarps * wc_pup_warp_bytes<T>(V, RR));
+  double *red = reinterpret_cast<double *>(smem + align16((size_t)kWarps * wc_pup_warp_bytes<T>(V, RR) +
+                                                          (size_t)nblk * p * p * sizeof(T)));
   for (int e = threadIdx.x; e < nblk * p * p; e += blockDim.x) sB[e] = (T)beta[e];
   const int c = geo.col, j = c / p, b = c - j * p;
   const bool act = block_active(active, global, j);
+  double *slotR = red + threadIdx.x * p;
+  if constexpr (RR)
+    for (int a = 0; a < p; ++a) slotR[a] = 0.0;
   __syncthreads();
   T bcol[PM];
   {
@@ -499,6 +526,9 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
 #pragma unroll
     for (int a = 0; a < PM; ++a) bcol[a] = a < p ? bj[a * p] : T(0);
   }
+  GramAcc<RR ? PM : 1> acc;
+  acc.zero();
+  int pass = 0;
   const int kv = k / V;
   for (int64_t rb = geo.rb0; rb < geo.nrb; rb += geo.rbs) {
     const int64_t R0 = rb * geo.rc;
@@ -506,22 +536,27 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
     int mc;
     geo.mem_pos(R0, row, mc);
     const int64_t o = row * kv + mc / V;
-    VecU<T, V> pv, rv;
+    VecU<T, V> pv, rv, zv;
     if (row < n) {
       pv.v = reinterpret_cast<const VT *>(P)[o];
       rv.v = reinterpret_cast<const VT *>(R)[o];
+      zv = rv;
       if constexpr (ZS) {   // Z = M^{-1} R
         const T di = dinv[row];
 #pragma unroll
-        for (int v = 0; v < V; ++v) rv.e[v] *= di;
+        for (int v = 0; v < V; ++v) zv.e[v] *= di;
       }
     } else {
 #pragma unroll
-      for (int v = 0; v < V; ++v) pv.e[v] = rv.e[v] = T(0);
+      for (int v = 0; v < V; ++v) pv.e[v] = rv.e[v] = zv.e[v] = T(0);
     }
     const int tm = 32 * geo.sm + geo.om;
 #pragma unroll
-    for (int v = 0; v < V; ++v) { sP[tm + v] = pv.e[v]; sR[tm + v] = rv.e[v]; }
+    for (int v = 0; v < V; ++v) {
+      sP[tm + v] = pv.e[v];
+      sR[tm + v] = zv.e[v];
+      if constexpr (RR) sRb[tm + v] = G::conv(rv.e[v]);
+    }
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < V; ++s) {
@@ -536,8 +571,27 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
           if (a < p) out = fma_t(prow[a], bcol[a], out);
       }
       sN[t] = out;
+      if constexpr (RR) sNb[t] = G::conv(out);
     }
     __syncwarp();
+    if constexpr (RR) {
+      if (act) {
+#pragma unroll
+        for (int s = 0; s < V; ++s) {
+          const int t = 32 * s + geo.lane;
+          BT nrow[PM];
+          load_row<BT, PM>(sNb + t - b, nrow, p);
+          const BT rb2 = sRb[t];
+#pragma unroll
+          for (int a = 0; a < PM; ++a)
+            if (a < p) G::add(acc.s[a], acc.c[a], nrow[a], rb2);
+        }
+      }
+      if (++pass == kFlushPasses / V) {
+        pass = 0;
+        acc.flush(slotR, p);
+      }
+    }
     if (row < n) {
       VecU<T, V> po;
 #pragma unroll
@@ -545,6 +599,10 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
       reinterpret_cast<VT *>(P)[o] = po.v;
     }
     __syncwarp();
+  }
+  if constexpr (RR) {
+    acc.flush(slotR, p);
+    wc_cta_reduce(red, k, p, partR + (int64_t)blockIdx.x * k * p);
   }
 }
 

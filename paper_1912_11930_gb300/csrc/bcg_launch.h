@@ -22,6 +22,7 @@ struct StreamGrids {
   int res;       // K0 CTAs
   int alpha_circ;   // K1 stores alpha by circulant diagonals (symmetric product, half the terms)
   int rho_circ;     // K2 stores rho by circulant diagonals
+  int rho_k3;       // the recomputed rho is formed by K3 (next iteration's) and a BDOT after K0, not by K1
 };
 
 // Sizes the grids for n rows from the occupancy of each kernel variant (capped to whole waves of SMs).
@@ -39,8 +40,10 @@ cudaError_t launch_update_xr(T *X, T *R, const T *P, const T *Q, int64_t n, int 
                              const double *lam, const int *active, double *partRho, double *partN,
                              const DevStatus *st, int grid, cudaStream_t s, const T *dinv);
 template <typename T>
+// partR: with rho_k3, the partials of the next iteration's recomputed rho <<P_new, R>>_S (one row per CTA)
 cudaError_t launch_update_p(T *P, const T *R, int64_t n, int k, int p, int global, const double *beta,
-                            const int *active, DevStatus *st, int grid, cudaStream_t s, const T *dinv);
+                            const int *active, DevStatus *st, int grid, cudaStream_t s, const T *dinv,
+                            double *partR);
 template <typename T>
 cudaError_t launch_residual(const OpDesc &A, const T *X, const T *B, T *R, T *P, float *R32, float *P32, int64_t n,
                             int k, double *partN, int grid, cudaStream_t s, const T *dinv);
@@ -76,12 +79,14 @@ size_t small_ws_doubles(int p);
 bool small_needs_gws(int p);
 
 cudaError_t small_prepare(int p);
-cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int k, int p, int global,
-                                const int *active, double *lam, double *rho_rec, DevStatus *st, double *gws,
-                                int alpha_circ, cudaStream_t s);
+// nparts: partial rows of alpha; nparts_r: partial rows of the recomputed rho
+cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int nparts_r, int k, int p,
+                                int global, const int *active, double *lam, double *rho_rec, DevStatus *st,
+                                double *gws, int alpha_circ, cudaStream_t s);
 // nparts: partial rows of rho; nparts_n: partial rows of the column norms
 cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int nparts_n, int k, int p,
-                              int global, double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
+                              int global, const double *tol2, const double *r0n2, double *rn2, int *active,
+                              int *block_iters,
                               const double *rho_rec, double *beta, DevStatus *st, double *gws, int rho_circ,
                               cudaStream_t s);
 cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, int global, double *r0n2, double *rn2,

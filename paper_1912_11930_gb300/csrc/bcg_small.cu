@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
                                                            int p, int global, const int *__restrict__ active,
                                                            double *__restrict__ lam, double *__restrict__ rho_rec,
                                                            DevStatus *st, double *gws, int alpha_circ,
-                                                           int split) {
+                                                           int split, int nparts_r) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   const int pp = p * p;
@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
   reduce_block(partA, nparts, k, p, global, jb, tmp, scr);
   if (alpha_circ) unpack_circulant(tmp, sA, p);
   else transpose_into(tmp, sA, p);
-  reduce_block(partR, nparts, k, p, global, jb, tmp, scr);
+  reduce_block(partR, nparts_r, k, p, global, jb, tmp, scr);
   transpose_into(tmp, sR, p);
   for (int e = threadIdx.x; e < pp; e += blockDim.x) rho_rec[(int64_t)jb * pp + e] = sR[e];
   {
@@ -232,7 +232,8 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
 // K4b: per-column norms, stopping test, beta_j = rho_rec_j^{-1} rho_j by LU with partial pivoting.
 __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restrict__ partRho,
                                                          const double *__restrict__ partN, int nparts, int k, int p,
-                                                         int global, double tol2, const double *__restrict__ r0n2,
+                                                         int global, const double *__restrict__ tol2p,
+                                                         const double *__restrict__ r0n2,
                                                          double *__restrict__ rn2, int *__restrict__ active,
                                                          int *__restrict__ block_iters,
                                                          const double *__restrict__ rho_rec,
@@ -243,6 +244,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
   if (!active[jb]) return;
   const int pp = p * p;
   const int it = st->cur;
+  const double tol2 = *tol2p;   // squared tolerance in device memory: a captured graph serves every tolerance
   const int c0 = global ? 0 : jb * p, c1 = global ? k : c0 + p;
   extern __shared__ __align__(16) double sm_dyn[];
   double *sm = gws ? gws + (int64_t)jb * small_ws_doubles_dev(p) : sm_dyn;
@@ -637,21 +639,23 @@ static cudaError_t launch_trsm(int p, int nblk, int chol, const double *gws, con
   return cudaGetLastError();
 }
 
-cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int k, int p, int global,
-                                const int *active, double *lam, double *rho_rec, DevStatus *st, double *gws,
-                                int alpha_circ, cudaStream_t s) {
+cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int nparts_r, int k, int p,
+                                int global, const int *active, double *lam, double *rho_rec, DevStatus *st,
+                                double *gws, int alpha_circ, cudaStream_t s) {
   const int nblk = global ? 1 : k / p;
   if (small_needs_gws(p) && gws == nullptr) return cudaErrorInvalidValue;
   const int split = small_split(p) ? 1 : 0;
   k_solve_lambda<<<nblk, kSmallNT, small_smem(p), s>>>(partA, partR, nparts, k, p, global, active, lam, rho_rec, st,
-                                                       small_needs_gws(p) ? gws : nullptr, alpha_circ, split);
+                                                       small_needs_gws(p) ? gws : nullptr, alpha_circ, split,
+                                                       nparts_r);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !split) return e;
   return launch_trsm(p, nblk, 1, gws, active, lam, st, s);
 }
 
 cudaError_t launch_solve_beta(const double *partRho, const double *partN, int nparts, int nparts_n, int k, int p,
-                              int global, double tol2, const double *r0n2, double *rn2, int *active, int *block_iters,
+                              int global, const double *tol2, const double *r0n2, double *rn2, int *active,
+                              int *block_iters,
                               const double *rho_rec, double *beta, DevStatus *st, double *gws, int rho_circ,
                               cudaStream_t s) {
   const int nblk = global ? 1 : k / p;

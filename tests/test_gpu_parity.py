@@ -389,3 +389,23 @@ def test_large_p_breakdown_and_frozen_blocks(torch_dev):
     assert r.block_iters[0] == 0 and np.all(X[:, :64] == 0.0)
     ref = O.solve(M.to_scipy(), B[:, 64:], p=64, sub="classical", tol=0.0, maxit=m)
     assert _rel(X[:, 64:], ref.X) <= 1e-9
+
+
+def test_mixed_graph_replay_matches_plain_launches(torch_dev):
+    """The refinement steps ask their inner solves for different tolerances; the captured batch of inner
+    iterations must honour each one: graphs on and off give the same bits over three refinement steps."""
+    torch, dev = torch_dev
+    from paper_1912_11930_gb300 import bcg
+    M = mat("p3d_30")
+    B = torch.from_numpy(W.rhs(M.n, 16, seed=61)).to(dev)
+    S = bcg.Solver.from_matrix(M, k=16, p=8, sub="hybrid", prec="fp32_refine", device=dev)
+    X_g, r_g = S.solve(B, tol=1e-12, maxit=5000)
+    S.set_option("graph", 0)
+    X_n, r_n = S.solve(B, tol=1e-12, maxit=5000)
+    S.set_option("graph", 1)
+    X_g2, r_g2 = S.solve(B, tol=1e-9, maxit=5000)     # the cached graph serves another tolerance
+    S.set_option("graph", 0)
+    X_n2, r_n2 = S.solve(B, tol=1e-9, maxit=5000)
+    S.close()
+    assert r_g.ok and r_g.outer_iters >= 3 and r_g.iters == r_n.iters and torch.equal(X_g, X_n)
+    assert r_g2.ok and r_g2.iters == r_n2.iters and torch.equal(X_g2, X_n2)
