@@ -351,9 +351,12 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM, RR>()) kw_op_g
 // ---------------------------------------------------------------------------------------------------
 // K2 (warp-chunk): X += P lambda, R -= Q lambda, rho = <<Z, R>>_S, column norms (ZS: Z = M^{-1} R).
 // K2 keeps fewer live values than K1: its unpreconditioned FP32 instantiations up to p = 8 fit 64 registers
-// (4 CTAs per SM)
+// (4 CTAs per SM); the FP64 one at p = 16 runs better at 2 CTAs without spills than at 3 with them
+// (3.61 / 3.71 ms, 128^3, k = 32)
 template <typename T, int PM, bool ZS>
-constexpr int wc_min_ctas_upd() { return (sizeof(T) == 4 && PM <= 8 && !ZS) ? 4 : wc_min_ctas<PM>(); }
+constexpr int wc_min_ctas_upd() {
+  return (sizeof(T) == 4 && PM <= 8 && !ZS) ? 4 : ((sizeof(T) == 8 && PM == 16) ? 2 : wc_min_ctas<PM>());
+}
 
 template <typename T, int PM, int V, bool ZS>
 __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_xr(T *__restrict__ X, T *__restrict__ R, const T *__restrict__ P,
