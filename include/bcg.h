@@ -136,10 +136,15 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
 
 /*
  * bcg_set_option -- tune a handle. Keys:
- *   "inner_tol"    FP32_REFINE: smallest relative residual reduction an inner solve is asked for
- *                  (default 3e-5); each inner solve targets the reduction still needed by the outer
- *                  tolerance (times 0.5), but not less than this
- *   "max_outer"    FP32_REFINE: maximum refinement steps (default 30)
+ *   "refine"       FP32_REFINE strategy: 1 (default) residual replacement -- one FP32 block CG process whose
+ *                  correction is flushed into the FP64 X, and whose residual is replaced by the FP64
+ *                  B - A X, every time its residual has dropped tenfold (the process is restarted only if
+ *                  a block's FP32 directions lose rank); 0 restarted iterative refinement -- every step
+ *                  solves A D = R from D = 0 in FP32 and adds D to X in FP64
+ *   "inner_tol"    FP32_REFINE with refine = 0: smallest relative residual reduction an inner solve is
+ *                  asked for (default 3e-5); each inner solve targets the reduction still needed by the
+ *                  outer tolerance (times 0.5), but not less than this
+ *   "max_outer"    FP32_REFINE with refine = 0: maximum refinement steps (default 30)
  *   "check_every"  iterations launched between two host reads of the device status word (default 8;
  *                  converged iterations in between are skipped on the device at launch cost only)
  *   "graph"        1 = replay the batch of iterations as a captured CUDA graph, 0 = plain launches

@@ -94,6 +94,7 @@ struct bcg_ctx {
   int use_graph = 1;
   int profile = 0;
   int precond = 0;                     // 0: M = I; 1: Jacobi, M = diag(A)
+  int refine = 1;                      // FP32_REFINE: 1 residual replacement, 0 restarted refinement
   // live per-kernel timing (profile = 1): CUDA events around every launch of an executed iteration
   static constexpr int kKernels = 6;   // K1 op_gram, K4a solve_lambda, K2 update_xr, K4b solve_beta, K3 update_p, K0 residual
   double prof_ms[kKernels] = {0, 0, 0, 0, 0, 0};
@@ -488,7 +489,106 @@ bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int ma
   return st;
 }
 
-// FP64 iterative refinement around FP32 inner block-CG solves.
+// FP32 block CG with FP64 residual replacement (refine = 1). One Krylov process in FP32 (BOP and block updates;
+// Gram matrices FP64-accurate, p x p solves in FP64) accumulates a correction D; whenever its recursive
+// residual has dropped by kReplaceDrop since the last replacement, and when every block has stopped, the
+// correction is flushed into the FP64 iterate (X += D, D = 0) and the residual is replaced by the FP64 true
+// residual B - A X. P is kept, and Algorithm 1 recomputes rho = <<P, R>>_S from the replaced residual in the
+// next iteration, so the process continues instead of restarting. Converged when every column's true
+// residual is below tol (relative to the initial one); blocks that stopped on their recursive residual too
+// early are reopened.
+constexpr double kReplaceDrop = 0.1;
+
+bcg_status solve_replace(bcg_ctx *h, const double *B, double *X, double tol, int maxit, bcg_info *info) {
+  cudaStream_t s = h->stream;
+  const int64_t nk = h->n * h->k;
+  const double tol2 = tol * tol;
+  // (re)start of the Krylov process from the FP64 residual: R32 = fl(R), P32 = fl(M^{-1} R), D = 0. The per-column
+  // stopping test stays relative to the initial residual (r0n2 = the first start's norms).
+  auto start = [&](bool first) -> bcg_status {
+    CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, h->R32, h->P32, h->n, h->k, h->partN, h->g64.res, s,
+                               dinv_of<double>(h)));
+    if (first) CK(launch_reduce_norms(h->partN, h->g64.res, h->k, h->outer0, s));
+    CK(launch_init_status(h->partN, h->g64.res, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters,
+                          h->lam, h->beta, h->st, s));
+    if (!first) CK(cudaMemcpyAsync(h->r0n2, h->outer0, sizeof(double) * h->k, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemsetAsync(h->D32, 0, sizeof(float) * nk, s));
+    CKS(first_rho_rec<float>(h, h->P32, h->R32, h->g32));
+    return BCG_OK;
+  };
+  CKS(start(true));
+  CKS(fetch_vec(h, h->outer0, 0));
+  bcg_status st = BCG_ERR_NOT_CONVERGED;
+  int replaced = 0, restarts = 0, stalls = 0, brk = -1, base_iters = 0;
+  double m_true = max_ratio(h->h_vec, h->h_vec, h->k) > 0 ? 1.0 : 0.0;   // relative to the initial residual
+  double last2 = 1.0, best = INFINITY;
+  if (m_true == 0.0) st = BCG_OK;   // B - A X = 0 in every column
+  while (st == BCG_ERR_NOT_CONVERGED) {
+    CKS(run_iterations<float>(h, h->A32, h->D32, h->R32, h->P32, h->Q32, h->g32, tol2, h->check_every,
+                              &h->graph32, &h->graph32_batch));
+    const DevStatus fin = *h->h_st;
+    const int iters = base_iters + fin.iter;
+    if (fin.flags & ST_NUMERIC) { st = BCG_ERR_NUMERIC; break; }
+    const bool broke = (fin.flags & ST_BREAKDOWN) != 0;
+    if (broke && fin.breakdown_iter <= 1) { brk = iters; st = BCG_ERR_BREAKDOWN; break; }
+    const bool done = (fin.flags & ST_DONE) != 0;
+    CKS(fetch_vec(h, h->rn2, 1));
+    CKS(fetch_vec(h, h->r0n2, 0));
+    double rec2 = 0.0;   // squared max relative recursive residual
+    for (int cc = 0; cc < h->k; ++cc) {
+      const double r = h->h_vec[cc] > 0 ? h->h_vec[h->k + cc] / h->h_vec[cc] : 0.0;
+      if (!(r <= rec2)) rec2 = r;
+    }
+    if (!(broke || done || rec2 < kReplaceDrop * kReplaceDrop * last2 || iters >= maxit)) continue;
+    // residual replacement: X += D, D = 0, R = B - A X in FP64 (R32 = fl(R)); P and the Krylov process stay
+    CK(launch_add_correction(X, h->D32, nk, h->nsm, s));
+    CK(cudaMemsetAsync(h->D32, 0, sizeof(float) * nk, s));
+    CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, h->R32, nullptr, h->n, h->k, h->partN, h->g64.res, s,
+                               nullptr));
+    CK(launch_reduce_norms(h->partN, h->g64.res, h->k, h->rtn2, s));
+    ++replaced;
+    CKS(fetch_vec(h, h->outer0, 0));
+    CKS(fetch_vec(h, h->rtn2, 2));
+    m_true = max_ratio(h->h_vec + 2 * h->k, h->h_vec, h->k);
+    if (!std::isfinite(m_true)) { st = BCG_ERR_NUMERIC; break; }
+    if (m_true <= tol) { st = BCG_OK; break; }
+    if (iters >= maxit) break;
+    if (m_true >= 0.9 * best) {
+      if (++stalls >= 3) break;
+    } else {
+      stalls = 0;
+    }
+    best = std::min(best, m_true);
+    last2 = m_true * m_true;
+    if (broke) {
+      // the FP32 directions of a block became dependent (its alpha or recomputed rho lost rank): restart the
+      // Krylov process from the FP64 residual, as a restarted refinement step would
+      base_iters = iters;
+      ++restarts;
+      CKS(start(false));
+    } else if (done) {
+      CK(launch_reactivate(h->rtn2, h->r0n2, tol2, h->k, h->p, h->global, h->active, h->st, s));
+    }
+  }
+  CKS(read_status(h));
+  const int iters = base_iters + h->h_st->iter;
+  CKS(fill_block_iters(h));
+  if (info) {
+    info->status = st;
+    info->iters = iters;
+    info->outer_iters = replaced;
+    info->breakdown_iter = brk;
+    info->max_rel_res_recursive = m_true;
+    info->max_rel_res_true = m_true;
+  }
+  if (st != BCG_OK)
+    fail(st, "mixed-precision solve stopped with status %d after %d iterations, %d replacements, %d restarts", st,
+         iters, replaced, restarts);
+  return st;
+}
+
+// FP64 iterative refinement around FP32 inner block-CG solves (refine = 0): each step restarts the inner
+// Krylov process from the FP64 residual.
 bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int maxit, bcg_info *info) {
   cudaStream_t s = h->stream;
   const int64_t nk = h->n * h->k;
@@ -737,6 +837,9 @@ bcg_status bcg_set_option(bcg_handle h, const char *key, double value) {
     if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "profile must be 0 or 1");
     h->profile = (int)value;
     for (int i = 0; i < bcg_ctx::kKernels; ++i) { h->prof_ms[i] = 0.0; h->prof_count[i] = 0; }
+  } else if (!strcmp(key, "refine")) {
+    if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "refine must be 0 (restart) or 1 (replace)");
+    h->refine = (int)value;
   } else if (!strcmp(key, "precond")) {
     if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "precond must be 0 (none) or 1 (Jacobi)");
     h->precond = (int)value;
@@ -761,13 +864,15 @@ bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(BCG_ERR_INVALID_ARG, "tol must be finite and > 0");
   if (maxit < 1) return fail(BCG_ERR_INVALID_ARG, "maxit must be >= 1");
   g_last_error.clear();
-  if (h->perm == nullptr)
-    return h->prec == BCG_FP64 ? solve_fp64(h, B, X, tol, maxit, info) : solve_refine(h, B, X, tol, maxit, info);
+  auto run = [&](const double *Bs, double *Xs) {
+    if (h->prec == BCG_FP64) return solve_fp64(h, Bs, Xs, tol, maxit, info);
+    return h->refine ? solve_replace(h, Bs, Xs, tol, maxit, info) : solve_refine(h, Bs, Xs, tol, maxit, info);
+  };
+  if (h->perm == nullptr) return run(B, X);
   // SELL-C-sigma handle: iterate on the permuted system (Pi A Pi^T)(Pi X) = Pi B
   CK(launch_permute_rows(B, h->perm, h->n, h->k, h->Bp, 0, h->nsm, h->stream));
   CK(launch_permute_rows(X, h->perm, h->n, h->k, h->Xp, 0, h->nsm, h->stream));
-  const bcg_status st = h->prec == BCG_FP64 ? solve_fp64(h, h->Bp, h->Xp, tol, maxit, info)
-                                            : solve_refine(h, h->Bp, h->Xp, tol, maxit, info);
+  const bcg_status st = run(h->Bp, h->Xp);
   if (st == BCG_ERR_INVALID_ARG || st == BCG_ERR_CUDA || st == BCG_ERR_OOM) return st;
   const std::string msg = g_last_error;
   CK(launch_permute_rows(h->Xp, h->perm, h->n, h->k, X, 1, h->nsm, h->stream));

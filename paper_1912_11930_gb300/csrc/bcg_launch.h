@@ -93,6 +93,8 @@ cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, in
                                int *active, int *block_iters, double *lam, double *beta, DevStatus *st,
                                cudaStream_t s);
 cudaError_t launch_reduce_norms(const double *partN, int nparts, int k, double *out, cudaStream_t s);
+cudaError_t launch_reactivate(const double *rtn2, const double *r0n2, double tol2, int k, int p, int global,
+                              int *active, DevStatus *st, cudaStream_t s);
 cudaError_t launch_sum_partials(const double *part, int nparts, int64_t E, double *out, int nsm, cudaStream_t s);
 cudaError_t launch_gather_rows(const double *P, const int32_t *rows, int64_t nrows, int k, double *buf, int nsm,
                                cudaStream_t s);

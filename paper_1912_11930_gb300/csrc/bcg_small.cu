@@ -513,6 +513,29 @@ __global__ void k_init_status(const double *__restrict__ partN, int nparts, int 
   }
 }
 
+// Residual replacement found columns whose true residual is not yet below the tolerance although every
+// block had stopped on its recursive residual: reopen those blocks (their P is kept) and clear the
+// "done" flag so that the iterations resume.
+__global__ void k_reactivate(const double *__restrict__ rtn2, const double *__restrict__ r0n2, double tol2, int k,
+                             int p, int global, int *__restrict__ active, DevStatus *st) {
+  const int nblk = global ? 1 : k / p;
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  for (int jb = threadIdx.x; jb < nblk; jb += blockDim.x) {
+    const int c0 = global ? 0 : jb * p, c1 = global ? k : c0 + p;
+    bool need = false;
+    for (int c = c0; c < c1; ++c) need = need || !(rtn2[c] <= tol2 * r0n2[c]);
+    active[jb] = need ? 1 : 0;
+    if (need) atomicAdd(&cnt, 1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && st->flags == ST_DONE) {
+    st->n_active = cnt;
+    st->flags = cnt > 0 ? 0 : ST_DONE;
+  }
+}
+
 // Sum BDOT partials in CTA order into gamma (per distinct block p*p, row-major a*p + b).
 __global__ void __launch_bounds__(kSmallNT) k_finish_gram(const double *__restrict__ part, int nparts, int k, int p,
                                                           int global, double *__restrict__ gamma, double *gws) {
@@ -687,6 +710,12 @@ cudaError_t launch_finish_gram(const double *part, int nparts, int k, int p, int
     if (e != cudaSuccess) return e;
   }
   k_finish_gram<<<nblk, kSmallNT, sm, s>>>(part, nparts, k, p, global, gamma, g ? gws : nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reactivate(const double *rtn2, const double *r0n2, double tol2, int k, int p, int global,
+                              int *active, DevStatus *st, cudaStream_t s) {
+  k_reactivate<<<1, kSmallNT, 0, s>>>(rtn2, r0n2, tol2, k, p, global, active, st);
   return cudaGetLastError();
 }
 

@@ -409,3 +409,24 @@ def test_mixed_graph_replay_matches_plain_launches(torch_dev):
     S.close()
     assert r_g.ok and r_g.outer_iters >= 3 and r_g.iters == r_n.iters and torch.equal(X_g, X_n)
     assert r_g2.ok and r_g2.iters == r_n2.iters and torch.equal(X_g2, X_n2)
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+def test_mixed_strategies_reach_fp64_accuracy(torch_dev, refine):
+    """Both mixed-precision strategies (restarted refinement, residual replacement) reach a 1e-12 true residual
+    and the FP64 oracle's solution, on the per-element (k = 6) and warp-chunk (k = 16) layouts."""
+    torch, dev = torch_dev
+    from paper_1912_11930_gb300 import bcg
+    for name, k, p in (("p3d_30", 6, 3), ("vc_20", 16, 8)):
+        M = mat(name)
+        A = M.to_scipy()
+        B = W.rhs(M.n, k, seed=71)
+        S = bcg.Solver.from_matrix(M, k=k, p=p, sub="hybrid", prec="fp32_refine", device=dev)
+        S.set_option("refine", refine)
+        X, r = S.solve(torch.from_numpy(B).to(dev), tol=1e-12, maxit=20000)
+        S.close()
+        X = X.cpu().numpy()
+        assert r.ok, r
+        true = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
+        assert np.all(true <= 1.5e-12)
+        assert _rel(X, O.solve(A, B, p=p, sub="hybrid", tol=1e-13, maxit=5000).X) <= 1e-8
