@@ -57,9 +57,10 @@ typedef enum {
 
 typedef enum {
   BCG_FP64 = 0,              /* every step in IEEE FP64                                               */
-  BCG_FP32_REFINE = 1        /* FP64 iterative refinement around an FP32 inner block CG: operator
-                                products and block updates in FP32, Gram matrices accumulated in
-                                FP64, p x p Cholesky/LU solves and the outer residual in FP64       */
+  BCG_FP32_REFINE = 1        /* FP32 block CG inside FP64 residual recomputation: operator products
+                                and block updates in FP32, Gram matrices FP64-accurate, p x p
+                                Cholesky/LU solves, the solution and its residual in FP64; residual
+                                replacement or restarted refinement (option "refine")               */
 } bcg_precision;
 
 typedef enum {
@@ -71,8 +72,8 @@ typedef enum {
 typedef struct {
   int32_t status;                 /* bcg_status of the solve                                         */
   int32_t iters;                  /* FP64: products Q = A P performed (max over blocks);
-                                     FP32_REFINE: total inner iterations over all outer steps         */
-  int32_t outer_iters;            /* FP32_REFINE: refinement steps (0 for FP64)                      */
+                                     FP32_REFINE: total FP32 iterations                               */
+  int32_t outer_iters;            /* FP32_REFINE: residual replacements or refinement steps (0: FP64) */
   int32_t breakdown_iter;         /* iteration of a breakdown, -1 if none                            */
   double max_rel_res_recursive;   /* max_s ||R_s|| / ||R_s^0|| of the recursive residual            */
   double max_rel_res_true;        /* max_s ||B_s - A X_s|| / ||B_s - A X_s^0||, recomputed in FP64   */

@@ -1,14 +1,18 @@
 // C ABI of libbcg.so (declared in include/bcg.h) and the host-side iteration driver.
 //
-// One solve is: K0 (R = B - A X, P = R, ||R^0_c||^2) and a status reset, then iterations of
+// One solve is: K0 (R = B - A X, P = M^{-1} R, ||R^0_c||^2) and a status reset, then iterations of
 //   K1  Q = A P, alpha = <<P,Q>>, rho_rec = <<P,R>>        (BOP + 2 BDOT, Algorithm 1)
 //   K4a lambda = alpha^{-1} rho_rec                          (BSOLVE, Cholesky)
-//   K2  X += P lambda, R -= Q lambda, rho = <<R,R>>, ||R_c||  (2 BAXPY + BDOT)
+//   K2  X += P lambda, R -= Q lambda, rho = <<Z,R>>, ||R_c|| (2 BAXPY + BDOT)
 //   K4b stopping test, beta = rho_rec^{-1} rho                (BSOLVE, LU with partial pivoting)
-//   K3  P = R + P beta                                        (BAXPY)
+//   K3  P = Z + P beta                                        (BAXPY)
 // launched in batches of `check_every` iterations (optionally replayed as one CUDA graph) between two
 // host reads of the device status word; once the device has flagged completion the remaining kernels
-// of a batch return immediately.
+// of a batch return immediately. For FP64 with 2 <= p <= 16 the recomputed rho_rec of the next iteration
+// is formed by K3 instead of K1 (and the first one by a BDOT after K0). p > 32 runs tiled kernels with the
+// same roles. The mixed form (FP32_REFINE) runs the same iteration in FP32 with FP64 residual replacement
+// (solve_replace) or restarted refinement (solve_refine); SELL handles iterate on the permuted system;
+// row-sharded handles are driven phase by phase by the caller (bcg_rows_*).
 #include <cuda_runtime.h>
 
 #include <algorithm>

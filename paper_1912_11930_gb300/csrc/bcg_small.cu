@@ -641,6 +641,10 @@ int lp_chunks(int64_t n, int k, int p, int nsm) {
 bool small_needs_gws(int p) { return p > kMaxP || small_ws_doubles_dev(p) * sizeof(double) > kSmallSmemMax; }
 static size_t small_smem(int p) { return small_needs_gws(p) ? 0 : small_ws_doubles_dev(p) * sizeof(double); }
 static bool small_split(int p) { return p > kMaxP; }
+// Threads of a p x p solve CTA: its time is the partial-sum reduction when there are many partial rows and
+// the serial factorization steps (each a barrier) when there are few; 128 threads measured faster below
+// 8192 partial entries per block (64^2 Poisson, k = 8: 9.4 -> 7.9 ms per solve), 512 above (128^3, k = 32).
+static int small_threads(int nparts, int p) { return (int64_t)nparts * p * p < 8192 ? 128 : kSmallNT; }
 
 cudaError_t small_prepare(int p) {
   const size_t sm = small_smem(p);
@@ -668,9 +672,9 @@ cudaError_t launch_solve_lambda(const double *partA, const double *partR, int np
   const int nblk = global ? 1 : k / p;
   if (small_needs_gws(p) && gws == nullptr) return cudaErrorInvalidValue;
   const int split = small_split(p) ? 1 : 0;
-  k_solve_lambda<<<nblk, kSmallNT, small_smem(p), s>>>(partA, partR, nparts, k, p, global, active, lam, rho_rec, st,
-                                                       small_needs_gws(p) ? gws : nullptr, alpha_circ, split,
-                                                       nparts_r);
+  k_solve_lambda<<<nblk, small_threads(std::max(nparts, nparts_r), p), small_smem(p), s>>>(
+      partA, partR, nparts, k, p, global, active, lam, rho_rec, st, small_needs_gws(p) ? gws : nullptr, alpha_circ,
+      split, nparts_r);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !split) return e;
   return launch_trsm(p, nblk, 1, gws, active, lam, st, s);
@@ -684,9 +688,9 @@ cudaError_t launch_solve_beta(const double *partRho, const double *partN, int np
   const int nblk = global ? 1 : k / p;
   if (small_needs_gws(p) && gws == nullptr) return cudaErrorInvalidValue;
   const int split = small_split(p) ? 1 : 0;
-  k_solve_beta<<<nblk, kSmallNT, small_smem(p), s>>>(partRho, partN, nparts, k, p, global, tol2, r0n2, rn2, active,
-                                                     block_iters, rho_rec, beta, st, small_needs_gws(p) ? gws : nullptr,
-                                                     rho_circ, nparts_n, split);
+  k_solve_beta<<<nblk, small_threads(nparts, p), small_smem(p), s>>>(
+      partRho, partN, nparts, k, p, global, tol2, r0n2, rn2, active, block_iters, rho_rec, beta, st,
+      small_needs_gws(p) ? gws : nullptr, rho_circ, nparts_n, split);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !split) return e;
   return launch_trsm(p, nblk, 0, gws, active, beta, st, s);
