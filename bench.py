@@ -172,10 +172,11 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------------------------------------------
 # Other workloads (not the default line): measured with `python bench.py --workload NAME`
 EXTRA_WORKLOADS = ("poisson2d_64_k8", "varcoef3d_160_k64_mixed", "varcoef3d_160_k64_jacobi", "stencil27_100_k16_autograd",
-                   "poisson3d_96_sweep", "sell_vs_csr")
+                   "poisson3d_96_sweep", "sell_vs_csr", "large_blocks_64_k256")
 
 
-def time_solve(bcg, torch, M, B, *, k, p, sub, prec, form="csr", tol=1e-8, reps=2, dev=None, opts=None, warm=True):
+def time_solve(bcg, torch, M, B, *, k, p, sub, prec, form="csr", tol=1e-8, reps=2, dev=None, opts=None, warm=True,
+               maxit=20000):
     """Warm-up solve (unless warm=False), then the mean of `reps` timed solves from X0 = 0 (CUDA events on the
     solver's stream)."""
     S = bcg.Solver.from_matrix(M, k=k, p=p, sub=sub, prec=prec, form=form, device=dev)
@@ -183,14 +184,14 @@ def time_solve(bcg, torch, M, B, *, k, p, sub, prec, form="csr", tol=1e-8, reps=
         S.set_option(key, v)
     X = torch.zeros_like(B)
     if warm:
-        S.solve(B, X, tol=tol, maxit=20000)
+        S.solve(B, X, tol=tol, maxit=maxit)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(S.stream)
     for _ in range(reps):
         with torch.cuda.stream(S.stream):
             X.zero_()
-        X, r = S.solve(B, X, tol=tol, maxit=20000)
+        X, r = S.solve(B, X, tol=tol, maxit=maxit)
     e1.record(S.stream)
     torch.cuda.synchronize()
     S.close()
@@ -271,6 +272,21 @@ def run_extra(name, args):
         out.update(value=rows[0]["k1_ms"] / 1e3, unit="s", dtype="f64",
                    config={"workload": "sell_vs_csr_k1_time", "iterations_profiled": 24}, results=rows,
                    note="value: K1 time of the first row (128^3 Poisson, k = 1, CSR), seconds per launch")
+    elif name == "large_blocks_64_k256":
+        # classical block CG with k = p = 256 (tiled kernels, p x p solves in global memory): 24 iterations of
+        # each form, for the large-block launch profile
+        M = W.poisson3d(64)
+        k = 256
+        B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev)
+        rows = []
+        for prec in ("fp64", "fp32_refine"):
+            t, r, _ = time_solve(bcg, torch, M, B, k=k, p=k, sub="classical", prec=prec, tol=1e-300, reps=1, dev=dev,
+                                 warm=False, maxit=24)
+            rows.append(dict(prec=prec, s=t, iterations=r.iters, status=bcg.STATUS_NAMES[r.status],
+                             ms_per_iteration=t * 1e3 / max(r.iters, 1)))
+        out.update(value=rows[0]["s"], dtype="f64 (and f32 with f64 residual replacement)",
+                   config={"workload": "poisson3d_64_csr_k256_classical_24_iterations", "n": M.n, "k": k, "p": k},
+                   results=rows)
     elif name == "stencil27_100_k16_autograd":
         from paper_1912_11930_gb300.autograd import bcg_solve_autograd
         M = W.stencil27(100, seed=0)

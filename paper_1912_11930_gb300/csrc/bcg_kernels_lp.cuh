@@ -12,7 +12,6 @@
 namespace bcgk {
 
 constexpr int kLT = 32;      // tile edge
-constexpr int kLRows = 64;   // rows of a BAXPY output tile
 
 __host__ __device__ constexpr bool lp_layout_ok(int k, int p) {
   return p > 32 && p <= kNT && p % kLT == 0 && k % p == 0 && k <= kNT;
@@ -115,9 +114,14 @@ __global__ void __launch_bounds__(kNT) kl_gram(const T *__restrict__ X, const T 
 }
 
 // OUT_j = BASE_j + sign * Y_j C_j (C_j row-major p x p per distinct block, FP64 in memory). grid.x = column
-// tiles (k/32), grid.y = row tiles of 64. OUT may equal BASE; Y must not alias OUT. bump != 0: CTA (0,0)
+// tiles (k/32), grid.y = row tiles of kLRows. OUT may equal BASE; Y must not alias OUT. bump != 0: CTA (0,0)
 // advances the iteration counter (this launch then plays the role of K3).
 // bscale (optional): BASE's row r is multiplied by bscale[r] (P = M^{-1} R + P beta).
+// Register tiling: thread (ty4, tx4) owns rows 4 ty4 .. 4 ty4 + 3 and columns 4 tx4 .. 4 tx4 + 3 of the
+// 128 x 32 output tile; per step of the contraction it reads 4 Y values and 4 C values (two 16-byte shared
+// loads for FP32) for 16 FMAs. Y is staged transposed (Yt[a][row]) so that those loads are vectors.
+constexpr int kLRows = 128;   // rows of a BAXPY output tile
+constexpr int kLYs = kLRows + 4;   // padded row length of the transposed Y tile (16-byte aligned rows)
 template <typename T>
 __global__ void __launch_bounds__(kNT) kl_baxpy(T *OUT, const T *BASE, const T *__restrict__ Y,
                                                 const double *__restrict__ C, int64_t n, int k, int p, int global,
@@ -125,45 +129,55 @@ __global__ void __launch_bounds__(kNT) kl_baxpy(T *OUT, const T *BASE, const T *
                                                 int bump, const T *__restrict__ bscale) {
   if (st->flags != 0) return;
   if (bump && blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) st->cur += 1;
-  __shared__ T Ys[kLRows][kLT + 1];
-  __shared__ T Cs[kLT][kLT + 1];
+  __shared__ __align__(16) T Yt[kLT][kLYs];
+  __shared__ __align__(16) T Cs[kLT][kLT + 4];
   const int c0 = blockIdx.x * kLT;
   const int j = c0 / p, b0 = c0 - j * p;
-  const int tx = threadIdx.x % kLT, ty = threadIdx.x / kLT;   // column tx, rows ty + 8 m
+  const int tx4 = threadIdx.x % 8, ty4 = threadIdx.x / 8;   // columns 4 tx4 + v, rows 4 ty4 + u
   const int64_t r0 = (int64_t)blockIdx.y * kLRows;
   const double *Cj = C + (int64_t)(global ? 0 : j) * p * p;
   const bool act = block_active(active, global, j);
-  T acc[kLRows / 8];
+  T acc[4][4];
 #pragma unroll
-  for (int m = 0; m < kLRows / 8; ++m) {
-    const int64_t r = r0 + ty + 8 * m;
-    acc[m] = r < n ? (bscale ? BASE[r * k + c0 + tx] * bscale[r] : BASE[r * k + c0 + tx]) : T(0);
+  for (int u = 0; u < 4; ++u) {
+    const int64_t r = r0 + 4 * ty4 + u;
+    const T s = (r < n && bscale) ? bscale[r] : T(1);
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = r < n ? BASE[r * k + c0 + 4 * tx4 + v] * s : T(0);
   }
   if (act) {
     for (int a0 = 0; a0 < p; a0 += kLT) {
-      for (int e = threadIdx.x; e < kLRows * kLT; e += kNT) {
+      for (int e = threadIdx.x; e < kLRows * kLT; e += kNT) {   // coalesced rows of Y, stored transposed
         const int rr = e / kLT, aa = e % kLT;
         const int64_t r = r0 + rr;
-        Ys[rr][aa] = r < n ? Y[r * k + (int64_t)j * p + a0 + aa] : T(0);
+        Yt[aa][rr] = r < n ? Y[r * k + (int64_t)j * p + a0 + aa] : T(0);
       }
       for (int e = threadIdx.x; e < kLT * kLT; e += kNT) {
         const int aa = e / kLT, bb = e % kLT;
         Cs[aa][bb] = sign * (T)Cj[(int64_t)(a0 + aa) * p + b0 + bb];
       }
       __syncthreads();
-#pragma unroll 8
+#pragma unroll 4
       for (int aa = 0; aa < kLT; ++aa) {
-        const T cv = Cs[aa][tx];
+        T yv[4], cv[4];
 #pragma unroll
-        for (int m = 0; m < kLRows / 8; ++m) acc[m] = fma_t(Ys[ty + 8 * m][aa], cv, acc[m]);
+        for (int u = 0; u < 4; ++u) yv[u] = Yt[aa][4 * ty4 + u];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) cv[v] = Cs[aa][4 * tx4 + v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) acc[u][v] = fma_t(yv[u], cv[v], acc[u][v]);
       }
       __syncthreads();
     }
   }
 #pragma unroll
-  for (int m = 0; m < kLRows / 8; ++m) {
-    const int64_t r = r0 + ty + 8 * m;
-    if (r < n) OUT[r * k + c0 + tx] = acc[m];
+  for (int u = 0; u < 4; ++u) {
+    const int64_t r = r0 + 4 * ty4 + u;
+    if (r < n)
+#pragma unroll
+      for (int v = 0; v < 4; ++v) OUT[r * k + c0 + 4 * tx4 + v] = acc[u][v];
   }
 }
 
