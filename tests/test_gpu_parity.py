@@ -430,3 +430,57 @@ def test_mixed_strategies_reach_fp64_accuracy(torch_dev, refine):
         true = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
         assert np.all(true <= 1.5e-12)
         assert _rel(X, O.solve(A, B, p=p, sub="hybrid", tol=1e-13, maxit=5000).X) <= 1e-8
+
+
+# ---- full size, the configurations bench.py times --------------------------------------------------------------
+def test_full_size_equal_iterations_against_oracle(torch_dev):
+    """128^3 Poisson, k = 32, hybrid p = 8, FP64 (the default bench line): four iterations on the GPU against four
+    oracle iterations on the whole matrix, 1e-9 (the oracle needs a few seconds per iteration at this size)."""
+    torch, dev = torch_dev
+    from paper_1912_11930_gb300 import bcg
+    M = W.poisson3d(128)
+    k, p, m = 32, 8, 4
+    B = W.rhs(M.n, k, seed=0)
+    S = bcg.Solver.from_matrix(M, k=k, p=p, sub="hybrid", device=dev)
+    X, r = S.solve(torch.from_numpy(B).to(dev), tol=NEVER, maxit=m)
+    S.close()
+    assert r.status == 5 and r.iters == m
+    ref = O.solve(M.to_scipy(), B, p=p, sub="hybrid", tol=0.0, maxit=m)
+    assert _rel(X.cpu().numpy(), ref.X) <= 1e-9
+
+
+def test_full_size_mixed_poisson128(torch_dev):
+    """The bench's mixed variant (128^3, k = 32, hybrid p = 8): true residual <= 1e-8 recomputed on the host, and,
+    with residual replacement, as many iterations as the FP64 form (+-2)."""
+    torch, dev = torch_dev
+    from paper_1912_11930_gb300 import bcg
+    M = W.poisson3d(128)
+    k = 32
+    B = W.rhs(M.n, k, seed=0)
+    Bt = torch.from_numpy(B).to(dev)
+    S64 = bcg.Solver.from_matrix(M, k=k, p=8, sub="hybrid", prec="fp64", device=dev)
+    _, r64 = S64.solve(Bt, tol=1e-8)
+    S64.close()
+    S = bcg.Solver.from_matrix(M, k=k, p=8, sub="hybrid", prec="fp32_refine", device=dev)
+    X, r = S.solve(Bt, tol=1e-8)
+    S.close()
+    assert r.ok and r64.ok
+    res = np.linalg.norm(B - M.to_scipy() @ X.cpu().numpy(), axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(res <= 1.5e-8)
+    assert abs(r.iters - r64.iters) <= 2, (r.iters, r64.iters)
+
+
+def test_full_size_varcoef160_mixed_to_1e10(torch_dev):
+    """Configuration 3 (160^3 log-normal variable coefficients, stencil form, k = 64, hybrid p = 16, mixed form
+    refined to 1e-10): every column's true residual, recomputed on the host from the CSR matrix, <= 1e-10."""
+    torch, dev = torch_dev
+    from paper_1912_11930_gb300 import bcg
+    M = W.varcoef3d(160, seed=0)
+    k = 64
+    B = W.rhs(M.n, k, seed=0)
+    S = bcg.Solver.from_matrix(M, k=k, p=16, sub="hybrid", prec="fp32_refine", form="stencil", device=dev)
+    X, r = S.solve(torch.from_numpy(B).to(dev), tol=1e-10, maxit=20000)
+    S.close()
+    assert r.ok, r
+    res = np.linalg.norm(B - M.to_scipy() @ X.cpu().numpy(), axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(res <= 1.5e-10), res.max()
