@@ -499,9 +499,12 @@ bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int ma
 // correction is flushed into the FP64 iterate (X += D, D = 0) and the residual is replaced by the FP64 true
 // residual B - A X. P is kept, and Algorithm 1 recomputes rho = <<P, R>>_S from the replaced residual in the
 // next iteration, so the process continues instead of restarting. Converged when every column's true
-// residual is below tol (relative to the initial one); blocks that stopped on their recursive residual too
-// early are reopened.
+// residual is below tol (relative to the initial one); blocks that stopped on their recursive residual before
+// that are reopened; if a block's directions lose rank, a cycle stops making progress, or the process has run
+// more iterations than the system has rows (in exact arithmetic it would have terminated: its directions are
+// spent), the process restarts from the FP64 residual.
 constexpr double kReplaceDrop = 0.1;
+constexpr int kReplaceMinCycle = 64;   // shortest window after which a replacement cycle can count as stalled
 
 bcg_status solve_replace(bcg_ctx *h, const double *B, double *X, double tol, int maxit, bcg_info *info) {
   cudaStream_t s = h->stream;
@@ -526,6 +529,8 @@ bcg_status solve_replace(bcg_ctx *h, const double *B, double *X, double tol, int
   int replaced = 0, restarts = 0, stalls = 0, brk = -1, base_iters = 0;
   double m_true = max_ratio(h->h_vec, h->h_vec, h->k) > 0 ? 1.0 : 0.0;   // relative to the initial residual
   double last2 = 1.0, best = INFINITY;
+  int cycle_start = 0, longest = 0;   // iteration of the last replacement, longest cycle between replacements
+  const int min_cycle = (int)std::min<int64_t>(kReplaceMinCycle, h->n);
   if (m_true == 0.0) st = BCG_OK;   // B - A X = 0 in every column
   while (st == BCG_ERR_NOT_CONVERGED) {
     CKS(run_iterations<float>(h, h->A32, h->D32, h->R32, h->P32, h->Q32, h->g32, tol2, h->check_every,
@@ -543,7 +548,13 @@ bcg_status solve_replace(bcg_ctx *h, const double *B, double *X, double tol, int
       const double r = h->h_vec[cc] > 0 ? h->h_vec[h->k + cc] / h->h_vec[cc] : 0.0;
       if (!(r <= rec2)) rec2 = r;
     }
-    if (!(broke || done || rec2 < kReplaceDrop * kReplaceDrop * last2 || iters >= maxit)) continue;
+    // a cycle running longer than twice the longest one so far (and at least min(kReplaceMinCycle, n)
+    // iterations) gets a replacement too; if that shows no 10 % gain of the true residual, the kept directions
+    // no longer help and the process restarts (below)
+    const bool forced = iters - cycle_start > std::max(2 * longest, min_cycle);
+    if (!(broke || done || forced || rec2 < kReplaceDrop * kReplaceDrop * last2 || iters >= maxit)) continue;
+    longest = std::max(longest, iters - cycle_start);
+    cycle_start = iters;
     // residual replacement: X += D, D = 0, R = B - A X in FP64 (R32 = fl(R)); P and the Krylov process stay
     CK(launch_add_correction(X, h->D32, nk, h->nsm, s));
     CK(cudaMemsetAsync(h->D32, 0, sizeof(float) * nk, s));
@@ -553,10 +564,13 @@ bcg_status solve_replace(bcg_ctx *h, const double *B, double *X, double tol, int
     ++replaced;
     CKS(fetch_vec(h, h->outer0, 0));
     CKS(fetch_vec(h, h->rtn2, 2));
+    const double m_prev = m_true;
     m_true = max_ratio(h->h_vec + 2 * h->k, h->h_vec, h->k);
     if (!std::isfinite(m_true)) { st = BCG_ERR_NUMERIC; break; }
     if (m_true <= tol) { st = BCG_OK; break; }
     if (iters >= maxit) break;
+    const bool stuck = forced && !(m_true < 0.9 * m_prev);
+    const bool spent = iters - base_iters > h->n;   // more iterations than rows since the process (re)started
     if (m_true >= 0.9 * best) {
       if (++stalls >= 3) break;
     } else {
@@ -564,13 +578,17 @@ bcg_status solve_replace(bcg_ctx *h, const double *B, double *X, double tol, int
     }
     best = std::min(best, m_true);
     last2 = m_true * m_true;
-    if (broke) {
-      // the FP32 directions of a block became dependent (its alpha or recomputed rho lost rank): restart the
-      // Krylov process from the FP64 residual, as a restarted refinement step would
+    if (broke || stuck || spent) {
+      // the FP32 directions of a block became dependent (its alpha or recomputed rho lost rank), the cycle
+      // stalled, or the process outran the dimension of the system (the FP32 process has used up what its
+      // directions can resolve): restart the Krylov process from the FP64 residual, as a restarted refinement
+      // step would
       base_iters = iters;
       ++restarts;
       CKS(start(false));
     } else if (done) {
+      // every block stopped on its recursive residual but some true residuals are still above the tolerance:
+      // reopen those blocks with their directions
       CK(launch_reactivate(h->rtn2, h->r0n2, tol2, h->k, h->p, h->global, h->active, h->st, s));
     }
   }

@@ -484,3 +484,29 @@ def test_full_size_varcoef160_mixed_to_1e10(torch_dev):
     assert r.ok, r
     res = np.linalg.norm(B - M.to_scipy() @ X.cpu().numpy(), axis=0) / np.linalg.norm(B, axis=0)
     assert np.all(res <= 1.5e-10), res.max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_refine"])
+@pytest.mark.parametrize("form", ["csr", "sell", "stencil"])
+def test_tiny_systems(torch_dev, prec, form):
+    """Fewer rows than one warp chunk or one SELL chunk (n = 6 and 27), k from 1 to 8: the solution of the tiny
+    SPD system to the requested tolerance, against a dense solve -- or, where the block Krylov space runs out
+    before convergence (classical k = 8 on n = 27: Algorithm 1 has no deflation), a breakdown like the
+    oracle's."""
+    torch, dev = torch_dev
+    from paper_1912_11930_gb300 import bcg
+    for M in (W.poisson2d(2, 3), W.poisson3d(3)):
+        A = M.to_scipy()
+        for k, p, sub in ((1, 1, "parallel"), (4, 2, "hybrid"), (8, 8, "classical")):
+            if k > M.n:
+                continue
+            B = W.rhs(M.n, k, seed=81)
+            S = bcg.Solver.from_matrix(M, k=k, p=p, sub=sub, prec=prec, form=form, device=dev)
+            X, r = S.solve(torch.from_numpy(B).to(dev), tol=1e-10, maxit=200)
+            S.close()
+            ref = O.solve(A, B, p=p, sub=sub, tol=1e-10, maxit=200)
+            if ref.status == O.BREAKDOWN:
+                assert r.status == bcg.BREAKDOWN, (M.n, k, p, r)
+                continue
+            assert r.ok, (M.n, k, p, r)
+            assert _rel(X.cpu().numpy(), np.linalg.solve(A.toarray(), B)) <= 1e-8
