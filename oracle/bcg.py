@@ -33,6 +33,20 @@ Readings of places where the paper is silent, garbled or inconsistent (each one 
   (their lambda and beta are zero from then on); global/classical stop all columns together. A zero
   column converges at iteration 0. The iteration count is the number of products Q = A P.
 * R6 no deflation: a breakdown is reported (status BREAKDOWN), never hidden.
+
+``solve_retooled`` is the retooled block CG that Section 3 points to for the stability of the method
+(A. A. Dubrulle, "Retooling the method of block conjugate gradients", Electron. Trans. Numer. Anal. 12,
+2001): the residual is carried as R = Q C with an orthonormal Q and a p x p factor C, and the search
+directions are built from Q, so differently scaled residual columns do not make the small systems
+ill-conditioned. Readings (also in DESIGN.md):
+* R12 the QR factorisation of Dubrulle's method is taken within the subalgebra as a Cholesky QR: with
+  gamma = <<T, T>>_S = L L^T, C-factor psi = L^T and Q = T psi^{-1}; restricted to the hybrid family
+  (hybrid, parallel, classical), whose products give every column's norm.
+* R13 a Cholesky pivot of the retooled form fails when it is <= 64 eps times its own diagonal entry
+  (column-relative, so that a right-hand side scaled column by column factors like the unscaled one).
+* R14 the stopping test uses ||R_s||^2 = (C^T gamma C)_ss (the old C and the new gamma, before psi is
+  formed), so a block that has converged needs no further factorisation; a failure of the very first
+  factorisation is a breakdown in iteration 1.
 """
 from __future__ import annotations
 
@@ -258,6 +272,140 @@ def solve(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, sub: str =
     with np.errstate(invalid="ignore", divide="ignore"):
         rel_rec = np.where(r0 > 0, rn / np.where(r0 > 0, r0, 1.0), 0.0)
         rt = colnorms(B - bop(A, X))
+        rel_true = np.where(r0 > 0, rt / np.where(r0 > 0, r0, 1.0), rt)
+    return Result(X, status, it, block_iters, brk, rel_rec, rel_true, hist)
+
+
+def cholesky_lower_colrel(G: np.ndarray):
+    """Cholesky G = L L^T from G's lower triangle, no pivoting; breakdown (None) when a pivot is
+    <= 64 eps times its own diagonal entry G_aa, or not finite (reading R13)."""
+    p = G.shape[0]
+    L = np.zeros_like(G)
+    for a in range(p):
+        d = G[a, a] - L[a, :a] @ L[a, :a]
+        if not (np.isfinite(d) and d > PIVOT_FACTOR * EPS * G[a, a]):
+            return None
+        L[a, a] = np.sqrt(d)
+        L[a + 1:, a] = (G[a + 1:, a] - L[a + 1:, :a] @ L[a, :a]) / L[a, a]
+    return L
+
+
+def retooled_solution_coefficient(xi: np.ndarray, C: np.ndarray) -> np.ndarray:
+    """lambda = xi C: the step along S that moves X by S alpha^{-1} <<S, R>> with <<S, R>> = C."""
+    return xi @ C
+
+
+def retooled_direction(Q: np.ndarray, S: np.ndarray, psi: np.ndarray) -> np.ndarray:
+    """S^{i+1} = Q^{i+1} + S^i psi^T (the retooled form of P^{i+1} = R^i + P^i beta)."""
+    return Q + S @ psi.T
+
+
+def solve_retooled(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, sub: str = "hybrid",
+                   tol: float = 1e-8, maxit: int = 1000, record: bool = False) -> Result:
+    """Dubrulle's retooled block CG (Electron. Trans. Numer. Anal. 12, 2001) in the hybrid family of
+    subalgebras, FP64, step by step; M = I. Per iteration, for every block that has not converged:
+
+        W = A S;  alpha = <<S, W>>;  xi = alpha^{-1};  X += S (xi C);  T = Q - W xi;
+        gamma = <<T, T>>;  ||R_s||^2 = (C^T gamma C)_ss  (stopping test);
+        gamma = psi^T psi (Cholesky);  C = psi C;  Q = T psi^{-1};  S = Q + S psi^T
+
+    starting from R^0 = B - A X^0 = Q C (Cholesky QR) and S = Q. In exact arithmetic X^i is Algorithm 1's
+    iterate (P^i = S^i C^{i-1}, R^i = Q^i C^i)."""
+    B = np.asarray(B, dtype=np.float64)
+    n, k = B.shape
+    kind, p = canonical_subalgebra(sub, k, p)
+    if kind != "hybrid":
+        raise ValueError("the retooled form runs in the hybrid, parallel and classical subalgebras")
+    q = k // p
+    X = np.zeros_like(B) if X0 is None else np.array(X0, dtype=np.float64, copy=True)
+    hist = {"X": [], "Q": [], "S": [], "C": []} if record else {}
+
+    def cols(j):
+        return slice(j * p, (j + 1) * p)
+
+    R = B - bop(A, X)
+    r0 = np.sqrt(np.sum(R * R, axis=0))
+    if not (np.all(np.isfinite(r0)) and np.all(np.isfinite(X))):
+        return Result(X, NUMERIC, 0, np.zeros(q, dtype=np.int64), -1, r0 * np.nan, r0 * np.nan, hist)
+    rn = r0.copy()
+    active = np.array([not np.all(r0[cols(j)] <= tol * r0[cols(j)]) for j in range(q)])
+    block_iters = np.zeros(q, dtype=np.int64)
+    status, brk, it = OK, -1, 0
+    # R^0 = Q^0 C^0 (Cholesky QR of every active block), S^1 = Q^0
+    C = np.zeros((q, p, p))
+    Q = np.zeros_like(B)
+    gamma = block_product(R, R, p, "hybrid")
+    for j in range(q):
+        if not active[j]:
+            continue
+        L = cholesky_lower_colrel(gamma[j])
+        if L is None:
+            status, brk = BREAKDOWN, 1
+            break
+        C[j] = L.T
+        Q[:, cols(j)] = sla.solve_triangular(L, R[:, cols(j)].T, lower=True).T
+    S = Q.copy()
+    if record and status == OK:
+        hist["X"].append(X.copy()); hist["Q"].append(Q.copy()); hist["S"].append(S.copy())
+        hist["C"].append(C.copy())
+
+    while status == OK and np.any(active) and it < maxit:
+        it += 1
+        block_iters[active] = it
+        # W = A S ; alpha = <<S, W>>
+        Wm = bop(A, S)
+        alpha = block_product(S, Wm, p, "hybrid")
+        # xi = alpha^{-1} (Cholesky) ; lambda = xi C
+        xi = np.zeros((q, p, p))
+        lam = np.zeros((q, p, p))
+        for j in range(q):
+            if not active[j]:
+                continue
+            L = cholesky_lower_colrel(alpha[j])
+            if L is None:
+                status, brk = BREAKDOWN, it
+                break
+            Linv = sla.solve_triangular(L, np.eye(p), lower=True)
+            xi[j] = Linv.T @ Linv
+            lam[j] = retooled_solution_coefficient(xi[j], C[j])
+        if status != OK:
+            break
+        # X += S lambda ; T = Q - W xi
+        X = baxpy(X, S, lam, +1.0)
+        T = baxpy(Q, Wm, xi, -1.0)
+        # gamma = <<T, T>> ; ||R_s||^2 = (C^T gamma C)_ss since R = T C
+        gamma = block_product(T, T, p, "hybrid")
+        for j in range(q):
+            if active[j]:
+                rn[cols(j)] = np.sqrt(np.diag(C[j].T @ gamma[j] @ C[j]))
+        if not np.all(np.isfinite(rn)):
+            status = NUMERIC
+            break
+        for j in range(q):
+            if active[j] and np.all(rn[cols(j)] <= tol * r0[cols(j)]):
+                active[j] = False
+        # T = Q^+ psi (Cholesky QR); C = psi C ; S = Q^+ + S psi^T
+        for j in range(q):
+            if not active[j]:
+                continue
+            L = cholesky_lower_colrel(gamma[j])
+            if L is None:
+                status, brk = BREAKDOWN, it
+                break
+            psi = L.T
+            C[j] = psi @ C[j]
+            Qj = sla.solve_triangular(L, T[:, cols(j)].T, lower=True).T
+            S[:, cols(j)] = retooled_direction(Qj, S[:, cols(j)], psi)
+            Q[:, cols(j)] = Qj
+        if record:
+            hist["X"].append(X.copy()); hist["Q"].append(Q.copy()); hist["S"].append(S.copy())
+            hist["C"].append(C.copy())
+
+    if status == OK and np.any(active):
+        status = NOT_CONVERGED
+    with np.errstate(invalid="ignore", divide="ignore"):
+        rel_rec = np.where(r0 > 0, rn / np.where(r0 > 0, r0, 1.0), 0.0)
+        rt = np.sqrt(np.sum((B - bop(A, X)) ** 2, axis=0))
         rel_true = np.where(r0 > 0, rt / np.where(r0 > 0, r0, 1.0), rt)
     return Result(X, status, it, block_iters, brk, rel_rec, rel_true, hist)
 
