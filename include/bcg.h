@@ -156,6 +156,14 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
  *                  (Section 3 allows any SPD M; Z = M^{-1} R is formed on the fly by the kernels that
  *                  read R, from 1/diag(A) computed at create time and by bcg_update_values; the mixed
  *                  form uses an FP32 copy). Every diagonal entry must be positive.
+ *   "retooled"     1 = Dubrulle's retooled block CG (Electron. Trans. Numer. Anal. 12, 2001; the stability
+ *                  reference of Section 3) instead of Algorithm 1's recurrences: the residual is carried as
+ *                  R = Q C with Q orthonormal in the S-product (a Cholesky QR per block) and the search
+ *                  directions are built from Q; the same iterates in exact arithmetic, but a right-hand side
+ *                  whose columns differ in scale by many orders factors like a well-scaled one. Each Cholesky
+ *                  pivot is tested against its own diagonal entry. FP64 handles of the hybrid, parallel or
+ *                  classical subalgebra with M = I only (INVALID_ARG otherwise, from bcg_set_option or, for
+ *                  "precond", from bcg_solve); 0 = Algorithm 1 (default).
  * Unknown keys or out-of-range values return INVALID_ARG.
  */
 bcg_status bcg_set_option(bcg_handle h, const char *key, double value);

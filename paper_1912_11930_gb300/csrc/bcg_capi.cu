@@ -99,6 +99,7 @@ struct bcg_ctx {
   int profile = 0;
   int precond = 0;                     // 0: M = I; 1: Jacobi, M = diag(A)
   int refine = 1;                      // FP32_REFINE: 1 residual replacement, 0 restarted refinement
+  int retooled = 0;                    // FP64: 1 Dubrulle's retooled block CG instead of Algorithm 1's recurrences
   // live per-kernel timing (profile = 1): CUDA events around every launch of an executed iteration
   static constexpr int kKernels = 6;   // K1 op_gram, K4a solve_lambda, K2 update_xr, K4b solve_beta, K3 update_p, K0 residual
   double prof_ms[kKernels] = {0, 0, 0, 0, 0, 0};
@@ -115,6 +116,7 @@ struct bcg_ctx {
   int *active = nullptr, *block_iters = nullptr;
   double *gws = nullptr;               // global workspace of the p x p solves when p is large
   double *dinv64 = nullptr;            // 1 / diag(A) (Jacobi preconditioner)
+  double *dr_C = nullptr, *dr_xi = nullptr, *dr_psiinv = nullptr, *dr_phi = nullptr;   // retooled form, p x p per block
   float *dinv32 = nullptr;             // its FP32 copy for the mixed form's inner solve
   int32_t *rowidx = nullptr;           // CSR row of each entry (gradient)
   DevStatus *st = nullptr;
@@ -216,6 +218,12 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CKS(h->alloc(&h->active, h->nblk));
   CKS(h->alloc(&h->block_iters, h->nblk));
   if (small_needs_gws(h->p)) CKS(h->alloc(&h->gws, (size_t)h->nblk * small_ws_doubles(h->p)));
+  if (h->prec == BCG_FP64 && !h->global) {
+    CKS(h->alloc(&h->dr_C, pp));
+    CKS(h->alloc(&h->dr_xi, pp));
+    CKS(h->alloc(&h->dr_psiinv, pp));
+    CKS(h->alloc(&h->dr_phi, pp));
+  }
   CKS(h->alloc(&h->dinv64, (size_t)h->n));
   if (h->prec == BCG_FP32_REFINE) CKS(h->alloc(&h->dinv32, (size_t)h->n));
   CKS(h->alloc(&h->st, 1));
@@ -489,6 +497,97 @@ bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int ma
   if (st != BCG_OK) {
     const char *what = st == BCG_ERR_NUMERIC ? "non-finite value" : st == BCG_ERR_BREAKDOWN ? "breakdown" : "maxit reached";
     fail(st, "solve stopped: %s after %d iterations", what, fin.iter);
+  }
+  return st;
+}
+
+// Dubrulle's retooled block CG (option "retooled"; Electron. Trans. Numer. Anal. 12, 2001, the stability reference
+// of Section 3), FP64, hybrid family, M = I; the kernels and the recurrences are described in bcg_retooled.inc.
+// Three n x k buffers rotate: W = A S is dead once T = Q - W xi is formed, so Q^+ = T psi^{-1} is written into
+// it, and S^+ = Q^+ + S psi^T into T's buffer (no update writes a buffer it reads by whole blocks of p columns,
+// which the tiled large-block kernels need). Q = T psi^{-1} is a product without a base term: the streaming
+// update takes a NULL base, the tiled one a zeroed output (T + T (psi^{-1} - I) would cancel digits in
+// proportion to the column norms of R^0). Plain launches, a status read every check_every iterations.
+bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, int maxit, bcg_info *info) {
+  if (h->precond) return fail(BCG_ERR_INVALID_ARG, "the retooled form runs with M = I (option precond = 0)");
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
+  const int k = h->k, p = h->p;
+  const bool lp = p > kMaxP;
+  const int np_g = lp ? h->g64.op : dr_gram_grid(n, k, p, h->nsm, h->nparts);
+  auto gram = [&](const double *Xv, const double *Yv, double *part) -> cudaError_t {
+    return lp ? launch_lp_gram<double>(Xv, Yv, n, k, p, 0, h->active, part, np_g, h->st, s, nullptr)
+              : launch_dr_gram(Xv, Yv, n, k, p, h->active, part, np_g, h->st, s);
+  };
+  auto baxpy = [&](double *OUT, const double *BASE, const double *Yv, const double *Cm, double sign,
+                   int bump) -> cudaError_t {
+    return lp ? launch_lp_baxpy<double>(OUT, BASE, Yv, Cm, n, k, p, 0, sign, h->active, h->st, bump, s, nullptr)
+              : launch_dr_baxpy(OUT, BASE, Yv, Cm, n, k, p, sign, h->active, h->st, bump, h->nsm, s);
+  };
+  // OUT = Y C (no base term)
+  auto bmul = [&](double *OUT, const double *Yv, const double *Cm) -> cudaError_t {
+    if (!lp) return launch_dr_baxpy(OUT, nullptr, Yv, Cm, n, k, p, 1.0, h->active, h->st, 0, h->nsm, s);
+    cudaError_t e = cudaMemsetAsync(OUT, 0, sizeof(double) * (size_t)n * k, s);
+    if (e != cudaSuccess) return e;
+    return launch_lp_baxpy<double>(OUT, OUT, Yv, Cm, n, k, p, 0, 1.0, h->active, h->st, 0, s, nullptr);
+  };
+  auto bop = [&](const double *Sv, double *Wv) -> cudaError_t {
+    return k % 2 == 0 ? launch_lp_bop<double>(h->A64, Sv, Wv, n, k, h->st, h->nsm, s)
+                      : launch_dr_bop(h->A64, Sv, Wv, n, k, h->st, h->nsm, s);
+  };
+  double *W = h->R, *S = h->P, *Qb = h->Q;
+  // R^0 = B - A X^0 (in W's buffer) = Q^0 C^0, S^1 = Q^0
+  CK(launch_residual<double>(h->A64, X, B, W, nullptr, nullptr, nullptr, n, k, h->partN, h->g64.res, s, nullptr));
+  CK(launch_init_status(h->partN, h->g64.res, k, p, 0, h->r0n2, h->rn2, h->active, h->block_iters, h->lam,
+                        h->beta, h->st, s));
+  CK(gram(W, W, h->partA));
+  CK(launch_dr_start(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_psiinv, h->st, h->gws, s));
+  CK(bmul(Qb, W, h->dr_psiinv));
+  CK(cudaMemcpyAsync(S, Qb, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
+  CKS(set_tol2(h, tol * tol));
+  CKS(read_status(h));
+  int launched = 0;
+  while (h->h_st->flags == 0 && launched < maxit) {
+    const int nb = std::min(h->check_every, maxit - launched);
+    for (int i = 0; i < nb; ++i) {
+      CK(bop(S, W));                                    // W = A S
+      CK(gram(S, W, h->partA));                         // alpha = <<S, W>>
+      CK(launch_dr_xi(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws, s));
+      CK(baxpy(X, X, S, h->lam, 1.0, 0));               // X += S lambda, lambda = xi C
+      CK(baxpy(Qb, Qb, W, h->dr_xi, -1.0, 0));          // T = Q - W xi
+      CK(gram(Qb, Qb, h->partRho));                     // gamma = <<T, T>>
+      CK(launch_dr_psi(h->partRho, np_g, k, p, h->tol2_dev, h->r0n2, h->rn2, h->active, h->block_iters, h->dr_C,
+                       h->dr_psiinv, h->dr_phi, h->st, h->gws, s));
+      CK(bmul(W, Qb, h->dr_psiinv));                    // Q^+ = T psi^{-1}
+      CK(baxpy(Qb, W, S, h->dr_phi, 1.0, 1));           // S^+ = Q^+ + S psi^T; the iteration ends
+      double *old_s = S;
+      S = Qb;
+      Qb = W;
+      W = old_s;
+    }
+    launched += nb;
+    CKS(read_status(h));
+  }
+  const DevStatus fin = *h->h_st;
+  CKS(fill_block_iters(h));
+  CK(launch_residual<double>(h->A64, X, B, W, nullptr, nullptr, nullptr, n, k, h->partN, h->g64.res, s, nullptr));
+  CK(launch_reduce_norms(h->partN, h->g64.res, k, h->rtn2, s));
+  CKS(fetch_vec(h, h->r0n2, 0));
+  CKS(fetch_vec(h, h->rn2, 1));
+  CKS(fetch_vec(h, h->rtn2, 2));
+  const double *r0 = h->h_vec, *rn = h->h_vec + k, *rt = h->h_vec + 2 * k;
+  const bcg_status st = status_from_flags(fin.flags, (fin.flags & ST_DONE) != 0);
+  if (info) {
+    info->status = st;
+    info->iters = fin.iter;
+    info->outer_iters = 0;
+    info->breakdown_iter = (fin.flags & ST_BREAKDOWN) ? fin.breakdown_iter : -1;
+    info->max_rel_res_recursive = max_ratio(rn, r0, k);
+    info->max_rel_res_true = max_ratio(rt, r0, k);
+  }
+  if (st != BCG_OK) {
+    const char *what = st == BCG_ERR_NUMERIC ? "non-finite value" : st == BCG_ERR_BREAKDOWN ? "breakdown" : "maxit reached";
+    fail(st, "solve stopped: %s after %d iterations (retooled form)", what, fin.iter);
   }
   return st;
 }
@@ -869,6 +968,11 @@ bcg_status bcg_set_option(bcg_handle h, const char *key, double value) {
       cudaGraphExecDestroy(h->graph32);
       h->graph32 = nullptr;
     }
+  } else if (!strcmp(key, "retooled")) {
+    if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "retooled must be 0 or 1");
+    if (value == 1.0 && (h->prec != BCG_FP64 || h->global || h->rows_mode))
+      return fail(BCG_ERR_INVALID_ARG, "the retooled form needs an FP64 handle of the hybrid, parallel or classical subalgebra");
+    h->retooled = (int)value;
   } else if (!strcmp(key, "graph")) {
     if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "graph must be 0 or 1");
     h->use_graph = (int)value;
@@ -887,7 +991,10 @@ bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32
   if (maxit < 1) return fail(BCG_ERR_INVALID_ARG, "maxit must be >= 1");
   g_last_error.clear();
   auto run = [&](const double *Bs, double *Xs) {
-    if (h->prec == BCG_FP64) return solve_fp64(h, Bs, Xs, tol, maxit, info);
+    if (h->prec == BCG_FP64) {
+      if (h->retooled) return solve_retooled(h, Bs, Xs, tol, maxit, info);
+      return solve_fp64(h, Bs, Xs, tol, maxit, info);
+    }
     return h->refine ? solve_replace(h, Bs, Xs, tol, maxit, info) : solve_refine(h, Bs, Xs, tol, maxit, info);
   };
   if (h->perm == nullptr) return run(B, X);

@@ -106,4 +106,23 @@ cudaError_t launch_grad_values(const int32_t *rowidx, const int32_t *colind, con
                                int64_t nnz, int k, double *grad, int nsm, cudaStream_t s);
 cudaError_t launch_row_index(const int64_t *rowptr, int64_t n, int32_t *rowidx, int nsm, cudaStream_t s);
 
+// Retooled block CG (bcg_retooled.inc), FP64, hybrid family: streaming kernels for p <= 32 (the large-block
+// path uses launch_lp_*), and the per-block Cholesky QR kernels. Cf (C), xi, lam, psiinv (psi^{-1}) and
+// phi (psi^T) hold one row-major p x p matrix per block. launch_dr_baxpy: BASE may be NULL (zero).
+int dr_gram_grid(int64_t n, int k, int p, int nsm, int cap);
+cudaError_t launch_dr_bop(const OpDesc &A, const double *S, double *W, int64_t n, int k, const DevStatus *st,
+                          int nsm, cudaStream_t s);
+cudaError_t launch_dr_gram(const double *X, const double *Y, int64_t n, int k, int p, const int *active,
+                           double *part, int grid, const DevStatus *st, cudaStream_t s);
+cudaError_t launch_dr_baxpy(double *OUT, const double *BASE, const double *Y, const double *C, int64_t n, int k,
+                            int p, double sign, const int *active, DevStatus *st, int bump, int nsm,
+                            cudaStream_t s);
+cudaError_t launch_dr_start(const double *partG, int nparts, int k, int p, const int *active, double *Cf,
+                            double *psiinv, DevStatus *st, double *gws, cudaStream_t s);
+cudaError_t launch_dr_xi(const double *partA, int nparts, int k, int p, const int *active, const double *Cf,
+                         double *xi, double *lam, DevStatus *st, double *gws, cudaStream_t s);
+cudaError_t launch_dr_psi(const double *partG, int nparts, int k, int p, const double *tol2, const double *r0n2,
+                          double *rn2, int *active, int *block_iters, double *Cf, double *psiinv, double *phi,
+                          DevStatus *st, double *gws, cudaStream_t s);
+
 }  // namespace bcgk

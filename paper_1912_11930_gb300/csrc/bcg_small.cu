@@ -773,4 +773,6 @@ cudaError_t launch_row_index(const int64_t *rowptr, int64_t n, int32_t *rowidx, 
   return cudaGetLastError();
 }
 
+#include "bcg_retooled.inc"
+
 }  // namespace bcgk
