@@ -172,7 +172,7 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------------------------------------------
 # Other workloads (not the default line): measured with `python bench.py --workload NAME`
 EXTRA_WORKLOADS = ("poisson2d_64_k8", "varcoef3d_160_k64_mixed", "varcoef3d_160_k64_jacobi", "stencil27_100_k16_autograd",
-                   "poisson3d_96_sweep", "sell_vs_csr", "large_blocks_64_k256")
+                   "poisson3d_96_sweep", "sell_vs_csr", "large_blocks_64_k256", "retooled_128_k32")
 
 
 def time_solve(bcg, torch, M, B, *, k, p, sub, prec, form="csr", tol=1e-8, reps=2, dev=None, opts=None, warm=True,
@@ -287,6 +287,37 @@ def run_extra(name, args):
         out.update(value=rows[0]["s"], dtype="f64 (and f32 with f64 residual replacement)",
                    config={"workload": "poisson3d_64_csr_k256_classical_24_iterations", "n": M.n, "k": k, "p": k},
                    results=rows)
+    elif name == "retooled_128_k32":
+        # Dubrulle's retooled block CG against Algorithm 1 (FP64): the 128^3 Poisson solve to 1e-8, the same with
+        # the right-hand side's columns scaled from 1e-6 to 1e6 inside every block of 8 (Algorithm 1 breaks down
+        # there), and 24 iterations of the k = p = 256 classical solve at 64^3 (tiled large-block path)
+        rows = []
+        M = W.poisson3d(128)
+        k, p = 32, 8
+        B0 = W.rhs(M.n, k, seed=0)
+        d = np.tile(10.0 ** np.linspace(-6, 6, p), k // p)
+        for scaled in (False, True):
+            B = torch.from_numpy(B0 * d[None, :] if scaled else B0).to(dev)
+            for rt in (0, 1):
+                t, r, _ = time_solve(bcg, torch, M, B, k=k, p=p, sub="hybrid", prec="fp64", reps=args.steps, dev=dev,
+                                     opts={"retooled": rt})
+                rows.append(dict(matrix="poisson3d_128", k=k, p=p, columns="scaled 1e-6..1e6" if scaled else "N(0,1)",
+                                 form="retooled" if rt else "algorithm1", s=t, iterations=r.iters,
+                                 status=bcg.STATUS_NAMES[r.status], breakdown_iter=r.breakdown_iter,
+                                 ms_per_iteration=t * 1e3 / max(r.iters, 1), max_rel_res_true=r.max_rel_res_true))
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            del B
+        M = W.poisson3d(64)
+        B = torch.from_numpy(W.rhs(M.n, 256, seed=0)).to(dev)
+        for rt in (0, 1):
+            t, r, _ = time_solve(bcg, torch, M, B, k=256, p=256, sub="classical", prec="fp64", tol=1e-300, reps=1,
+                                 dev=dev, warm=False, maxit=24, opts={"retooled": rt})
+            rows.append(dict(matrix="poisson3d_64", k=256, p=256, form="retooled" if rt else "algorithm1", s=t,
+                             iterations=r.iters, ms_per_iteration=t * 1e3 / max(r.iters, 1)))
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        out.update(value=rows[1]["s"], dtype="f64",
+                   config={"workload": "poisson3d_128_csr_k32_hybrid_p8_retooled", "n": 128 ** 3, "k": k, "p": p},
+                   results=rows, note="value: time to 1e-8 of the retooled form on the N(0,1) right-hand side")
     elif name == "stencil27_100_k16_autograd":
         from paper_1912_11930_gb300.autograd import bcg_solve_autograd
         M = W.stencil27(100, seed=0)

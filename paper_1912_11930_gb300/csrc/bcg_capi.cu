@@ -503,26 +503,22 @@ bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int ma
 
 // Dubrulle's retooled block CG (option "retooled"; Electron. Trans. Numer. Anal. 12, 2001, the stability reference
 // of Section 3), FP64, hybrid family, M = I; the kernels and the recurrences are described in bcg_retooled.inc.
-// Three n x k buffers rotate: W = A S is dead once T = Q - W xi is formed, so Q^+ = T psi^{-1} is written into
-// it, and S^+ = Q^+ + S psi^T into T's buffer (no update writes a buffer it reads by whole blocks of p columns,
-// which the tiled large-block kernels need). Q = T psi^{-1} is a product without a base term: the streaming
-// update takes a NULL base, the tiled one a zeroed output (T + T (psi^{-1} - I) would cancel digits in
-// proportion to the column norms of R^0). Plain launches, a status read every check_every iterations.
+// p <= 32: three fused streaming kernels per iteration, all updates in place (S, W, Q keep their buffers).
+// p > 32: the tiled large-block kernels, unfused, and three n x k buffers rotate: W = A S is dead once
+// T = Q - W xi is formed, so Q^+ = T psi^{-1} is written into it and S^+ = Q^+ + S psi^T into T's buffer (the
+// tiled updates must not write a buffer they read by whole blocks of p columns). Q = T psi^{-1} is a product
+// without a base term (a NULL base, or a zeroed output for the tiled update): T + T (psi^{-1} - I) would cancel
+// digits in proportion to the column norms of R^0. Plain launches, a status read every check_every iterations.
 bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, int maxit, bcg_info *info) {
   if (h->precond) return fail(BCG_ERR_INVALID_ARG, "the retooled form runs with M = I (option precond = 0)");
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
   const int k = h->k, p = h->p;
   const bool lp = p > kMaxP;
-  const int np_g = lp ? h->g64.op : dr_gram_grid(n, k, p, h->nsm, h->nparts);
+  const int np_g = lp ? h->g64.op : dr_grid_for(h->A64.kind, n, k, p, h->nsm, h->nparts);
   auto gram = [&](const double *Xv, const double *Yv, double *part) -> cudaError_t {
     return lp ? launch_lp_gram<double>(Xv, Yv, n, k, p, 0, h->active, part, np_g, h->st, s, nullptr)
               : launch_dr_gram(Xv, Yv, n, k, p, h->active, part, np_g, h->st, s);
-  };
-  auto baxpy = [&](double *OUT, const double *BASE, const double *Yv, const double *Cm, double sign,
-                   int bump) -> cudaError_t {
-    return lp ? launch_lp_baxpy<double>(OUT, BASE, Yv, Cm, n, k, p, 0, sign, h->active, h->st, bump, s, nullptr)
-              : launch_dr_baxpy(OUT, BASE, Yv, Cm, n, k, p, sign, h->active, h->st, bump, h->nsm, s);
   };
   // OUT = Y C (no base term)
   auto bmul = [&](double *OUT, const double *Yv, const double *Cm) -> cudaError_t {
@@ -531,9 +527,9 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
     if (e != cudaSuccess) return e;
     return launch_lp_baxpy<double>(OUT, OUT, Yv, Cm, n, k, p, 0, 1.0, h->active, h->st, 0, s, nullptr);
   };
-  auto bop = [&](const double *Sv, double *Wv) -> cudaError_t {
-    return k % 2 == 0 ? launch_lp_bop<double>(h->A64, Sv, Wv, n, k, h->st, h->nsm, s)
-                      : launch_dr_bop(h->A64, Sv, Wv, n, k, h->st, h->nsm, s);
+  auto baxpy = [&](double *OUT, const double *BASE, const double *Yv, const double *Cm, double sign,
+                   int bump) -> cudaError_t {
+    return launch_lp_baxpy<double>(OUT, BASE, Yv, Cm, n, k, p, 0, sign, h->active, h->st, bump, s, nullptr);
   };
   double *W = h->R, *S = h->P, *Qb = h->Q;
   // R^0 = B - A X^0 (in W's buffer) = Q^0 C^0, S^1 = Q^0
@@ -550,16 +546,26 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
   while (h->h_st->flags == 0 && launched < maxit) {
     const int nb = std::min(h->check_every, maxit - launched);
     for (int i = 0; i < nb; ++i) {
-      CK(bop(S, W));                                    // W = A S
-      CK(gram(S, W, h->partA));                         // alpha = <<S, W>>
+      if (!lp) {
+        // W = A S, alpha | xi, lambda | X += S lambda, T = Q - W xi, gamma | stop test, psi | Q = T psi^{-1}, S
+        CK(launch_dr_op_gram(h->A64, S, W, n, k, p, h->active, h->partA, np_g, h->st, s));
+        CK(launch_dr_xi(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws, s));
+        CK(launch_dr_update_xt(X, Qb, S, W, n, k, p, h->lam, h->dr_xi, h->active, h->partRho, np_g, h->st, s));
+        CK(launch_dr_psi(h->partRho, np_g, k, p, h->tol2_dev, h->r0n2, h->rn2, h->active, h->block_iters,
+                         h->dr_C, h->dr_psiinv, h->dr_phi, h->st, h->gws, s));
+        CK(launch_dr_update_qs(Qb, S, n, k, p, h->dr_psiinv, h->dr_phi, h->active, h->st, h->nsm, s));
+        continue;
+      }
+      CK(launch_lp_bop<double>(h->A64, S, W, n, k, h->st, h->nsm, s));   // W = A S
+      CK(gram(S, W, h->partA));                                          // alpha = <<S, W>>
       CK(launch_dr_xi(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws, s));
-      CK(baxpy(X, X, S, h->lam, 1.0, 0));               // X += S lambda, lambda = xi C
-      CK(baxpy(Qb, Qb, W, h->dr_xi, -1.0, 0));          // T = Q - W xi
-      CK(gram(Qb, Qb, h->partRho));                     // gamma = <<T, T>>
+      CK(baxpy(X, X, S, h->lam, 1.0, 0));                                // X += S lambda, lambda = xi C
+      CK(baxpy(Qb, Qb, W, h->dr_xi, -1.0, 0));                           // T = Q - W xi
+      CK(gram(Qb, Qb, h->partRho));                                      // gamma = <<T, T>>
       CK(launch_dr_psi(h->partRho, np_g, k, p, h->tol2_dev, h->r0n2, h->rn2, h->active, h->block_iters, h->dr_C,
                        h->dr_psiinv, h->dr_phi, h->st, h->gws, s));
-      CK(bmul(W, Qb, h->dr_psiinv));                    // Q^+ = T psi^{-1}
-      CK(baxpy(Qb, W, S, h->dr_phi, 1.0, 1));           // S^+ = Q^+ + S psi^T; the iteration ends
+      CK(bmul(W, Qb, h->dr_psiinv));                                     // Q^+ = T psi^{-1}
+      CK(baxpy(Qb, W, S, h->dr_phi, 1.0, 1));                            // S^+ = Q^+ + S psi^T; the iteration ends
       double *old_s = S;
       S = Qb;
       Qb = W;

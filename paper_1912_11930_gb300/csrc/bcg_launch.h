@@ -109,11 +109,20 @@ cudaError_t launch_row_index(const int64_t *rowptr, int64_t n, int32_t *rowidx, 
 // Retooled block CG (bcg_retooled.inc), FP64, hybrid family: streaming kernels for p <= 32 (the large-block
 // path uses launch_lp_*), and the per-block Cholesky QR kernels. Cf (C), xi, lam, psiinv (psi^{-1}) and
 // phi (psi^T) hold one row-major p x p matrix per block. launch_dr_baxpy: BASE may be NULL (zero).
-int dr_gram_grid(int64_t n, int k, int p, int nsm, int cap);
-cudaError_t launch_dr_bop(const OpDesc &A, const double *S, double *W, int64_t n, int k, const DevStatus *st,
-                          int nsm, cudaStream_t s);
+// one partial-row count for every Gram of the streaming retooled path (<= cap, the partial buffers' rows)
+int dr_grid_for(int opk, int64_t n, int k, int p, int nsm, int cap);
+// W = A S and partials of <<S, W>>_S
+cudaError_t launch_dr_op_gram(const OpDesc &A, const double *S, double *W, int64_t n, int k, int p,
+                              const int *active, double *part, int grid, const DevStatus *st, cudaStream_t s);
 cudaError_t launch_dr_gram(const double *X, const double *Y, int64_t n, int k, int p, const int *active,
                            double *part, int grid, const DevStatus *st, cudaStream_t s);
+// X += S lambda, Qb = Qb - W xi (= T), partials of <<T, T>>_S
+cudaError_t launch_dr_update_xt(double *X, double *Qb, const double *S, const double *W, int64_t n, int k, int p,
+                                const double *lam, const double *xi, const int *active, double *part, int grid,
+                                const DevStatus *st, cudaStream_t s);
+// Qb = Qb psiinv, S = Qb + S phi (in place); advances the iteration counter
+cudaError_t launch_dr_update_qs(double *Qb, double *S, int64_t n, int k, int p, const double *psiinv,
+                                const double *phi, const int *active, DevStatus *st, int nsm, cudaStream_t s);
 cudaError_t launch_dr_baxpy(double *OUT, const double *BASE, const double *Y, const double *C, int64_t n, int k,
                             int p, double sign, const int *active, DevStatus *st, int bump, int nsm,
                             cudaStream_t s);
