@@ -172,7 +172,8 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------------------------------------------
 # Other workloads (not the default line): measured with `python bench.py --workload NAME`
 EXTRA_WORKLOADS = ("poisson2d_64_k8", "varcoef3d_160_k64_mixed", "varcoef3d_160_k64_jacobi", "stencil27_100_k16_autograd",
-                   "poisson3d_96_sweep", "sell_vs_csr", "large_blocks_64_k256", "retooled_128_k32")
+                   "poisson3d_96_sweep", "sell_vs_csr", "large_blocks_64_k256", "retooled_128_k32",
+                   "repetitions_varcoef2d_512_128rhs")
 
 
 def time_solve(bcg, torch, M, B, *, k, p, sub, prec, form="csr", tol=1e-8, reps=2, dev=None, opts=None, warm=True,
@@ -318,6 +319,34 @@ def run_extra(name, args):
         out.update(value=rows[1]["s"], dtype="f64",
                    config={"workload": "poisson3d_128_csr_k32_hybrid_p8_retooled", "n": 128 ** 3, "k": k, "p": p},
                    results=rows, note="value: time to 1e-8 of the retooled form on the N(0,1) right-hand side")
+    elif name == "repetitions_varcoef2d_512_128rhs":
+        # the repetition study of Section 4: 128 right-hand sides solved as r = 128 / k block solves of k columns
+        # (p = 16), on a 2D heterogeneous 5-point problem (512^2, log-normal face coefficients) with the Jacobi
+        # preconditioner standing in for the paper's ILU; time to 1e-8 for all 128 columns
+        M = W.varcoef2d(512, seed=0)
+        K, p = 128, 16
+        B = torch.from_numpy(W.rhs(M.n, K, seed=0)).to(dev)
+        rows = []
+        for prec in ("fp64", "fp32_refine"):
+            for k in (16, 32, 64, 128):
+                S = bcg.Solver.from_matrix(M, k=k, p=p, sub="hybrid", prec=prec, device=dev)
+                S.set_option("precond", 1)
+                S.solve_columns(B[:, :k], tol=1e-300, maxit=16)   # warm-up: kernels, graphs
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                X, res = S.solve_columns(B, tol=1e-8, maxit=20000)
+                e1.record()
+                torch.cuda.synchronize()
+                S.close()
+                rows.append(dict(prec=prec, k=k, p=p, r=K // k, s=e0.elapsed_time(e1) / 1e3,
+                                 iterations=[x.iters for x in res], status=[bcg.STATUS_NAMES[x.status] for x in res],
+                                 max_rel_res_true=max(x.max_rel_res_true for x in res)))
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        out.update(value=rows[0]["s"], dtype="f64 (and f32 inner, f64 residual replacement)",
+                   config={"workload": "varcoef2d_512_csr_128rhs_hybrid_p16_jacobi_repetitions", "n": M.n,
+                           "rhs": K, "p": p}, results=rows,
+                   note="value: FP64, k = 16 (r = 8 solves); every row solves all 128 columns to 1e-8")
     elif name == "stencil27_100_k16_autograd":
         from paper_1912_11930_gb300.autograd import bcg_solve_autograd
         M = W.stencil27(100, seed=0)

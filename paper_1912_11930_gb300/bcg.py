@@ -331,6 +331,26 @@ class Solver:
         self._leave()
         return X, self._result(st, info)
 
+    def solve_columns(self, B, X=None, tol=1e-8, maxit=10000):
+        """Solve for K = r k right-hand sides with this k-column handle: r = K / k solves in sequence, one per
+        group of k consecutive columns (the repetition schedule of the whole-solver experiment in Section 4,
+        where 128 right-hand sides run as r = 128 / k block solves). B, X: n x K row-major device tensors;
+        X is updated in place (zeros if None). Returns (X, [SolveResult per group])."""
+        torch = self.torch
+        K = B.shape[1]
+        if K % self.k:
+            raise BCGError(INVALID_ARG, f"{K} right-hand sides are not a multiple of the handle's k = {self.k}")
+        if X is None:
+            X = torch.zeros_like(B)
+        results = []
+        for g in range(K // self.k):
+            cols = slice(g * self.k, (g + 1) * self.k)
+            Xg = X[:, cols].contiguous()
+            Xg, r = self.solve(B[:, cols].contiguous(), Xg, tol=tol, maxit=maxit)
+            X[:, cols] = Xg
+            results.append(r)
+        return X, results
+
     def solve_host(self, B, X, tol=1e-8, maxit=10000):
         st, info = bcg_solve_host(self.h, B, X, tol, maxit)
         return X, self._result(st, info)

@@ -16,6 +16,9 @@ Workloads (the paper's whole-solver experiment in Section 4 uses a 2D heterogene
 * ``varcoef3d``      7-point variable-coefficient diffusion: one coefficient per cell face (boundary faces
                      included) drawn i.i.d. exp(N(0, sigma^2)); A_ii = h^-2 * sum of the cell's six face
                      coefficients, A_ij = -h^-2 * (coefficient of the shared face).
+* ``varcoef2d``      5-point variable-coefficient diffusion on nx x ny, the 2D form of ``varcoef3d`` (the
+                     heterogeneous 2D Poisson problem of the whole-solver experiment): x-faces (ny, nx+1)
+                     then y-faces (ny+1, nx), i.i.d. exp(N(0, sigma^2)); CSR only.
 * ``stencil27``      27-point SPD matrix: one value -U(0.5, 1.5) per unordered neighbour pair (so A is
                      symmetric), diagonal = row sum of |off-diagonals| + 0.1 (strictly diagonally dominant).
 * ``powerlaw_laplacian``  graph Laplacian + I of a random graph whose out-degrees follow a Pareto law
@@ -161,6 +164,30 @@ def varcoef3d(nx: int, ny: int | None = None, nz: int | None = None, seed: int =
                      meta=dict(name=f"varcoef3d_{nx}x{ny}x{nz}", h=h, sigma=sigma, seed=seed))
 
 
+def varcoef2d(nx: int, ny: int | None = None, seed: int = 0, sigma: float = 1.0) -> CSRMatrix:
+    ny = nx if ny is None else ny
+    h = 1.0 / (nx + 1)
+    s = 1.0 / (h * h)
+    rng = np.random.default_rng(seed + 2)
+    fx = np.exp(sigma * rng.standard_normal(ny * (nx + 1))).reshape(ny, nx + 1)
+    fy = np.exp(sigma * rng.standard_normal((ny + 1) * nx)).reshape(ny + 1, nx)
+    n = nx * ny
+    diag = (fx[:, :-1] + fx[:, 1:] + fy[:-1, :] + fy[1:, :]).reshape(n)
+    idx = np.arange(n, dtype=np.int64)
+    ix, iy = idx % nx, idx // nx
+    rows, cols, vals = [idx], [idx], [s * diag]
+    for dx, dy in ((-1, 0), (1, 0), (0, -1), (0, 1)):
+        ok = (ix + dx >= 0) & (ix + dx < nx) & (iy + dy >= 0) & (iy + dy < ny)
+        r = idx[ok]
+        x, y = ix[ok], iy[ok]
+        f = fx[y, x + (1 if dx > 0 else 0)] if dx else fy[y + (1 if dy > 0 else 0), x]
+        rows.append(r)
+        cols.append(r + dx + dy * nx)
+        vals.append(-s * f)
+    rowptr, colind, v = _assemble(n, np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+    return CSRMatrix(n, rowptr, colind, v, meta=dict(name=f"varcoef2d_{nx}x{ny}", h=h, sigma=sigma, seed=seed))
+
+
 _OFFSETS27 = [(dx, dy, dz) for dz in (-1, 0, 1) for dy in (-1, 0, 1) for dx in (-1, 0, 1)
               if (dx, dy, dz) != (0, 0, 0)]
 # the 13 "forward" offsets: lexicographically positive (dz, dy, dx)
@@ -263,4 +290,6 @@ def make_matrix(kind: str, size: int, seed: int = 0) -> CSRMatrix:
         return varcoef3d(size, seed=seed)
     if kind == "stencil27":
         return stencil27(size, seed=seed)
+    if kind == "varcoef2d":
+        return varcoef2d(size, seed=seed)
     raise ValueError(kind)

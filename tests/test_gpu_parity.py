@@ -510,3 +510,31 @@ def test_tiny_systems(torch_dev, prec, form):
                 continue
             assert r.ok, (M.n, k, p, r)
             assert _rel(X.cpu().numpy(), np.linalg.solve(A.toarray(), B)) <= 1e-8
+
+
+def test_solve_columns_is_r_block_solves(torch_dev):
+    """The repetition schedule (Section 4's study: K right-hand sides as r = K / k block solves of k columns)
+    gives, group by group, the bitwise result of separate solves, and each group matches the oracle."""
+    torch, dev = torch_dev
+    from paper_1912_11930_gb300 import bcg
+    M = W.varcoef2d(40, 33, seed=3)
+    A = M.to_scipy()
+    K, k, p = 24, 8, 4
+    B = W.rhs(M.n, K, seed=9)
+    S = bcg.Solver.from_matrix(M, k=k, p=p, sub="hybrid", prec="fp64", device=dev)
+    S.set_option("precond", 1)
+    Bt = torch.from_numpy(B).to(dev)
+    X, res = S.solve_columns(Bt, tol=1e-9, maxit=2000)
+    assert len(res) == K // k and all(r.ok for r in res)
+    for g in range(K // k):
+        cols = slice(g * k, (g + 1) * k)
+        Xg, rg = S.solve(Bt[:, cols].contiguous(), tol=1e-9, maxit=2000)
+        assert torch.equal(Xg, X[:, cols]) and rg.iters == res[g].iters
+        ref = O.solve(A, B[:, cols], p=p, sub="hybrid", tol=1e-9, maxit=2000, precond="jacobi")
+        assert abs(ref.iters - res[g].iters) <= 2
+        Xn = X[:, cols].cpu().numpy()
+        assert np.all(np.linalg.norm(B[:, cols] - A @ Xn, axis=0) <= 1.5e-9 * np.linalg.norm(B[:, cols], axis=0))
+        assert _rel(Xn, ref.X) <= 1e-6
+    with pytest.raises(bcg.BCGError):
+        S.solve_columns(Bt[:, :20].contiguous())
+    S.close()

@@ -15,7 +15,8 @@ def test_poisson_nnz_closed_forms():
 
 
 @pytest.mark.parametrize("make", [lambda: W.poisson2d(5, 4), lambda: W.poisson3d(3, 4, 2),
-                                  lambda: W.varcoef3d(3, 4, 2, seed=1), lambda: W.stencil27(3, 2, 4, seed=2)])
+                                  lambda: W.varcoef3d(3, 4, 2, seed=1), lambda: W.stencil27(3, 2, 4, seed=2),
+                                  lambda: W.varcoef2d(5, 3, seed=1)])
 def test_symmetric_positive_definite(make):
     M = make()
     A = M.to_scipy().toarray()
@@ -46,6 +47,17 @@ def test_varcoef_rows_sum_to_boundary_faces():
     bnd[:, 0, :] += fy[:, 0, :]; bnd[:, -1, :] += fy[:, -1, :]
     bnd[0] += fz[0]; bnd[-1] += fz[-1]
     assert np.allclose(np.asarray(A.sum(axis=1)).ravel(), M.stencil["scale"] * bnd.ravel(), rtol=1e-12)
+
+
+def test_varcoef2d_is_the_2d_operator():
+    """Unit coefficients give the 5-point Poisson matrix; nonzeros 5n - 2(nx + ny); interior row sums vanish."""
+    M = W.varcoef2d(7, 5, seed=2, sigma=0.0)
+    assert np.array_equal(M.to_scipy().toarray(), W.poisson2d(7, 5).to_scipy().toarray())
+    V = W.varcoef2d(7, 5, seed=2)
+    assert V.nnz == 5 * 35 - 2 * 12
+    rs = np.asarray(V.to_scipy().sum(axis=1)).ravel().reshape(5, 7)
+    assert np.allclose(rs[1:-1, 1:-1], 0.0, atol=1e-9 * np.abs(V.vals).max())
+    assert np.all(rs[0] > 0) and np.all(rs[:, 0] > 0)
 
 
 def test_seeds():
