@@ -36,16 +36,17 @@ REF_ITERS = 354
 ORACLE_SAMPLE_ITERS = 3
 # DRAM bytes per launch of the dominant kernel (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu
 # capture at 96^3 (profiles/<kernel>_poisson3d_96_*.md), scaled by rows to the 128^3 launch. Valid only for the
-# device source the capture was taken on: sha256 prefix of KERNEL_SOURCES concatenated; reported as null once
-# that source changes.
-KERNEL_SOURCES = ["bcg_kernels.cuh", "bcg_kernels_wc.cuh", "bcg_kernels_lp.cuh", "bcg_stream.inc"]
-TRAFFIC = {("update_xr", "poisson3d_128_csr_k32_hybrid_p8_fp64"): ("d3ab035fd0470ab9", 1.3274e9 * 2097152 / 884736)}
+# device source the capture was taken on: sha256 prefix of the files that define the kernel (its body, the
+# helpers it calls and its launcher), concatenated; reported as null once one of them changes.
+UPDATE_XR_SOURCES = ("bcg_kernels.cuh", "bcg_kernels_wc.cuh", "bcg_stream.inc")
+TRAFFIC = {("update_xr", "poisson3d_128_csr_k32_hybrid_p8_fp64"):
+           (UPDATE_XR_SOURCES, "7e13b544f9f58e10", 1.3274e9 * 2097152 / 884736)}
 
 
-def kernel_source_sha():
+def kernel_source_sha(files):
     import hashlib
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES:
+    for name in files:
         with open(os.path.join(ROOT, "paper_1912_11930_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -507,8 +508,8 @@ def main():
     # (the block products run as error-free FP32 arithmetic and are reported beside it)
     traffic = None
     ent = TRAFFIC.get((dom, w["name"]))
-    if ent and ent[0] == kernel_source_sha():
-        traffic = ent[1]
+    if ent and ent[1] == kernel_source_sha(ent[0]):
+        traffic = ent[2]
     roofline = {"bound": "alu", "kernel": dom, "achieved": d["fp64_tflops"], "peak": NOMINAL_FP64_TFLOPS,
                 "unit": "TFLOP/s", "frac": d["fp64_tflops"] / NOMINAL_FP64_TFLOPS, "traffic": traffic,
                 "counted": "algorithmic FP64-FMA flops of the kernel (BOP / BAXPY); its block products run as "
