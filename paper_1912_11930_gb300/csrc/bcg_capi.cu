@@ -503,7 +503,8 @@ bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int ma
 
 // Dubrulle's retooled block CG (option "retooled"; Electron. Trans. Numer. Anal. 12, 2001, the stability reference
 // of Section 3), FP64, hybrid family, M = I; the kernels and the recurrences are described in bcg_retooled.inc.
-// p <= 32: three fused streaming kernels per iteration, all updates in place (S, W, Q keep their buffers).
+// p <= 32: Algorithm 1's K1 for W = A S and alpha, then two fused streaming updates, all in place (S, W, Q
+// keep their buffers).
 // p > 32: the tiled large-block kernels, unfused, and three n x k buffers rotate: W = A S is dead once
 // T = Q - W xi is formed, so Q^+ = T psi^{-1} is written into it and S^+ = Q^+ + S psi^T into T's buffer (the
 // tiled updates must not write a buffer they read by whole blocks of p columns). Q = T psi^{-1} is a product
@@ -515,7 +516,7 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
   const int64_t n = h->n;
   const int k = h->k, p = h->p;
   const bool lp = p > kMaxP;
-  const int np_g = lp ? h->g64.op : dr_grid_for(h->A64.kind, n, k, p, h->nsm, h->nparts);
+  const int np_g = lp ? h->g64.op : dr_grid_for(n, k, p, h->nsm, h->nparts);
   auto gram = [&](const double *Xv, const double *Yv, double *part) -> cudaError_t {
     return lp ? launch_lp_gram<double>(Xv, Yv, n, k, p, 0, h->active, part, np_g, h->st, s, nullptr)
               : launch_dr_gram(Xv, Yv, n, k, p, h->active, part, np_g, h->st, s);
@@ -547,9 +548,12 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
     const int nb = std::min(h->check_every, maxit - launched);
     for (int i = 0; i < nb; ++i) {
       if (!lp) {
-        // W = A S, alpha | xi, lambda | X += S lambda, T = Q - W xi, gamma | stop test, psi | Q = T psi^{-1}, S
-        CK(launch_dr_op_gram(h->A64, S, W, n, k, p, h->active, h->partA, np_g, h->st, s));
-        CK(launch_dr_xi(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws, s));
+        // W = A S, alpha (K1; where K1 also forms a recomputed rho, it reads Q and the result is unused) |
+        // xi, lambda | X += S lambda, T = Q - W xi, gamma | stop test, psi | Q = T psi^{-1}, S
+        CK(launch_op_gram<double>(h->A64, S, Qb, W, n, k, p, 0, h->active, h->partA, h->partR, h->st, h->g64.op,
+                                  s));
+        CK(launch_dr_xi(h->partA, h->g64.op, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws,
+                        h->g64.alpha_circ, s));
         CK(launch_dr_update_xt(X, Qb, S, W, n, k, p, h->lam, h->dr_xi, h->active, h->partRho, np_g, h->st, s));
         CK(launch_dr_psi(h->partRho, np_g, k, p, h->tol2_dev, h->r0n2, h->rn2, h->active, h->block_iters,
                          h->dr_C, h->dr_psiinv, h->dr_phi, h->st, h->gws, s));
@@ -558,7 +562,7 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
       }
       CK(launch_lp_bop<double>(h->A64, S, W, n, k, h->st, h->nsm, s));   // W = A S
       CK(gram(S, W, h->partA));                                          // alpha = <<S, W>>
-      CK(launch_dr_xi(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws, s));
+      CK(launch_dr_xi(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws, 0, s));
       CK(baxpy(X, X, S, h->lam, 1.0, 0));                                // X += S lambda, lambda = xi C
       CK(baxpy(Qb, Qb, W, h->dr_xi, -1.0, 0));                           // T = Q - W xi
       CK(gram(Qb, Qb, h->partRho));                                      // gamma = <<T, T>>

@@ -109,11 +109,8 @@ cudaError_t launch_row_index(const int64_t *rowptr, int64_t n, int32_t *rowidx, 
 // Retooled block CG (bcg_retooled.inc), FP64, hybrid family: streaming kernels for p <= 32 (the large-block
 // path uses launch_lp_*), and the per-block Cholesky QR kernels. Cf (C), xi, lam, psiinv (psi^{-1}) and
 // phi (psi^T) hold one row-major p x p matrix per block. launch_dr_baxpy: BASE may be NULL (zero).
-// one partial-row count for every Gram of the streaming retooled path (<= cap, the partial buffers' rows)
-int dr_grid_for(int opk, int64_t n, int k, int p, int nsm, int cap);
-// W = A S and partials of <<S, W>>_S
-cudaError_t launch_dr_op_gram(const OpDesc &A, const double *S, double *W, int64_t n, int k, int p,
-                              const int *active, double *part, int grid, const DevStatus *st, cudaStream_t s);
+// partial-row count of the gamma products of the streaming retooled path (<= cap, the partial buffers' rows)
+int dr_grid_for(int64_t n, int k, int p, int nsm, int cap);
 cudaError_t launch_dr_gram(const double *X, const double *Y, int64_t n, int k, int p, const int *active,
                            double *part, int grid, const DevStatus *st, cudaStream_t s);
 // X += S lambda, Qb = Qb - W xi (= T), partials of <<T, T>>_S
@@ -128,8 +125,9 @@ cudaError_t launch_dr_baxpy(double *OUT, const double *BASE, const double *Y, co
                             cudaStream_t s);
 cudaError_t launch_dr_start(const double *partG, int nparts, int k, int p, const int *active, double *Cf,
                             double *psiinv, DevStatus *st, double *gws, cudaStream_t s);
+// alpha_circ: the alpha partials are K1's circulant-diagonal storage
 cudaError_t launch_dr_xi(const double *partA, int nparts, int k, int p, const int *active, const double *Cf,
-                         double *xi, double *lam, DevStatus *st, double *gws, cudaStream_t s);
+                         double *xi, double *lam, DevStatus *st, double *gws, int alpha_circ, cudaStream_t s);
 cudaError_t launch_dr_psi(const double *partG, int nparts, int k, int p, const double *tol2, const double *r0n2,
                           double *rn2, int *active, int *block_iters, double *Cf, double *psiinv, double *phi,
                           DevStatus *st, double *gws, cudaStream_t s);
