@@ -61,16 +61,27 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def kernel_model(n, k, p, z, s, a_bytes):
+def rho_in_k3(k, p, prec):
+    """Where the library forms the recomputed rho (the dispatch rule rho_in_k3 of its streaming kernels):
+    in K3 of the previous iteration for FP64 with 2 <= p <= 16 in the warp-chunk layout (k even, and k | 32,
+    or 32 | k with k / 32 | 8 and p | 32); in K1 otherwise."""
+    wc = k <= 256 and k % 2 == 0 and (32 % k == 0 or (k % 32 == 0 and 8 % (k // 32) == 0 and 32 % p == 0))
+    return prec == "fp64" and 2 <= p <= 16 and wc
+
+
+def kernel_model(n, k, p, z, s, a_bytes, rho_k3=False):
     """Algorithmic flops and bytes per launch of each iteration kernel (the paper's Table 1 omega and beta per
-    kernel, fused as the kernels fuse them): K1 = BOP + 2 BDOT, K2 = 2 BAXPY + BDOT + column norms,
-    K3 = BAXPY. `alu` is the part executed as native arithmetic of the block vectors' precision (BOP and
+    kernel, fused as the kernels fuse them): K1 = BOP + BDOT alpha (+ BDOT of the recomputed rho, reading R),
+    K2 = 2 BAXPY + BDOT + column norms, K3 = BAXPY (+ the next recomputed rho when rho_k3: R is read there
+    anyway). `alu` is the part executed as native arithmetic of the block vectors' precision (BOP and
     BAXPY: FP64 FMAs in the FP64 form, FP32 FMAs in the mixed form); `gram` is the block-product part,
     which runs as error-free (Dot2) FP32 arithmetic with FP64-class accuracy in both forms."""
+    k1_grams = 1.0 if rho_k3 else 2.0
     return {
-        "op_gram": dict(alu=2.0 * k * z, gram=4.0 * n * p * k, bytes=a_bytes + 3.0 * n * k * s),
+        "op_gram": dict(alu=2.0 * k * z, gram=k1_grams * 2.0 * n * p * k,
+                        bytes=a_bytes + (2.0 if rho_k3 else 3.0) * n * k * s),
         "update_xr": dict(alu=4.0 * n * p * k, gram=2.0 * n * p * k + 2.0 * n * k, bytes=6.0 * n * k * s),
-        "update_p": dict(alu=2.0 * n * p * k, gram=0.0, bytes=3.0 * n * k * s),
+        "update_p": dict(alu=2.0 * n * p * k, gram=2.0 * n * p * k if rho_k3 else 0.0, bytes=3.0 * n * k * s),
     }
 
 
@@ -482,9 +493,12 @@ def main():
     ok = all(r.ok and r.max_rel_res_true <= 1.5 * w["tol"] for r in results)
 
     # roofline of the dominant kernel
-    s_bytes = 8
-    a_bytes = 12.0 * z + 8.0 * (n + 1)
-    model = kernel_model(n, k, p, z, s_bytes, a_bytes)
+    # the profiled kernels are the FP64 iteration, or the FP32 inner iteration of the mixed form (FP32 block
+    # vectors and an FP32 copy of the CSR values)
+    fp64 = w["prec"] == "fp64"
+    s_bytes = 8 if fp64 else 4
+    a_bytes = (12.0 if fp64 else 8.0) * z + 8.0 * (n + 1)
+    model = kernel_model(n, k, p, z, s_bytes, a_bytes, rho_k3=rho_in_k3(k, p, w["prec"]))
     hbm_peak, hbm_src = peaks()
     per_kernel = {}
     for name, (tot, cnt) in prof.items():
@@ -522,7 +536,7 @@ def main():
     launched_iters = int(math.ceil(iters / 8.0) * 8)
     # per solve: K0, status reset, (FP64 with 2 <= p <= 16) the BDOT of the first recomputed rho, 5 kernels per
     # launched iteration (batches of 8), then K0 and a norm reduction for the true residual
-    setup = 4 + (1 if (w["prec"] == "fp64" and 2 <= p <= 16) else 0)
+    setup = 4 + (1 if rho_in_k3(k, p, w["prec"]) else 0)
     gpu_launches = args.steps * (setup + 5 * launched_iters)
 
     line = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
