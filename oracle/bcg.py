@@ -17,7 +17,7 @@ Paper passages followed:
 * Section 4, whole-solver experiment: the stopping rule "2-norm of every residual column reduced by the
   factor tol".
 
-Readings of places where the paper is silent, garbled or inconsistent (each one is also in the design doc):
+Readings of places where the paper is silent, garbled or inconsistent:
 * R1 sign of the direction update: Algorithm 1 prints P^{i+1} = Z - P beta. With beta = rho_{i-1}^{-1}
   rho_i > 0 at k = 1 this contradicts CG, so the oracle uses P^{i+1} = Z + P beta.
 * R2 global product: the printed sum runs from 0 to q; the proof of the global-rate lemma stacks
@@ -38,7 +38,7 @@ Readings of places where the paper is silent, garbled or inconsistent (each one 
 (A. A. Dubrulle, "Retooling the method of block conjugate gradients", Electron. Trans. Numer. Anal. 12,
 2001): the residual is carried as R = Q C with an orthonormal Q and a p x p factor C, and the search
 directions are built from Q, so differently scaled residual columns do not make the small systems
-ill-conditioned. Readings (also in DESIGN.md):
+ill-conditioned. Readings:
 * R12 the QR factorisation of Dubrulle's method is taken within the subalgebra as a Cholesky QR: with
   gamma = <<T, T>>_S = L L^T, C-factor psi = L^T and Q = T psi^{-1}; restricted to the hybrid family
   (hybrid, parallel, classical), whose products give every column's norm.
