@@ -169,9 +169,11 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
 bcg_status bcg_set_option(bcg_handle h, const char *key, double value);
 
 /*
- * bcg_solve -- Algorithm 1 (Section 3) with M = I (or Jacobi, option "precond") from X^0 = X to the
- * stopping rule of Section 4's whole-solver experiment: every column s with ||R_s|| <= tol ||R_s^0|| (recursive residual, 2-norm).
- * Hybrid/parallel blocks stop updating once all their columns pass; global/classical stop together.
+ * bcg_solve -- Algorithm 1 (Section 3) with M = I (or Jacobi, option "precond"; or Dubrulle's retooled
+ * form of it, option "retooled") from X^0 = X to the stopping rule of Section 4's whole-solver experiment:
+ * every column s with ||R_s|| <= tol ||R_s^0|| (recursive residual, 2-norm; the retooled form evaluates it
+ * as (C^T gamma C)_ss from its factored residual R = Q C). Hybrid/parallel blocks stop updating once all
+ * their columns pass; global/classical stop together.
  *   B      device double[n*k], row-major, not modified
  *   X      device double[n*k], row-major; in: X^0, out: the solution (or last iterate on error)
  *   tol    > 0 (FP32_REFINE: tolerance of the FP64 outer residual)
