@@ -174,3 +174,20 @@ def test_retooled_degenerate_cases_and_arguments(torch_dev):
     S.close()
     assert r1.ok and r2.ok and abs(r1.iters - r2.iters) <= 2
     assert _rel(X2.cpu().numpy(), X1.cpu().numpy()) <= 1e-7
+
+
+def test_retooled_full_size_against_oracle(torch_dev):
+    """The retooled bench workload (128^3 Poisson, k = 32, hybrid p = 8, FP64): four iterations on the GPU
+    against four iterations of the oracle's retooled form on the whole matrix, 1e-9."""
+    torch, dev = torch_dev
+    from paper_1912_11930_gb300 import bcg
+    M = W.poisson3d(128)
+    k, p, m = 32, 8, 4
+    B = W.rhs(M.n, k, seed=0)
+    S = bcg.Solver.from_matrix(M, k=k, p=p, sub="hybrid", prec="fp64", device=dev)
+    S.set_option("retooled", 1)
+    X, r = S.solve(torch.from_numpy(B).to(dev), tol=NEVER, maxit=m)
+    S.close()
+    assert r.status == 5 and r.iters == m
+    ref = O.solve_retooled(M.to_scipy(), B, p=p, sub="hybrid", tol=0.0, maxit=m)
+    assert _rel(X.cpu().numpy(), ref.X) <= 1e-9
