@@ -24,6 +24,24 @@
  *    recent failure of the calling thread.
  *  - Work is ordered on the handle's CUDA stream; bcg_solve returns after the final status is known.
  *  - A handle may be used by one thread at a time.
+ *
+ * Arithmetic of the FP64 form (BCG_FP64):
+ *  - BOP (Y = A X), the block updates (BAXPY) and the p x p Cholesky/LU solves (BSOLVE) are IEEE FP64
+ *    operations (fused multiply-adds).
+ *  - Block products (BDOT: alpha, the recomputed rho, rho, the column norms of the stopping test) are not
+ *    summed with FP64 operations. Each FP64 operand column c is first scaled by an exact power of two 2^-s_c
+ *    (s_c from the column's latest 2-norm in the solver, from its largest entry in bcg_bdot), then every value
+ *    is split into two floats hi + lo holding its leading 48 significant bits (|x - hi - lo| <= 2^-47 |x|).
+ *    The products hi*hi (exactly, by TwoProd), hi*lo and lo*hi are accumulated as an unevaluated float pair
+ *    per entry with error-free transformations (algorithm Dot2 of Ogita, Rump & Oishi, SIAM J. Sci. Comput.
+ *    26(6), 2005); lo*lo (relative weight 2^-48) is dropped. Every 128 rows each pair is scaled back by
+ *    2^(s_a + s_b) and added into FP64 sums, which are reduced over threads and CTAs in FP64 in a fixed
+ *    order (bitwise repeatable).
+ *  - Error: |computed - exact| <= about 2^-46 sum_r |x_ra y_rb| per entry (tested at 1e-13 of that sum), plus
+ *    at most n 2^-100 max_r|x_ra| max_r|y_rb| from entries whose scaled product falls below FP32's range.
+ *  - Range: any FP64 operands whose products and sums are finite in FP64 (tested with entries from 1e-300 to
+ *    1e300 and exact zeros, and with B scaled by 1e+-30 and A by 1e+-10); within the solver a column may
+ *    grow by about 2^50 or shrink by about 2^49 between two norm updates without loss.
  */
 #ifndef BCG_H
 #define BCG_H
@@ -56,11 +74,15 @@ typedef enum {
 } bcg_subalgebra;
 
 typedef enum {
-  BCG_FP64 = 0,              /* every step in IEEE FP64                                               */
+  BCG_FP64 = 0,              /* FP64 iteration vectors and updates, FP64-accurate block products (see
+                                "Arithmetic of the FP64 form" above)                                  */
   BCG_FP32_REFINE = 1        /* FP32 block CG inside FP64 residual recomputation: operator products
                                 and block updates in FP32, Gram matrices FP64-accurate, p x p
                                 Cholesky/LU solves, the solution and its residual in FP64; residual
-                                replacement or restarted refinement (option "refine")               */
+                                replacement or restarted refinement (option "refine"). The FP32
+                                process of block j runs on R_j 2^-sigma_j, an exact scaling with
+                                sigma_j the exponent of the block's largest FP64 column norm, so
+                                FP32's range never limits the scale of B or X                        */
 } bcg_precision;
 
 typedef enum {
@@ -152,7 +174,8 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
  *                  (default 1; graphs need a non-NULL stream)
  *   "profile"      1 = time every iteration kernel with CUDA events (see bcg_profile), 0 = off;
  *                  setting it resets the counters
- *   "precond"      preconditioner M of Algorithm 1: 0 = identity (default), 1 = Jacobi, M = diag(A)
+ *   "precond"      preconditioner M of Algorithm 1 (its steps P^1 = M^{-1} R^0 and Z = M^{-1} R; Section 3):
+ *                  0 = identity (default), 1 = Jacobi, M = diag(A)
  *                  (Section 3 allows any SPD M; Z = M^{-1} R is formed on the fly by the kernels that
  *                  read R, from 1/diag(A) computed at create time and by bcg_update_values; the mixed
  *                  form uses an FP32 copy). Every diagonal entry must be positive.
@@ -185,7 +208,7 @@ bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32
                      bcg_info *info);
 
 /*
- * bcg_solve_host -- bcg_solve on HOST arrays: copies B and X^0 to the handle's device staging
+ * bcg_solve_host -- bcg_solve (Algorithm 1, Section 3) on HOST arrays: copies B and X^0 to the handle's device staging
  * buffers (allocated at the first call, 2 n k doubles), solves, and copies X back. Same arguments
  * and statuses as bcg_solve, with B and X in host memory.
  */
@@ -194,7 +217,9 @@ bcg_status bcg_solve_host(bcg_handle h, const double *B, double *X, double tol, 
 
 /*
  * bcg_block_iters -- per distinct block (q for hybrid/parallel/classical, 1 for global) the
- * iteration at which it froze in the last solve (or the last iteration if it never did).
+ * iteration at which it froze in the last solve (or the last iteration if it never did): the per-block
+ * stopping of Section 4's rule in the hybrid subalgebra, whose blocks are independent solves (Section 3).
+ * Statuses: OK, or INVALID_ARG for a NULL handle or output.
  * out: host int32[cap]; returns INVALID_ARG if cap is smaller than the number of blocks.
  */
 bcg_status bcg_block_iters(bcg_handle h, int32_t *out, int32_t cap);
@@ -210,15 +235,18 @@ bcg_status bcg_block_iters(bcg_handle h, int32_t *out, int32_t cap);
 bcg_status bcg_grad_values(bcg_handle h, const double *Lambda, const double *X, double *grad);
 
 /*
- * bcg_update_values -- rebind the CSR values (same pattern) or the varcoef faces: vals is a device
- * array of the same length as at create time; it is borrowed from now on.
+ * bcg_update_values -- rebind the operator of BOP (Section 3's kernel list, Y = A X): the CSR values
+ * (same pattern) or the varcoef faces. vals is a device array of the same length as at create time; it is
+ * borrowed from now on. 1/diag(A) (Jacobi) and the operator maxima behind the Gram shifts are recomputed.
+ * Returns INVALID_ARG for a NULL handle, a non-device pointer or a constant-stencil handle, or CUDA.
  */
 bcg_status bcg_update_values(bcg_handle h, const double *vals);
 
 /*
  * bcg_bdot -- the BDOT kernel alone (Section 3; Section 2, Definition "Relevant *-subalgebras"):
- * gamma = <<X, Y>>_S for the handle's k, p and subalgebra, accumulated in FP64 with per-CTA partials in
- * the handle's workspace and summed in a fixed order.
+ * gamma = <<X, Y>>_S for the handle's k, p and subalgebra, accumulated as described under "Arithmetic of the
+ * FP64 form" (shifts from the column maxima of X and of Y, found by one extra pass over each), with per-CTA
+ * partials in the handle's workspace summed in a fixed order.
  *   X, Y   device double[n*k], row-major
  *   gamma  device double[nblk*p*p], nblk = q (hybrid/parallel/classical) or 1 (global); block jb's entry
  *          (a, b) = sum_i X[i, jb*p + a] Y[i, jb*p + b] (global: summed over the q blocks) at jb*p*p + a*p + b
@@ -239,18 +267,21 @@ bcg_status bcg_bdot_f32(bcg_handle h, const float *X, const float *Y, double *ga
  * Some callers cannot call cudaMalloc: code that runs while a CUDA graph is being captured and must not
  * allocate, plug-ins whose host application owns every device allocation through its own pool, and
  * latency-critical paths where an allocation may block or fail. This entry point needs no handle (creating
- * one allocates) and allocates nothing: the per-CTA partial sums live in one static device array of
- * 262,144 doubles (2 MiB) that every GPU which loads the library holds until the process exits. The
- * caller passes the inputs and the output.
- *   n, k, p, sub  as for bcg_create_csr (1 <= k <= 256, p divides k, p <= 32; k*p must fit the array)
+ * one allocates) and allocates nothing: the column maxima and exponent shifts of X and Y and the per-CTA
+ * partial sums live in one static device array of 262,144 doubles (2 MiB) that every GPU which loads the
+ * library holds until the process exits. The caller passes the inputs and the output.
+ *   n, k, p, sub  as for bcg_create_csr (1 <= k <= 256, p divides k, p <= 32; k*p <= 261,120)
  *   X, Y          device double[n*k], row-major
  *   gamma         device double[nblk*p*p], layout as for bcg_bdot
- *   cuda_stream   stream to order the two launches on; the call returns once they are enqueued
- * The first call on a device looks up that device's address of the array (cudaGetSymbolAddress) and
- * should therefore come before any stream capture. Every call shares the array and overwrites the
- * partial sums it uses before reading them (nothing has to start at zero), so calls that overlap on the
- * GPU -- on different streams, or from several threads -- race and must be serialised by the caller.
- * Returns INVALID_ARG (sizes beyond the limits, non-device pointers, unknown subalgebra) or CUDA.
+ *   cuda_stream   stream to order the work on; the call returns once it is enqueued
+ * X, Y and gamma must live on the current device, whose copy of the array is used. The first call on a
+ * device looks up that device's address of the array (cudaGetSymbolAddress) and should therefore come
+ * before any stream capture. Every call shares the array: it clears the column maxima (a memset of the
+ * array, which allocates nothing) and overwrites the partial sums it uses before reading them, so calls
+ * that overlap on the GPU -- on different streams, or from several threads -- race and must be serialised
+ * by the caller. The arithmetic is bcg_bdot's.
+ * Returns INVALID_ARG (sizes beyond the limits, non-device pointers or pointers of another device, unknown
+ * subalgebra) or CUDA.
  */
 bcg_status bcg_bdot_noalloc(int64_t n, int32_t k, int32_t p, int32_t sub, const double *X, const double *Y,
                             double *gamma, void *cuda_stream);

@@ -114,6 +114,11 @@ struct bcg_ctx {
   double *lam = nullptr, *beta = nullptr, *rho_rec = nullptr;
   double *r0n2 = nullptr, *rn2 = nullptr, *rtn2 = nullptr, *outer0 = nullptr;
   int *active = nullptr, *block_iters = nullptr;
+  int *sh = nullptr;                   // exponent shifts of the FP64 Gram operands, 3 k ints (roles R, P, Q)
+  double *opmax = nullptr;             // [max row sum of |A|, max |diag(A)^{-1}|] (offsets of the P and Q shifts)
+  double *tmp2k = nullptr;             // 2 k doubles: standalone BDOT column maxima, the mixed form's scaled norms
+  int *bdot_sh = nullptr;              // standalone BDOT: their shifts (2 k)
+  int *msig = nullptr;                 // mixed form: exponent of the FP32 process's scale per column (k)
   double *gws = nullptr;               // global workspace of the p x p solves when p is large
   double *dinv64 = nullptr;            // 1 / diag(A) (Jacobi preconditioner)
   double *dr_C = nullptr, *dr_xi = nullptr, *dr_psiinv = nullptr, *dr_phi = nullptr;   // retooled form, p x p per block
@@ -217,6 +222,12 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CKS(h->alloc(&h->outer0, h->k));
   CKS(h->alloc(&h->active, h->nblk));
   CKS(h->alloc(&h->block_iters, h->nblk));
+  CKS(h->alloc(&h->sh, 3 * (size_t)h->k));
+  CK(cudaMemsetAsync(h->sh, 0, 3 * sizeof(int) * h->k, h->stream));
+  CKS(h->alloc(&h->opmax, 2));
+  CKS(h->alloc(&h->tmp2k, 2 * (size_t)h->k));
+  CKS(h->alloc(&h->bdot_sh, 2 * (size_t)h->k));
+  if (h->prec == BCG_FP32_REFINE) CKS(h->alloc(&h->msig, h->k));
   if (small_needs_gws(h->p)) CKS(h->alloc(&h->gws, (size_t)h->nblk * small_ws_doubles(h->p)));
   if (h->prec == BCG_FP64 && !h->global) {
     CKS(h->alloc(&h->dr_C, pp));
@@ -237,7 +248,7 @@ bcg_status setup_workspace(bcg_ctx *h) {
 }
 
 bcg_status make_fp32_copy(bcg_ctx *h) {
-  CK(launch_inv_diag(h->A64, h->n, h->dinv64, h->nsm, h->stream));
+  CK(launch_inv_diag(h->A64, h->n, h->dinv64, h->opmax, h->nsm, h->stream));
   if (h->dinv32) CK(launch_cast_to_float(h->dinv64, h->dinv32, h->n, h->nsm, h->stream));
   if (h->prec != BCG_FP32_REFINE) return BCG_OK;
   h->A32 = h->A64;
@@ -254,6 +265,19 @@ bcg_status make_fp32_copy(bcg_ctx *h) {
     else h->A32.faces = h->vals32;
   }
   return BCG_OK;
+}
+
+// Gram shifts of a solve in precision T: the FP64 form keeps them with its column norms; FP32 operands are
+// accumulated unshifted.
+template <typename T>
+ShiftCtl shifts_of(const bcg_ctx *h) {
+  ShiftCtl sc;
+  if (sizeof(T) == 8) {
+    sc.sh = h->sh;
+    sc.opmax = h->opmax;
+    sc.precond = h->precond;
+  }
+  return sc;
 }
 
 template <typename T>
@@ -277,7 +301,9 @@ bcg_status set_tol2(bcg_ctx *h, double tol2) {
 template <typename T>
 bcg_status first_rho_rec(bcg_ctx *h, const T *P, const T *R, const StreamGrids &g) {
   if (!g.rho_k3) return BCG_OK;
-  CK(launch_bdot<T>(P, R, h->n, h->k, h->p, h->partR, h->precond ? g.pup_zs : g.pup, h->stream));
+  const int *sh = shifts_of<T>(h).sh;
+  CK(launch_bdot<T>(P, R, h->n, h->k, h->p, h->partR, h->precond ? g.pup_zs : g.pup, h->stream,
+                    sh_role(sh, h->k, SH_P), sh_role(sh, h->k, SH_R)));
   return BCG_OK;
 }
 
@@ -288,21 +314,23 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
   cudaStream_t s = h->stream;
 #define REC(i) do { if (ev) CK(cudaEventRecord(ev[i], s)); } while (0)
   const int gu = h->precond ? g.upd_zs : g.upd, gp = h->precond ? g.pup_zs : g.pup;
+  const ShiftCtl sc = shifts_of<T>(h);
   REC(0);
-  CK(launch_op_gram<T>(A, P, R, Q, h->n, h->k, h->p, h->global, h->active, h->partA, h->partR, h->st, g.op, s));
+  CK(launch_op_gram<T>(A, P, R, Q, h->n, h->k, h->p, h->global, h->active, h->partA, h->partR, h->st, g.op, s,
+                       sc.sh));
   REC(1); REC(2);
   CK(launch_solve_lambda(h->partA, h->partR, g.op, g.rho_k3 ? gp : g.op, h->k, h->p, h->global, h->active, h->lam,
                          h->rho_rec, h->st, h->gws, g.alpha_circ, s));
   REC(3); REC(4);
   CK(launch_update_xr<T>(X, R, P, Q, h->n, h->k, h->p, h->global, h->lam, h->active, h->partRho, h->partN, h->st,
-                         gu, s, dinv_of<T>(h)));
+                         gu, s, dinv_of<T>(h), sc.sh));
   REC(5); REC(6);
   CK(launch_solve_beta(h->partRho, h->partN, gu, gu, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
                        h->active,
-                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, g.rho_circ, s));
+                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, g.rho_circ, s, sc));
   REC(7); REC(8);
   CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv_of<T>(h),
-                        h->partR));
+                        h->partR, sc.sh));
   REC(9);
 #undef REC
   return BCG_OK;
@@ -314,19 +342,22 @@ template <typename T>
 bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g) {
   cudaStream_t s = h->stream;
   const int ch = g.op;
+  const ShiftCtl sc = shifts_of<T>(h);
+  const int *shR = sh_role(sc.sh, h->k, SH_R), *shP = sh_role(sc.sh, h->k, SH_P), *shQ = sh_role(sc.sh, h->k, SH_Q);
   CK(launch_lp_bop<T>(A, P, Q, h->n, h->k, h->st, h->nsm, s));
-  CK(launch_lp_gram<T>(P, Q, h->n, h->k, h->p, h->global, h->active, h->partA, ch, h->st, s, nullptr));
-  CK(launch_lp_gram<T>(P, R, h->n, h->k, h->p, h->global, h->active, h->partR, ch, h->st, s, nullptr));
+  CK(launch_lp_gram<T>(P, Q, h->n, h->k, h->p, h->global, h->active, h->partA, ch, h->st, s, nullptr, shP, shQ));
+  CK(launch_lp_gram<T>(P, R, h->n, h->k, h->p, h->global, h->active, h->partR, ch, h->st, s, nullptr, shP, shR));
   CK(launch_solve_lambda(h->partA, h->partR, ch, ch, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
                          h->gws, 0, s));
   CK(launch_lp_baxpy<T>(X, X, P, h->lam, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 0, s, nullptr));
   CK(launch_lp_baxpy<T>(R, R, Q, h->lam, h->n, h->k, h->p, h->global, -1.0, h->active, h->st, 0, s, nullptr));
   // rho = <<Z, R>> with Z = M^{-1} R formed on the fly
-  CK(launch_lp_gram<T>(R, R, h->n, h->k, h->p, h->global, h->active, h->partRho, ch, h->st, s, dinv_of<T>(h)));
-  CK(launch_lp_colnorm<T>(R, h->n, h->k, h->partN, g.res, h->st, s));   // a full-GPU grid, like K0's
+  CK(launch_lp_gram<T>(R, R, h->n, h->k, h->p, h->global, h->active, h->partRho, ch, h->st, s, dinv_of<T>(h), shP,
+                       shR));
+  CK(launch_lp_colnorm<T>(R, h->n, h->k, h->partN, g.res, h->st, s, shR));   // a full-GPU grid, like K0's
   CK(launch_solve_beta(h->partRho, h->partN, ch, g.res, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
                        h->active,
-                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s));
+                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s, sc));
   CK(launch_lp_baxpy<T>(Q, R, P, h->beta, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 1, s, dinv_of<T>(h)));
   return BCG_OK;
 }
@@ -472,7 +503,7 @@ bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int ma
   CK(launch_residual<double>(h->A64, X, B, h->R, h->P, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, s,
                              dinv_of<double>(h)));
   CK(launch_init_status(h->partN, h->g64.res, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters,
-                        h->lam, h->beta, h->st, s));
+                        h->lam, h->beta, h->st, s, shifts_of<double>(h)));
   CKS(first_rho_rec<double>(h, h->P, h->R, h->g64));
   CKS(run_iterations<double>(h, h->A64, X, h->R, h->P, h->Q, h->g64, tol2, maxit, nullptr, nullptr));
   const DevStatus fin = *h->h_st;
@@ -517,9 +548,13 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
   const int k = h->k, p = h->p;
   const bool lp = p > kMaxP;
   const int np_g = lp ? h->g64.op : dr_grid_for(n, k, p, h->nsm, h->nparts);
-  auto gram = [&](const double *Xv, const double *Yv, double *part) -> cudaError_t {
-    return lp ? launch_lp_gram<double>(Xv, Yv, n, k, p, 0, h->active, part, np_g, h->st, s, nullptr)
-              : launch_dr_gram(Xv, Yv, n, k, p, h->active, part, np_g, h->st, s);
+  // Gram shifts: R^0 is taken at the scale of its column norms (gamma^0 = <<R^0, R^0>>); afterwards every
+  // operand is of unit scale (Q orthonormal, S built from it) except W = A S (role Q: the operator's offset)
+  const ShiftCtl sc = shifts_of<double>(h);
+  const int *shR = sh_role(sc.sh, k, SH_R), *shP = sh_role(sc.sh, k, SH_P), *shQ = sh_role(sc.sh, k, SH_Q);
+  auto gram = [&](const double *Xv, const double *Yv, double *part, const int *shx, const int *shy) -> cudaError_t {
+    return lp ? launch_lp_gram<double>(Xv, Yv, n, k, p, 0, h->active, part, np_g, h->st, s, nullptr, shx, shy)
+              : launch_dr_gram(Xv, Yv, n, k, p, h->active, part, np_g, h->st, s, shx, shy);
   };
   // OUT = Y C (no base term)
   auto bmul = [&](double *OUT, const double *Yv, const double *Cm) -> cudaError_t {
@@ -536,9 +571,10 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
   // R^0 = B - A X^0 (in W's buffer) = Q^0 C^0, S^1 = Q^0
   CK(launch_residual<double>(h->A64, X, B, W, nullptr, nullptr, nullptr, n, k, h->partN, h->g64.res, s, nullptr));
   CK(launch_init_status(h->partN, h->g64.res, k, p, 0, h->r0n2, h->rn2, h->active, h->block_iters, h->lam,
-                        h->beta, h->st, s));
-  CK(gram(W, W, h->partA));
+                        h->beta, h->st, s, sc));
+  CK(gram(W, W, h->partA, shR, shR));
   CK(launch_dr_start(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_psiinv, h->st, h->gws, s));
+  CK(launch_fill_shifts(nullptr, k, sc, s));
   CK(bmul(Qb, W, h->dr_psiinv));
   CK(cudaMemcpyAsync(S, Qb, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
   CKS(set_tol2(h, tol * tol));
@@ -551,7 +587,7 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
         // W = A S, alpha (K1; where K1 also forms a recomputed rho, it reads Q and the result is unused) |
         // xi, lambda | X += S lambda, T = Q - W xi, gamma | stop test, psi | Q = T psi^{-1}, S
         CK(launch_op_gram<double>(h->A64, S, Qb, W, n, k, p, 0, h->active, h->partA, h->partR, h->st, h->g64.op,
-                                  s));
+                                  s, sc.sh));
         CK(launch_dr_xi(h->partA, h->g64.op, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws,
                         h->g64.alpha_circ, s));
         CK(launch_dr_update_xt(X, Qb, S, W, n, k, p, h->lam, h->dr_xi, h->active, h->partRho, np_g, h->st, s));
@@ -561,11 +597,11 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
         continue;
       }
       CK(launch_lp_bop<double>(h->A64, S, W, n, k, h->st, h->nsm, s));   // W = A S
-      CK(gram(S, W, h->partA));                                          // alpha = <<S, W>>
+      CK(gram(S, W, h->partA, shP, shQ));                                // alpha = <<S, W>>
       CK(launch_dr_xi(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws, 0, s));
       CK(baxpy(X, X, S, h->lam, 1.0, 0));                                // X += S lambda, lambda = xi C
       CK(baxpy(Qb, Qb, W, h->dr_xi, -1.0, 0));                           // T = Q - W xi
-      CK(gram(Qb, Qb, h->partRho));                                      // gamma = <<T, T>>
+      CK(gram(Qb, Qb, h->partRho, shR, shR));                            // gamma = <<T, T>>
       CK(launch_dr_psi(h->partRho, np_g, k, p, h->tol2_dev, h->r0n2, h->rn2, h->active, h->block_iters, h->dr_C,
                        h->dr_psiinv, h->dr_phi, h->st, h->gws, s));
       CK(bmul(W, Qb, h->dr_psiinv));                                     // Q^+ = T psi^{-1}
@@ -619,15 +655,19 @@ bcg_status solve_replace(bcg_ctx *h, const double *B, double *X, double tol, int
   cudaStream_t s = h->stream;
   const int64_t nk = h->n * h->k;
   const double tol2 = tol * tol;
-  // (re)start of the Krylov process from the FP64 residual: R32 = fl(R), P32 = fl(M^{-1} R), D = 0. The per-column
-  // stopping test stays relative to the initial residual (r0n2 = the first start's norms).
+  // (re)start of the Krylov process from the FP64 residual R: R32 = fl(R 2^-sigma), P32 = fl(M^{-1} R 2^-sigma),
+  // D = 0, with sigma fixed per block until the next restart (launch_mixed_scale). The per-column stopping test
+  // stays relative to the initial residual (r0n2 = the first start's norms, in the process's scale).
   auto start = [&](bool first) -> bcg_status {
-    CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, h->R32, h->P32, h->n, h->k, h->partN, h->g64.res, s,
-                               dinv_of<double>(h)));
-    if (first) CK(launch_reduce_norms(h->partN, h->g64.res, h->k, h->outer0, s));
-    CK(launch_init_status(h->partN, h->g64.res, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters,
-                          h->lam, h->beta, h->st, s));
-    if (!first) CK(cudaMemcpyAsync(h->r0n2, h->outer0, sizeof(double) * h->k, cudaMemcpyDeviceToDevice, s));
+    CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, s,
+                               nullptr));
+    CK(launch_reduce_norms(h->partN, h->g64.res, h->k, h->rtn2, s));
+    if (first) CK(cudaMemcpyAsync(h->outer0, h->rtn2, sizeof(double) * h->k, cudaMemcpyDeviceToDevice, s));
+    CK(launch_mixed_scale(h->rtn2, h->outer0, h->k, h->p, h->global, h->msig, h->partN, h->tmp2k, s));
+    CK(launch_cast_scaled(h->Q, dinv_of<double>(h), h->msig, h->n, h->k, h->R32, h->P32, h->nsm, s));
+    CK(launch_init_status(h->partN, 1, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters, h->lam,
+                          h->beta, h->st, s, shifts_of<float>(h)));
+    CK(cudaMemcpyAsync(h->r0n2, h->tmp2k, sizeof(double) * h->k, cudaMemcpyDeviceToDevice, s));
     CK(cudaMemsetAsync(h->D32, 0, sizeof(float) * nk, s));
     CKS(first_rho_rec<float>(h, h->P32, h->R32, h->g32));
     return BCG_OK;
@@ -664,11 +704,12 @@ bcg_status solve_replace(bcg_ctx *h, const double *B, double *X, double tol, int
     if (!(broke || done || forced || rec2 < kReplaceDrop * kReplaceDrop * last2 || iters >= maxit)) continue;
     longest = std::max(longest, iters - cycle_start);
     cycle_start = iters;
-    // residual replacement: X += D, D = 0, R = B - A X in FP64 (R32 = fl(R)); P and the Krylov process stay
-    CK(launch_add_correction(X, h->D32, nk, h->nsm, s));
+    // residual replacement: X += D 2^sigma, D = 0, R = B - A X in FP64 (R32 = fl(R 2^-sigma)); P and the Krylov
+    // process stay
+    CK(launch_add_correction(X, h->D32, nk, h->k, h->msig, h->nsm, s));
     CK(cudaMemsetAsync(h->D32, 0, sizeof(float) * nk, s));
     CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, h->R32, nullptr, h->n, h->k, h->partN, h->g64.res, s,
-                               nullptr));
+                               nullptr, h->msig));
     CK(launch_reduce_norms(h->partN, h->g64.res, h->k, h->rtn2, s));
     ++replaced;
     CKS(fetch_vec(h, h->outer0, 0));
@@ -698,7 +739,7 @@ bcg_status solve_replace(bcg_ctx *h, const double *B, double *X, double tol, int
     } else if (done) {
       // every block stopped on its recursive residual but some true residuals are still above the tolerance:
       // reopen those blocks with their directions
-      CK(launch_reactivate(h->rtn2, h->r0n2, tol2, h->k, h->p, h->global, h->active, h->st, s));
+      CK(launch_reactivate(h->rtn2, h->outer0, tol2, h->k, h->p, h->global, h->active, h->st, s));
     }
   }
   CKS(read_status(h));
@@ -728,9 +769,10 @@ bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int 
   double last_max = INFINITY;
   int stalls = 0;
   for (;;) {
-    // outer residual in FP64, rounded to FP32 as the inner right-hand side (R32 = P32 = fl(R))
-    CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, h->R32, h->P32, h->n, h->k, h->partN, h->g64.res, s,
-                               dinv_of<double>(h)));
+    // outer residual R in FP64; the inner right-hand side is R32 = fl(R 2^-sigma), P32 = fl(M^{-1} R 2^-sigma)
+    // with a fresh scale per block (launch_mixed_scale)
+    CK(launch_residual<double>(h->A64, X, B, h->Q, nullptr, nullptr, nullptr, h->n, h->k, h->partN, h->g64.res, s,
+                               nullptr));
     CK(launch_reduce_norms(h->partN, h->g64.res, h->k, h->rtn2, s));
     if (outer == 0) CK(cudaMemcpyAsync(h->outer0, h->rtn2, sizeof(double) * h->k, cudaMemcpyDeviceToDevice, s));
     CKS(fetch_vec(h, h->outer0, 0));
@@ -751,8 +793,10 @@ bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int 
     const double itol = std::min(0.5, std::max(h->inner_tol, 0.5 * tol / m));
     const double itol2 = itol * itol;
     CK(cudaMemsetAsync(h->D32, 0, sizeof(float) * nk, s));
-    CK(launch_init_status(h->partN, h->g64.res, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters,
-                          h->lam, h->beta, h->st, s));
+    CK(launch_mixed_scale(h->rtn2, nullptr, h->k, h->p, h->global, h->msig, h->partN, nullptr, s));
+    CK(launch_cast_scaled(h->Q, dinv_of<double>(h), h->msig, h->n, h->k, h->R32, h->P32, h->nsm, s));
+    CK(launch_init_status(h->partN, 1, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters, h->lam,
+                          h->beta, h->st, s, shifts_of<float>(h)));
     CKS(first_rho_rec<float>(h, h->P32, h->R32, h->g32));
     CKS(run_iterations<float>(h, h->A32, h->D32, h->R32, h->P32, h->Q32, h->g32, itol2, maxit, &h->graph32,
                               &h->graph32_batch));
@@ -765,7 +809,7 @@ bcg_status solve_refine(bcg_ctx *h, const double *B, double *X, double tol, int 
       break;
     }
     // a later inner breakdown or maxit still leaves a useful correction: apply it and refine on
-    CK(launch_add_correction(X, h->D32, nk, h->nsm, s));
+    CK(launch_add_correction(X, h->D32, nk, h->k, h->msig, h->nsm, s));
     ++outer;
   }
   CKS(fill_block_iters(h));
@@ -796,16 +840,18 @@ bcg_status rows_phase(bcg_ctx *h, int phase) {
   const bool lp = h->p > kMaxP;
   const int gu = h->precond ? g.upd_zs : g.upd, gp = h->precond ? g.pup_zs : g.pup;
   const double *dinv = dinv_of<double>(h);
+  const ShiftCtl sc = shifts_of<double>(h);
+  const int *shR = sh_role(sc.sh, h->k, SH_R), *shP = sh_role(sc.sh, h->k, SH_P), *shQ = sh_role(sc.sh, h->k, SH_Q);
   if (phase == 1) {
     if (lp) {
       CK(launch_lp_bop<double>(h->A64, h->P, h->Q, h->n, h->k, h->st, h->nsm, s));
       CK(launch_lp_gram<double>(h->P, h->Q, h->n, h->k, h->p, h->global, h->active, h->partA, g.op, h->st, s,
-                                nullptr));
+                                nullptr, shP, shQ));
       CK(launch_lp_gram<double>(h->P, h->R, h->n, h->k, h->p, h->global, h->active, h->partR, g.op, h->st, s,
-                                nullptr));
+                                nullptr, shP, shR));
     } else {
       CK(launch_op_gram<double>(h->A64, h->P, h->R, h->Q, h->n, h->k, h->p, h->global, h->active, h->partA,
-                                h->partR, h->st, g.op, s));
+                                h->partR, h->st, g.op, s, sc.sh));
     }
     CK(launch_sum_partials(h->partA, g.op, E, h->sums1, h->nsm, s));
     // the recomputed rho: from this K1, or (rho_k3) already summed after the previous K3 / the start
@@ -819,27 +865,27 @@ bcg_status rows_phase(bcg_ctx *h, int phase) {
       CK(launch_lp_baxpy<double>(h->R, h->R, h->Q, h->lam, h->n, h->k, h->p, h->global, -1.0, h->active, h->st, 0, s,
                                  nullptr));
       CK(launch_lp_gram<double>(h->R, h->R, h->n, h->k, h->p, h->global, h->active, h->partRho, g.op, h->st, s,
-                                dinv));
-      CK(launch_lp_colnorm<double>(h->R, h->n, h->k, h->partN, g.res, h->st, s));
+                                dinv, shP, shR));
+      CK(launch_lp_colnorm<double>(h->R, h->n, h->k, h->partN, g.res, h->st, s, shR));
       CK(launch_sum_partials(h->partRho, g.op, E, h->sums2, h->nsm, s));
       CK(launch_sum_partials(h->partN, g.res, h->k, h->sums2 + E, h->nsm, s));
     } else {
       CK(launch_update_xr<double>(h->X_rows, h->R, h->P, h->Q, h->n, h->k, h->p, h->global, h->lam, h->active,
-                                  h->partRho, h->partN, h->st, gu, s, dinv));
+                                  h->partRho, h->partN, h->st, gu, s, dinv, sc.sh));
       CK(launch_sum_partials(h->partRho, gu, E, h->sums2, h->nsm, s));
       CK(launch_sum_partials(h->partN, gu, h->k, h->sums2 + E, h->nsm, s));
     }
   } else {
     CK(launch_solve_beta(h->sums2, h->sums2 + E, 1, 1, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
                          h->active,
-                         h->block_iters, h->rho_rec, h->beta, h->st, h->gws, lp ? 0 : g.rho_circ, s));
+                         h->block_iters, h->rho_rec, h->beta, h->st, h->gws, lp ? 0 : g.rho_circ, s, sc));
     if (lp) {
       CK(launch_lp_baxpy<double>(h->Q, h->R, h->P, h->beta, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 1, s,
                                  dinv));
       std::swap(h->P, h->Q);   // the new P was written into Q's buffer
     } else {
       CK(launch_update_p<double>(h->P, h->R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv,
-                                 h->partR));
+                                 h->partR, sc.sh));
       if (g.rho_k3) CK(launch_sum_partials(h->partR, gp, E, h->sums1 + E, h->nsm, s));
     }
   }
@@ -1078,13 +1124,17 @@ bcg_status bcg_bdot(bcg_handle h, const double *X, const double *Y, double *gamm
   if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
   if (!is_device_ptr(X) || !is_device_ptr(Y) || !is_device_ptr(gamma))
     return fail(BCG_ERR_INVALID_ARG, "X, Y and gamma must be device pointers");
+  // Gram shifts from the column maxima of X and of Y (a pass over each operand)
+  int *shX = h->bdot_sh, *shY = h->bdot_sh + h->k;
+  CK(launch_col_shifts(X, h->n, h->k, h->tmp2k, shX, h->nsm, h->stream));
+  CK(launch_col_shifts(Y, h->n, h->k, h->tmp2k + h->k, shY, h->nsm, h->stream));
   if (h->p > kMaxP) {
     CK(launch_lp_gram<double>(X, Y, h->n, h->k, h->p, h->global, nullptr, h->partA, h->g64.op, nullptr, h->stream,
-                              nullptr));
+                              nullptr, shX, shY));
     CK(launch_finish_gram(h->partA, h->g64.op, h->k, h->p, h->global, gamma, h->gws, h->stream));
   } else {
     const int grid = std::min(h->nparts, bdot_grid<double>(h->n, h->k, h->p, h->nsm));
-    CK(launch_bdot<double>(X, Y, h->n, h->k, h->p, h->partA, grid, h->stream));
+    CK(launch_bdot<double>(X, Y, h->n, h->k, h->p, h->partA, grid, h->stream, shX, shY));
     CK(launch_finish_gram(h->partA, grid, h->k, h->p, h->global, gamma, h->gws, h->stream));
   }
   CK(cudaStreamSynchronize(h->stream));
@@ -1097,11 +1147,11 @@ bcg_status bcg_bdot_f32(bcg_handle h, const float *X, const float *Y, double *ga
     return fail(BCG_ERR_INVALID_ARG, "X, Y and gamma must be device pointers");
   if (h->p > kMaxP) {
     CK(launch_lp_gram<float>(X, Y, h->n, h->k, h->p, h->global, nullptr, h->partA, h->g64.op, nullptr, h->stream,
-                             nullptr));
+                             nullptr, nullptr, nullptr));
     CK(launch_finish_gram(h->partA, h->g64.op, h->k, h->p, h->global, gamma, h->gws, h->stream));
   } else {
     const int grid = std::min(h->nparts, bdot_grid<float>(h->n, h->k, h->p, h->nsm));
-    CK(launch_bdot<float>(X, Y, h->n, h->k, h->p, h->partA, grid, h->stream));
+    CK(launch_bdot<float>(X, Y, h->n, h->k, h->p, h->partA, grid, h->stream, nullptr, nullptr));
     CK(launch_finish_gram(h->partA, grid, h->k, h->p, h->global, gamma, h->gws, h->stream));
   }
   CK(cudaStreamSynchronize(h->stream));
@@ -1181,6 +1231,9 @@ bcg_status bcg_rows_start(bcg_handle h, const double *B, double *X, double tol) 
                              dinv_of<double>(h)));
   CK(launch_sum_partials(h->partN, h->g64.res, h->k, h->sums2 + E, h->nsm, h->stream));
   if (h->g64.rho_k3) {   // the first recomputed rho travels in sums1 with the first alpha
+    // its Gram shifts from this rank's own column norms (the partial sums are unshifted, so ranks need not agree;
+    // bcg_rows_start_status rewrites the shifts from the summed norms)
+    CK(launch_fill_shifts(h->sums2 + E, h->k, shifts_of<double>(h), h->stream));
     CKS(first_rho_rec<double>(h, h->P, h->R, h->g64));
     CK(launch_sum_partials(h->partR, h->precond ? h->g64.pup_zs : h->g64.pup, E, h->sums1 + E, h->nsm, h->stream));
   }
@@ -1191,7 +1244,7 @@ bcg_status bcg_rows_start_status(bcg_handle h) {
   CKS(rows_handle(h));
   const int64_t E = (int64_t)h->k * h->p;
   CK(launch_init_status(h->sums2 + E, 1, h->k, h->p, h->global, h->r0n2, h->rn2, h->active, h->block_iters, h->lam,
-                        h->beta, h->st, h->stream));
+                        h->beta, h->st, h->stream, shifts_of<double>(h)));
   return BCG_OK;
 }
 

@@ -15,6 +15,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cstring>
 #include <cuda_runtime.h>
 
 namespace bcgk {
@@ -101,21 +102,92 @@ __device__ __forceinline__ void two_sum_acc(float &s, float &c, float p, float e
   c = __fadd_rn(c, __fadd_rn(err, e));
 }
 
-// Tiny, huge or non-finite values: plain conversions. Kept out of line so that the compiler cannot if-convert
-// this branch into every call (its FP64 instructions would then run for every element on the narrow pipe).
-static __device__ __noinline__ float2 split_f64_rare(double x) {
-  const float hi = (float)x;
-  return make_float2(hi, isfinite(x) ? (float)(x - (double)hi) : 0.0f);
+// ---- Exponent shifts of FP64 Gram operands ----------------------------------------------------------------
+// The float pairs cover FP32's exponent range only, while the block products of the method are defined on FP64
+// values (Section 2). So every FP64 operand column c is scaled by an exact power of two 2^-s_c before it is
+// split, and each flushed partial sum of entry (a, b) is scaled back by 2^(s_a + s_b) in FP64. Scaling by a power
+// of two commutes with rounding, so for values whose scaled products stay inside FP32's range the sums are
+// bitwise those of the unshifted arithmetic; the shift only moves the window.
+//
+// Shifts are chosen from FP64 column norms the solver already holds (the latest ||R_c||^2 of every column), so
+// that a scaled column has 2-norm about 2^kGramCenter. An operand of another scale than R adds a uniform offset
+// (M^{-1} R: the exponent of max|diag(A)^{-1}|; A P: that of A's largest absolute row sum besides). A shift array
+// holds one int per column (NULL: no shift). Without flushes in between, a scaled product loses accuracy below
+// about 2^-102 (error terms turn subnormal) and overflows at 2^121 (128 rows summed): with a column norm of 2^10
+// that leaves a factor of about 2^49 of shrinking and 2^50 of growth of a column between two norm updates.
+constexpr int kGramCenter = 10;
+constexpr int kGramShiftMax = 1000;
+
+__host__ __device__ __forceinline__ int clamp_shift(int s) {
+  return s < -kGramShiftMax ? -kGramShiftMax : (s > kGramShiftMax ? kGramShiftMax : s);
+}
+// floor(log2(sqrt(v))) - kGramCenter for a squared norm v (zero or subnormal v: the smallest normal exponent;
+// non-finite v: no shift)
+__host__ __device__ __forceinline__ int shift_from_norm2(double v) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+#else
+  unsigned long long u;
+  memcpy(&u, &v, sizeof u);
+#endif
+  int e = (int)((u >> 52) & 0x7FF);
+  if (e == 0x7FF) return 0;
+  if (e == 0) e = 1;
+  return ((e - 1023) >> 1) - kGramCenter;
+}
+// floor(log2 v) for a finite v > 0 (normal), else 0: the uniform offset taken from one of the operator maxima
+__host__ __device__ __forceinline__ int exponent_of(double v) {
+#ifdef __CUDA_ARCH__
+  const unsigned long long u = (unsigned long long)__double_as_longlong(v);
+#else
+  unsigned long long u;
+  memcpy(&u, &v, sizeof u);
+#endif
+  const int e = (int)((u >> 52) & 0x7FF);
+  return (e == 0 || e == 0x7FF || (u >> 63)) ? 0 : e - 1023;
 }
 
-// x = hi + lo with hi = x truncated to 24 significant bits and lo = the remaining 29 bits truncated to 24.
-// Both halves are assembled from the bit pattern with integer operations only (no FP64 or conversion
-// instruction: on GB300 those share the narrow FP64 pipe) whenever both are normal floats.
-__device__ __forceinline__ float2 split_f64(double x) {
+// Where a solve's shift array lives and how its three rows are offset (see the roles in bcg_launch.h).
+struct ShiftCtl {
+  int *sh = nullptr;                  // 3 k ints, rewritten with the column norms (NULL: no shifts)
+  const double *opmax = nullptr;      // [max row sum of |A|, max |diag(A)^{-1}|] (NULL: no offsets)
+  int precond = 0;                    // 1: directions are M^{-1} R (Jacobi), offset by the second maximum
+};
+// Shifts of column c (of k) from its squared norm n2.
+__device__ __forceinline__ void write_shifts(const ShiftCtl &sc, int k, int c, double n2) {
+  if (sc.sh == nullptr) return;
+  const int base = shift_from_norm2(n2);
+  const int dA = sc.opmax ? exponent_of(sc.opmax[0]) : 0;
+  const int dP = (sc.opmax && sc.precond) ? exponent_of(sc.opmax[1]) : 0;
+  sc.sh[c] = clamp_shift(base);
+  sc.sh[k + c] = clamp_shift(base + dP);
+  sc.sh[2 * k + c] = clamp_shift(base + dP + dA);
+}
+
+// 2^e for |e| <= kGramShiftMax
+__device__ __forceinline__ double pow2d(int e) { return __longlong_as_double((long long)(e + 1023) << 52); }
+__device__ __forceinline__ int shift_at(const int *__restrict__ sh, int c) { return sh ? __ldg(sh + c) : 0; }
+
+// Tiny, huge or non-finite values (after the shift): plain conversions of x 2^-sh. Kept out of line so that the
+// compiler cannot if-convert this branch into every call (its FP64 instructions would then run for every
+// element on the narrow pipe).
+static __device__ __noinline__ float2 split_f64_rare(double x, int sh) {
+  if (!isfinite(x)) return make_float2((float)x, 0.0f);
+  const double xs = ldexp(x, -sh);
+  const float hi = (float)xs;
+  return make_float2(hi, isfinite(hi) ? (float)(xs - (double)hi) : 0.0f);
+}
+
+// x 2^-sh = hi + lo with hi = x truncated to 24 significant bits and lo = the remaining 29 bits truncated to
+// 24. Both halves are assembled from the bit pattern with integer operations only (no FP64 or conversion
+// instruction: on GB300 those share the narrow FP64 pipe) whenever x is a normal double and both halves are
+// normal floats.
+__device__ __forceinline__ float2 split_f64(double x, int sh) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const unsigned hi32 = (unsigned)(u >> 32);
-  const int e = (int)((hi32 >> 20) & 0x7FFu);
-  if (e >= 949 && e <= 1150) {
+  const int ef = (int)((hi32 >> 20) & 0x7FFu);
+  const int e = ef - sh;   // biased exponent of x 2^-sh
+  if ((unsigned)(ef - 1) < 0x7FEu && (unsigned)(e - 949) <= 201u) {
     const unsigned sign = hi32 & 0x80000000u;
     const float hi = __uint_as_float(sign | ((unsigned)(e - 896) << 23) | (unsigned)((u >> 29) & 0x7FFFFFu));
     // low part: rem * 2^(e - 1075) with rem < 2^29; normalise rem by its leading one
@@ -126,7 +198,7 @@ __device__ __forceinline__ float2 split_f64(double x) {
     return make_float2(hi, rem ? __uint_as_float(lob) : 0.0f);
   }
   if ((u << 1) == 0ull) return make_float2(__uint_as_float(hi32 & 0x80000000u), 0.0f);   // +-0
-  return split_f64_rare(x);
+  return split_f64_rare(x, sh);
 }
 
 template <typename T>
@@ -134,7 +206,9 @@ struct Gram;
 template <>
 struct Gram<float> {
   using B = float;   // broadcast / operand representation
+  static constexpr bool kShifted = false;   // FP32 operands are accumulated as they are
   __device__ static B conv(float v) { return v; }
+  __device__ static B conv(float v, int) { return v; }
   __device__ static B zero() { return 0.0f; }
   __device__ static void add(float &s, float &c, B x, B y) {
     const float p = __fmul_rn(x, y);
@@ -144,7 +218,9 @@ struct Gram<float> {
 template <>
 struct Gram<double> {
   using B = float2;
-  __device__ static B conv(double v) { return split_f64(v); }
+  static constexpr bool kShifted = true;
+  __device__ static B conv(double v) { return split_f64(v, 0); }
+  __device__ static B conv(double v, int sh) { return split_f64(v, sh); }
   __device__ static B zero() { return make_float2(0.0f, 0.0f); }
   __device__ static void add(float &s, float &c, B x, B y) {
     const float p = __fmul_rn(x.x, y.x);
@@ -195,7 +271,41 @@ struct GramAcc {
         c[a] = 0.0f;
       }
   }
+  // the same for shifted operands: entry a is scaled back by 2^(sx(a) + sy) (two exact multiplications)
+  template <class SX>
+  __device__ __forceinline__ void flush_shifted(double *slot, int p, SX sx, int sy) {
+    const double fy = pow2d(sy);
+#pragma unroll
+    for (int a = 0; a < PM; ++a)
+      if (a < p) {
+        const double fx = pow2d(sx(a));
+        slot[a] += ((double)s[a] * fx) * fy;
+        slot[a] += ((double)c[a] * fx) * fy;
+        s[a] = 0.0f;
+        c[a] = 0.0f;
+      }
+  }
 };
+
+// Flush helper for kernels templated on the precision: FP32 operands are not shifted.
+template <typename T, int PM, class SX>
+__device__ __forceinline__ void gram_flush(GramAcc<PM> &acc, double *slot, int p, SX sx, int sy) {
+  if constexpr (Gram<T>::kShifted) acc.flush_shifted(slot, p, sx, sy);
+  else acc.flush(slot, p);
+}
+// A single float pair (a column norm) flushed with shift 2 sy.
+template <typename T>
+__device__ __forceinline__ void norm_flush(double &slot, float &s, float &c, int sy) {
+  if constexpr (Gram<T>::kShifted) {
+    const double f = pow2d(sy);
+    slot += ((double)s * f) * f;
+    slot += ((double)c * f) * f;
+  } else {
+    slot += (double)s;
+    slot += (double)c;
+  }
+  s = c = 0.0f;
+}
 
 // Sum the FP64 slots of all row slots of the CTA in fixed order: out[e] = sum_g red[g*E + e].
 __device__ __forceinline__ void cta_sum_slots(const double *red, int E, int rpp, double *__restrict__ out) {
@@ -350,13 +460,15 @@ template <typename T, int OPK, int PM, bool RR>
 __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
                                                  T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                  const int *__restrict__ active, double *__restrict__ partA,
-                                                 double *__restrict__ partR, const DevStatus *__restrict__ st) {
+                                                 double *__restrict__ partR, const DevStatus *__restrict__ st,
+                                                 const int *__restrict__ shP, const int *__restrict__ shQ,
+                                                 const int *__restrict__ shR) {
   using G = Gram<T>;
   using BT = typename G::B;
   constexpr int RPT = rpt_op<T>();
   if (st != nullptr && st->flags != 0) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  BT *sP = reinterpret_cast<BT *>(smem);   // [RPT][kNT]
+  BT *sPt = reinterpret_cast<BT *>(smem);   // [RPT][kNT]
   double *redA = reinterpret_cast<double *>(smem + (size_t)RPT * kNT * sizeof(double));
   double *redR = redA + kNT * p;
   const int rpp = kNT / k;
@@ -365,6 +477,8 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
   const bool slot = g < rpp;
   const int j = c / p;
   const bool act = slot && block_active(active, global, j);
+  const int sP = shift_at(shP, c), sQ = shift_at(shQ, c), sR = shift_at(shR, c);
+  auto sxP = [&](int a) { return shift_at(shP, j * p + a); };
   double *slotA = redA + ((int64_t)g * k + c) * p, *slotR = redR + ((int64_t)g * k + c) * p;
   if (slot)
     for (int a = 0; a < p; ++a) { slotA[a] = 0.0; if (RR) slotR[a] = 0.0; }
@@ -393,16 +507,16 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
     for (int u = 0; u < RPT; ++u) {
       const int64_t r = row0 + u * rpp + g;
       if (act && r < n) Q[r * k + c] = qv[u];
-      qb[u] = G::conv(qv[u]);
-      rb[u] = G::conv(rv[u]);
-      if (slot) sP[u * kNT + g * k + c] = G::conv(pv[u]);
+      qb[u] = G::conv(qv[u], sQ);
+      rb[u] = G::conv(rv[u], sR);
+      if (slot) sPt[u * kNT + g * k + c] = G::conv(pv[u], sP);
     }
     row_sync(wl);
     if (act) {
 #pragma unroll
       for (int u = 0; u < RPT; ++u) {
         BT prow[PM];
-        load_row<BT, PM>(sP + u * kNT + g * k + j * p, prow, p);
+        load_row<BT, PM>(sPt + u * kNT + g * k + j * p, prow, p);
 #pragma unroll
         for (int a = 0; a < PM; ++a) {
           if (a < p) {
@@ -415,10 +529,10 @@ __global__ void __launch_bounds__(kNT) k_op_gram(OpDesc A, const T *__restrict__
     row_sync(wl);
     if (++pass == kFlushPasses / RPT) {
       pass = 0;
-      if (slot) { accA.flush(slotA, p); if (RR) accR.flush(slotR, p); }
+      if (slot) { gram_flush<T>(accA, slotA, p, sxP, sQ); if (RR) gram_flush<T>(accR, slotR, p, sxP, sR); }
     }
   }
-  if (slot) { accA.flush(slotA, p); if (RR) accR.flush(slotR, p); }
+  if (slot) { gram_flush<T>(accA, slotA, p, sxP, sQ); if (RR) gram_flush<T>(accR, slotR, p, sxP, sR); }
   const int E = k * p;
   cta_sum_slots(redA, E, rpp, partA + (int64_t)blockIdx.x * E);
   if constexpr (RR) cta_sum_slots(redR, E, rpp, partR + (int64_t)blockIdx.x * E);
@@ -437,7 +551,8 @@ __global__ void __launch_bounds__(kNT, upd_min_ctas<PM>()) k_update_xr(T *__rest
                                                    const T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                    const double *__restrict__ lam, const int *__restrict__ active,
                                                    double *__restrict__ partRho, double *__restrict__ partN,
-                                                   const DevStatus *__restrict__ st, const T *__restrict__ dinv) {
+                                                   const DevStatus *__restrict__ st, const T *__restrict__ dinv,
+                                                   const int *__restrict__ shZ, const int *__restrict__ shR) {
   using G = Gram<T>;
   using BT = typename G::B;
   constexpr int RPT = rpt_stream<T>();
@@ -458,6 +573,8 @@ __global__ void __launch_bounds__(kNT, upd_min_ctas<PM>()) k_update_xr(T *__rest
   const bool slot = g < rpp;
   const int j = c / p, b = c - j * p;
   const bool act = slot && block_active(active, global, j);
+  const int sZ = shift_at(shZ, c), sR = shift_at(shR, c);
+  auto sxZ = [&](int a) { return shift_at(shZ, j * p + a); };
   double *slotRho = red + ((int64_t)g * k + c) * p;
   double *slotN = nred + (int64_t)g * k + c;
   if (slot) {
@@ -518,8 +635,8 @@ __global__ void __launch_bounds__(kNT, upd_min_ctas<PM>()) k_update_xr(T *__rest
     for (int u = 0; u < RPT; ++u) {
       const int64_t r = row0 + u * rpp + g;
       const bool live = act && r < n;
-      rb[u] = live ? G::conv(rv[u]) : G::zero();
-      if (slot) sRb[u * kNT + g * k + c] = live ? (ZS ? G::conv(rv[u] * dinv[r]) : rb[u]) : G::zero();
+      rb[u] = live ? G::conv(rv[u], sR) : G::zero();
+      if (slot) sRb[u * kNT + g * k + c] = live ? (ZS ? G::conv(rv[u] * dinv[r], sZ) : G::conv(rv[u], sZ)) : G::zero();
     }
     row_sync(wl);
     if (act) {
@@ -537,17 +654,14 @@ __global__ void __launch_bounds__(kNT, upd_min_ctas<PM>()) k_update_xr(T *__rest
     if (++pass == kFlushPasses / RPT) {
       pass = 0;
       if (slot) {
-        acc.flush(slotRho, p);
-        *slotN += (double)ns;
-        *slotN += (double)nc;
-        ns = nc = 0.0f;
+        gram_flush<T>(acc, slotRho, p, sxZ, sR);
+        norm_flush<T>(*slotN, ns, nc, sR);
       }
     }
   }
   if (slot) {
-    acc.flush(slotRho, p);
-    *slotN += (double)ns;
-    *slotN += (double)nc;
+    gram_flush<T>(acc, slotRho, p, sxZ, sR);
+    norm_flush<T>(*slotN, ns, nc, sR);
   }
   const int E = k * p;
   cta_sum_slots(red, E, rpp, partRho + (int64_t)blockIdx.x * E);
@@ -616,13 +730,15 @@ __global__ void __launch_bounds__(kNT) k_update_p(T *__restrict__ P, const T *__
 
 // ---------------------------------------------------------------------------------------------------
 // K0: R = B - A X (and optionally P = R), per-column ||R_c||^2 partials. T is the precision of X, B, R;
-// R32/P32 (optional) receive a float copy of R and of P (the mixed-precision inner right-hand side).
-// dinv (optional): P = M^{-1} R with the Jacobi preconditioner M = diag(A).
+// R32/P32 (optional) receive a float copy of R and of P (the mixed-precision inner right-hand side), scaled by
+// 2^-sig[c] when sig is given. dinv (optional): P = M^{-1} R with the Jacobi preconditioner M = diag(A).
 template <typename T, int OPK>
 __global__ void __launch_bounds__(kNT) k_residual(OpDesc A, const T *__restrict__ X, const T *__restrict__ B,
                                                   T *__restrict__ R, T *__restrict__ P, float *__restrict__ R32,
                                                   float *__restrict__ P32, int64_t n, int k,
-                                                  double *__restrict__ partN, const T *__restrict__ dinv) {
+                                                  double *__restrict__ partN, const T *__restrict__ dinv,
+                                                  const int *__restrict__ sig) {
+  const double fs = sig != nullptr ? pow2d(-sig[threadIdx.x % k]) : 1.0;   // this thread's column is t mod k
   extern __shared__ __align__(16) unsigned char smem[];
   double *red = reinterpret_cast<double *>(smem);
   const int rpp = kNT / k;
@@ -638,8 +754,8 @@ __global__ void __launch_bounds__(kNT) k_residual(OpDesc A, const T *__restrict_
       const T zv = dinv ? rv * dinv[r] : rv;   // P^1 = M^{-1} R^0
       if (R) R[o] = rv;
       if (P) P[o] = zv;
-      if (R32) { R32[o] = (float)rv; }
-      if (P32) { P32[o] = (float)zv; }
+      if (R32) { R32[o] = (float)((double)rv * fs); }
+      if (P32) { P32[o] = (float)((double)zv * fs); }
       const double rd = (double)rv;
       accN = fma(rd, rd, accN);
     }
@@ -651,7 +767,8 @@ __global__ void __launch_bounds__(kNT) k_residual(OpDesc A, const T *__restrict_
 // BDOT alone: per-CTA partials of gamma = <<X, Y>>_S (entry (a, b) of block j = sum_rows X[jp+a] Y[jp+b]).
 template <typename T, int PM>
 __global__ void __launch_bounds__(kNT) k_bdot(const T *__restrict__ X, const T *__restrict__ Y, int64_t n, int k,
-                                              int p, double *__restrict__ part) {
+                                              int p, double *__restrict__ part, const int *__restrict__ shX,
+                                              const int *__restrict__ shY) {
   using G = Gram<T>;
   using BT = typename G::B;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -662,6 +779,8 @@ __global__ void __launch_bounds__(kNT) k_bdot(const T *__restrict__ X, const T *
   const int g = threadIdx.x / k, c = threadIdx.x - g * k;
   const bool slot = g < rpp;
   const int j = c / p;
+  const int cshX = shift_at(shX, c), cshY = shift_at(shY, c);
+  auto sxX = [&](int a) { return shift_at(shX, j * p + a); };
   double *sl = red + ((int64_t)g * k + c) * p;
   if (slot)
     for (int a = 0; a < p; ++a) sl[a] = 0.0;
@@ -672,7 +791,7 @@ __global__ void __launch_bounds__(kNT) k_bdot(const T *__restrict__ X, const T *
   for (int64_t row0 = (int64_t)blockIdx.x * rpp; row0 < n; row0 += stride) {
     const int64_t r = row0 + g;
     BT xb = G::zero(), yb = G::zero();
-    if (slot && r < n) { xb = G::conv(X[r * k + c]); yb = G::conv(Y[r * k + c]); }
+    if (slot && r < n) { xb = G::conv(X[r * k + c], cshX); yb = G::conv(Y[r * k + c], cshY); }
     if (slot) sX[g * k + c] = xb;
     row_sync(wl);
     if (slot) {
@@ -685,31 +804,41 @@ __global__ void __launch_bounds__(kNT) k_bdot(const T *__restrict__ X, const T *
     row_sync(wl);
     if (++pass == kFlushPasses) {
       pass = 0;
-      if (slot) acc.flush(sl, p);
+      if (slot) gram_flush<T>(acc, sl, p, sxX, cshY);
     }
   }
-  if (slot) acc.flush(sl, p);
+  if (slot) gram_flush<T>(acc, sl, p, sxX, cshY);
   cta_sum_slots(red, k * p, rpp, part + (int64_t)blockIdx.x * k * p);
 }
 
-// Inverse diagonal of the operator (Jacobi preconditioner M = diag(A)): one value per row.
+// Inverse diagonal of the operator (Jacobi preconditioner M = diag(A)): one value per row. Also the two maxima
+// the exponent shifts of the Gram operands are offset by (as bit patterns of non-negative doubles, which order
+// like the integers; the caller zeroes them first): opmax[0] = max over rows of sum_j |A_rj| (a bound of ||A||_2
+// for symmetric A), opmax[1] = max |1 / A_rr|.
 template <typename T, int OPK>
-__global__ void k_inv_diag(OpDesc A, int64_t n, T *__restrict__ dinv) {
+__global__ void k_inv_diag(OpDesc A, int64_t n, T *__restrict__ dinv, unsigned long long *__restrict__ opmax) {
+  double mrow = 0.0, mdinv = 0.0;
   for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    double d = 0.0;
+    double d = 0.0, rabs = 0.0;
     if constexpr (OPK == OP_CSR) {
       const double *v = static_cast<const double *>(A.vals);
-      for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e)
+      for (int64_t e = A.rowptr[r]; e < A.rowptr[r + 1]; ++e) {
         if (A.colind[e] == r) d += v[e];
+        rabs += fabs(v[e]);
+      }
     } else if constexpr (OPK == OP_SELL) {
       const double *v = static_cast<const double *>(A.vals);
       const int64_t base = A.rowptr[r / kSellC] + r % kSellC;
-      for (int j = 0; j < A.rowlen[r]; ++j)
+      for (int j = 0; j < A.rowlen[r]; ++j) {
         if (A.colind[base + (int64_t)j * kSellC] == r) d += v[base + (int64_t)j * kSellC];
+        rabs += fabs(v[base + (int64_t)j * kSellC]);
+      }
     } else if constexpr (OPK == OP_ST5) {
       d = 4.0 * A.scale;
+      rabs = 8.0 * fabs(A.scale);
     } else if constexpr (OPK == OP_ST7) {
       d = 6.0 * A.scale;
+      rabs = 12.0 * fabs(A.scale);
     } else {
       const int nx = A.nx, ny = A.ny, nz = A.nz;
       const int64_t pl = (int64_t)nx * ny;
@@ -721,8 +850,23 @@ __global__ void k_inv_diag(OpDesc A, int64_t n, T *__restrict__ dinv) {
       const int64_t by = ((int64_t)iz * (ny + 1) + iy) * nx + ix;
       const int64_t bz = ((int64_t)iz * ny + iy) * nx + ix;
       d = A.scale * (((fx[bx] + fx[bx + 1]) + (fy[by] + fy[by + nx])) + (fz[bz] + fz[bz + pl]));
+      rabs = 2.0 * fabs(d);
     }
     dinv[r] = (T)(1.0 / d);
+    mrow = fmax(mrow, rabs);
+    mdinv = fmax(mdinv, fabs(1.0 / d));
+  }
+  if (opmax == nullptr) return;
+  unsigned long long b0 = (unsigned long long)__double_as_longlong(mrow);
+  unsigned long long b1 = (unsigned long long)__double_as_longlong(mdinv);
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long t0 = __shfl_xor_sync(0xffffffffu, b0, o), t1 = __shfl_xor_sync(0xffffffffu, b1, o);
+    b0 = t0 > b0 ? t0 : b0;
+    b1 = t1 > b1 ? t1 : b1;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(opmax, b0);
+    atomicMax(opmax + 1, b1);
   }
 }
 

@@ -33,6 +33,20 @@ __global__ void __launch_bounds__(kNT) kl_bop(OpDesc A, const T *__restrict__ P,
   }
 }
 
+// d += (s + c) 2^(sx + sy) (FP64 operands were shifted before their split; FP32 ones were not)
+template <typename T>
+__device__ __forceinline__ void lp_flush(double &d, float &s, float &c, int sx, int sy) {
+  if constexpr (Gram<T>::kShifted) {
+    const double fx = pow2d(sx), fy = pow2d(sy);
+    d += ((double)s * fx) * fy;
+    d += ((double)c * fx) * fy;
+  } else {
+    d += (double)s;
+    d += (double)c;
+  }
+  s = c = 0.0f;
+}
+
 // Partials of gamma = <<X, Y>>_S: grid.x = 32 x 32 tiles (block j, a-tile, b-tile), grid.y = row chunks.
 // Partial row blockIdx.y holds entry (a, b) of block j at j*p*p + b*p + a (the layout of the small path).
 // xscale (optional): X's row r is multiplied by xscale[r] (forms Z = M^{-1} R on the fly).
@@ -40,16 +54,23 @@ template <typename T>
 __global__ void __launch_bounds__(kNT) kl_gram(const T *__restrict__ X, const T *__restrict__ Y, int64_t n, int k,
                                                int p, int global, const int *__restrict__ active,
                                                double *__restrict__ part, const DevStatus *__restrict__ st,
-                                               const T *__restrict__ xscale) {
+                                               const T *__restrict__ xscale, const int *__restrict__ shX,
+                                               const int *__restrict__ shY) {
   using G = Gram<T>;
   using BT = typename G::B;
   if (st != nullptr && st->flags != 0) return;
   __shared__ BT Xs[kLT][kLT + 1], Ys[kLT][kLT + 1];
+  __shared__ int sxs[kLT], sys[kLT];   // exponent shifts of this tile's X and Y columns
   const int ta_n = p / kLT;
   const int tile = blockIdx.x;
   const int j = tile / (ta_n * ta_n);
   const int ta = (tile / ta_n) % ta_n, tb = tile % ta_n;
   const int a0 = ta * kLT, b0 = tb * kLT;
+  if (threadIdx.x < kLT) {
+    sxs[threadIdx.x] = G::kShifted ? shift_at(shX, j * p + a0 + threadIdx.x) : 0;
+    sys[threadIdx.x] = G::kShifted ? shift_at(shY, j * p + b0 + threadIdx.x) : 0;
+  }
+  __syncthreads();
   const int ty = threadIdx.x / 16, tx = threadIdx.x % 16;   // this thread: a = a0+2ty+{0,1}, b = b0+2tx+{0,1}
   double *out = part + (int64_t)blockIdx.y * k * p + (int64_t)j * p * p;
   const bool act = block_active(active, global, j);
@@ -71,8 +92,8 @@ __global__ void __launch_bounds__(kNT) kl_gram(const T *__restrict__ X, const T 
         BT xb = G::zero(), yb = G::zero();
         if (r < r_end) {
           const T xv = X[r * k + (int64_t)j * p + a0 + cc];
-          xb = G::conv(xscale ? xv * xscale[r] : xv);
-          yb = G::conv(Y[r * k + (int64_t)j * p + b0 + cc]);
+          xb = G::conv(xscale ? xv * xscale[r] : xv, sxs[cc]);
+          yb = G::conv(Y[r * k + (int64_t)j * p + b0 + cc], sys[cc]);
         }
         Xs[rr][cc] = xb;
         Ys[rr][cc] = yb;
@@ -94,11 +115,7 @@ __global__ void __launch_bounds__(kNT) kl_gram(const T *__restrict__ X, const T 
 #pragma unroll
         for (int u = 0; u < 2; ++u)
 #pragma unroll
-          for (int v = 0; v < 2; ++v) {
-            d[u][v] += (double)s[u][v];
-            d[u][v] += (double)c[u][v];
-            s[u][v] = c[u][v] = 0.0f;
-          }
+          for (int v = 0; v < 2; ++v) lp_flush<T>(d[u][v], s[u][v], c[u][v], sxs[2 * ty + u], sys[2 * tx + v]);
       }
     }
   }
@@ -106,8 +123,7 @@ __global__ void __launch_bounds__(kNT) kl_gram(const T *__restrict__ X, const T 
   for (int u = 0; u < 2; ++u)
 #pragma unroll
     for (int v = 0; v < 2; ++v) {
-      d[u][v] += (double)s[u][v];
-      d[u][v] += (double)c[u][v];
+      lp_flush<T>(d[u][v], s[u][v], c[u][v], sxs[2 * ty + u], sys[2 * tx + v]);
       const int a = a0 + 2 * ty + u, b = b0 + 2 * tx + v;
       out[(int64_t)b * p + a] = d[u][v];
     }
@@ -184,7 +200,8 @@ __global__ void __launch_bounds__(kNT) kl_baxpy(T *OUT, const T *BASE, const T *
 // Per-column ||R_c||^2 partials (Dot2), one partial row of k entries per CTA.
 template <typename T>
 __global__ void __launch_bounds__(kNT) kl_colnorm(const T *__restrict__ R, int64_t n, int k,
-                                                  double *__restrict__ partN, const DevStatus *__restrict__ st) {
+                                                  double *__restrict__ partN, const DevStatus *__restrict__ st,
+                                                  const int *__restrict__ shR) {
   using G = Gram<T>;
   using BT = typename G::B;
   if (st != nullptr && st->flags != 0) return;
@@ -192,23 +209,21 @@ __global__ void __launch_bounds__(kNT) kl_colnorm(const T *__restrict__ R, int64
   const int rpp = kNT / k;
   const int g = threadIdx.x / k, c = threadIdx.x - g * k;
   const bool slot = g < rpp;
+  const int sR = G::kShifted ? shift_at(shR, c) : 0;
   float s = 0.0f, cc = 0.0f;
   double d = 0.0;
   int pass = 0;
   if (slot) {
     for (int64_t r = (int64_t)blockIdx.x * rpp + g; r < n; r += (int64_t)gridDim.x * rpp) {
-      const BT v = G::conv(R[r * k + c]);
+      const BT v = G::conv(R[r * k + c], sR);
       G::add(s, cc, v, v);
       if (++pass == kFlushPasses) {
         pass = 0;
-        d += (double)s;
-        d += (double)cc;
-        s = cc = 0.0f;
+        norm_flush<T>(d, s, cc, sR);
       }
     }
   }
-  d += (double)s;
-  d += (double)cc;
+  norm_flush<T>(d, s, cc, sR);
   red[threadIdx.x] = slot ? d : 0.0;
   cta_sum_slots(red, k, rpp, partN + (int64_t)blockIdx.x * k);
 }

@@ -266,7 +266,9 @@ template <typename T, int OPK, int PM, int V, bool RR>
 __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM, RR>()) kw_op_gram(OpDesc A, const T *__restrict__ P, const T *__restrict__ R,
                                                   T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                   const int *__restrict__ active, double *__restrict__ partA,
-                                                  double *__restrict__ partR, const DevStatus *__restrict__ st) {
+                                                  double *__restrict__ partR, const DevStatus *__restrict__ st,
+                                                  const int *__restrict__ shP, const int *__restrict__ shQ,
+                                                  const int *__restrict__ shR) {
   using G = Gram<T>;
   using BT = typename G::B;
   using VT = typename VecOf<T, V>::type;
@@ -275,6 +277,19 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM, RR>()) kw_op_g
   WcGeom geo;
   geo.init(n, k, V);
   static_assert(sizeof(BT) == wc_bt_size<T>(), "broadcast tile element");
+  // the memory-phase columns of a lane are the same in every chunk: their exponent shifts stay in registers
+  int mshP[V], mshQ[V], mshR[V];
+  {
+    int64_t row0;
+    int mc0;
+    geo.mem_pos(0, row0, mc0);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      mshP[v] = G::kShifted ? shift_at(shP, mc0 + v) : 0;
+      mshQ[v] = G::kShifted ? shift_at(shQ, mc0 + v) : 0;
+      mshR[v] = (G::kShifted && RR) ? shift_at(shR, mc0 + v) : 0;
+    }
+  }
   BT *tile = reinterpret_cast<BT *>(smem + (size_t)geo.warp * wc_op_warp_bytes<T>(V));
   BT *sP = tile, *sQ = tile + 32 * V, *sR = tile + 64 * V;
   double *redA = reinterpret_cast<double *>(smem + (size_t)kWarps * wc_op_warp_bytes<T>(V));
@@ -286,6 +301,11 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM, RR>()) kw_op_g
   // alpha is symmetric: lane b accumulates only its circulant diagonals d = 0..p/2, entry ((b + d) mod p, b)
   // (d = p/2 only for b < p/2); the recomputed rho stays a full product. p == PM here (p divides 32).
   constexpr int PMH = PM == 1 ? 1 : PM / 2 + 1;
+  // flush scales: accumulator d of alpha holds entry ((b + d) mod p, b); accR entry a holds (a, b)
+  auto sxA = [&](int d) { return shift_at(shP, j * p + ((b + d) & (PM - 1))); };
+  auto sxR = [&](int a) { return shift_at(shP, j * p + a); };
+  const int syQ = G::kShifted ? shift_at(shQ, c) : 0;
+  const int syR = (G::kShifted && RR) ? shift_at(shR, c) : 0;
   GramAcc<PMH> accA;
   GramAcc<RR ? PM : 1> accR;
   accA.zero();
@@ -311,9 +331,9 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM, RR>()) kw_op_g
 #pragma unroll
     for (int v = 0; v < V; ++v) {
       const int t = 32 * geo.sm + geo.om + v;
-      sP[t] = G::conv(pv.e[v]);
-      sQ[t] = G::conv(qv.e[v]);
-      if constexpr (RR) sR[t] = G::conv(rv.e[v]);
+      sP[t] = G::conv(pv.e[v], mshP[v]);
+      sQ[t] = G::conv(qv.e[v], mshQ[v]);
+      if constexpr (RR) sR[t] = G::conv(rv.e[v], mshR[v]);
     }
     __syncwarp();
     if (act) {
@@ -337,12 +357,12 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM, RR>()) kw_op_g
     __syncwarp();
     if (++pass == kFlushPasses / V) {
       pass = 0;
-      accA.flush(slotA, PMH);
-      if constexpr (RR) accR.flush(slotR, p);
+      gram_flush<T>(accA, slotA, PMH, sxA, syQ);
+      if constexpr (RR) gram_flush<T>(accR, slotR, p, sxR, syR);
     }
   }
-  accA.flush(slotA, PMH);
-  if constexpr (RR) accR.flush(slotR, p);
+  gram_flush<T>(accA, slotA, PMH, sxA, syQ);
+  if constexpr (RR) gram_flush<T>(accR, slotR, p, sxR, syR);
   const int E = k * p;
   wc_cta_reduce(redA, k, p, partA + (int64_t)blockIdx.x * E);
   if constexpr (RR) wc_cta_reduce(redR, k, p, partR + (int64_t)blockIdx.x * E);
@@ -363,7 +383,8 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_x
                                                     const T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                     const double *__restrict__ lam, const int *__restrict__ active,
                                                     double *__restrict__ partRho, double *__restrict__ partN,
-                                                    const DevStatus *__restrict__ st, const T *__restrict__ dinv) {
+                                                    const DevStatus *__restrict__ st, const T *__restrict__ dinv,
+                                                    const int *__restrict__ shZ, const int *__restrict__ shR) {
   using G = Gram<T>;
   using BT = typename G::B;
   using VT = typename VecOf<T, V>::type;
@@ -390,6 +411,11 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_x
   *slotN = 0.0;
   __syncthreads();
   constexpr int PMH = PM == 1 ? 1 : PM / 2 + 1;   // rho = R^T R is symmetric: circulant diagonals only
+  // compute-phase shifts: this lane's column for R, and the broadcast Z columns at flush time
+  // without a preconditioner Z = R, and the P role's shift equals the R role's
+  const int cshR = G::kShifted ? shift_at(shR, c) : 0;
+  const int cshZ = (G::kShifted && ZS) ? shift_at(shZ, c) : cshR;
+  auto sxZ = [&](int d) { return shift_at(shZ, j * p + ((b + d) & (PM - 1))); };
   T lcol[PM];
   {
     const T *lj = sL + (global ? 0 : j) * p * p + b;
@@ -447,9 +473,9 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_x
       // broadcast Z = M^{-1} R (R without a preconditioner); the own operand R is re-read from sR below
       if constexpr (ZS) {
         const int64_t rw = R0 + (int64_t)s * geo.gr + geo.ro;
-        sRb[t] = G::conv(rw < n ? r * dinv[rw] : T(0));
+        sRb[t] = G::conv(rw < n ? r * dinv[rw] : T(0), cshZ);
       } else {
-        sRb[t] = G::conv(r);
+        sRb[t] = G::conv(r, cshZ);
       }
     }
     __syncwarp();
@@ -457,7 +483,7 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_x
 #pragma unroll
       for (int s = 0; s < V; ++s) {
         const int t = 32 * s + geo.lane;
-        const BT rb2 = ZS ? G::conv(sR[t]) : sRb[t];   // own operand: R
+        const BT rb2 = ZS ? G::conv(sR[t], cshR) : sRb[t];   // own operand: R
         const BT *rowr = sRb + t - b;                      // broadcast: Z
 #pragma unroll
         for (int d = 0; d < PMH; ++d)
@@ -475,15 +501,12 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_x
     __syncwarp();
     if (++pass == kFlushPasses / V) {
       pass = 0;
-      acc.flush(slotRho, PMH);
-      *slotN += (double)ns;
-      *slotN += (double)nc;
-      ns = nc = 0.0f;
+      gram_flush<T>(acc, slotRho, PMH, sxZ, cshR);
+      norm_flush<T>(*slotN, ns, nc, cshR);
     }
   }
-  acc.flush(slotRho, PMH);
-  *slotN += (double)ns;
-  *slotN += (double)nc;
+  gram_flush<T>(acc, slotRho, PMH, sxZ, cshR);
+  norm_flush<T>(*slotN, ns, nc, cshR);
   const int E = k * p;
   wc_cta_reduce(red, k, p, partRho + (int64_t)blockIdx.x * E);
   wc_cta_reduce(nred, k, 1, partN + (int64_t)blockIdx.x * k);
@@ -498,7 +521,8 @@ template <typename T, int PM, int V, bool ZS, bool RR>
 __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *__restrict__ R, int64_t n, int k,
                                                    int p, int global, const double *__restrict__ beta,
                                                    const int *__restrict__ active, DevStatus *__restrict__ st,
-                                                   const T *__restrict__ dinv, double *__restrict__ partR) {
+                                                   const T *__restrict__ dinv, double *__restrict__ partR,
+                                                   const int *__restrict__ shP, const int *__restrict__ shR) {
   using G = Gram<T>;
   using BT = typename G::B;
   using VT = typename VecOf<T, V>::type;
@@ -531,6 +555,16 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
   }
   GramAcc<RR ? PM : 1> acc;
   acc.zero();
+  // RR shifts: P_new and R in the compute phase (this lane's column); with the Jacobi scaling R is converted in
+  // the memory phase (the tile then holds Z), by the shift table s_shR
+  __shared__ int s_shR[kNT];
+  if (G::kShifted && RR && ZS) {
+    for (int cc = threadIdx.x; cc < k; cc += blockDim.x) s_shR[cc] = shift_at(shR, cc);
+    __syncthreads();
+  }
+  const int sPn = (G::kShifted && RR) ? shift_at(shP, c) : 0;
+  const int syR = (G::kShifted && RR) ? shift_at(shR, c) : 0;
+  auto sxP = [&](int a) { return shift_at(shP, j * p + a); };
   int pass = 0;
   const int kv = k / V;
   for (int64_t rb = geo.rb0; rb < geo.nrb; rb += geo.rbs) {
@@ -558,7 +592,7 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
     for (int v = 0; v < V; ++v) {
       sP[tm + v] = pv.e[v];
       sR[tm + v] = zv.e[v];
-      if constexpr (RR) sRb[tm + v] = G::conv(rv.e[v]);
+      if constexpr (RR && ZS) sRb[tm + v] = G::conv(rv.e[v], G::kShifted ? s_shR[mc + v] : 0);
     }
     __syncwarp();
 #pragma unroll
@@ -574,7 +608,7 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
           if (a < p) out = fma_t(prow[a], bcol[a], out);
       }
       sN[t] = out;
-      if constexpr (RR) sNb[t] = G::conv(out);
+      if constexpr (RR) sNb[t] = G::conv(out, sPn);
     }
     __syncwarp();
     if constexpr (RR) {
@@ -584,7 +618,7 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
           const int t = 32 * s + geo.lane;
           BT nrow[PM];
           load_row<BT, PM>(sNb + t - b, nrow, p);
-          const BT rb2 = sRb[t];
+          const BT rb2 = ZS ? sRb[t] : G::conv(sR[t], syR);   // own operand R (the tile holds Z = R)
 #pragma unroll
           for (int a = 0; a < PM; ++a)
             if (a < p) G::add(acc.s[a], acc.c[a], nrow[a], rb2);
@@ -592,7 +626,7 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
       }
       if (++pass == kFlushPasses / V) {
         pass = 0;
-        acc.flush(slotR, p);
+        gram_flush<T>(acc, slotR, p, sxP, syR);
       }
     }
     if (row < n) {
@@ -604,7 +638,7 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
     __syncwarp();
   }
   if constexpr (RR) {
-    acc.flush(slotR, p);
+    gram_flush<T>(acc, slotR, p, sxP, syR);
     wc_cta_reduce(red, k, p, partR + (int64_t)blockIdx.x * k * p);
   }
 }

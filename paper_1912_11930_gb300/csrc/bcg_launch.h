@@ -13,6 +13,13 @@ namespace bcgk {
 // Largest p handled by the streaming kernels (per-thread Gram accumulators live in registers).
 constexpr int kMaxP = 32;
 
+// Exponent shifts of the FP64 Gram operands (bcg_kernels.cuh): a solver's shift array holds 3 k ints, one row
+// of k per operand role -- R (the residual), P (directions and Z = M^{-1} R: R's shift plus the exponent of
+// max|diag(A)^{-1}| under the Jacobi preconditioner), Q (A P: P's shift plus the exponent of A's largest
+// absolute row sum). The small-solve kernels rewrite it from the column norms whenever those change.
+enum ShiftRole { SH_R = 0, SH_P = 1, SH_Q = 2 };
+inline const int *sh_role(const int *sh, int k, int role) { return sh ? sh + (size_t)role * k : nullptr; }
+
 struct StreamGrids {
   int op;        // K1 CTAs
   int upd;       // K2 CTAs
@@ -32,25 +39,28 @@ cudaError_t stream_grids(int opkind, int64_t n, int k, int p, int global, int ns
 template <typename T>
 cudaError_t launch_op_gram(const OpDesc &A, const T *P, const T *R, T *Q, int64_t n, int k, int p, int global,
                            const int *active, double *partA, double *partR, const DevStatus *st, int grid,
-                           cudaStream_t s);
+                           cudaStream_t s, const int *sh);
 // dinv (optional, n values): inverse diagonal of the Jacobi preconditioner; Z = M^{-1} R is formed on the
 // fly where Algorithm 1 needs it (NULL: M = I).
 template <typename T>
 cudaError_t launch_update_xr(T *X, T *R, const T *P, const T *Q, int64_t n, int k, int p, int global,
                              const double *lam, const int *active, double *partRho, double *partN,
-                             const DevStatus *st, int grid, cudaStream_t s, const T *dinv);
+                             const DevStatus *st, int grid, cudaStream_t s, const T *dinv, const int *sh);
 template <typename T>
 // partR: with rho_k3, the partials of the next iteration's recomputed rho <<P_new, R>>_S (one row per CTA)
 cudaError_t launch_update_p(T *P, const T *R, int64_t n, int k, int p, int global, const double *beta,
                             const int *active, DevStatus *st, int grid, cudaStream_t s, const T *dinv,
-                            double *partR);
+                            double *partR, const int *sh);
 template <typename T>
+// sig (optional): R32 and P32 receive R 2^-sigma_c (the mixed form's scale)
 cudaError_t launch_residual(const OpDesc &A, const T *X, const T *B, T *R, T *P, float *R32, float *P32, int64_t n,
-                            int k, double *partN, int grid, cudaStream_t s, const T *dinv);
-cudaError_t launch_inv_diag(const OpDesc &A, int64_t n, double *dinv, int nsm, cudaStream_t s);
+                            int k, double *partN, int grid, cudaStream_t s, const T *dinv, const int *sig = nullptr);
+// also the operator maxima behind the Gram shift offsets (opmax: 2 doubles, or NULL)
+cudaError_t launch_inv_diag(const OpDesc &A, int64_t n, double *dinv, double *opmax, int nsm, cudaStream_t s);
 
 template <typename T>
-cudaError_t launch_bdot(const T *X, const T *Y, int64_t n, int k, int p, double *part, int grid, cudaStream_t s);
+cudaError_t launch_bdot(const T *X, const T *Y, int64_t n, int k, int p, double *part, int grid, cudaStream_t s,
+                        const int *shX, const int *shY);
 template <typename T>
 int bdot_grid(int64_t n, int k, int p, int nsm);
 cudaError_t launch_finish_gram(const double *part, int nparts, int k, int p, int global, double *gamma, double *gws,
@@ -65,14 +75,15 @@ cudaError_t launch_lp_bop(const OpDesc &A, const T *P, T *Q, int64_t n, int k, c
                           cudaStream_t s);
 template <typename T>
 cudaError_t launch_lp_gram(const T *X, const T *Y, int64_t n, int k, int p, int global, const int *active,
-                           double *part, int chunks, const DevStatus *st, cudaStream_t s, const T *xscale);
+                           double *part, int chunks, const DevStatus *st, cudaStream_t s, const T *xscale,
+                           const int *shX, const int *shY);
 template <typename T>
 cudaError_t launch_lp_baxpy(T *OUT, const T *BASE, const T *Y, const double *C, int64_t n, int k, int p, int global,
                             double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
                             const T *bscale);
 template <typename T>
 cudaError_t launch_lp_colnorm(const T *R, int64_t n, int k, double *partN, int grid, const DevStatus *st,
-                              cudaStream_t s);
+                              cudaStream_t s, const int *shR);
 
 // doubles of per-block workspace of the p x p solves; kept in global memory (gws) when too big for shared
 size_t small_ws_doubles(int p);
@@ -88,10 +99,12 @@ cudaError_t launch_solve_beta(const double *partRho, const double *partN, int np
                               int global, const double *tol2, const double *r0n2, double *rn2, int *active,
                               int *block_iters,
                               const double *rho_rec, double *beta, DevStatus *st, double *gws, int rho_circ,
-                              cudaStream_t s);
+                              cudaStream_t s, const ShiftCtl &sc);
 cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, int global, double *r0n2, double *rn2,
                                int *active, int *block_iters, double *lam, double *beta, DevStatus *st,
-                               cudaStream_t s);
+                               cudaStream_t s, const ShiftCtl &sc);
+// Rewrites sc.sh from the squared column norms n2 (NULL: every column's base shift 0, offsets only).
+cudaError_t launch_fill_shifts(const double *n2, int k, const ShiftCtl &sc, cudaStream_t s);
 cudaError_t launch_reduce_norms(const double *partN, int nparts, int k, double *out, cudaStream_t s);
 cudaError_t launch_reactivate(const double *rtn2, const double *r0n2, double tol2, int k, int p, int global,
                               int *active, DevStatus *st, cudaStream_t s);
@@ -100,7 +113,18 @@ cudaError_t launch_gather_rows(const double *P, const int32_t *rows, int64_t nro
                                cudaStream_t s);
 cudaError_t launch_permute_rows(const double *src, const int32_t *perm, int64_t n, int k, double *dst, int scatter,
                                 int nsm, cudaStream_t s);
-cudaError_t launch_add_correction(double *X, const float *D, int64_t len, int nsm, cudaStream_t s);
+// X += D 2^sigma_c with the mixed form's per-column scale exponents sig (NULL: 0)
+cudaError_t launch_add_correction(double *X, const float *D, int64_t len, int k, const int *sig, int nsm,
+                                  cudaStream_t s);
+// Gram shifts of a standalone BDOT operand: sh[c] from max_r |X[r][c]| (cmax: k doubles of scratch)
+cudaError_t launch_col_shifts(const double *X, int64_t n, int k, double *cmax, int *sh, int nsm, cudaStream_t s);
+// the mixed form's FP32 scale per block from the squared column norms cur; cur_s, ref_s (optional) receive cur
+// and ref in the scaled process's units
+cudaError_t launch_mixed_scale(const double *cur, const double *ref, int k, int p, int global, int *sig,
+                               double *cur_s, double *ref_s, cudaStream_t s);
+// R32 = fl(R 2^-sigma), P32 = fl(M^{-1} R 2^-sigma) (P32, dinv optional)
+cudaError_t launch_cast_scaled(const double *R, const double *dinv, const int *sig, int64_t n, int k, float *R32,
+                               float *P32, int nsm, cudaStream_t s);
 cudaError_t launch_cast_to_float(const double *src, float *dst, int64_t len, int nsm, cudaStream_t s);
 cudaError_t launch_grad_values(const int32_t *rowidx, const int32_t *colind, const double *Lam, const double *X,
                                int64_t nnz, int k, double *grad, int nsm, cudaStream_t s);
@@ -112,7 +136,8 @@ cudaError_t launch_row_index(const int64_t *rowptr, int64_t n, int32_t *rowidx, 
 // partial-row count of the gamma products of the streaming retooled path (<= cap, the partial buffers' rows)
 int dr_grid_for(int64_t n, int k, int p, int nsm, int cap);
 cudaError_t launch_dr_gram(const double *X, const double *Y, int64_t n, int k, int p, const int *active,
-                           double *part, int grid, const DevStatus *st, cudaStream_t s);
+                           double *part, int grid, const DevStatus *st, cudaStream_t s, const int *shX,
+                           const int *shY);
 // X += S lambda, Qb = Qb - W xi (= T), partials of <<T, T>>_S
 cudaError_t launch_dr_update_xt(double *X, double *Qb, const double *S, const double *W, int64_t n, int k, int p,
                                 const double *lam, const double *xi, const int *active, double *part, int grid,

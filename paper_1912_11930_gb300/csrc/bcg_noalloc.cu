@@ -3,9 +3,10 @@
 // Some callers cannot call cudaMalloc at all: code running inside a CUDA-graph capture that must not
 // allocate, plug-ins of hosts that own every device allocation through their own pool, or real-time paths
 // where an allocation may block or fail. This entry point computes the same block product as bcg_bdot but
-// needs no handle (creating one allocates) and no workspace: its per-CTA partial sums live in one
-// file-scope device array of fixed size, kNoAllocScratchDoubles doubles (2 MiB), which every GPU that loads
-// the library holds until the process exits. The paper has no counterpart; it is a deployment variant.
+// needs no handle (creating one allocates) and no workspace: its column maxima, exponent shifts and per-CTA
+// partial sums live in one file-scope device array of fixed size, kNoAllocScratchDoubles doubles (2 MiB), which
+// every GPU that loads the library holds until the process exits. The paper has no counterpart; it is a
+// deployment variant.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,7 +20,10 @@ void bcg_internal_set_error(const char *msg);   // bcg_capi.cu
 
 namespace {
 
-constexpr int kNoAllocScratchDoubles = 1 << 18;   // 2 MiB of FP64 partial sums
+constexpr int kNoAllocScratchDoubles = 1 << 18;   // 2 MiB
+// layout: [0, 2k) column maxima of X and of Y, then 2k int shifts; the partial sums start at kPartOff
+// (k <= 256 keeps the head below 1024 doubles, and the partials 256-byte aligned)
+constexpr int kPartOff = 1024;
 constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
@@ -35,14 +39,17 @@ bcg_status noalloc_fail(bcg_status s, const char *msg, cudaError_t e = cudaSucce
   return s;
 }
 
-bool device_pointer(const void *p) {
-  if (p == nullptr) return false;
+// 1: device (or managed) memory of device dev; 0: not device memory; -1: device memory of another device
+int device_pointer(const void *p, int dev) {
+  if (p == nullptr) return 0;
   cudaPointerAttributes at;
   if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
     cudaGetLastError();
-    return false;
+    return 0;
   }
-  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+  if (at.type == cudaMemoryTypeManaged) return 1;
+  if (at.type != cudaMemoryTypeDevice) return 0;
+  return at.device == dev ? 1 : -1;
 }
 
 }  // namespace
@@ -63,14 +70,18 @@ extern "C" bcg_status bcg_bdot_noalloc(int64_t n, int32_t k, int32_t p, int32_t 
   if (p < 1 || k % p != 0) return noalloc_fail(BCG_ERR_INVALID_ARG, "p must divide k");
   if (p > kMaxP) return noalloc_fail(BCG_ERR_INVALID_ARG, "p > 32 is not supported");
   const int64_t per_cta = (int64_t)k * p;   // doubles of one CTA's partial
-  if (per_cta > kNoAllocScratchDoubles)
-    return noalloc_fail(BCG_ERR_INVALID_ARG, "k*p exceeds the static scratch (262144 doubles)");
-  if (!device_pointer(X) || !device_pointer(Y) || !device_pointer(gamma))
-    return noalloc_fail(BCG_ERR_INVALID_ARG, "X, Y and gamma must be device pointers");
+  if (per_cta > kNoAllocScratchDoubles - kPartOff)
+    return noalloc_fail(BCG_ERR_INVALID_ARG, "k*p exceeds the static scratch (261120 doubles)");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(BCG_ERR_CUDA, "cudaGetDevice", e);
   if (dev < 0 || dev >= kMaxDevices) return noalloc_fail(BCG_ERR_INVALID_ARG, "device ordinal out of range");
+  const int kx = device_pointer(X, dev), ky = device_pointer(Y, dev), kg = device_pointer(gamma, dev);
+  if (kx == 0 || ky == 0 || kg == 0)
+    return noalloc_fail(BCG_ERR_INVALID_ARG, "X, Y and gamma must be device pointers");
+  if (kx < 0 || ky < 0 || kg < 0)
+    return noalloc_fail(BCG_ERR_INVALID_ARG,
+                        "X, Y and gamma must live on the current device (the scratch used is this device's)");
   // Set-up on the first call on this device: in host code g_noalloc_scratch names a host-side shadow, so the
   // kernel must be given the device address, looked up here with this device current.
   double *scratch = g_scratch_addr[dev].load(std::memory_order_acquire);
@@ -84,12 +95,19 @@ extern "C" bcg_status bcg_bdot_noalloc(int64_t n, int32_t k, int32_t p, int32_t 
   int nsm = 0;
   e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   if (e != cudaSuccess) return noalloc_fail(BCG_ERR_CUDA, "cudaDeviceGetAttribute", e);
-  // every CTA overwrites its whole partial row, so nothing in the scratch has to start at zero
-  const int grid = (int)std::min<int64_t>(bdot_grid<double>(n, k, p, nsm), kNoAllocScratchDoubles / per_cta);
+  // Every CTA overwrites its whole partial row, so the partials need no clearing; the column maxima are cleared
+  // by launch_col_shifts (a memset of the array, which allocates nothing).
+  const int grid = (int)std::min<int64_t>(bdot_grid<double>(n, k, p, nsm), (kNoAllocScratchDoubles - kPartOff) / per_cta);
   cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-  e = launch_bdot<double>(X, Y, n, k, p, scratch, grid, s);
+  double *cmax = scratch;
+  int *sh = reinterpret_cast<int *>(scratch + 2 * k);
+  double *part = scratch + kPartOff;
+  e = launch_col_shifts(X, n, k, cmax, sh, nsm, s);
+  if (e == cudaSuccess) e = launch_col_shifts(Y, n, k, cmax + k, sh + k, nsm, s);
+  if (e != cudaSuccess) return noalloc_fail(BCG_ERR_CUDA, "column maxima launch", e);
+  e = launch_bdot<double>(X, Y, n, k, p, part, grid, s, sh, sh + k);
   if (e != cudaSuccess) return noalloc_fail(BCG_ERR_CUDA, "BDOT launch", e);
-  e = launch_finish_gram(scratch, grid, k, p, global, gamma, nullptr, s);
+  e = launch_finish_gram(part, grid, k, p, global, gamma, nullptr, s);
   if (e != cudaSuccess) return noalloc_fail(BCG_ERR_CUDA, "reduction launch", e);
   return BCG_OK;
 }

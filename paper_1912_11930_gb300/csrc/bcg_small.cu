@@ -238,7 +238,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
                                                          int *__restrict__ block_iters,
                                                          const double *__restrict__ rho_rec,
                                                          double *__restrict__ beta, DevStatus *st, double *gws,
-                                                         int rho_circ, int nparts_n, int split) {
+                                                         int rho_circ, int nparts_n, int split, ShiftCtl sc) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   if (!active[jb]) return;
@@ -256,6 +256,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
   for (int c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
     const double s = sm[c - c0];
     rn2[c] = s;
+    write_shifts(sc, k, c, s);   // Gram shifts of the next products follow the new norms
     if (!isfinite(s)) finite = false;
     if (!(s <= tol2 * r0n2[c])) conv = false;
   }
@@ -479,7 +480,7 @@ __global__ void __launch_bounds__(256) k_trsm_cols(int p, int chol, const double
 __global__ void k_init_status(const double *__restrict__ partN, int nparts, int k, int p, int global,
                               double *__restrict__ r0n2, double *__restrict__ rn2, int *__restrict__ active,
                               int *__restrict__ block_iters, double *__restrict__ lam, double *__restrict__ beta,
-                              DevStatus *st) {
+                              DevStatus *st, ShiftCtl sc) {
   const int nblk = global ? 1 : k / p;
   __shared__ int nact, nonfinite;
   if (threadIdx.x == 0) { nact = 0; nonfinite = 0; }
@@ -490,6 +491,7 @@ __global__ void k_init_status(const double *__restrict__ partN, int nparts, int 
     const double s = ncol[c];
     r0n2[c] = s;
     rn2[c] = s;
+    write_shifts(sc, k, c, s);
     if (!isfinite(s)) atomicOr(&nonfinite, 1);
   }
   __syncthreads();
@@ -551,6 +553,13 @@ __global__ void __launch_bounds__(kSmallNT) k_finish_gram(const double *__restri
   }
 }
 
+// Gram shifts from the squared norms n2 (NULL: every column taken at the squared norm 2^(2 kGramCenter), whose
+// base shift is 0, so that only the role offsets remain).
+__global__ void k_fill_shifts(const double *__restrict__ n2, int k, ShiftCtl sc) {
+  const double unit2 = (double)(1 << kGramCenter) * (double)(1 << kGramCenter);
+  for (int c = threadIdx.x; c < k; c += blockDim.x) write_shifts(sc, k, c, n2 ? n2[c] : unit2);
+}
+
 __global__ void k_reduce_norms(const double *__restrict__ partN, int nparts, int k, double *__restrict__ out) {
   __shared__ double ncol[kNT], nscr[kSmallNT > kNT ? kSmallNT : kNT];
   det_reduce(k, nparts, [&](int pi, int c) { return partN[(int64_t)pi * k + c]; }, ncol, nscr);
@@ -595,9 +604,65 @@ __global__ void k_permute_rows(const double *__restrict__ src, const int32_t *__
 }
 
 // X64 += D32 (the refinement update of the mixed-precision form)
-__global__ void k_add_correction(double *__restrict__ X, const float *__restrict__ D, int64_t len) {
+// X += D 2^sigma_c (sig: the FP32 process's scale exponent per column, NULL: 0), len = n k
+__global__ void k_add_correction(double *__restrict__ X, const float *__restrict__ D, int64_t len, int k,
+                                 const int *__restrict__ sig) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x)
-    X[i] += (double)D[i];
+    X[i] += sig ? (double)D[i] * pow2d(sig[i % k]) : (double)D[i];
+}
+
+// Column maxima for the shifts of a standalone BDOT: out[c] = max_r |X[r][c]| as the bit pattern of a
+// non-negative double (ordered like the integers; the caller zeroes out first). Thread (g, c) of a CTA covers
+// rows g, g + rows per CTA pass, ... of column c. (The maximum itself, not its square: the square of an entry
+// above 1e154 would overflow.)
+__global__ void __launch_bounds__(kNT) k_col_maxabs(const double *__restrict__ X, int64_t n, int k,
+                                                    unsigned long long *__restrict__ out) {
+  const int rpp = kNT / k;
+  const int g = threadIdx.x / k, c = threadIdx.x - g * k;
+  if (g >= rpp) return;
+  double m = 0.0;
+  for (int64_t r = (int64_t)blockIdx.x * rpp + g; r < n; r += (int64_t)gridDim.x * rpp) m = fmax(m, fabs(X[r * k + c]));
+  atomicMax(out + c, (unsigned long long)__double_as_longlong(m));
+}
+
+// sh[c] = floor(log2 cmax[c]) - kGramCenter: the column's largest entry scaled into [2^10, 2^11) (a zero or
+// subnormal maximum: the shift of 1.0; one row, no role offsets)
+__global__ void k_shift_from_max(const double *__restrict__ cmax, int k, int *__restrict__ sh) {
+  for (int c = threadIdx.x; c < k; c += blockDim.x) sh[c] = clamp_shift(exponent_of(cmax[c]) - kGramCenter);
+}
+
+// Mixed form: the FP32 process of block j runs on R_j 2^-sigma_j, an exact scaling, so that FP32 holds its values
+// whatever the scale of the FP64 residual (FP32 alone covers about 1e-38 .. 3e38). sigma_j = floor(log2 of the
+// largest column norm of the block) (global: of all columns; 0 for a zero or non-finite block), stored for every
+// column of the block. cur_s = cur 2^(-2 sigma), ref_s = ref 2^(-2 sigma) (squared norms in the process's scale).
+__global__ void k_mixed_scale(const double *__restrict__ cur, const double *__restrict__ ref, int k, int p,
+                              int global, int *__restrict__ sig, double *__restrict__ cur_s,
+                              double *__restrict__ ref_s) {
+  const int nblk = global ? 1 : k / p;
+  for (int jb = threadIdx.x; jb < nblk; jb += blockDim.x) {
+    const int c0 = global ? 0 : jb * p, c1 = global ? k : c0 + p;
+    double m = 0.0;
+    for (int c = c0; c < c1; ++c) m = fmax(m, cur[c]);
+    const int sg = exponent_of(m) >> 1;
+    const double f = pow2d(-2 * sg);
+    for (int c = c0; c < c1; ++c) {
+      sig[c] = sg;
+      if (cur_s) cur_s[c] = cur[c] * f;
+      if (ref_s) ref_s[c] = ref[c] * f;
+    }
+  }
+}
+
+// R32 = fl(R 2^-sigma_c), P32 = fl(M^{-1} R 2^-sigma_c) (dinv NULL: M = I), n x k row-major
+__global__ void k_cast_scaled(const double *__restrict__ R, const double *__restrict__ dinv,
+                              const int *__restrict__ sig, int64_t n, int k, float *__restrict__ R32,
+                              float *__restrict__ P32) {
+  const int64_t len = n * k;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < len; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = R[i] * pow2d(-sig[i % k]);
+    R32[i] = (float)v;
+    if (P32) P32[i] = (float)(dinv ? v * dinv[i / k] : v);
+  }
 }
 
 __global__ void k_cast_to_float(const double *__restrict__ src, float *__restrict__ dst, int64_t len) {
@@ -684,13 +749,13 @@ cudaError_t launch_solve_beta(const double *partRho, const double *partN, int np
                               int global, const double *tol2, const double *r0n2, double *rn2, int *active,
                               int *block_iters,
                               const double *rho_rec, double *beta, DevStatus *st, double *gws, int rho_circ,
-                              cudaStream_t s) {
+                              cudaStream_t s, const ShiftCtl &sc) {
   const int nblk = global ? 1 : k / p;
   if (small_needs_gws(p) && gws == nullptr) return cudaErrorInvalidValue;
   const int split = small_split(p) ? 1 : 0;
   k_solve_beta<<<nblk, small_threads(nparts, p), small_smem(p), s>>>(
       partRho, partN, nparts, k, p, global, tol2, r0n2, rn2, active, block_iters, rho_rec, beta, st,
-      small_needs_gws(p) ? gws : nullptr, rho_circ, nparts_n, split);
+      small_needs_gws(p) ? gws : nullptr, rho_circ, nparts_n, split, sc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !split) return e;
   return launch_trsm(p, nblk, 0, gws, active, beta, st, s);
@@ -698,8 +763,15 @@ cudaError_t launch_solve_beta(const double *partRho, const double *partN, int np
 
 cudaError_t launch_init_status(const double *partN, int nparts, int k, int p, int global, double *r0n2, double *rn2,
                                int *active, int *block_iters, double *lam, double *beta, DevStatus *st,
-                               cudaStream_t s) {
-  k_init_status<<<1, kSmallNT, 0, s>>>(partN, nparts, k, p, global, r0n2, rn2, active, block_iters, lam, beta, st);
+                               cudaStream_t s, const ShiftCtl &sc) {
+  k_init_status<<<1, kSmallNT, 0, s>>>(partN, nparts, k, p, global, r0n2, rn2, active, block_iters, lam, beta, st,
+                                       sc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_shifts(const double *n2, int k, const ShiftCtl &sc, cudaStream_t s) {
+  if (sc.sh == nullptr) return cudaSuccess;
+  k_fill_shifts<<<1, 256, 0, s>>>(n2, k, sc);
   return cudaGetLastError();
 }
 
@@ -752,8 +824,30 @@ cudaError_t launch_permute_rows(const double *src, const int32_t *perm, int64_t 
   return cudaGetLastError();
 }
 
-cudaError_t launch_add_correction(double *X, const float *D, int64_t len, int nsm, cudaStream_t s) {
-  k_add_correction<<<stream_grid(len, nsm), 256, 0, s>>>(X, D, len);
+cudaError_t launch_add_correction(double *X, const float *D, int64_t len, int k, const int *sig, int nsm,
+                                  cudaStream_t s) {
+  k_add_correction<<<stream_grid(len, nsm), 256, 0, s>>>(X, D, len, k, sig);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_shifts(const double *X, int64_t n, int k, double *cmax, int *sh, int nsm, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(cmax, 0, sizeof(double) * k, s);
+  if (e != cudaSuccess) return e;
+  k_col_maxabs<<<stream_grid(n * k, nsm), kNT, 0, s>>>(X, n, k, reinterpret_cast<unsigned long long *>(cmax));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  k_shift_from_max<<<1, 256, 0, s>>>(cmax, k, sh);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mixed_scale(const double *cur, const double *ref, int k, int p, int global, int *sig,
+                               double *cur_s, double *ref_s, cudaStream_t s) {
+  k_mixed_scale<<<1, 256, 0, s>>>(cur, ref, k, p, global, sig, cur_s, ref_s);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cast_scaled(const double *R, const double *dinv, const int *sig, int64_t n, int k, float *R32,
+                               float *P32, int nsm, cudaStream_t s) {
+  k_cast_scaled<<<stream_grid(n * k, nsm), 256, 0, s>>>(R, dinv, sig, n, k, R32, P32);
   return cudaGetLastError();
 }
 

@@ -4,7 +4,9 @@ hold at any size (forward and adjoint residuals, sampled gradient entries recomp
 import numpy as np
 import pytest
 
+from oracle import bcg as O
 from paper_1912_11930_gb300 import workloads as W
+from parity_check import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -39,6 +41,12 @@ def test_gradient_dense_and_finite_differences(lib):
     gv = vals.grad.cpu().numpy()
     assert np.linalg.norm(gv - g_dense) <= 1e-8 * np.linalg.norm(g_dense)
     assert np.linalg.norm(B.grad.cpu().numpy() - Lam) <= 1e-8 * np.linalg.norm(Lam)
+    # the oracle's forward solve, adjoint solve and gradient formula, element by element
+    fwd, adj, g_or = O.solve_and_grad(M.to_scipy(), M.rowptr, M.colind, Bn, Wn, p=k, sub="hybrid", tol=1e-13)
+    assert fwd.status == O.OK and adj.status == O.OK
+    assert_close(X.detach().cpu().numpy(), fwd.X, 1e-9, "X")
+    assert_close(B.grad.cpu().numpy(), adj.X, 1e-9, "dL/dB")
+    assert_close(gv, g_or, 1e-9, "dL/dvals")
     # central differences of the loss through the GPU solver itself, symmetric pairs perturbed together
     pos = {(int(rows[e]), int(M.colind[e])): e for e in range(M.nnz)}
     rng = np.random.default_rng(1)
@@ -85,4 +93,25 @@ def test_full_size_27pt_100_k16(lib):
     for e in rng.choice(M.nnz, 500, replace=False):
         ref = -float(np.dot(Lam[rows[e]], Xn[M.colind[e]]))
         assert abs(gv[e] - ref) <= 1e-12 * max(1.0, abs(ref))
+    # independent of the gradient formula: the directional derivative of the loss along a random symmetric
+    # perturbation D of the stored values (D_ij = D_ji, so A stays symmetric), by central differences through
+    # two further solves, against sum_e grad_e D_e
+    key = rows.astype(np.int64) * M.n + M.colind   # entry (i, j) -> i n + j; its transpose is j n + i
+    srt = np.argsort(key)
+    swap = srt[np.searchsorted(key[srt], M.colind.astype(np.int64) * M.n + rows)]   # index of the transposed entry
+    assert np.array_equal(key[swap], M.colind.astype(np.int64) * M.n + rows)
+    tri = rng.standard_normal(M.nnz)
+    D = 1e-7 * np.abs(M.vals) * (tri + tri[swap]) / 2.0
+    f = []
+    with torch.no_grad():
+        base = vals.detach().clone()
+        for sgn in (1.0, -1.0):
+            vals.copy_(base + sgn * torch.from_numpy(D).to(dev))
+            Xp, r = S.solve(B.detach().contiguous(), tol=1e-12)
+            assert r.ok
+            f.append(float((Wt * Xp).sum()))
+        vals.copy_(base)
+    fd = (f[0] - f[1]) / 2.0
+    an = float(np.dot(gv, D))
+    assert abs(fd - an) <= 1e-6 * abs(an), (fd, an)
     S.close()

@@ -11,15 +11,12 @@ import pytest
 import scipy.sparse as sp
 
 from oracle import bcg as O
-from paper_1912_11930_gb300 import workloads as W
+from paper_1912_11930_gb300 import bcg, workloads as W
+from parity_check import assert_close, rel_elem, rel_fro as _rel
 
 pytestmark = pytest.mark.gpu
 
 NEVER = 1e-300   # a tolerance no iterate reaches: the solve runs exactly maxit iterations
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.fixture(scope="module")
@@ -77,10 +74,9 @@ def test_fp64_equal_iterations(torch_dev, name, sub, k, p, m):
     B = W.rhs(M.n, k, seed=1)
     X0 = 0.01 * W.rhs(M.n, k, seed=2)
     Xg, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, maxit=m, X0=X0)
-    assert r.status == 5 and r.iters == m            # NOT_CONVERGED after exactly m iterations
+    assert r.status == bcg.NOT_CONVERGED and r.iters == m            # NOT_CONVERGED after exactly m iterations
     ref = O.solve(M.to_scipy(), B, X0=X0, p=p, sub=sub, tol=0.0, maxit=m)
-    err = _rel(Xg, ref.X)
-    assert err <= 1e-9, err
+    assert_close(Xg, ref.X, 1e-9)
 
 
 # last field: compare X at equal iteration counts (not on the variable-coefficient matrix, whose converged
@@ -120,10 +116,10 @@ def test_fp64_converged_counts_and_solution(torch_dev, name, sub, k, p, compare_
         for j, it in enumerate(r.block_iters):
             blk = slice(j * pp, (j + 1) * pp)
             rj = O.solve(A, B[:, blk], p=pp, sub="hybrid", tol=0.0, maxit=it)
-            assert _rel(Xg[:, blk], rj.X) <= 1e-9
+            assert_close(Xg[:, blk], rj.X, 1e-9)
     else:
         rj = O.solve(A, B, p=p, sub=sub, tol=0.0, maxit=r.iters)
-        assert _rel(Xg, rj.X) <= 1e-9
+        assert_close(Xg, rj.X, 1e-9)
 
 
 @pytest.mark.parametrize("kind_name", ["p2d_37x29", "p3d_30", "vc_20"])
@@ -134,9 +130,9 @@ def test_stencil_matches_csr(torch_dev, kind_name):
     B = W.rhs(M.n, k, seed=4)
     a, ra = gpu_solve(torch_dev, M, B, k=k, p=p, sub="hybrid", form="csr", maxit=m)
     b, rb = gpu_solve(torch_dev, M, B, k=k, p=p, sub="hybrid", form="stencil", maxit=m)
-    assert _rel(b, a) <= 1e-11
+    assert_close(b, a, 1e-11)
     ref = O.solve(M.to_scipy(), B, p=p, sub="hybrid", tol=0.0, maxit=m)
-    assert _rel(b, ref.X) <= 1e-9
+    assert_close(b, ref.X, 1e-9)
 
 
 def test_bop_matches_sparse_product(torch_dev):
@@ -149,7 +145,7 @@ def test_bop_matches_sparse_product(torch_dev):
             S = bcg.Solver.from_matrix(M, k=k, p=1, sub="parallel", device=dev)
             Y = S.bop(torch.from_numpy(X).to(dev)).cpu().numpy()
             S.close()
-            assert _rel(Y, M.to_scipy() @ X) <= 1e-14
+            assert_close(Y, M.to_scipy() @ X, 1e-14)
 
 
 def test_deterministic_and_host_entry(torch_dev):
@@ -244,7 +240,7 @@ def test_mixed_precision_refinement(torch_dev, name, sub, k, p, form):
     true = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
     assert np.all(true <= 1.5e-12)
     ref = O.solve(A, B, p=p, sub=sub, tol=1e-13, maxit=5000)
-    assert _rel(X, ref.X) <= 1e-8
+    assert_close(X, ref.X, 1e-8)
     # time-to-1e-8 semantics: the refinement stops once every column's FP64 residual is below tol
     X8, r8 = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, prec="fp32_refine", form=form, tol=1e-8, maxit=5000)
     true8 = np.linalg.norm(B - A @ X8, axis=0) / np.linalg.norm(B, axis=0)
@@ -330,9 +326,9 @@ def test_large_p_equal_iterations(torch_dev, name, sub, k, p, m, prec):
     M = mat(name)
     B = W.rhs(M.n, k, seed=31)
     Xg, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, prec=prec, maxit=m)
-    assert r.status == 5 and r.iters == m
+    assert r.status == bcg.NOT_CONVERGED and r.iters == m
     ref = O.solve(M.to_scipy(), B, p=p, sub=sub, tol=0.0, maxit=m)
-    assert _rel(Xg, ref.X) <= 1e-9
+    assert_close(Xg, ref.X, 1e-9)
 
 
 @pytest.mark.parametrize("sub,k,p", [("classical", 64, 64), ("hybrid", 256, 128), ("global", 256, 64),
@@ -388,7 +384,7 @@ def test_large_p_breakdown_and_frozen_blocks(torch_dev):
     X, r = gpu_solve(torch_dev, M, B, k=128, p=64, sub="hybrid", maxit=m)
     assert r.block_iters[0] == 0 and np.all(X[:, :64] == 0.0)
     ref = O.solve(M.to_scipy(), B[:, 64:], p=64, sub="classical", tol=0.0, maxit=m)
-    assert _rel(X[:, 64:], ref.X) <= 1e-9
+    assert_close(X[:, 64:], ref.X, 1e-9)
 
 
 def test_mixed_graph_replay_matches_plain_launches(torch_dev):
@@ -429,7 +425,7 @@ def test_mixed_strategies_reach_fp64_accuracy(torch_dev, refine):
         assert r.ok, r
         true = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
         assert np.all(true <= 1.5e-12)
-        assert _rel(X, O.solve(A, B, p=p, sub="hybrid", tol=1e-13, maxit=5000).X) <= 1e-8
+        assert_close(X, O.solve(A, B, p=p, sub="hybrid", tol=1e-13, maxit=5000).X, 1e-8)
 
 
 # ---- full size, the configurations bench.py times --------------------------------------------------------------
@@ -444,9 +440,9 @@ def test_full_size_equal_iterations_against_oracle(torch_dev):
     S = bcg.Solver.from_matrix(M, k=k, p=p, sub="hybrid", device=dev)
     X, r = S.solve(torch.from_numpy(B).to(dev), tol=NEVER, maxit=m)
     S.close()
-    assert r.status == 5 and r.iters == m
+    assert r.status == bcg.NOT_CONVERGED and r.iters == m
     ref = O.solve(M.to_scipy(), B, p=p, sub="hybrid", tol=0.0, maxit=m)
-    assert _rel(X.cpu().numpy(), ref.X) <= 1e-9
+    assert_close(X.cpu().numpy(), ref.X, 1e-9)
 
 
 def test_full_size_mixed_poisson128(torch_dev):
@@ -509,7 +505,7 @@ def test_tiny_systems(torch_dev, prec, form):
                 assert r.status == bcg.BREAKDOWN, (M.n, k, p, r)
                 continue
             assert r.ok, (M.n, k, p, r)
-            assert _rel(X.cpu().numpy(), np.linalg.solve(A.toarray(), B)) <= 1e-8
+            assert_close(X.cpu().numpy(), np.linalg.solve(A.toarray(), B), 1e-8)
 
 
 def test_solve_columns_is_r_block_solves(torch_dev):
@@ -534,7 +530,17 @@ def test_solve_columns_is_r_block_solves(torch_dev):
         assert abs(ref.iters - res[g].iters) <= 2
         Xn = X[:, cols].cpu().numpy()
         assert np.all(np.linalg.norm(B[:, cols] - A @ Xn, axis=0) <= 1.5e-9 * np.linalg.norm(B[:, cols], axis=0))
-        assert _rel(Xn, ref.X) <= 1e-6
+        # every block against the oracle at its own (equal) iteration count; the bar is 1e-9, widened to ten
+        # times the oracle's own spread under 1e-16 relative perturbations of B (the log-normal coefficients
+        # amplify rounding over the ~100 iterations of this solve)
+        for j, it in enumerate(res[g].block_iters):
+            blk = slice(j * p, (j + 1) * p)
+            Bj = B[:, cols][:, blk]
+            rj = O.solve(A, Bj, p=p, sub="hybrid", tol=0.0, maxit=int(it), precond="jacobi")
+            spread = max(rel_elem(O.solve(A, Bj * (1 + 1e-16 * np.random.default_rng(sd).standard_normal(Bj.shape)),
+                                          p=p, sub="hybrid", tol=0.0, maxit=int(it), precond="jacobi").X, rj.X)
+                         for sd in range(2))
+            assert_close(Xn[:, blk], rj.X, max(1e-9, 10 * spread), what=f"group {g} block {j} ({it} iterations)")
     with pytest.raises(bcg.BCGError):
         S.solve_columns(Bt[:, :20].contiguous())
     S.close()

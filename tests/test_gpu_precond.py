@@ -12,15 +12,12 @@ import numpy as np
 import pytest
 
 from oracle import bcg as O
-from paper_1912_11930_gb300 import workloads as W
+from paper_1912_11930_gb300 import bcg, workloads as W
+from parity_check import assert_close, rel_fro as _rel
 
 pytestmark = pytest.mark.gpu
 
 NEVER = 1e-300
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.fixture(scope="module")
@@ -77,10 +74,9 @@ def test_jacobi_fp64_equal_iterations(torch_dev, name, form, sub, k, p, m):
     B = W.rhs(M.n, k, seed=1)
     X0 = 0.01 * W.rhs(M.n, k, seed=2)
     Xg, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, form=form, maxit=m, X0=X0)
-    assert r.status == 5 and r.iters == m
+    assert r.status == bcg.NOT_CONVERGED and r.iters == m
     ref = O.solve(M.to_scipy(), B, X0=X0, p=p, sub=sub, tol=0.0, maxit=m, precond="jacobi")
-    err = _rel(Xg, ref.X)
-    assert err <= 1e-9, err
+    assert_close(Xg, ref.X, 1e-9)
 
 
 @pytest.mark.parametrize("name,sub,k,p", [("vc_20", "hybrid", 16, 4), ("s27_15", "hybrid", 16, 16),
@@ -115,7 +111,7 @@ def test_jacobi_mixed_precision(torch_dev, name, form, sub, k, p):
     true = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
     assert np.all(true <= 1.5e-12)
     ref = O.solve(A, B, p=p, sub=sub, tol=1e-13, maxit=5000, precond="jacobi")
-    assert _rel(X, ref.X) <= 1e-8
+    assert_close(X, ref.X, 1e-8)
 
 
 def test_jacobi_option_toggles_and_update_values(torch_dev):
@@ -135,13 +131,13 @@ def test_jacobi_option_toggles_and_update_values(torch_dev):
     S.set_option("precond", 0)
     X_back, _ = S.solve(Bt, tol=NEVER, maxit=m)
     assert torch.equal(X_plain, X_back)
-    assert _rel(X_plain.cpu().numpy(), O.solve(A, B, p=p, sub="hybrid", tol=0.0, maxit=m).X) <= 1e-9
-    assert _rel(X_jac.cpu().numpy(), O.solve(A, B, p=p, sub="hybrid", tol=0.0, maxit=m, precond="jacobi").X) <= 1e-9
+    assert_close(X_plain.cpu().numpy(), O.solve(A, B, p=p, sub="hybrid", tol=0.0, maxit=m).X, 1e-9)
+    assert_close(X_jac.cpu().numpy(), O.solve(A, B, p=p, sub="hybrid", tol=0.0, maxit=m, precond="jacobi").X, 1e-9)
     S.set_option("precond", 1)
     S.update_values(torch.from_numpy(2.0 * M.vals).to(dev))
     X2, _ = S.solve(Bt, tol=NEVER, maxit=m)
     ref2 = O.solve(2.0 * A, B, p=p, sub="hybrid", tol=0.0, maxit=m, precond="jacobi")
-    assert _rel(X2.cpu().numpy(), ref2.X) <= 1e-9
+    assert_close(X2.cpu().numpy(), ref2.X, 1e-9)
     with pytest.raises(bcg.BCGError, match="precond"):
         S.set_option("precond", 2)
     S.close()

@@ -11,15 +11,12 @@ import numpy as np
 import pytest
 
 from oracle import bcg as O
-from paper_1912_11930_gb300 import workloads as W
+from paper_1912_11930_gb300 import bcg, workloads as W
+from parity_check import assert_close, rel_fro as _rel
 
 pytestmark = pytest.mark.gpu
 
 NEVER = 1e-300
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.fixture(scope="module")
@@ -80,9 +77,9 @@ def test_retooled_equal_iterations(torch_dev, name, form, sub, k, p, m):
     B = W.rhs(M.n, k, seed=1)
     X0 = 0.01 * W.rhs(M.n, k, seed=2)
     Xg, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, form=form, maxit=m, X0=X0)
-    assert r.status == 5 and r.iters == m
+    assert r.status == bcg.NOT_CONVERGED and r.iters == m
     ref = O.solve_retooled(M.to_scipy(), B, X0=X0, p=p, sub=sub, tol=0.0, maxit=m)
-    assert _rel(Xg, ref.X) <= 1e-9
+    assert_close(Xg, ref.X, 1e-9)
 
 
 @pytest.mark.parametrize("name,sub,k,p", [("p2d_37x29", "hybrid", 8, 4), ("p3d_30", "hybrid", 32, 8),
@@ -129,7 +126,7 @@ def test_retooled_badly_scaled_columns(torch_dev, k, p, sub):
     assert np.all(res <= 1.5 * tol)
     ref = O.solve_retooled(A, Bs, p=p, sub=sub, tol=tol, maxit=2000)
     assert ref.status == O.OK and abs(ref.iters - rs.iters) <= 2
-    assert _rel(Xs / d[None, :], Xu) <= 1e-5   # both within cond(A) tol of A^{-1} B
+    assert_close(Xs / d[None, :], Xu, 1e-5)   # both within cond(A) tol of A^{-1} B
 
 
 def test_retooled_degenerate_cases_and_arguments(torch_dev):
@@ -143,7 +140,8 @@ def test_retooled_degenerate_cases_and_arguments(torch_dev):
     X, r = gpu_solve(torch_dev, M, Bz, k=8, p=4, sub="hybrid", tol=1e-10, maxit=500)
     assert r.status == bcg.OK and r.block_iters[1] == 0 and np.all(X[:, 4:] == 0.0)
     ref = O.solve_retooled(M.to_scipy(), Bz, p=4, sub="hybrid", tol=1e-10, maxit=500)
-    assert abs(r.iters - ref.iters) <= 2 and _rel(X, ref.X) <= 1e-8
+    assert abs(r.iters - ref.iters) <= 2
+    assert_close(X, ref.X, 1e-8)
     # an all-zero right-hand side: nothing to do
     X, r = gpu_solve(torch_dev, M, np.zeros_like(B), k=8, p=4, sub="hybrid", tol=1e-10, maxit=5)
     assert r.status == bcg.OK and r.iters == 0 and np.all(X == 0.0)
@@ -173,7 +171,7 @@ def test_retooled_degenerate_cases_and_arguments(torch_dev):
     X2, r2 = S.solve(torch.from_numpy(B).to(dev), tol=1e-8, maxit=500)
     S.close()
     assert r1.ok and r2.ok and abs(r1.iters - r2.iters) <= 2
-    assert _rel(X2.cpu().numpy(), X1.cpu().numpy()) <= 1e-7
+    assert_close(X2.cpu().numpy(), X1.cpu().numpy(), 1e-7)
 
 
 def test_retooled_full_size_against_oracle(torch_dev):
@@ -188,6 +186,6 @@ def test_retooled_full_size_against_oracle(torch_dev):
     S.set_option("retooled", 1)
     X, r = S.solve(torch.from_numpy(B).to(dev), tol=NEVER, maxit=m)
     S.close()
-    assert r.status == 5 and r.iters == m
+    assert r.status == bcg.NOT_CONVERGED and r.iters == m
     ref = O.solve_retooled(M.to_scipy(), B, p=p, sub="hybrid", tol=0.0, maxit=m)
-    assert _rel(X.cpu().numpy(), ref.X) <= 1e-9
+    assert_close(X.cpu().numpy(), ref.X, 1e-9)

@@ -5,15 +5,12 @@ import numpy as np
 import pytest
 
 from oracle import bcg as O
-from paper_1912_11930_gb300 import workloads as W
+from paper_1912_11930_gb300 import bcg, workloads as W
+from parity_check import assert_close, rel_fro as _rel
 
 pytestmark = pytest.mark.gpu
 
 NEVER = 1e-300
-
-
-def _rel(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
 @pytest.fixture(scope="module")
@@ -64,9 +61,9 @@ def test_sell_fp64_equal_iterations(torch_dev, name, sub, k, p, sigma, m):
     B = W.rhs(M.n, k, seed=1)
     X0 = 0.01 * W.rhs(M.n, k, seed=2)
     X, r = sell_solve(torch_dev, M, B, k=k, p=p, sub=sub, sigma=sigma, maxit=m, X0=X0)
-    assert r.status == 5 and r.iters == m
+    assert r.status == bcg.NOT_CONVERGED and r.iters == m
     ref = O.solve(M.to_scipy(), B, X0=X0, p=p, sub=sub, tol=0.0, maxit=m)
-    assert _rel(X, ref.X) <= 1e-9
+    assert_close(X, ref.X, 1e-9)
 
 
 def test_sell_bop_and_host_entry(torch_dev):
@@ -77,7 +74,7 @@ def test_sell_bop_and_host_entry(torch_dev):
     X = W.rhs(M.n, k, seed=9)
     S = bcg.Solver.from_matrix(M, k=k, p=4, sub="hybrid", form="sell", sigma=256, device=dev)
     Y = S.bop(torch.from_numpy(X).to(dev)).cpu().numpy()
-    assert _rel(Y, M.to_scipy() @ X) <= 1e-14
+    assert_close(Y, M.to_scipy() @ X, 1e-14)
     B = W.rhs(M.n, k, seed=10)
     Xd, rd = S.solve(torch.from_numpy(B).to(dev), tol=1e-8)
     Xh, rh = S.solve_host(B, np.zeros_like(B), tol=1e-8)
@@ -105,7 +102,7 @@ def test_sell_converged_and_mixed(torch_dev, precond):
                         maxit=5000, precond=precond)
     assert rm.ok
     ref12 = O.solve(A, B, p=p, sub="hybrid", tol=1e-13, maxit=5000, precond=pre)
-    assert _rel(Xm, ref12.X) <= 1e-8
+    assert_close(Xm, ref12.X, 1e-8)
 
 
 def test_sell_update_values(torch_dev):
@@ -120,4 +117,4 @@ def test_sell_update_values(torch_dev):
     X, r = S.solve(torch.from_numpy(B).to(dev), tol=NEVER, maxit=12)
     S.close()
     ref = O.solve(3.0 * M.to_scipy(), B, p=4, sub="hybrid", tol=0.0, maxit=12)
-    assert _rel(X.cpu().numpy(), ref.X) <= 1e-9
+    assert_close(X.cpu().numpy(), ref.X, 1e-9)
