@@ -66,7 +66,7 @@ def rho_in_k3(k, p, prec):
     in K3 of the previous iteration for FP64 with 2 <= p <= 16 in the warp-chunk layout (k even, and k | 32,
     or 32 | k with k / 32 | 8 and p | 32); in K1 otherwise."""
     wc = k <= 256 and k % 2 == 0 and (32 % k == 0 or (k % 32 == 0 and 8 % (k // 32) == 0 and 32 % p == 0))
-    return prec == "fp64" and 2 <= p <= 16 and wc
+    return prec in ("fp64", "fp64_df") and 2 <= p <= 16 and wc
 
 
 def kernel_model(n, k, p, z, s, a_bytes, rho_k3=False):
@@ -415,7 +415,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--grid", type=int, default=WORKLOAD["grid"],
                     help="Poisson grid edge (smaller grids only for profiling captures)")
-    ap.add_argument("--prec", default=WORKLOAD["prec"], choices=["fp64", "fp32_refine"],
+    ap.add_argument("--prec", default=WORKLOAD["prec"], choices=["fp64", "fp32_refine", "fp64_df"],
                     help="precision of the timed solve (profiling captures of the mixed form)")
     ap.add_argument("--workload", default=None, choices=EXTRA_WORKLOADS,
                     help="measure one of the other workloads instead of the default line")
@@ -495,7 +495,7 @@ def main():
     # roofline of the dominant kernel
     # the profiled kernels are the FP64 iteration, or the FP32 inner iteration of the mixed form (FP32 block
     # vectors and an FP32 copy of the CSR values)
-    fp64 = w["prec"] == "fp64"
+    fp64 = w["prec"] in ("fp64", "fp64_df")
     s_bytes = 8 if fp64 else 4
     a_bytes = (12.0 if fp64 else 8.0) * z + 8.0 * (n + 1)
     model = kernel_model(n, k, p, z, s_bytes, a_bytes, rho_k3=rho_in_k3(k, p, w["prec"]))
@@ -541,7 +541,9 @@ def main():
 
     line = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if w["prec"] == "fp64" else "f32 inner, f64 refinement",
+            "vs_baseline": None,
+            "dtype": {"fp64": "f64", "fp64_df": "f64 (double-float block updates)"}.get(w["prec"],
+                                                                                     "f32 inner, f64 refinement"),
             "data": "synthetic",
             "config": {"workload": w["name"], "n": n, "nnz": z, "k": k, "p": p, "subalgebra": w["sub"],
                        "tol": w["tol"], "rhs_per_rank": k, "l2": "inputs larger than L2 (537 MB per block vector)",
@@ -567,9 +569,11 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_variants:
         variants = {}
+        X64 = X.cpu().numpy()   # the timed FP64 solve's solution (parity-tested against the oracle)
         for vname, sub, vp, prec in (("parallel_p1_fp64", "parallel", 1, "fp64"),
                                      ("global_p32_fp64", "global", 32, "fp64"),
-                                     ("hybrid_p8_fp32_refine", "hybrid", 8, "fp32_refine")):
+                                     ("hybrid_p8_fp32_refine", "hybrid", 8, "fp32_refine"),
+                                     ("hybrid_p8_fp64_df", "hybrid", 8, "fp64_df")):
             V = bcg.Solver.from_matrix(M, k=k, p=vp, sub=sub, prec=prec, device=dev)
             Xv = torch.zeros_like(B)
             V.solve(B, Xv, tol=w["tol"], maxit=20000)
@@ -582,10 +586,18 @@ def main():
             torch.cuda.synchronize()
             variants[vname] = {"s": a0.elapsed_time(a1) / 1e3, "iterations": rv.iters, "outer": rv.outer_iters,
                                "status": bcg.STATUS_NAMES[rv.status], "max_rel_res_true": rv.max_rel_res_true}
+            if prec != "fp64" and w["prec"] == "fp64":
+                # the variant's solution against the FP64 solve of the same system (both to 1e-8): relative error,
+                # over the whole block and column by column in the max norm
+                Xn = Xv.cpu().numpy()
+                variants[vname]["rel_err_vs_fp64"] = float(np.linalg.norm(Xn - X64) / np.linalg.norm(X64))
+                variants[vname]["rel_err_vs_fp64_elementwise"] = float(
+                    np.max(np.max(np.abs(Xn - X64), axis=0) / np.max(np.abs(X64), axis=0)))
             V.close()
         variants["hybrid_p8_fp64"] = {"s": ms_max / 1e3, "iterations": iters}
         line["variants"] = variants
         line["mixed_vs_fp64_speedup"] = variants["hybrid_p8_fp64"]["s"] / variants["hybrid_p8_fp32_refine"]["s"]
+        line["df_vs_fp64_speedup"] = variants["hybrid_p8_fp64"]["s"] / variants["hybrid_p8_fp64_df"]["s"]
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample(w["grid"], k, p, w["sub"], ORACLE_SAMPLE_ITERS, seed=0)

@@ -76,13 +76,21 @@ typedef enum {
 typedef enum {
   BCG_FP64 = 0,              /* FP64 iteration vectors and updates, FP64-accurate block products (see
                                 "Arithmetic of the FP64 form" above)                                  */
-  BCG_FP32_REFINE = 1        /* FP32 block CG inside FP64 residual recomputation: operator products
+  BCG_FP32_REFINE = 1,       /* FP32 block CG inside FP64 residual recomputation: operator products
                                 and block updates in FP32, Gram matrices FP64-accurate, p x p
                                 Cholesky/LU solves, the solution and its residual in FP64; residual
                                 replacement or restarted refinement (option "refine"). The FP32
                                 process of block j runs on R_j 2^-sigma_j, an exact scaling with
                                 sigma_j the exponent of the block's largest FP64 column norm, so
                                 FP32's range never limits the scale of B or X                        */
+  BCG_FP64_DF = 2            /* BCG_FP64 with the block updates (BAXPY: X += P lambda, R -= Q lambda,
+                                P = Z + P beta) in double-float arithmetic where the shapes allow it
+                                (2 <= p <= 16 with k | 32 or 32 | k, k even): each sum of p products
+                                is accumulated in float pairs from 48-bit splits of its operands and
+                                added to the FP64 value with two FP64 additions. Error per update
+                                about 2^-46 sum_a |y_a l_ab|, against about p 2^-53 of it with FP64
+                                FMAs; 4 instead of 4 p FP64 operations per element of K2. Other
+                                shapes run BCG_FP64's updates. The retooled form is not available. */
 } bcg_precision;
 
 typedef enum {

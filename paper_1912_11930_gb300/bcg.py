@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libbcg.so")
 OK, INVALID_ARG, CUDA_ERR, OOM, BREAKDOWN, NOT_CONVERGED, NUMERIC, TIMEOUT = range(8)
 STATUS_NAMES = ["OK", "INVALID_ARG", "CUDA", "OOM", "BREAKDOWN", "NOT_CONVERGED", "NUMERIC", "TIMEOUT"]
 SUBALGEBRA = {"hybrid": 0, "global": 1, "parallel": 2, "classical": 3}
-PRECISION = {"fp64": 0, "fp32_refine": 1}
+PRECISION = {"fp64": 0, "fp32_refine": 1, "fp64_df": 2}
 STENCIL = {"5pt_2d": 0, "7pt_3d": 1, "7pt_3d_varcoef": 2}
 
 _lib = None

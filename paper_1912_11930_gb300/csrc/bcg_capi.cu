@@ -172,7 +172,8 @@ bcg_status validate_common(int32_t k, int32_t *p, int32_t sub, int32_t prec, int
   if (*p < 1 || k % *p != 0) return fail(BCG_ERR_INVALID_ARG, "p=%d must divide k=%d", *p, k);
   if (*p > kMaxP && (*p % 32 != 0 || *p > kNT))
     return fail(BCG_ERR_INVALID_ARG, "p=%d: blocks wider than %d must be a multiple of 32 (and <= %d)", *p, kMaxP, kNT);
-  if (prec != BCG_FP64 && prec != BCG_FP32_REFINE) return fail(BCG_ERR_INVALID_ARG, "unknown precision %d", prec);
+  if (prec != BCG_FP64 && prec != BCG_FP32_REFINE && prec != BCG_FP64_DF)
+    return fail(BCG_ERR_INVALID_ARG, "unknown precision %d", prec);
   return BCG_OK;
 }
 
@@ -185,7 +186,8 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CK(stream_grids<double>(h->opkind, h->n, h->k, h->p, h->global, h->nsm, &h->g64));
   // partial rows: every grid that writes them (K0, K1, K2, and K3 for the recomputed rho)
   auto grids_max = [](const StreamGrids &g) {
-    return std::max(std::max(std::max(g.op, g.res), std::max(g.upd, g.upd_zs)), std::max(g.pup, g.pup_zs));
+    return std::max(std::max(std::max(std::max(g.op, g.res), std::max(g.upd, g.upd_zs)), std::max(g.pup, g.pup_zs)),
+                    std::max(std::max(g.upd_df, g.upd_zs_df), std::max(g.pup_df, g.pup_zs_df)));
   };
   int np = grids_max(h->g64);
   if (h->prec == BCG_FP32_REFINE) {
@@ -196,7 +198,7 @@ bcg_status setup_workspace(bcg_ctx *h) {
   const size_t nk = (size_t)h->n * h->k;
   const size_t E = (size_t)h->k * h->p;
   const size_t pp = (size_t)h->nblk * h->p * h->p;
-  if (h->prec == BCG_FP64) {
+  if (h->prec != BCG_FP32_REFINE) {
     // P (and Q, which trades places with P for p > 32) also hold the halo rows of a row-sharded handle
     const size_t nck = (size_t)std::max(h->ncols, h->n) * h->k;
     CKS(h->alloc(&h->R, nk));
@@ -229,7 +231,7 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CKS(h->alloc(&h->bdot_sh, 2 * (size_t)h->k));
   if (h->prec == BCG_FP32_REFINE) CKS(h->alloc(&h->msig, h->k));
   if (small_needs_gws(h->p)) CKS(h->alloc(&h->gws, (size_t)h->nblk * small_ws_doubles(h->p)));
-  if (h->prec == BCG_FP64 && !h->global) {
+  if (h->prec != BCG_FP32_REFINE && !h->global) {
     CKS(h->alloc(&h->dr_C, pp));
     CKS(h->alloc(&h->dr_xi, pp));
     CKS(h->alloc(&h->dr_psiinv, pp));
@@ -280,6 +282,23 @@ ShiftCtl shifts_of(const bcg_ctx *h) {
   return sc;
 }
 
+// The K2 / K3 grids of an iteration in precision T, and whether its block updates run in double-float arithmetic
+// (precision BCG_FP64_DF, where the shapes allow; the partial-row counts of K2 and K3 follow the grid used).
+template <typename T>
+bool df_updates(const bcg_ctx *h, const StreamGrids &g) {
+  return sizeof(T) == 8 && h->prec == BCG_FP64_DF && (h->precond ? g.upd_zs_df : g.upd_df) > 0;
+}
+template <typename T>
+int grid_upd(const bcg_ctx *h, const StreamGrids &g) {
+  if (df_updates<T>(h, g)) return h->precond ? g.upd_zs_df : g.upd_df;
+  return h->precond ? g.upd_zs : g.upd;
+}
+template <typename T>
+int grid_pup(const bcg_ctx *h, const StreamGrids &g) {
+  if (df_updates<T>(h, g)) return h->precond ? g.pup_zs_df : g.pup_df;
+  return h->precond ? g.pup_zs : g.pup;
+}
+
 template <typename T>
 const T *dinv_of(const bcg_ctx *h);
 template <>
@@ -302,7 +321,7 @@ template <typename T>
 bcg_status first_rho_rec(bcg_ctx *h, const T *P, const T *R, const StreamGrids &g) {
   if (!g.rho_k3) return BCG_OK;
   const int *sh = shifts_of<T>(h).sh;
-  CK(launch_bdot<T>(P, R, h->n, h->k, h->p, h->partR, h->precond ? g.pup_zs : g.pup, h->stream,
+  CK(launch_bdot<T>(P, R, h->n, h->k, h->p, h->partR, grid_pup<T>(h, g), h->stream,
                     sh_role(sh, h->k, SH_P), sh_role(sh, h->k, SH_R)));
   return BCG_OK;
 }
@@ -313,7 +332,8 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
                             cudaEvent_t *ev = nullptr) {
   cudaStream_t s = h->stream;
 #define REC(i) do { if (ev) CK(cudaEventRecord(ev[i], s)); } while (0)
-  const int gu = h->precond ? g.upd_zs : g.upd, gp = h->precond ? g.pup_zs : g.pup;
+  const int gu = grid_upd<T>(h, g), gp = grid_pup<T>(h, g);
+  const int df = df_updates<T>(h, g) ? 1 : 0;
   const ShiftCtl sc = shifts_of<T>(h);
   REC(0);
   CK(launch_op_gram<T>(A, P, R, Q, h->n, h->k, h->p, h->global, h->active, h->partA, h->partR, h->st, g.op, s,
@@ -323,14 +343,14 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
                          h->rho_rec, h->st, h->gws, g.alpha_circ, s));
   REC(3); REC(4);
   CK(launch_update_xr<T>(X, R, P, Q, h->n, h->k, h->p, h->global, h->lam, h->active, h->partRho, h->partN, h->st,
-                         gu, s, dinv_of<T>(h), sc.sh));
+                         gu, s, dinv_of<T>(h), sc.sh, df));
   REC(5); REC(6);
   CK(launch_solve_beta(h->partRho, h->partN, gu, gu, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
                        h->active,
                        h->block_iters, h->rho_rec, h->beta, h->st, h->gws, g.rho_circ, s, sc));
   REC(7); REC(8);
   CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv_of<T>(h),
-                        h->partR, sc.sh));
+                        h->partR, sc.sh, df));
   REC(9);
 #undef REC
   return BCG_OK;
@@ -1047,7 +1067,7 @@ bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32
   if (maxit < 1) return fail(BCG_ERR_INVALID_ARG, "maxit must be >= 1");
   g_last_error.clear();
   auto run = [&](const double *Bs, double *Xs) {
-    if (h->prec == BCG_FP64) {
+    if (h->prec != BCG_FP32_REFINE) {
       if (h->retooled) return solve_retooled(h, Bs, Xs, tol, maxit, info);
       return solve_fp64(h, Bs, Xs, tol, maxit, info);
     }

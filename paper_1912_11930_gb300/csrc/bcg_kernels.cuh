@@ -231,6 +231,64 @@ struct Gram<double> {
   }
 };
 
+// ---- Double-float block updates (precision BCG_FP64_DF) ----------------------------------------------------
+// A block update out_b = base_b + sum_a y_a l_ab (BAXPY) with the p products off the FP64 pipe: y_a and l_ab are
+// split into 48-bit float pairs (after exact power-of-two shifts that put them inside FP32's range), the products
+// are accumulated as one float pair (s, c) exactly as the Gram entries are (TwoProd of the high parts, the two
+// cross terms, TwoSum), and s 2^t and c 2^t are added to the FP64 base with two FP64 additions. The error of the
+// increment is about 2^-46 sum_a |y_a l_ab| (FP64 FMAs: about p 2^-53 of it).
+
+// x 2^-sh as a float pair, branch-free: a normal x whose scaled value lies in [2^-74, 2^128) gives the split of
+// split_f64; a scaled value below 2^-74, zero or subnormal gives (0, 0); above the range or non-finite, (+-inf, 0).
+// The update operands are scaled by their columns' shifts (about 2^10 times the column norm), so only entries
+// more than 2^84 below their column's norm are flushed: far below FP64's own norm-wise update error.
+__device__ __forceinline__ float2 split_f64_ftz(double x, int sh) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi32 = (unsigned)(u >> 32);
+  const int ef = (int)((hi32 >> 20) & 0x7FFu);
+  const int e = ef - sh;
+  const unsigned sign = hi32 & 0x80000000u;
+  const bool ok = (unsigned)(ef - 1) < 0x7FEu && (unsigned)(e - 949) <= 201u;
+  const bool big = ef == 0x7FF || (ef != 0 && e > 1150);
+  const unsigned hib = sign | ((unsigned)(e - 896) << 23) | (unsigned)((u >> 29) & 0x7FFFFFu);
+  const unsigned rem = (unsigned)(u & 0x1FFFFFFFu);
+  const int msb = 31 - __clz(rem);
+  const unsigned mant = msb >= 23 ? rem >> (msb - 23) : rem << (23 - msb);
+  const unsigned lob = sign | ((unsigned)(msb + e - 948) << 23) | (mant & 0x7FFFFFu);
+  const float hi = ok ? __uint_as_float(hib) : (big ? __uint_as_float(sign | 0x7F800000u) : 0.0f);
+  return make_float2(hi, (ok && rem != 0u) ? __uint_as_float(lob) : 0.0f);
+}
+
+// v 2^t as a double, built from the bit pattern with integer operations and selects only (no conversion
+// instruction, which would occupy the FP64 pipe): a non-finite v stays non-finite, an overflow gives +-inf, and
+// a zero or subnormal v, or an underflow, gives 0 (the pair being converted is an accumulator of products of
+// magnitude 2^-102 and more, so a subnormal part carries nothing).
+__device__ __forceinline__ double f2d_scaled(float v, int t) {
+  const unsigned u = __float_as_uint(v);
+  const int ex = (int)((u >> 23) & 0xFFu);
+  int eb = ex + 896 + t;   // biased FP64 exponent of v 2^t
+  eb = ex == 0xFF ? 0x7FF : min(eb, 0x7FF);
+  const unsigned man = (eb == 0x7FF && ex != 0xFF) ? 0u : (u & 0x7FFFFFu);
+  const unsigned hi = (u & 0x80000000u) | ((unsigned)max(eb, 0) << 20) | (man >> 3);
+  return (ex == 0 || eb <= 0) ? 0.0 : __hiloint2double((int)hi, (int)(man << 29));
+}
+
+// Column b of a p x p update matrix for the float-pair products y_a l_ab, y_a taken at the column shifts sh of
+// block j (y~_a = y_a 2^-sh_a): out[a] = the float pair of l_ab 2^(sh_a - t), with t = max_a (exponent of l_ab +
+// sh_a), so that every |y~_a l~_ab| <= 2^(kGramCenter + 2) and sum_a y_a l_ab = 2^t sum_a y~_a l~_ab. Returns t.
+template <int PM>
+__device__ __forceinline__ int df_matrix_col(const double (&l)[PM], int p, const int *__restrict__ sh, int j,
+                                             float2 (&out)[PM]) {
+  int t = -2 * kGramShiftMax - 2000;
+#pragma unroll
+  for (int a = 0; a < PM; ++a)
+    if (a < p && l[a] != 0.0) t = max(t, exponent_of(fabs(l[a])) + shift_at(sh, j * p + a));
+  if (t < -2 * kGramShiftMax - 1000) t = 0;   // an all-zero column
+#pragma unroll
+  for (int a = 0; a < PM; ++a) out[a] = a < p ? split_f64(l[a], t - shift_at(sh, j * p + a)) : make_float2(0.0f, 0.0f);
+  return t;
+}
+
 // Read row[a] for a < PM from shared memory, 16 bytes at a time when the row start is aligned.
 template <typename E, int PM>
 __device__ __forceinline__ void load_row(const E *row, E (&out)[PM], int p) {

@@ -373,18 +373,25 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_op<T, OPK, PM, RR>()) kw_op_g
 // K2 keeps fewer live values than K1: its unpreconditioned FP32 instantiations up to p = 8 fit 64 registers
 // (4 CTAs per SM); the FP64 one at p = 16 runs better at 2 CTAs without spills than at 3 with them
 // (3.61 / 3.71 ms, 128^3, k = 32)
-template <typename T, int PM, bool ZS>
+// The double-float instantiations are bound by instruction issue, not by the FP64 pipe: 2 CTAs per SM without
+// spills rather than 3 with them.
+template <typename T, int PM, bool ZS, bool DF = false>
 constexpr int wc_min_ctas_upd() {
-  return (sizeof(T) == 4 && PM <= 8 && !ZS) ? 4 : ((sizeof(T) == 8 && PM == 16) ? 2 : wc_min_ctas<PM>());
+  return DF ? 2 : (sizeof(T) == 4 && PM <= 8 && !ZS) ? 4 : ((sizeof(T) == 8 && PM == 16) ? 2 : wc_min_ctas<PM>());
 }
 
-template <typename T, int PM, int V, bool ZS>
-__global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_xr(T *__restrict__ X, T *__restrict__ R, const T *__restrict__ P,
+// DF (FP64, p >= 2): the two BAXPYs in double-float arithmetic (bcg_kernels.cuh); the P and Q tiles then hold
+// float pairs of P and Q scaled by their columns' P- and Q-role shifts (shPr, shQr, which differ by one uniform
+// offset), and lambda's column is normalised into float pairs once per thread.
+template <typename T, int PM, int V, bool ZS, bool DF = false>
+__global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS, DF>()) kw_update_xr(T *__restrict__ X, T *__restrict__ R, const T *__restrict__ P,
                                                     const T *__restrict__ Q, int64_t n, int k, int p, int global,
                                                     const double *__restrict__ lam, const int *__restrict__ active,
                                                     double *__restrict__ partRho, double *__restrict__ partN,
                                                     const DevStatus *__restrict__ st, const T *__restrict__ dinv,
-                                                    const int *__restrict__ shZ, const int *__restrict__ shR) {
+                                                    const int *__restrict__ shZ, const int *__restrict__ shR,
+                                                    const int *__restrict__ shPr, const int *__restrict__ shQr) {
+  static_assert(!DF || sizeof(T) == 8, "double-float updates replace FP64 arithmetic");
   using G = Gram<T>;
   using BT = typename G::B;
   using VT = typename VecOf<T, V>::type;
@@ -422,6 +429,23 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_x
 #pragma unroll
     for (int a = 0; a < PM; ++a) lcol[a] = a < p ? lj[a * p] : T(0);
   }
+  // DF: lambda's column as float pairs, the block shifts of this lane's memory-phase columns (tile writes) and
+  // the output exponents of its compute-phase column (X += 2^tx (s + c), R -= 2^tr (s' + c'))
+  float2 lpair[DF ? PM : 1];
+  int dfSPm[DF ? V : 1], dfSQm[DF ? V : 1], dfTx = 0, dfTr = 0;
+  if constexpr (DF) {
+    int64_t row0;
+    int mc0;
+    geo.mem_pos(0, row0, mc0);
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+      dfSPm[v] = shift_at(shPr, mc0 + v);
+      dfSQm[v] = shift_at(shQr, mc0 + v);
+    }
+    dfTx = df_matrix_col<PM>(lcol, p, shPr, j, lpair);
+    dfTr = dfTx + (shift_at(shQr, c) - shift_at(shPr, c));   // Q~ = Q 2^-(shP + dA): R's increment scales by 2^dA
+  }
+  float2 *sPf = reinterpret_cast<float2 *>(sP), *sQf = reinterpret_cast<float2 *>(sQ);
   GramAcc<PMH> acc;
   acc.zero();
   float ns = 0.0f, nc = 0.0f;
@@ -448,8 +472,13 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_x
     for (int v = 0; v < V; ++v) {
       sX[tm + v] = xv.e[v];
       sR[tm + v] = rv.e[v];
-      sP[tm + v] = pv.e[v];
-      sQ[tm + v] = qv.e[v];
+      if constexpr (DF) {
+        sPf[tm + v] = split_f64_ftz(pv.e[v], dfSPm[v]);
+        sQf[tm + v] = split_f64_ftz(qv.e[v], dfSQm[v]);
+      } else {
+        sP[tm + v] = pv.e[v];
+        sQ[tm + v] = qv.e[v];
+      }
     }
     __syncwarp();
     // BAXPY x 2 for each sub-pass; the new residual is written as its broadcast representation
@@ -457,7 +486,22 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_x
     for (int s = 0; s < V; ++s) {
       const int t = 32 * s + geo.lane;
       T x = sX[t], r = sR[t];
-      if (act) {
+      if constexpr (DF) {
+        if (act) {
+          float2 prow[PM], qrow[PM];
+          load_row<float2, PM>(sPf + t - b, prow, p);
+          load_row<float2, PM>(sQf + t - b, qrow, p);
+          float xs = 0.0f, xc = 0.0f, rs = 0.0f, rc = 0.0f;
+#pragma unroll
+          for (int a = 0; a < PM; ++a)
+            if (a < p) {
+              Gram<double>::add(xs, xc, prow[a], lpair[a]);
+              Gram<double>::add(rs, rc, qrow[a], lpair[a]);
+            }
+          x = (x + f2d_scaled(xs, dfTx)) + f2d_scaled(xc, dfTx);
+          r = (r - f2d_scaled(rs, dfTr)) - f2d_scaled(rc, dfTr);
+        }
+      } else if (act) {
         T prow[PM], qrow[PM];
         load_row<T, PM>(sP + t - b, prow, p);
         load_row<T, PM>(sQ + t - b, qrow, p);
@@ -517,12 +561,15 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS>()) kw_update_x
 // RR: also the recomputed rho of the next iteration, <<P_new, R>>_S (Algorithm 1 recomputes
 // rho^{i-1} = <<P^i, R^{i-1}>>_S; both operands are in this kernel's registers, and its FP32 pipes are idle
 // while it waits on the FP64 pipe or on HBM). Partials as in K1, entry (a, b) of block j at j*p*p + b*p + a.
-template <typename T, int PM, int V, bool ZS, bool RR>
+// DF (FP64, p >= 2): the BAXPY in double-float arithmetic as in K2; the P tile then holds float pairs of P at its
+// columns' shifts, and a frozen block's rows are not rewritten (its P stays as it is in memory).
+template <typename T, int PM, int V, bool ZS, bool RR, bool DF = false>
 __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *__restrict__ R, int64_t n, int k,
                                                    int p, int global, const double *__restrict__ beta,
                                                    const int *__restrict__ active, DevStatus *__restrict__ st,
                                                    const T *__restrict__ dinv, double *__restrict__ partR,
                                                    const int *__restrict__ shP, const int *__restrict__ shR) {
+  static_assert(!DF || sizeof(T) == 8, "double-float updates replace FP64 arithmetic");
   using G = Gram<T>;
   using BT = typename G::B;
   using VT = typename VecOf<T, V>::type;
@@ -565,6 +612,21 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
   const int sPn = (G::kShifted && RR) ? shift_at(shP, c) : 0;
   const int syR = (G::kShifted && RR) ? shift_at(shR, c) : 0;
   auto sxP = [&](int a) { return shift_at(shP, j * p + a); };
+  // DF: beta's column as float pairs, the block shift of this lane's memory-phase columns and whether their block
+  // still iterates, and the output exponent of its compute-phase column (P = Z + 2^t (s + c))
+  float2 bpair[DF ? PM : 1];
+  int dfSPm[DF ? V : 1], dfT = 0;
+  bool act_m = true;
+  if constexpr (DF) {
+    int64_t row0;
+    int mc0;
+    geo.mem_pos(0, row0, mc0);
+#pragma unroll
+    for (int v = 0; v < V; ++v) dfSPm[v] = shift_at(shP, mc0 + v);
+    act_m = block_active(active, global, mc0 / p);
+    dfT = df_matrix_col<PM>(bcol, p, shP, j, bpair);
+  }
+  float2 *sPf = reinterpret_cast<float2 *>(sP);
   int pass = 0;
   const int kv = k / V;
   for (int64_t rb = geo.rb0; rb < geo.nrb; rb += geo.rbs) {
@@ -590,7 +652,8 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
     const int tm = 32 * geo.sm + geo.om;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      sP[tm + v] = pv.e[v];
+      if constexpr (DF) sPf[tm + v] = split_f64_ftz(pv.e[v], dfSPm[v]);
+      else sP[tm + v] = pv.e[v];
       sR[tm + v] = zv.e[v];
       if constexpr (RR && ZS) sRb[tm + v] = G::conv(rv.e[v], G::kShifted ? s_shR[mc + v] : 0);
     }
@@ -598,8 +661,18 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
 #pragma unroll
     for (int s = 0; s < V; ++s) {
       const int t = 32 * s + geo.lane;
-      T out = sP[t];
-      if (act) {
+      T out = DF ? T(0) : sP[t];
+      if constexpr (DF) {
+        if (act) {
+          float2 prow[PM];
+          load_row<float2, PM>(sPf + t - b, prow, p);
+          float ps = 0.0f, pc = 0.0f;
+#pragma unroll
+          for (int a = 0; a < PM; ++a)
+            if (a < p) Gram<double>::add(ps, pc, prow[a], bpair[a]);
+          out = (sR[t] + f2d_scaled(ps, dfT)) + f2d_scaled(pc, dfT);
+        }
+      } else if (act) {
         T prow[PM];
         load_row<T, PM>(sP + t - b, prow, p);
         out = sR[t];
@@ -629,7 +702,7 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
         gram_flush<T>(acc, slotR, p, sxP, syR);
       }
     }
-    if (row < n) {
+    if (row < n && act_m) {
       VecU<T, V> po;
 #pragma unroll
       for (int v = 0; v < V; ++v) po.e[v] = sN[tm + v];

@@ -26,6 +26,7 @@ struct StreamGrids {
   int pup;       // K3 CTAs
   int upd_zs;    // K2 CTAs, Jacobi-preconditioned instantiation
   int pup_zs;    // K3 CTAs, Jacobi-preconditioned instantiation
+  int upd_df, upd_zs_df, pup_df, pup_zs_df;   // the same with double-float updates (0: not available)
   int res;       // K0 CTAs
   int alpha_circ;   // K1 stores alpha by circulant diagonals (symmetric product, half the terms)
   int rho_circ;     // K2 stores rho by circulant diagonals
@@ -42,15 +43,18 @@ cudaError_t launch_op_gram(const OpDesc &A, const T *P, const T *R, T *Q, int64_
                            cudaStream_t s, const int *sh);
 // dinv (optional, n values): inverse diagonal of the Jacobi preconditioner; Z = M^{-1} R is formed on the
 // fly where Algorithm 1 needs it (NULL: M = I).
+// df: the block updates in double-float arithmetic (FP64 data, 2 <= p <= 32 warp-chunk shapes; elsewhere the
+// FP64 kernels run); grid must then be the df grid of StreamGrids.
 template <typename T>
 cudaError_t launch_update_xr(T *X, T *R, const T *P, const T *Q, int64_t n, int k, int p, int global,
                              const double *lam, const int *active, double *partRho, double *partN,
-                             const DevStatus *st, int grid, cudaStream_t s, const T *dinv, const int *sh);
+                             const DevStatus *st, int grid, cudaStream_t s, const T *dinv, const int *sh,
+                             int df = 0);
 template <typename T>
 // partR: with rho_k3, the partials of the next iteration's recomputed rho <<P_new, R>>_S (one row per CTA)
 cudaError_t launch_update_p(T *P, const T *R, int64_t n, int k, int p, int global, const double *beta,
                             const int *active, DevStatus *st, int grid, cudaStream_t s, const T *dinv,
-                            double *partR, const int *sh);
+                            double *partR, const int *sh, int df = 0);
 template <typename T>
 // sig (optional): R32 and P32 receive R 2^-sigma_c (the mixed form's scale)
 cudaError_t launch_residual(const OpDesc &A, const T *X, const T *B, T *R, T *P, float *R32, float *P32, int64_t n,
