@@ -179,50 +179,74 @@ class Result:
     history: dict = field(default_factory=dict)
 
 
+def _preconditioner(A, precond: str):
+    """z = M^{-1} r for M = I ("none") or M = diag(A) ("jacobi"); always a fresh array."""
+    if precond == "jacobi":
+        dinv = 1.0 / np.asarray(A.diagonal(), dtype=np.float64)
+        return lambda M_: M_ * dinv[:, None]
+    if precond == "none":
+        return lambda M_: M_.copy()
+    raise ValueError(f"unknown preconditioner {precond!r}")
+
+
+def _column_norms(M: np.ndarray) -> np.ndarray:
+    return np.sqrt(np.sum(M * M, axis=0))
+
+
+def _converged_blocks(rn, r0, tol, kind, p, q):
+    """Reading R5: a block has converged when every one of its columns has ||R_s|| <= tol ||R_s^0||; the global
+    subalgebra has one block made of all columns."""
+    col_ok = rn <= tol * r0
+    if kind == "hybrid":
+        return np.array([bool(np.all(col_ok[j * p:(j + 1) * p])) for j in range(q)])
+    return np.array([bool(np.all(col_ok))])
+
+
+def _step_length(P, AP, R, p, kind, active):
+    """The S-valued step along P that makes the new residual S-orthogonal to P: lambda = <<P, A P>>^{-1} <<P, R>>.
+    The second product is formed afresh from the current P and R (the recomputation of Section 3) and also
+    returned, since the direction coefficient divides by it (reading R3). Returns (alpha, <<P, R>>, lambda, ok)."""
+    curv = block_product(P, AP, p, kind)
+    proj = block_product(P, R, p, kind)
+    lam, ok = bsolve_cholesky(curv, proj, active)
+    return curv, proj, lam, ok
+
+
+def _direction_weight(proj, Z, R, p, kind, active):
+    """The S-valued weight of the old direction in the new one: beta = <<P, R_old>>^{-1} <<Z, R>>, by LU with
+    partial pivoting (reading R4). Returns (<<Z, R>>, beta, ok)."""
+    zr = block_product(Z, R, p, kind)
+    beta, ok = bsolve_lu(proj, zr, active)
+    return zr, beta, ok
+
+
 def solve(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, sub: str = "hybrid",
           tol: float = 1e-8, maxit: int = 1000, record: bool = False, precond: str = "none") -> Result:
-    """Algorithm 1 of Section 3, FP64, step by step.
+    """Block CG in a *-subalgebra S (Algorithm 1 of Section 3), FP64.
+
+    Conjugate directions in the S-module sense: from R = B - A X and the first direction P = M^{-1} R, every
+    iteration applies A to P, moves X by P lambda and R by -(A P) lambda with the step lambda of _step_length, stops
+    the blocks whose columns meet the stopping rule, and forms the next direction M^{-1} R + P beta with the weight
+    of _direction_weight (the "+" of reading R1). All products are S-products (block_product); all coefficients are
+    elements of S, given by their distinct p x p blocks.
 
     ``A`` is a scipy sparse matrix (or anything supporting ``A @ X``); B and X0 are n x k.
-    ``precond``: "none" (M = I) or "jacobi" (M = diag(A), applied as Z = M^{-1} R)."""
+    ``precond``: "none" (M = I) or "jacobi" (M = diag(A))."""
     B = np.asarray(B, dtype=np.float64)
     n, k = B.shape
     kind, p = canonical_subalgebra(sub, k, p)
     q = k // p
     nblk = q if kind == "hybrid" else 1
     X = np.zeros_like(B) if X0 is None else np.array(X0, dtype=np.float64, copy=True)
-
+    minv = _preconditioner(A, precond)
     hist = {"X": [], "R": [], "P": [], "Q": [], "alpha": [], "rho_rec": [], "rho": []} if record else {}
 
-    def colnorms(M):
-        return np.sqrt(np.sum(M * M, axis=0))
-
-    if precond == "jacobi":
-        dinv = 1.0 / np.asarray(A.diagonal(), dtype=np.float64)
-
-        def apply_minv(M_):
-            return M_ * dinv[:, None]
-    elif precond == "none":
-        def apply_minv(M_):
-            return M_.copy()
-    else:
-        raise ValueError(f"unknown preconditioner {precond!r}")
-
-    # R^0 = B - A X^0
     R = B - bop(A, X)
-    # P^1 = M^{-1} R^0
-    P = apply_minv(R)
-    r0 = colnorms(R)
+    P = minv(R)
+    r0 = _column_norms(R)
     if not (np.all(np.isfinite(r0)) and np.all(np.isfinite(X))):
         return Result(X, NUMERIC, 0, np.zeros(nblk, dtype=np.int64), -1, r0 * np.nan, r0 * np.nan, hist)
-
-    def block_converged(rn):
-        col_ok = rn <= tol * r0
-        if kind == "hybrid":
-            return np.array([bool(np.all(col_ok[j * p:(j + 1) * p])) for j in range(q)])
-        return np.array([bool(np.all(col_ok))])
-
-    active = ~block_converged(r0)
+    active = ~_converged_blocks(r0, r0, tol, kind, p, q)
     block_iters = np.zeros(nblk, dtype=np.int64)
     status, brk, it = OK, -1, 0
     if record:
@@ -231,47 +255,36 @@ def solve(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, sub: str =
     while np.any(active) and it < maxit:
         it += 1
         block_iters[active] = it
-        # Q^i = A P^i
-        Q = bop(A, P)
-        # alpha^i = <<P^i, Q^i>>
-        alpha = block_product(P, Q, p, kind)
-        # rho^{i-1} = <<P^i, R^{i-1}>>  (recomputed)
-        rho_rec = block_product(P, R, p, kind)
-        # lambda^i = (alpha^i)^{-1} rho^{i-1}
-        lam, ok = bsolve_cholesky(alpha, rho_rec, active)
+        AP = bop(A, P)
+        curv, proj, lam, ok = _step_length(P, AP, R, p, kind, active)
         if not ok:
             status, brk = BREAKDOWN, it
             break
-        # X^i = X^{i-1} + P^i lambda^i ;  R^i = R^{i-1} - Q^i lambda^i
         X = baxpy(X, P, lam, +1.0)
-        R = baxpy(R, Q, lam, -1.0)
-        rn = colnorms(R)
+        R = baxpy(R, AP, lam, -1.0)
+        rn = _column_norms(R)
         if not np.all(np.isfinite(rn)):
             status = NUMERIC
             break
-        active = active & ~block_converged(rn)
-        # Z^{i+1} = M^{-1} R^i ; rho^i = <<Z^{i+1}, R^i>>
-        Z = apply_minv(R)
-        rho = block_product(Z, R, p, kind)
-        # beta^i = (rho^{i-1})^{-1} rho^i
-        beta, ok = bsolve_lu(rho_rec, rho, active)
+        active = active & ~_converged_blocks(rn, r0, tol, kind, p, q)
+        Z = minv(R)
+        zr, beta, ok = _direction_weight(proj, Z, R, p, kind, active)
         if record:
-            hist["Q"].append(Q.copy()); hist["alpha"].append(alpha); hist["rho_rec"].append(rho_rec)
-            hist["rho"].append(rho)
+            hist["Q"].append(AP.copy()); hist["alpha"].append(curv); hist["rho_rec"].append(proj)
+            hist["rho"].append(zr)
         if not ok:
             status, brk = BREAKDOWN, it
             break
-        # P^{i+1} = Z^{i+1} + P^i beta^i   (sign reading R1)
         P = baxpy(Z, P, beta, +1.0)
         if record:
             hist["X"].append(X.copy()); hist["R"].append(R.copy()); hist["P"].append(P.copy())
 
     if status == OK and np.any(active):
         status = NOT_CONVERGED
-    rn = colnorms(R)
+    rn = _column_norms(R)
     with np.errstate(invalid="ignore", divide="ignore"):
         rel_rec = np.where(r0 > 0, rn / np.where(r0 > 0, r0, 1.0), 0.0)
-        rt = colnorms(B - bop(A, X))
+        rt = _column_norms(B - bop(A, X))
         rel_true = np.where(r0 > 0, rt / np.where(r0 > 0, r0, 1.0), rt)
     return Result(X, status, it, block_iters, brk, rel_rec, rel_true, hist)
 
