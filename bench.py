@@ -132,9 +132,9 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def oracle_sample(grid, k, p, sub, iters, seed):
-    """Time the CPU oracle on `iters` iterations of the workload in a fresh single-threaded process.
-    Returns (seconds per iteration, seconds of the sample)."""
+def oracle_sample(grid, k, p, sub, iters, seed, threads=1):
+    """Time the CPU oracle on `iters` iterations of the workload in a fresh process limited to `threads` BLAS /
+    OpenMP threads. Returns (seconds per iteration, seconds of the sample)."""
     code = f"""
 import json, sys, time
 sys.path.insert(0, {ROOT!r})
@@ -150,7 +150,8 @@ O.solve(A, B, p={p}, sub={sub!r}, tol=0.0, maxit={1 + iters})
 t2 = time.perf_counter()
 print(json.dumps(dict(per_iter=((t2 - t1) - (t1 - t0)) / {iters}, first=t1 - t0, total=t2 - t0)))
 """
-    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads), OPENBLAS_NUM_THREADS=str(threads),
+               MKL_NUM_THREADS=str(threads))
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
@@ -405,6 +406,106 @@ def run_extra(name, args):
     print(json.dumps(out), flush=True)
 
 
+def config_variants(bcg, W, torch, dev, np):
+    """The other configurations of the benchmark, one solve each (after the timed line; CUDA events on the solver's
+    stream): 2D 64^2 in three subalgebras; the 160^3 variable-coefficient problem in the mixed form (to 1e-10 and
+    1e-8) and in FP64 (to 1e-8); the differentiable 100^3 27-point solve (forward, adjoint, gradient); k = 256 at
+    96^3 for p = 1, 32, 256 in FP64 and in the mixed form. Every mixed or double-float result carries its relative
+    error against the FP64 solve of the same system (the FP64 form is parity-tested against the oracle)."""
+    out = {}
+
+    def rel_errs(Xa, Xb):
+        a, b = Xa.cpu().numpy(), Xb.cpu().numpy()
+        return {"rel_err_vs_fp64": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+                "rel_err_vs_fp64_elementwise": float(np.max(np.max(np.abs(a - b), axis=0) /
+                                                            np.maximum(np.max(np.abs(b), axis=0), 1e-300)))}
+
+    def row(t, r, **kw):
+        d = dict(kw, s=t, iterations=r.iters, outer=r.outer_iters, status=bcg.STATUS_NAMES[r.status],
+                 max_rel_res_true=r.max_rel_res_true)
+        print(json.dumps(d), file=sys.stderr, flush=True)
+        return d
+
+    def guarded(name, fn):
+        try:
+            out[name] = fn()
+        except Exception as e:   # a failing variant must not take the default line with it
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+
+    def cfg1():
+        M = W.poisson2d(64)
+        B = torch.from_numpy(W.rhs(M.n, 8, seed=0)).to(dev)
+        rows = []
+        for sub, p in (("hybrid", 4), ("global", 4), ("parallel", 1)):
+            t, r, _ = time_solve(bcg, torch, M, B, k=8, p=p, sub=sub, prec="fp64", reps=3, dev=dev)
+            rows.append(row(t, r, sub=sub, p=p, prec="fp64", tol=1e-8))
+        return {"workload": "poisson2d_64_csr_k8", "n": M.n, "results": rows}
+
+    def cfg3():
+        M = W.varcoef3d(160, seed=0)
+        k, p = 64, 16
+        B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev)
+        rows, X = [], {}
+        for prec, tol in (("fp64", 1e-8), ("fp32_refine", 1e-8), ("fp32_refine", 1e-10)):
+            t, r, Xr = time_solve(bcg, torch, M, B, k=k, p=p, sub="hybrid", prec=prec, form="stencil", tol=tol, reps=1,
+                                  dev=dev, warm=False)
+            rows.append(row(t, r, prec=prec, tol=tol))
+            if prec != "fp64":
+                rows[-1].update(rel_errs(Xr, X["fp64"]))
+            else:
+                X["fp64"] = Xr
+        del B, X
+        return {"workload": "varcoef3d_160_stencil_k64_hybrid_p16", "n": M.n, "results": rows,
+                "mixed_vs_fp64_speedup_at_1e8": rows[0]["s"] / rows[1]["s"]}
+
+    def cfg4():
+        from paper_1912_11930_gb300.autograd import bcg_solve_autograd
+        M = W.stencil27(100, seed=0)
+        k = 16
+        vals = torch.from_numpy(M.vals.copy()).to(dev).requires_grad_(True)
+        csr = (torch.from_numpy(M.rowptr).to(dev), torch.from_numpy(M.colind).to(dev), vals)
+        S = bcg.Solver(k=k, p=16, sub="hybrid", csr=csr, device=dev)
+        B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev).requires_grad_(True)
+        Wt = torch.from_numpy(W.loss_weights(M.n, k, seed=0)).to(dev)
+        times = []
+        for rep in range(2):
+            vals.grad = None
+            B.grad = None
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            X = bcg_solve_autograd(vals, B, S, tol=1e-8)
+            (Wt * X).sum().backward()
+            torch.cuda.synchronize()
+            times.append(time.perf_counter() - t0)
+        S.close()
+        return {"workload": "stencil27_100_csr_k16_hybrid_p16_forward_adjoint_gradient", "n": M.n, "nnz": M.nnz,
+                "s": times[-1], "note": "forward solve + adjoint solve + gradient kernel, tol 1e-8 (second run)"}
+
+    def cfg5():
+        M = W.poisson3d(96)
+        k = 256
+        B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev)
+        rows = []
+        for p, sub in ((1, "parallel"), (32, "hybrid"), (256, "classical")):
+            X64 = None
+            for prec in ("fp64", "fp32_refine"):
+                t, r, Xr = time_solve(bcg, torch, M, B, k=k, p=p, sub=sub, prec=prec, reps=1, dev=dev, warm=False)
+                rows.append(row(t, r, p=p, sub=sub, prec=prec, tol=1e-8))
+                if prec == "fp64":
+                    X64 = Xr
+                else:
+                    rows[-1].update(rel_errs(Xr, X64))
+            del X64
+        del B
+        return {"workload": "poisson3d_96_csr_k256", "n": M.n, "results": rows}
+
+    for name, fn in (("poisson2d_64_k8", cfg1), ("varcoef3d_160_k64", cfg3), ("stencil27_100_k16_autograd", cfg4),
+                     ("poisson3d_96_k256", cfg5)):
+        guarded(name, fn)
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -413,6 +514,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-configs", action="store_true", help="skip the other configurations after the variants")
     ap.add_argument("--grid", type=int, default=WORKLOAD["grid"],
                     help="Poisson grid edge (smaller grids only for profiling captures)")
     ap.add_argument("--prec", default=WORKLOAD["prec"], choices=["fp64", "fp32_refine", "fp64_df"],
@@ -598,6 +700,8 @@ def main():
         line["variants"] = variants
         line["mixed_vs_fp64_speedup"] = variants["hybrid_p8_fp64"]["s"] / variants["hybrid_p8_fp32_refine"]["s"]
         line["df_vs_fp64_speedup"] = variants["hybrid_p8_fp64"]["s"] / variants["hybrid_p8_fp64_df"]["s"]
+        if not args.no_configs:
+            line["configs"] = config_variants(bcg, W, torch, dev, np)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         smp = oracle_sample(w["grid"], k, p, w["sub"], ORACLE_SAMPLE_ITERS, seed=0)
@@ -607,6 +711,14 @@ def main():
                                           f"({smp['total']:.1f} s, single-threaded); time-to-tolerance = initial "
                                           f"residual + per-iteration time x the GPU's {iters} iterations",
                                 "per_iter_s": smp["per_iter"]}
+        ncores = len(os.sched_getaffinity(0))
+        sma = oracle_sample(w["grid"], k, p, w["sub"], ORACLE_SAMPLE_ITERS, seed=0, threads=ncores)
+        line["cpu_baseline_all_cores"] = {"value": sma["first"] + sma["per_iter"] * iters, "unit": "s",
+                                          "cores": ncores, "kind": "oracle",
+                                          "sample": f"as cpu_baseline with {ncores} BLAS / OpenMP threads (the oracle's "
+                                                    f"sparse products are single-threaded in scipy; its dense block "
+                                                    f"products use the threads) ({sma['total']:.1f} s)",
+                                          "per_iter_s": sma["per_iter"]}
     S.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

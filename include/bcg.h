@@ -374,6 +374,15 @@ bcg_status bcg_rows_finish(bcg_handle h, bcg_info *info);
 /* bcg_last_error -- message of the calling thread's most recent failure ("" if none). */
 const char *bcg_last_error(void);
 
+/*
+ * bcg_debug_fail_alloc -- failure injection for tests of the error paths (not part of the paper's method): after
+ * bcg_debug_fail_alloc(N), N >= 1, the N-th device workspace allocation made by the library from then on (in any
+ * handle, any thread) fails as if cudaMalloc had run out of memory, so the call making it returns BCG_ERR_OOM
+ * and frees everything it had allocated; the injection then disarms. N = 0 disarms it. Returns INVALID_ARG for
+ * N < 0. Process-wide; meant for single-threaded tests.
+ */
+bcg_status bcg_debug_fail_alloc(int32_t nth);
+
 /* bcg_destroy -- free the handle's workspace; NULL-safe. */
 void bcg_destroy(bcg_handle h);
 

@@ -71,6 +71,7 @@ def load():
         "bcg_rows_pack": [vp, vp, i64, vp],
         "bcg_rows_poll": [vp, ctypes.POINTER(i32)],
         "bcg_rows_finish": [vp, ctypes.POINTER(bcg_info)],
+        "bcg_debug_fail_alloc": [i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -82,6 +83,11 @@ def load():
     lib.bcg_destroy.restype = None
     _lib = lib
     return lib
+
+
+def bcg_debug_fail_alloc(nth: int):
+    """Make the nth device workspace allocation from now on fail with OOM (0 disarms); for error-path tests."""
+    _check(load().bcg_debug_fail_alloc(int(nth)))
 
 
 def bcg_last_error() -> str:

@@ -14,8 +14,10 @@
 // (solve_replace) or restarted refinement (solve_refine); SELL handles iterate on the permuted system;
 // row-sharded handles are driven phase by phase by the caller (bcg_rows_*).
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -71,6 +73,26 @@ bool is_device_ptr(const void *p) {
 
 // Lets the other C ABI translation unit (bcg_noalloc.cu) report through bcg_last_error.
 void bcg_internal_set_error(const char *msg) { g_last_error = msg; }
+
+namespace {
+// Allocation-failure injection for tests (bcg_debug_fail_alloc): the armed count of workspace allocations still
+// to succeed before one fails (0: disarmed).
+std::atomic<int> g_fail_alloc_in{0};
+bool injected_alloc_failure() {
+  int v = g_fail_alloc_in.load();
+  while (v > 0) {
+    if (g_fail_alloc_in.compare_exchange_weak(v, v - 1)) return v == 1;
+  }
+  return false;
+}
+
+// NVTX range for the lifetime of a scope (the library's phases and kernel launches; host-side markers that a
+// profiler shows on the timeline, free when none is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+}  // namespace
 
 struct bcg_ctx {
   // problem
@@ -136,6 +158,9 @@ struct bcg_ctx {
 
   template <typename U>
   bcg_status alloc(U **ptr, size_t count) {
+    if (injected_alloc_failure())
+      return fail(BCG_ERR_OOM, "cudaMalloc of %zu bytes failed: injected failure (bcg_debug_fail_alloc)",
+                  count * sizeof(U));
     void *p_ = nullptr;
     cudaError_t e = cudaMalloc(&p_, count * sizeof(U) + 16);
     if (e != cudaSuccess) {
@@ -336,21 +361,35 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
   const int df = df_updates<T>(h, g) ? 1 : 0;
   const ShiftCtl sc = shifts_of<T>(h);
   REC(0);
-  CK(launch_op_gram<T>(A, P, R, Q, h->n, h->k, h->p, h->global, h->active, h->partA, h->partR, h->st, g.op, s,
-                       sc.sh));
+  {
+    NvtxRange r_("K1 BOP + alpha");
+    CK(launch_op_gram<T>(A, P, R, Q, h->n, h->k, h->p, h->global, h->active, h->partA, h->partR, h->st, g.op, s,
+                         sc.sh));
+  }
   REC(1); REC(2);
-  CK(launch_solve_lambda(h->partA, h->partR, g.op, g.rho_k3 ? gp : g.op, h->k, h->p, h->global, h->active, h->lam,
-                         h->rho_rec, h->st, h->gws, g.alpha_circ, s));
+  {
+    NvtxRange r_("K4a lambda");
+    CK(launch_solve_lambda(h->partA, h->partR, g.op, g.rho_k3 ? gp : g.op, h->k, h->p, h->global, h->active, h->lam,
+                           h->rho_rec, h->st, h->gws, g.alpha_circ, s));
+  }
   REC(3); REC(4);
-  CK(launch_update_xr<T>(X, R, P, Q, h->n, h->k, h->p, h->global, h->lam, h->active, h->partRho, h->partN, h->st,
-                         gu, s, dinv_of<T>(h), sc.sh, df));
+  {
+    NvtxRange r_("K2 X, R update + rho");
+    CK(launch_update_xr<T>(X, R, P, Q, h->n, h->k, h->p, h->global, h->lam, h->active, h->partRho, h->partN, h->st,
+                           gu, s, dinv_of<T>(h), sc.sh, df));
+  }
   REC(5); REC(6);
-  CK(launch_solve_beta(h->partRho, h->partN, gu, gu, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
-                       h->active,
-                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, g.rho_circ, s, sc));
+  {
+    NvtxRange r_("K4b stop test + beta");
+    CK(launch_solve_beta(h->partRho, h->partN, gu, gu, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
+                         h->active, h->block_iters, h->rho_rec, h->beta, h->st, h->gws, g.rho_circ, s, sc));
+  }
   REC(7); REC(8);
-  CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv_of<T>(h),
-                        h->partR, sc.sh, df));
+  {
+    NvtxRange r_("K3 P update");
+    CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv_of<T>(h),
+                          h->partR, sc.sh, df));
+  }
   REC(9);
 #undef REC
   return BCG_OK;
@@ -1059,6 +1098,7 @@ bcg_status bcg_set_option(bcg_handle h, const char *key, double value) {
 }
 
 bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32_t maxit, bcg_info *info) {
+  NvtxRange range_("bcg_solve");
   if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
   if (h->rows_mode) return fail(BCG_ERR_INVALID_ARG, "row-sharded handle: drive it with the bcg_rows_* calls");
   if (!is_device_ptr(B) || !is_device_ptr(X)) return fail(BCG_ERR_INVALID_ARG, "B and X must be device pointers");
@@ -1093,10 +1133,9 @@ bcg_status bcg_solve_host(bcg_handle h, const double *B, double *X, double tol, 
   if (!(tol > 0.0) || !std::isfinite(tol)) return fail(BCG_ERR_INVALID_ARG, "tol must be finite and > 0");
   if (maxit < 1) return fail(BCG_ERR_INVALID_ARG, "maxit must be >= 1");
   const size_t bytes = sizeof(double) * (size_t)h->n * h->k;
-  if (h->stageB == nullptr) {
-    CKS(h->alloc(&h->stageB, (size_t)h->n * h->k));
-    CKS(h->alloc(&h->stageX, (size_t)h->n * h->k));
-  }
+  // each staging buffer is allocated once; a failed allocation leaves its pointer NULL, so the next call retries it
+  if (h->stageB == nullptr) CKS(h->alloc(&h->stageB, (size_t)h->n * h->k));
+  if (h->stageX == nullptr) CKS(h->alloc(&h->stageX, (size_t)h->n * h->k));
   CK(cudaMemcpyAsync(h->stageB, B, bytes, cudaMemcpyHostToDevice, h->stream));
   CK(cudaMemcpyAsync(h->stageX, X, bytes, cudaMemcpyHostToDevice, h->stream));
   const bcg_status st = bcg_solve(h, h->stageB, h->stageX, tol, maxit, info);
@@ -1324,6 +1363,12 @@ bcg_status bcg_rows_finish(bcg_handle h, bcg_info *info) {
 }
 
 const char *bcg_last_error(void) { return g_last_error.c_str(); }
+
+bcg_status bcg_debug_fail_alloc(int32_t nth) {
+  if (nth < 0) return fail(BCG_ERR_INVALID_ARG, "nth=%d must be >= 0", nth);
+  g_fail_alloc_in.store(nth);
+  return BCG_OK;
+}
 
 void bcg_destroy(bcg_handle h) {
   if (h == nullptr) return;
