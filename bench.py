@@ -293,11 +293,12 @@ def run_extra(name, args):
         k = 256
         B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev)
         rows = []
-        for prec in ("fp64", "fp32_refine"):
+        for prec, tc in (("fp64", 1), ("fp64", 0), ("fp32_refine", 1)):
             t, r, _ = time_solve(bcg, torch, M, B, k=k, p=k, sub="classical", prec=prec, tol=1e-300, reps=1, dev=dev,
-                                 warm=False, maxit=24)
-            rows.append(dict(prec=prec, s=t, iterations=r.iters, status=bcg.STATUS_NAMES[r.status],
+                                 warm=False, maxit=24, opts={"tensor_cores": tc})
+            rows.append(dict(prec=prec, tensor_cores=tc, s=t, iterations=r.iters, status=bcg.STATUS_NAMES[r.status],
                              ms_per_iteration=t * 1e3 / max(r.iters, 1)))
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
         out.update(value=rows[0]["s"], dtype="f64 (and f32 with f64 residual replacement)",
                    config={"workload": "poisson3d_64_csr_k256_classical_24_iterations", "n": M.n, "k": k, "p": k},
                    results=rows)

@@ -122,6 +122,7 @@ struct bcg_ctx {
   int precond = 0;                     // 0: M = I; 1: Jacobi, M = diag(A)
   int refine = 1;                      // FP32_REFINE: 1 residual replacement, 0 restarted refinement
   int retooled = 0;                    // FP64: 1 Dubrulle's retooled block CG instead of Algorithm 1's recurrences
+  int tensor_cores = 1;                // FP64, p a multiple of 64: block updates on the tensor cores (tcgen05)
   // live per-kernel timing (profile = 1): CUDA events around every launch of an executed iteration
   static constexpr int kKernels = 6;   // K1 op_gram, K4a solve_lambda, K2 update_xr, K4b solve_beta, K3 update_p, K0 residual
   double prof_ms[kKernels] = {0, 0, 0, 0, 0, 0};
@@ -142,6 +143,9 @@ struct bcg_ctx {
   int *bdot_sh = nullptr;              // standalone BDOT: their shifts (2 k)
   int *msig = nullptr;                 // mixed form: exponent of the FP32 process's scale per column (k)
   double *gws = nullptr;               // global workspace of the p x p solves when p is large
+  uint16_t *tc_cs = nullptr;           // tensor-core block updates: bf16 digit images of lambda or beta
+  int *tc_cexp = nullptr;              // their column exponents
+  int *tc_ecol = nullptr;              // tensor-core block products: the operands' column exponent fields (2 k)
   double *dinv64 = nullptr;            // 1 / diag(A) (Jacobi preconditioner)
   double *dr_C = nullptr, *dr_xi = nullptr, *dr_psiinv = nullptr, *dr_phi = nullptr;   // retooled form, p x p per block
   float *dinv32 = nullptr;             // its FP32 copy for the mixed form's inner solve
@@ -256,6 +260,11 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CKS(h->alloc(&h->bdot_sh, 2 * (size_t)h->k));
   if (h->prec == BCG_FP32_REFINE) CKS(h->alloc(&h->msig, h->k));
   if (small_needs_gws(h->p)) CKS(h->alloc(&h->gws, (size_t)h->nblk * small_ws_doubles(h->p)));
+  if (h->prec != BCG_FP32_REFINE && tc_ok(h->k, h->p)) {
+    CKS(h->alloc(&h->tc_cs, tc_workspace_bytes(h->nblk, h->p) / sizeof(uint16_t)));
+    CKS(h->alloc(&h->tc_cexp, (size_t)h->nblk * h->p));
+    CKS(h->alloc(&h->tc_ecol, 2 * (size_t)h->k));
+  }
   if (h->prec != BCG_FP32_REFINE && !h->global) {
     CKS(h->alloc(&h->dr_C, pp));
     CKS(h->alloc(&h->dr_xi, pp));
@@ -395,6 +404,45 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
   return BCG_OK;
 }
 
+// One large-block update OUT = BASE (x bscale per row) + sign Y C: on the tensor cores where the handle allows it
+// (FP64 data, p a multiple of 64, option "tensor_cores"), else the tiled FMA kernel. `sliced` tells whether C's
+// bf16 digit images are already in the handle's workspace (lambda serves two updates).
+template <typename T>
+bcg_status lp_update(bcg_ctx *h, T *OUT, const T *BASE, const T *Y, const double *C, double sign, int bump,
+                     const T *bscale, bool &sliced) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->tensor_cores && h->tc_cs != nullptr) {
+      if (!sliced) {
+        CK(launch_tc_slice(C, h->nblk, h->p, h->tc_cs, h->tc_cexp, h->stream));
+        sliced = true;
+      }
+      CK(launch_tc_baxpy(OUT, BASE, Y, h->tc_cs, h->tc_cexp, h->n, h->k, h->p, h->global, sign, h->active, h->st,
+                         bump, h->stream, bscale, h->nsm));
+      return BCG_OK;
+    }
+  }
+  CK(launch_lp_baxpy<T>(OUT, BASE, Y, C, h->n, h->k, h->p, h->global, sign, h->active, h->st, bump, h->stream,
+                        bscale));
+  return BCG_OK;
+}
+
+// Partials of a large-block product <<X, Y>>_S (X's rows times xscale if given) into `chunks` partial rows: on the
+// tensor cores where the handle allows it (as lp_update), else the tiled Dot2 kernel.
+template <typename T>
+bcg_status lp_gram(bcg_ctx *h, const T *X, const T *Y, double *part, int chunks, const T *xscale, const int *shX,
+                   const int *shY) {
+  if constexpr (sizeof(T) == 8) {
+    if (h->tensor_cores && h->tc_ecol != nullptr) {
+      CK(launch_tc_gram(X, Y, xscale, h->n, h->k, h->p, h->global, h->active, part, chunks, h->tc_ecol, h->st,
+                        h->stream, h->nsm));
+      return BCG_OK;
+    }
+  }
+  CK(launch_lp_gram<T>(X, Y, h->n, h->k, h->p, h->global, h->active, part, chunks, h->st, h->stream, xscale, shX,
+                       shY));
+  return BCG_OK;
+}
+
 // One iteration with large blocks (p > 32): tiled products. The direction update cannot run in place across
 // column tiles, so it writes into the Q buffer (free at that point) and the caller swaps P and Q.
 template <typename T>
@@ -404,20 +452,20 @@ bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T 
   const ShiftCtl sc = shifts_of<T>(h);
   const int *shR = sh_role(sc.sh, h->k, SH_R), *shP = sh_role(sc.sh, h->k, SH_P), *shQ = sh_role(sc.sh, h->k, SH_Q);
   CK(launch_lp_bop<T>(A, P, Q, h->n, h->k, h->st, h->nsm, s));
-  CK(launch_lp_gram<T>(P, Q, h->n, h->k, h->p, h->global, h->active, h->partA, ch, h->st, s, nullptr, shP, shQ));
-  CK(launch_lp_gram<T>(P, R, h->n, h->k, h->p, h->global, h->active, h->partR, ch, h->st, s, nullptr, shP, shR));
+  CKS(lp_gram<T>(h, P, Q, h->partA, ch, nullptr, shP, shQ));
+  CKS(lp_gram<T>(h, P, R, h->partR, ch, nullptr, shP, shR));
   CK(launch_solve_lambda(h->partA, h->partR, ch, ch, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
                          h->gws, 0, s));
-  CK(launch_lp_baxpy<T>(X, X, P, h->lam, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 0, s, nullptr));
-  CK(launch_lp_baxpy<T>(R, R, Q, h->lam, h->n, h->k, h->p, h->global, -1.0, h->active, h->st, 0, s, nullptr));
+  bool lam_sliced = false, beta_sliced = false;
+  CKS(lp_update<T>(h, X, X, P, h->lam, 1.0, 0, nullptr, lam_sliced));
+  CKS(lp_update<T>(h, R, R, Q, h->lam, -1.0, 0, nullptr, lam_sliced));
   // rho = <<Z, R>> with Z = M^{-1} R formed on the fly
-  CK(launch_lp_gram<T>(R, R, h->n, h->k, h->p, h->global, h->active, h->partRho, ch, h->st, s, dinv_of<T>(h), shP,
-                       shR));
+  CKS(lp_gram<T>(h, R, R, h->partRho, ch, dinv_of<T>(h), shP, shR));
   CK(launch_lp_colnorm<T>(R, h->n, h->k, h->partN, g.res, h->st, s, shR));   // a full-GPU grid, like K0's
   CK(launch_solve_beta(h->partRho, h->partN, ch, g.res, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
                        h->active,
                        h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s, sc));
-  CK(launch_lp_baxpy<T>(Q, R, P, h->beta, h->n, h->k, h->p, h->global, 1.0, h->active, h->st, 1, s, dinv_of<T>(h)));
+  CKS(lp_update<T>(h, Q, R, P, h->beta, 1.0, 1, dinv_of<T>(h), beta_sliced));
   return BCG_OK;
 }
 
@@ -550,6 +598,7 @@ double max_ratio(const double *num2, const double *den2, int k) {
 }
 
 bcg_status status_from_flags(int flags, bool all_done) {
+  if (flags & ST_TIMEOUT) return BCG_ERR_TIMEOUT;
   if (flags & ST_NUMERIC) return BCG_ERR_NUMERIC;
   if (flags & ST_BREAKDOWN) return BCG_ERR_BREAKDOWN;
   if (!all_done) return BCG_ERR_NOT_CONVERGED;
@@ -1088,6 +1137,9 @@ bcg_status bcg_set_option(bcg_handle h, const char *key, double value) {
     if (value == 1.0 && (h->prec != BCG_FP64 || h->global || h->rows_mode))
       return fail(BCG_ERR_INVALID_ARG, "the retooled form needs an FP64 handle of the hybrid, parallel or classical subalgebra");
     h->retooled = (int)value;
+  } else if (!strcmp(key, "tensor_cores")) {
+    if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "tensor_cores must be 0 or 1");
+    h->tensor_cores = (int)value;
   } else if (!strcmp(key, "graph")) {
     if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "graph must be 0 or 1");
     h->use_graph = (int)value;

@@ -37,7 +37,8 @@ struct DevStatus {
   int n_active;        // distinct blocks still iterating
   int cur;             // number of the iteration in progress (1-based), advanced by K3
 };
-enum { ST_DONE = 1, ST_BREAKDOWN = 2, ST_NUMERIC = 4 };
+// ST_TIMEOUT: a bounded device-side wait (the tensor-core kernels' completion barriers) gave up
+enum { ST_DONE = 1, ST_BREAKDOWN = 2, ST_NUMERIC = 4, ST_TIMEOUT = 8 };
 
 // Operator description; vals/faces point to T (double or float) copies.
 struct OpDesc {

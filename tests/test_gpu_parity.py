@@ -544,3 +544,21 @@ def test_solve_columns_is_r_block_solves(torch_dev):
     with pytest.raises(bcg.BCGError):
         S.solve_columns(Bt[:, :20].contiguous())
     S.close()
+
+
+@pytest.mark.parametrize("name,sub,k,p,m", [("p3d_30", "classical", 64, 64, 6), ("p3d_30", "hybrid", 128, 64, 6),
+                                            ("p3d_30", "global", 128, 64, 5), ("s27_15", "classical", 128, 128, 4),
+                                            ("p3d_30", "classical", 256, 256, 3)])
+def test_large_p_tensor_cores_match_fma(torch_dev, name, sub, k, p, m):
+    """The tensor-core block products and updates (exact bf16 digit slices, option "tensor_cores", the default for
+    FP64 with p a multiple of 64) against the FP64-FMA / Dot2 tiled kernels at equal iteration counts, and the
+    Jacobi-preconditioned form (its rho product scales X's rows)."""
+    M = mat(name)
+    B = W.rhs(M.n, k, seed=33)
+    for jac in (0, 1):
+        a, ra = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, maxit=m, opts={"tensor_cores": 1, "precond": jac})
+        b, rb = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, maxit=m, opts={"tensor_cores": 0, "precond": jac})
+        assert ra.status == rb.status == bcg.NOT_CONVERGED and ra.iters == rb.iters == m
+        assert_close(a, b, 1e-10, f"tensor cores against FMA kernels (Jacobi {jac})")
+        ref = O.solve(M.to_scipy(), B, p=p, sub=sub, tol=0.0, maxit=m, precond="jacobi" if jac else "none")
+        assert_close(a, ref.X, 1e-9, f"tensor cores against the oracle (Jacobi {jac})")
