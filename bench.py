@@ -69,18 +69,22 @@ def rho_in_k3(k, p, prec):
     return prec in ("fp64", "fp64_df") and 2 <= p <= 16 and wc
 
 
-def kernel_model(n, k, p, z, s, a_bytes, rho_k3=False):
+def kernel_model(n, k, p, z, s, a_bytes, rho_k3=False, df=False):
     """Algorithmic flops and bytes per launch of each iteration kernel (the paper's Table 1 omega and beta per
     kernel, fused as the kernels fuse them): K1 = BOP + BDOT alpha (+ BDOT of the recomputed rho, reading R),
     K2 = 2 BAXPY + BDOT + column norms, K3 = BAXPY (+ the next recomputed rho when rho_k3: R is read there
     anyway). `alu` is the part executed as native arithmetic of the block vectors' precision (BOP and
     BAXPY: FP64 FMAs in the FP64 form, FP32 FMAs in the mixed form); `gram` is the block-product part,
-    which runs as error-free (Dot2) FP32 arithmetic with FP64-class accuracy in both forms."""
+    which runs as error-free (Dot2) FP32 arithmetic with FP64-class accuracy in both forms. With `df` (the
+    double-float residual update of precision fp64_df) K2's `alu` is X's FMAs plus one FP64 addition per
+    element of R, and R's 2 n p k flops move to `df`, summed in float pairs on the FP32 pipes."""
     k1_grams = 1.0 if rho_k3 else 2.0
+    upd_alu = 2.0 * n * p * k + n * k if df else 4.0 * n * p * k
     return {
         "op_gram": dict(alu=2.0 * k * z, gram=k1_grams * 2.0 * n * p * k,
                         bytes=a_bytes + (2.0 if rho_k3 else 3.0) * n * k * s),
-        "update_xr": dict(alu=4.0 * n * p * k, gram=2.0 * n * p * k + 2.0 * n * k, bytes=6.0 * n * k * s),
+        "update_xr": dict(alu=upd_alu, gram=2.0 * n * p * k + 2.0 * n * k, bytes=6.0 * n * k * s,
+                          df=2.0 * n * p * k if df else 0.0),
         "update_p": dict(alu=2.0 * n * p * k, gram=2.0 * n * p * k if rho_k3 else 0.0, bytes=3.0 * n * k * s),
     }
 
@@ -507,6 +511,133 @@ def config_variants(bcg, W, torch, dev, np):
     return out
 
 
+def run_rows(args, rank, world, local):
+    """`--mode rows`: the default workload as ONE problem whose rows are split over the ranks (strong scaling).
+    Each rank runs bcg_create_csr_rows on its rows; the halo rows of P and the two sums of partial block
+    products per iteration go through NCCL, enqueued on the handle's stream (no host wait inside a batch of 8
+    iterations), and every batch after the first is one CUDA graph replay. value = the slowest rank's seconds
+    to tolerance; e2e adds the per-step copies of each rank's rows of B (host -> device) and X (device ->
+    host)."""
+    import numpy as np
+    import scipy.sparse as sp
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if "MASTER_ADDR" in os.environ:
+        dist.init_process_group("nccl", device_id=dev)
+    else:   # one rank without a launcher: a one-rank NCCL group on a free local port
+        import socket
+        sk = socket.socket()
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+        sk.close()
+        dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1, device_id=dev)
+    if rank == 0:
+        import __graft_entry__
+        __graft_entry__.build()
+    dist.barrier()
+    from paper_1912_11930_gb300 import dist as D, workloads as W
+
+    w = dict(WORKLOAD)
+    if args.grid != w["grid"]:
+        w["grid"] = args.grid
+        w["name"] = w["name"].replace("128", str(args.grid))
+    M = W.poisson3d(w["grid"])
+    n, k, p = M.n, w["k"], w["p"]
+    comm = D.TorchComm(dist)
+    plan = D.local_plan(M.rowptr, M.colind, M.vals, D.row_bounds(n, world), rank)
+    D.fill_sends(plan, comm.all_gather_object(plan.requests))
+    r0, r1 = plan.bounds[rank], plan.bounds[rank + 1]
+    B_host = np.ascontiguousarray(W.rhs(n, k, seed=0)[r0:r1])   # one problem: every rank its rows of it
+    stream = torch.cuda.Stream(dev)
+    S = D.RowShardedSolver(plan, k=k, p=p, sub=w["sub"], comm=D.StreamComm(dist, stream), device=dev, graph=True)
+    B = torch.from_numpy(B_host).to(dev)
+    X = torch.zeros(plan.n_cols, k, dtype=torch.float64, device=dev)
+
+    def solve():
+        with torch.cuda.stream(stream):
+            X.zero_()
+        return S.solve(B, X, tol=w["tol"], maxit=20000)
+
+    for _ in range(args.warmup):
+        res = solve()
+        assert res.ok, res
+    clocks = ClockSampler(local)
+    clocks.start()
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    results = [solve() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    clk = clocks.stop()
+    ms_max = D.max_over_ranks(e0.elapsed_time(e1) / args.steps, dist, dev)
+
+    # true residual of the gathered solution: each rank's rows of B - A X from X with its halo rows
+    S._halo_x(X)
+    torch.cuda.synchronize()
+    L = sp.csr_matrix((plan.vals, plan.colind, plan.rowptr), shape=(plan.n_local, plan.n_cols))
+    part = torch.from_numpy(np.concatenate([np.sum((B_host - L @ X.cpu().numpy()) ** 2, axis=0),
+                                            np.sum(B_host ** 2, axis=0)])).to(dev)
+    dist.all_reduce(part)
+    part = part.cpu().numpy()
+    rel_true = float(np.max(np.sqrt(part[:k] / part[k:])))
+
+    # end to end: this rank's rows of B from pinned host memory, X back to pinned host memory, every step
+    Bp = torch.from_numpy(B_host).pin_memory()
+    Xp = torch.zeros(plan.n_local, k, dtype=torch.float64).pin_memory()
+    dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            B.copy_(Bp, non_blocking=True)
+        solve()
+        with torch.cuda.stream(stream):
+            Xp.copy_(X[:plan.n_local], non_blocking=True)
+        stream.synchronize()
+    e2e = D.max_over_ranks((time.perf_counter() - t0) / args.steps, dist, dev)
+
+    iters = results[-1].iters
+    z = M.nnz
+    model = kernel_model(n, k, p, z, 8, 12.0 * z + 8.0 * (n + 1), rho_k3=rho_in_k3(k, p, "fp64"))
+    iter_bytes = sum(v["bytes"] for v in model.values())
+    iter_s = ms_max * 1e-3 / max(iters, 1)
+    hbm_peak, hbm_src = peaks()
+    peers = len(plan.send)
+    launched = int(math.ceil(iters / 8.0) * 8)
+    line = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "strong",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": w["name"] + f"_rows{world}", "n": n, "nnz": z, "k": k, "p": p,
+                       "subalgebra": w["sub"], "tol": w["tol"],
+                       "l2": "inputs larger than L2 (537 MB per block vector at one rank)",
+                       "parallelism": f"rows split over {world} ranks: NCCL halo + 2 allreduces per iteration on "
+                                      "the handle's stream, CUDA graph per batch of 8 iterations"},
+            "iterations": iters, "converged": all(r.ok for r in results), "max_rel_res_true": rel_true,
+            "gb_per_iter_model": iter_bytes / 1e9,
+            "roofline": {"bound": "hbm", "kernel": "whole iteration (all ranks)", "unit": "GB/s",
+                         "achieved": iter_bytes / iter_s / 1e9, "peak": hbm_peak * world,
+                         "frac": iter_bytes / iter_s / 1e9 / (hbm_peak * world), "traffic": None,
+                         "peak_source": hbm_src,
+                         "note": "modelled bytes of one iteration over the seconds per iteration; the FP64 pipe, "
+                                 "not HBM, binds each rank's kernels"},
+            "gpu_launches": args.steps * (launched * (8 + peers) + 6),
+            "clocks": clk,
+            "e2e": {"value": e2e, "unit": "s", "h2d_bytes_per_step": (r1 - r0) * k * 8,
+                    "d2h_bytes_per_step": (r1 - r0) * k * 8}}
+    S.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    dist.barrier()
+    dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -522,6 +653,9 @@ def main():
                     help="precision of the timed solve (profiling captures of the mixed form)")
     ap.add_argument("--workload", default=None, choices=EXTRA_WORKLOADS,
                     help="measure one of the other workloads instead of the default line")
+    ap.add_argument("--mode", default="columns", choices=["columns", "rows"],
+                    help="columns: independent right-hand-side blocks per rank (weak scaling, the default line); "
+                         "rows: one problem split by rows over the ranks (strong scaling, NCCL on stream)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -533,6 +667,8 @@ def main():
         return run_reference(args, rank, world)
     if args.workload:
         return run_extra(args.workload, args)
+    if args.mode == "rows":
+        return run_rows(args, rank, world, int(os.environ.get("LOCAL_RANK", "0")))
 
     import numpy as np
     import torch
@@ -601,7 +737,8 @@ def main():
     fp64 = w["prec"] in ("fp64", "fp64_df")
     s_bytes = 8 if fp64 else 4
     a_bytes = (12.0 if fp64 else 8.0) * z + 8.0 * (n + 1)
-    model = kernel_model(n, k, p, z, s_bytes, a_bytes, rho_k3=rho_in_k3(k, p, w["prec"]))
+    model = kernel_model(n, k, p, z, s_bytes, a_bytes, rho_k3=rho_in_k3(k, p, w["prec"]),
+                         df=w["prec"] == "fp64_df" and rho_in_k3(k, p, w["prec"]))
     hbm_peak, hbm_src = peaks()
     per_kernel = {}
     for name, (tot, cnt) in prof.items():
@@ -612,6 +749,8 @@ def main():
                 sec = tot / cnt * 1e-3
                 entry["alg_gflop_fp64_pipe"] = mdl["alu"] / 1e9
                 entry["alg_gflop_gram_dot2"] = mdl["gram"] / 1e9
+                if mdl.get("df"):
+                    entry["alg_gflop_double_float"] = mdl["df"] / 1e9
                 entry["alg_gb"] = mdl["bytes"] / 1e9
                 entry["fp64_tflops"] = mdl["alu"] / sec / 1e12
                 entry["gbs"] = mdl["bytes"] / sec / 1e9
@@ -629,8 +768,10 @@ def main():
         traffic = ent[2]
     roofline = {"bound": "alu", "kernel": dom, "achieved": d["fp64_tflops"], "peak": NOMINAL_FP64_TFLOPS,
                 "unit": "TFLOP/s", "frac": d["fp64_tflops"] / NOMINAL_FP64_TFLOPS, "traffic": traffic,
-                "counted": "algorithmic FP64-FMA flops of the kernel (BOP / BAXPY); its block products run as "
-                           "error-free FP32 arithmetic and are listed under kernels.*.alg_gflop_gram_dot2",
+                "counted": "algorithmic FP64-pipe flops of the kernel (BOP / BAXPY FMAs; with fp64_df, K2's X "
+                           "FMAs and one addition per element of R); its block products (and fp64_df's R "
+                           "products) run as error-free FP32 arithmetic and are listed under "
+                           "kernels.*.alg_gflop_gram_dot2 (.alg_gflop_double_float)",
                 "peak_source": "nominal FP64 (GB300 FP64 vector and tensor rate; the P0 DFMA probe measured 1.19)",
                 "hbm_achieved_gbs": d["gbs"], "hbm_peak_gbs": hbm_peak, "hbm_frac": d["gbs"] / hbm_peak,
                 "hbm_peak_source": hbm_src}
@@ -645,7 +786,7 @@ def main():
     line = {"metric": METRIC, "value": ms_max / 1e3, "unit": "s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": False, "scaling": "weak",
             "vs_baseline": None,
-            "dtype": {"fp64": "f64", "fp64_df": "f64 (double-float block updates)"}.get(w["prec"],
+            "dtype": {"fp64": "f64", "fp64_df": "f64 (double-float residual update)"}.get(w["prec"],
                                                                                      "f32 inner, f64 refinement"),
             "data": "synthetic",
             "config": {"workload": w["name"], "n": n, "nnz": z, "k": k, "p": p, "subalgebra": w["sub"],

@@ -83,13 +83,15 @@ typedef enum {
                                 process of block j runs on R_j 2^-sigma_j, an exact scaling with
                                 sigma_j the exponent of the block's largest FP64 column norm, so
                                 FP32's range never limits the scale of B or X                        */
-  BCG_FP64_DF = 2            /* BCG_FP64 with the block updates (BAXPY: X += P lambda, R -= Q lambda,
-                                P = Z + P beta) in double-float arithmetic where the shapes allow it
-                                (2 <= p <= 16 with k | 32 or 32 | k, k even): each sum of p products
-                                is accumulated in float pairs from 48-bit splits of its operands and
-                                added to the FP64 value with two FP64 additions. Error per update
-                                about 2^-46 sum_a |y_a l_ab|, against about p 2^-53 of it with FP64
-                                FMAs; 4 instead of 4 p FP64 operations per element of K2. Other
+  BCG_FP64_DF = 2            /* BCG_FP64 with the residual update R -= Q lambda (BAXPY) in double-
+                                float arithmetic where the shapes allow it (2 <= p <= 16 with k | 32
+                                or 32 | k, k even): its sum of p products is accumulated in float
+                                pairs from 48-bit splits of its operands (on the FP32 pipes) and
+                                added to the FP64 value with one FP64 addition, while X += P lambda
+                                and P = Z + P beta keep their FP64 FMAs, so that the narrow FP64
+                                pipe and the FP32 pipes share K2's products. Error of R's update
+                                about 2^-46 sum_a |q_a l_ab|, against about p 2^-53 of it with FP64
+                                FMAs; p + 1 instead of 2 p FP64 operations per element of K2. Other
                                 shapes run BCG_FP64's updates. The retooled form is not available. */
 } bcg_precision;
 

@@ -216,7 +216,7 @@ bcg_status setup_workspace(bcg_ctx *h) {
   // partial rows: every grid that writes them (K0, K1, K2, and K3 for the recomputed rho)
   auto grids_max = [](const StreamGrids &g) {
     return std::max(std::max(std::max(std::max(g.op, g.res), std::max(g.upd, g.upd_zs)), std::max(g.pup, g.pup_zs)),
-                    std::max(std::max(g.upd_df, g.upd_zs_df), std::max(g.pup_df, g.pup_zs_df)));
+                    std::max(g.upd_df, g.upd_zs_df));
   };
   int np = grids_max(h->g64);
   if (h->prec == BCG_FP32_REFINE) {
@@ -316,8 +316,8 @@ ShiftCtl shifts_of(const bcg_ctx *h) {
   return sc;
 }
 
-// The K2 / K3 grids of an iteration in precision T, and whether its block updates run in double-float arithmetic
-// (precision BCG_FP64_DF, where the shapes allow; the partial-row counts of K2 and K3 follow the grid used).
+// The K2 / K3 grids of an iteration in precision T, and whether K2 sums R's update in double-float arithmetic
+// (precision BCG_FP64_DF, where the shapes allow; the partial-row count of K2 follows the grid used).
 template <typename T>
 bool df_updates(const bcg_ctx *h, const StreamGrids &g) {
   return sizeof(T) == 8 && h->prec == BCG_FP64_DF && (h->precond ? g.upd_zs_df : g.upd_df) > 0;
@@ -329,7 +329,6 @@ int grid_upd(const bcg_ctx *h, const StreamGrids &g) {
 }
 template <typename T>
 int grid_pup(const bcg_ctx *h, const StreamGrids &g) {
-  if (df_updates<T>(h, g)) return h->precond ? g.pup_zs_df : g.pup_df;
   return h->precond ? g.pup_zs : g.pup;
 }
 
@@ -397,7 +396,7 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
   {
     NvtxRange r_("K3 P update");
     CK(launch_update_p<T>(P, R, h->n, h->k, h->p, h->global, h->beta, h->active, h->st, gp, s, dinv_of<T>(h),
-                          h->partR, sc.sh, df));
+                          h->partR, sc.sh));
   }
   REC(9);
 #undef REC

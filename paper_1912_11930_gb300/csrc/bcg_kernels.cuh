@@ -233,11 +233,12 @@ struct Gram<double> {
 };
 
 // ---- Double-float block updates (precision BCG_FP64_DF) ----------------------------------------------------
-// A block update out_b = base_b + sum_a y_a l_ab (BAXPY) with the p products off the FP64 pipe: y_a and l_ab are
-// split into 48-bit float pairs (after exact power-of-two shifts that put them inside FP32's range), the products
-// are accumulated as one float pair (s, c) exactly as the Gram entries are (TwoProd of the high parts, the two
-// cross terms, TwoSum), and s 2^t and c 2^t are added to the FP64 base with two FP64 additions. The error of the
-// increment is about 2^-46 sum_a |y_a l_ab| (FP64 FMAs: about p 2^-53 of it).
+// A block update out_b = base_b + sum_a y_a l_ab (BAXPY) with part of the p products off the FP64 pipe: for those
+// terms y_a and l_ab are split into 48-bit float pairs (after exact power-of-two shifts that put them inside FP32's
+// range), the products are accumulated as one float pair (s, c) exactly as the Gram entries are (TwoProd of the
+// high parts, the two cross terms, TwoSum), and s 2^t and c 2^t are added to the FP64 value with two FP64
+// additions. The error of that part of the increment is about 2^-46 sum_a |y_a l_ab| (FP64 FMAs: about p 2^-53
+// of it). The other terms keep their FP64 FMAs, so that both pipes carry a share of the products.
 
 // x 2^-sh as a float pair, branch-free: a normal x whose scaled value lies in [2^-74, 2^128) gives the split of
 // split_f64; a scaled value below 2^-74, zero or subnormal gives (0, 0); above the range or non-finite, (+-inf, 0).
@@ -274,19 +275,48 @@ __device__ __forceinline__ double f2d_scaled(float v, int t) {
   return (ex == 0 || eb <= 0) ? 0.0 : __hiloint2double((int)hi, (int)(man << 29));
 }
 
-// Column b of a p x p update matrix for the float-pair products y_a l_ab, y_a taken at the column shifts sh of
-// block j (y~_a = y_a 2^-sh_a): out[a] = the float pair of l_ab 2^(sh_a - t), with t = max_a (exponent of l_ab +
-// sh_a), so that every |y~_a l~_ab| <= 2^(kGramCenter + 2) and sum_a y_a l_ab = 2^t sum_a y~_a l~_ab. Returns t.
+// (s + c) 2^t as one double, from the bit patterns of the two floats with integer operations only (so that the
+// update needs one FP64 addition, not two): both mantissas are aligned at the larger exponent in a 64-bit fixed-
+// point sum, which is normalised and truncated to 53 bits. Bits of the smaller part more than 62 places below the
+// larger one's leading bit are dropped, so the result is within 2^-52 of (s + c) 2^t relative to max(|s|, |c|).
+// A zero or subnormal part counts as zero (as in f2d_scaled), a non-finite part gives a non-finite result, an
+// overflow gives +-inf and an underflow 0.
+__device__ __forceinline__ double df_pair_to_double(float s, float c, int t) {
+  const unsigned us = __float_as_uint(s), uc = __float_as_uint(c);
+  const int es = (int)((us >> 23) & 0xFFu), ec = (int)((uc >> 23) & 0xFFu);
+  const int e = max(es, ec);
+  // mantissas with their hidden bit at bit 61 (each < 2^62, so the signed sum stays below 2^63)
+  const unsigned long long ms = es ? (unsigned long long)((us & 0x7FFFFFu) | 0x800000u) << 38 : 0ull;
+  const unsigned long long mc = ec ? (unsigned long long)((uc & 0x7FFFFFu) | 0x800000u) << 38 : 0ull;
+  const long long a = (long long)(ms >> min(e - es, 63)), b = (long long)(mc >> min(e - ec, 63));
+  const long long m = ((us >> 31) ? -a : a) + ((uc >> 31) ? -b : b);
+  const unsigned long long sign = (unsigned long long)m & 0x8000000000000000ull;
+  unsigned long long u = m < 0 ? (unsigned long long)(-m) : (unsigned long long)m;
+  const int lz = __clzll((long long)u);   // 64 for u == 0
+  u <<= (lz & 63);                        // leading bit at 63: value = u 2^(e - 188 - lz)
+  const int eb = e + 898 - lz + t;        // biased FP64 exponent of the leading bit
+  const double fin = __longlong_as_double((long long)(sign | ((unsigned long long)max(min(eb, 0x7FE), 1) << 52) |
+                                                      ((u >> 11) & 0xFFFFFFFFFFFFFull)));
+  const double inf = __longlong_as_double((long long)(sign | 0x7FF0000000000000ull));
+  const double r = (lz == 64 || eb <= 0) ? 0.0 : (eb >= 0x7FF ? inf : fin);
+  return (es == 0xFF || ec == 0xFF) ? f2d_scaled(es == 0xFF ? s : c, t) : r;
+}
+
+// Column b of a p x p update matrix for the float-pair products y_a l_ab (a0 <= a < p), y_a taken at the column
+// shifts sh of block j (y~_a = y_a 2^-sh_a): out[a] = the float pair of l_ab 2^(sh_a - t), with t = max_a
+// (exponent of l_ab + sh_a), so that every |y~_a l~_ab| <= 2^(kGramCenter + 2) and sum_a y_a l_ab = 2^t sum_a
+// y~_a l~_ab; out[a] = 0 for a < a0 (terms summed with FP64 FMAs instead). Returns t.
 template <int PM>
 __device__ __forceinline__ int df_matrix_col(const double (&l)[PM], int p, const int *__restrict__ sh, int j,
-                                             float2 (&out)[PM]) {
+                                             float2 (&out)[PM], int a0) {
   int t = -2 * kGramShiftMax - 2000;
 #pragma unroll
   for (int a = 0; a < PM; ++a)
-    if (a < p && l[a] != 0.0) t = max(t, exponent_of(fabs(l[a])) + shift_at(sh, j * p + a));
+    if (a >= a0 && a < p && l[a] != 0.0) t = max(t, exponent_of(fabs(l[a])) + shift_at(sh, j * p + a));
   if (t < -2 * kGramShiftMax - 1000) t = 0;   // an all-zero column
 #pragma unroll
-  for (int a = 0; a < PM; ++a) out[a] = a < p ? split_f64(l[a], t - shift_at(sh, j * p + a)) : make_float2(0.0f, 0.0f);
+  for (int a = 0; a < PM; ++a)
+    out[a] = (a >= a0 && a < p) ? split_f64(l[a], t - shift_at(sh, j * p + a)) : make_float2(0.0f, 0.0f);
   return t;
 }
 

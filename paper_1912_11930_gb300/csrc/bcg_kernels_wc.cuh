@@ -380,9 +380,11 @@ constexpr int wc_min_ctas_upd() {
   return DF ? 2 : (sizeof(T) == 4 && PM <= 8 && !ZS) ? 4 : ((sizeof(T) == 8 && PM == 16) ? 2 : wc_min_ctas<PM>());
 }
 
-// DF (FP64, p >= 2): the two BAXPYs in double-float arithmetic (bcg_kernels.cuh); the P and Q tiles then hold
-// float pairs of P and Q scaled by their columns' P- and Q-role shifts (shPr, shQr, which differ by one uniform
-// offset), and lambda's column is normalised into float pairs once per thread.
+// DF (FP64, p >= 2): the two BAXPYs split between the two pipes. X += P lambda keeps its p FP64 FMAs, and
+// R -= Q lambda is summed in double-float arithmetic (bcg_kernels.cuh) on the FP32 pipes and added to R with one
+// FP64 addition, so that the narrow FP64 pipe carries p + 1 operations per element instead of 2 p. The Q tile
+// then holds float pairs of Q scaled by its columns' Q-role shifts (shQr), and lambda's column is normalised into
+// float pairs once per thread.
 template <typename T, int PM, int V, bool ZS, bool DF = false>
 __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS, DF>()) kw_update_xr(T *__restrict__ X, T *__restrict__ R, const T *__restrict__ P,
                                                     const T *__restrict__ Q, int64_t n, int k, int p, int global,
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS, DF>()) kw_upda
                                                     double *__restrict__ partRho, double *__restrict__ partN,
                                                     const DevStatus *__restrict__ st, const T *__restrict__ dinv,
                                                     const int *__restrict__ shZ, const int *__restrict__ shR,
-                                                    const int *__restrict__ shPr, const int *__restrict__ shQr) {
+                                                    const int *__restrict__ shQr) {
   static_assert(!DF || sizeof(T) == 8, "double-float updates replace FP64 arithmetic");
   using G = Gram<T>;
   using BT = typename G::B;
@@ -424,28 +426,25 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS, DF>()) kw_upda
   const int cshZ = (G::kShifted && ZS) ? shift_at(shZ, c) : cshR;
   auto sxZ = [&](int d) { return shift_at(shZ, j * p + ((b + d) & (PM - 1))); };
   T lcol[PM];
-  {
-    const T *lj = sL + (global ? 0 : j) * p * p + b;
+  const T *lj = sL + (global ? 0 : j) * p * p + b;
 #pragma unroll
-    for (int a = 0; a < PM; ++a) lcol[a] = a < p ? lj[a * p] : T(0);
-  }
-  // DF: lambda's column as float pairs, the block shifts of this lane's memory-phase columns (tile writes) and
-  // the output exponents of its compute-phase column (X += 2^tx (s + c), R -= 2^tr (s' + c'))
+  for (int a = 0; a < PM; ++a) lcol[a] = a < p ? lj[a * p] : T(0);
+  // DF at p = 16: the FP64 column of lambda is re-read from shared memory (conflict-free: the lanes read
+  // consecutive entries of one row) so that it and the float-pair column fit the 128 registers of 2 CTAs per SM
+  constexpr bool kLamSmem = DF && PM > 8;
+  // DF: lambda's column as float pairs for Q's shifts, the Q shifts of this lane's memory-phase columns (tile
+  // writes) and the output exponent of its compute-phase column (R -= 2^tr (s + c))
   float2 lpair[DF ? PM : 1];
-  int dfSPm[DF ? V : 1], dfSQm[DF ? V : 1], dfTx = 0, dfTr = 0;
+  int dfSQm[DF ? V : 1], dfTr = 0;
   if constexpr (DF) {
     int64_t row0;
     int mc0;
     geo.mem_pos(0, row0, mc0);
 #pragma unroll
-    for (int v = 0; v < V; ++v) {
-      dfSPm[v] = shift_at(shPr, mc0 + v);
-      dfSQm[v] = shift_at(shQr, mc0 + v);
-    }
-    dfTx = df_matrix_col<PM>(lcol, p, shPr, j, lpair);
-    dfTr = dfTx + (shift_at(shQr, c) - shift_at(shPr, c));   // Q~ = Q 2^-(shP + dA): R's increment scales by 2^dA
+    for (int v = 0; v < V; ++v) dfSQm[v] = shift_at(shQr, mc0 + v);
+    dfTr = df_matrix_col<PM>(lcol, p, shQr, j, lpair, 0);
   }
-  float2 *sPf = reinterpret_cast<float2 *>(sP), *sQf = reinterpret_cast<float2 *>(sQ);
+  float2 *sQf = reinterpret_cast<float2 *>(sQ);
   GramAcc<PMH> acc;
   acc.zero();
   float ns = 0.0f, nc = 0.0f;
@@ -472,13 +471,9 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS, DF>()) kw_upda
     for (int v = 0; v < V; ++v) {
       sX[tm + v] = xv.e[v];
       sR[tm + v] = rv.e[v];
-      if constexpr (DF) {
-        sPf[tm + v] = split_f64_ftz(pv.e[v], dfSPm[v]);
-        sQf[tm + v] = split_f64_ftz(qv.e[v], dfSQm[v]);
-      } else {
-        sP[tm + v] = pv.e[v];
-        sQ[tm + v] = qv.e[v];
-      }
+      sP[tm + v] = pv.e[v];
+      if constexpr (DF) sQf[tm + v] = split_f64_ftz(qv.e[v], dfSQm[v]);
+      else sQ[tm + v] = qv.e[v];
     }
     __syncwarp();
     // BAXPY x 2 for each sub-pass; the new residual is written as its broadcast representation
@@ -488,18 +483,22 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS, DF>()) kw_upda
       T x = sX[t], r = sR[t];
       if constexpr (DF) {
         if (act) {
-          float2 prow[PM], qrow[PM];
-          load_row<float2, PM>(sPf + t - b, prow, p);
-          load_row<float2, PM>(sQf + t - b, qrow, p);
-          float xs = 0.0f, xc = 0.0f, rs = 0.0f, rc = 0.0f;
+          constexpr int C = PM > 8 ? 8 : PM;   // rows read in chunks of 8 terms (register pressure at p = 16)
+          float rs = 0.0f, rc = 0.0f;
 #pragma unroll
-          for (int a = 0; a < PM; ++a)
-            if (a < p) {
-              Gram<double>::add(xs, xc, prow[a], lpair[a]);
-              Gram<double>::add(rs, rc, qrow[a], lpair[a]);
-            }
-          x = (x + f2d_scaled(xs, dfTx)) + f2d_scaled(xc, dfTx);
-          r = (r - f2d_scaled(rs, dfTr)) - f2d_scaled(rc, dfTr);
+          for (int h = 0; h < PM; h += C) {
+            T prow[C];
+            float2 qrow[C];
+            load_row<T, C>(sP + t - b + h, prow, min(p - h, C));
+            load_row<float2, C>(sQf + t - b + h, qrow, min(p - h, C));
+#pragma unroll
+            for (int a = 0; a < C; ++a)
+              if (h + a < p) {
+                x = fma_t(prow[a], kLamSmem ? lj[(h + a) * p] : lcol[h + a], x);
+                Gram<double>::add(rs, rc, qrow[a], lpair[h + a]);
+              }
+          }
+          r = r - df_pair_to_double(rs, rc, dfTr);
         }
       } else if (act) {
         T prow[PM], qrow[PM];
@@ -561,15 +560,12 @@ __global__ void __launch_bounds__(kNT, wc_min_ctas_upd<T, PM, ZS, DF>()) kw_upda
 // RR: also the recomputed rho of the next iteration, <<P_new, R>>_S (Algorithm 1 recomputes
 // rho^{i-1} = <<P^i, R^{i-1}>>_S; both operands are in this kernel's registers, and its FP32 pipes are idle
 // while it waits on the FP64 pipe or on HBM). Partials as in K1, entry (a, b) of block j at j*p*p + b*p + a.
-// DF (FP64, p >= 2): the BAXPY in double-float arithmetic as in K2; the P tile then holds float pairs of P at its
-// columns' shifts, and a frozen block's rows are not rewritten (its P stays as it is in memory).
-template <typename T, int PM, int V, bool ZS, bool RR, bool DF = false>
+template <typename T, int PM, int V, bool ZS, bool RR>
 __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *__restrict__ R, int64_t n, int k,
                                                    int p, int global, const double *__restrict__ beta,
                                                    const int *__restrict__ active, DevStatus *__restrict__ st,
                                                    const T *__restrict__ dinv, double *__restrict__ partR,
                                                    const int *__restrict__ shP, const int *__restrict__ shR) {
-  static_assert(!DF || sizeof(T) == 8, "double-float updates replace FP64 arithmetic");
   using G = Gram<T>;
   using BT = typename G::B;
   using VT = typename VecOf<T, V>::type;
@@ -612,21 +608,6 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
   const int sPn = (G::kShifted && RR) ? shift_at(shP, c) : 0;
   const int syR = (G::kShifted && RR) ? shift_at(shR, c) : 0;
   auto sxP = [&](int a) { return shift_at(shP, j * p + a); };
-  // DF: beta's column as float pairs, the block shift of this lane's memory-phase columns and whether their block
-  // still iterates, and the output exponent of its compute-phase column (P = Z + 2^t (s + c))
-  float2 bpair[DF ? PM : 1];
-  int dfSPm[DF ? V : 1], dfT = 0;
-  bool act_m = true;
-  if constexpr (DF) {
-    int64_t row0;
-    int mc0;
-    geo.mem_pos(0, row0, mc0);
-#pragma unroll
-    for (int v = 0; v < V; ++v) dfSPm[v] = shift_at(shP, mc0 + v);
-    act_m = block_active(active, global, mc0 / p);
-    dfT = df_matrix_col<PM>(bcol, p, shP, j, bpair);
-  }
-  float2 *sPf = reinterpret_cast<float2 *>(sP);
   int pass = 0;
   const int kv = k / V;
   for (int64_t rb = geo.rb0; rb < geo.nrb; rb += geo.rbs) {
@@ -652,8 +633,7 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
     const int tm = 32 * geo.sm + geo.om;
 #pragma unroll
     for (int v = 0; v < V; ++v) {
-      if constexpr (DF) sPf[tm + v] = split_f64_ftz(pv.e[v], dfSPm[v]);
-      else sP[tm + v] = pv.e[v];
+      sP[tm + v] = pv.e[v];
       sR[tm + v] = zv.e[v];
       if constexpr (RR && ZS) sRb[tm + v] = G::conv(rv.e[v], G::kShifted ? s_shR[mc + v] : 0);
     }
@@ -661,18 +641,8 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
 #pragma unroll
     for (int s = 0; s < V; ++s) {
       const int t = 32 * s + geo.lane;
-      T out = DF ? T(0) : sP[t];
-      if constexpr (DF) {
-        if (act) {
-          float2 prow[PM];
-          load_row<float2, PM>(sPf + t - b, prow, p);
-          float ps = 0.0f, pc = 0.0f;
-#pragma unroll
-          for (int a = 0; a < PM; ++a)
-            if (a < p) Gram<double>::add(ps, pc, prow[a], bpair[a]);
-          out = (sR[t] + f2d_scaled(ps, dfT)) + f2d_scaled(pc, dfT);
-        }
-      } else if (act) {
+      T out = sP[t];
+      if (act) {
         T prow[PM];
         load_row<T, PM>(sP + t - b, prow, p);
         out = sR[t];
@@ -702,7 +672,7 @@ __global__ void __launch_bounds__(kNT) kw_update_p(T *__restrict__ P, const T *_
         gram_flush<T>(acc, slotR, p, sxP, syR);
       }
     }
-    if (row < n && act_m) {
+    if (row < n) {
       VecU<T, V> po;
 #pragma unroll
       for (int v = 0; v < V; ++v) po.e[v] = sN[tm + v];

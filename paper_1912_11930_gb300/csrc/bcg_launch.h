@@ -26,7 +26,7 @@ struct StreamGrids {
   int pup;       // K3 CTAs
   int upd_zs;    // K2 CTAs, Jacobi-preconditioned instantiation
   int pup_zs;    // K3 CTAs, Jacobi-preconditioned instantiation
-  int upd_df, upd_zs_df, pup_df, pup_zs_df;   // the same with double-float updates (0: not available)
+  int upd_df, upd_zs_df;   // K2 with double-float updates of R (0: not available)
   int res;       // K0 CTAs
   int alpha_circ;   // K1 stores alpha by circulant diagonals (symmetric product, half the terms)
   int rho_circ;     // K2 stores rho by circulant diagonals
@@ -54,7 +54,7 @@ template <typename T>
 // partR: with rho_k3, the partials of the next iteration's recomputed rho <<P_new, R>>_S (one row per CTA)
 cudaError_t launch_update_p(T *P, const T *R, int64_t n, int k, int p, int global, const double *beta,
                             const int *active, DevStatus *st, int grid, cudaStream_t s, const T *dinv,
-                            double *partR, const int *sh, int df = 0);
+                            double *partR, const int *sh);
 template <typename T>
 // sig (optional): R32 and P32 receive R 2^-sigma_c (the mixed form's scale)
 cudaError_t launch_residual(const OpDesc &A, const T *X, const T *B, T *R, T *P, float *R32, float *P32, int64_t n,

@@ -1,8 +1,9 @@
 """GPU parity of the double-float block updates (precision "fp64_df") against the CPU oracle.
 
-The form differs from BCG_FP64 only in how the block updates X += P lambda, R -= Q lambda and P = Z + P beta
-sum their p products: in float pairs from 48-bit splits (about 2^-46 of sum_a |y_a l_ab| per update against
-p 2^-53 of it with FP64 FMAs), with two FP64 additions into the FP64 value. The bars are the FP64 form's:
+The form differs from BCG_FP64 only in how the residual update R -= Q lambda sums its p products: in float
+pairs from 48-bit splits (about 2^-46 of sum_a |q_a l_ab| per update against p 2^-53 of it with FP64 FMAs),
+turned into one double with integer operations and added to R with one FP64 addition; X += P lambda and
+P = Z + P beta keep their FP64 FMAs. The bars are the FP64 form's:
 relative solution error <= 1e-9 against the oracle at equal iteration counts (Frobenius and element by
 element), converged counts within +-2, the true residual at the tolerance; and, at 128^3, k = 32, p = 8 (the
 bench workload), four iterations against the oracle on the whole matrix and a converged solve whose count
@@ -81,9 +82,8 @@ def test_df_equal_iterations(torch_dev, name, sub, k, p, m, jac):
 @pytest.mark.parametrize("name,sub,k,p", [("p2d_37x29", "hybrid", 8, 4), ("p3d_30", "hybrid", 32, 8),
                                           ("p3d_30", "global", 32, 32), ("s27_15", "hybrid", 16, 16)])
 def test_df_converged_counts_and_frozen_blocks(torch_dev, name, sub, k, p):
-    """Hybrid blocks freeze at their own iterations (a frozen block's rows are not rewritten): counts within +-2
-    of the oracle's, per block too, each block's X against the oracle at its own count, and the true residual
-    at the tolerance."""
+    """Hybrid blocks freeze at their own iterations: counts within +-2 of the oracle's, per block too, each
+    block's X against the oracle at its own count, and the true residual at the tolerance."""
     M = mat(name)
     A = M.to_scipy()
     B = W.rhs(M.n, k, seed=3)
