@@ -63,7 +63,9 @@ typedef enum {
                                 method of Section 3 has none); X holds the last completed iterate    */
   BCG_ERR_NOT_CONVERGED = 5, /* maxit reached; X holds the last iterate, info is filled              */
   BCG_ERR_NUMERIC = 6,       /* a non-finite value in B, X0 or a residual norm                       */
-  BCG_ERR_TIMEOUT = 7        /* a bounded device-side wait gave up                                  */
+  BCG_ERR_TIMEOUT = 7,       /* a bounded device-side wait gave up                                  */
+  BCG_ERR_GUARD = 8          /* option "guards": the guard bytes after a workspace buffer changed,
+                                i.e. a kernel wrote past the end of a buffer                         */
 } bcg_status;
 
 typedef enum {
@@ -197,6 +199,9 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
  *                  pivot is tested against its own diagonal entry. FP64 handles of the hybrid, parallel or
  *                  classical subalgebra with M = I only (INVALID_ARG otherwise, from bcg_set_option or, for
  *                  "precond", from bcg_solve); 0 = Algorithm 1 (default).
+ *   "guards"       1 = after each solve (bcg_solve, bcg_solve_host, bcg_rows_finish) compare the 16 guard
+ *                  bytes that follow every workspace buffer of the handle with the pattern written at
+ *                  allocation; a change returns BCG_ERR_GUARD naming the buffer. 0 = no check (default).
  * Unknown keys or out-of-range values return INVALID_ARG.
  */
 bcg_status bcg_set_option(bcg_handle h, const char *key, double value);
@@ -384,6 +389,14 @@ const char *bcg_last_error(void);
  * N < 0. Process-wide; meant for single-threaded tests.
  */
 bcg_status bcg_debug_fail_alloc(int32_t nth);
+
+/*
+ * bcg_debug_poke_guard -- test hook for the guard check (not part of the paper's method): overwrite the first
+ * guard byte after workspace buffer `index` of the handle (memory the handle allocated for its guards, so no
+ * access leaves an allocation). With option "guards" the next solve then returns BCG_ERR_GUARD. INVALID_ARG for
+ * an index outside the handle's buffers.
+ */
+bcg_status bcg_debug_poke_guard(bcg_handle h, int32_t index);
 
 /* bcg_destroy -- free the handle's workspace; NULL-safe. */
 void bcg_destroy(bcg_handle h);

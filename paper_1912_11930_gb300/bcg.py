@@ -14,8 +14,8 @@ from dataclasses import dataclass
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbcg.so")
 
-OK, INVALID_ARG, CUDA_ERR, OOM, BREAKDOWN, NOT_CONVERGED, NUMERIC, TIMEOUT = range(8)
-STATUS_NAMES = ["OK", "INVALID_ARG", "CUDA", "OOM", "BREAKDOWN", "NOT_CONVERGED", "NUMERIC", "TIMEOUT"]
+OK, INVALID_ARG, CUDA_ERR, OOM, BREAKDOWN, NOT_CONVERGED, NUMERIC, TIMEOUT, GUARD = range(9)
+STATUS_NAMES = ["OK", "INVALID_ARG", "CUDA", "OOM", "BREAKDOWN", "NOT_CONVERGED", "NUMERIC", "TIMEOUT", "GUARD"]
 SUBALGEBRA = {"hybrid": 0, "global": 1, "parallel": 2, "classical": 3}
 PRECISION = {"fp64": 0, "fp32_refine": 1, "fp64_df": 2}
 STENCIL = {"5pt_2d": 0, "7pt_3d": 1, "7pt_3d_varcoef": 2}
@@ -34,7 +34,7 @@ class bcg_info(ctypes.Structure):
 
 class BCGError(RuntimeError):
     def __init__(self, status: int, message: str):
-        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < 8 else status}: {message}")
+        super().__init__(f"{STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else status}: {message}")
         self.status = status
 
 
@@ -72,6 +72,7 @@ def load():
         "bcg_rows_poll": [vp, ctypes.POINTER(i32)],
         "bcg_rows_finish": [vp, ctypes.POINTER(bcg_info)],
         "bcg_debug_fail_alloc": [i32],
+        "bcg_debug_poke_guard": [vp, i32],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -88,6 +89,11 @@ def load():
 def bcg_debug_fail_alloc(nth: int):
     """Make the nth device workspace allocation from now on fail with OOM (0 disarms); for error-path tests."""
     _check(load().bcg_debug_fail_alloc(int(nth)))
+
+
+def bcg_debug_poke_guard(h, index: int):
+    """Overwrite one guard byte after workspace buffer `index` of handle h; for tests of option "guards"."""
+    _check(load().bcg_debug_poke_guard(h, int(index)))
 
 
 def bcg_last_error() -> str:

@@ -78,6 +78,10 @@ namespace {
 // Allocation-failure injection for tests (bcg_debug_fail_alloc): the armed count of workspace allocations still
 // to succeed before one fails (0: disarmed).
 std::atomic<int> g_fail_alloc_in{0};
+// Guard bytes after every workspace buffer (checked with option "guards")
+constexpr int kGuardBytes = 16;
+constexpr unsigned char kGuardByte = 0xA5;
+
 bool injected_alloc_failure() {
   int v = g_fail_alloc_in.load();
   while (v > 0) {
@@ -123,6 +127,7 @@ struct bcg_ctx {
   int refine = 1;                      // FP32_REFINE: 1 residual replacement, 0 restarted refinement
   int retooled = 0;                    // FP64: 1 Dubrulle's retooled block CG instead of Algorithm 1's recurrences
   int tensor_cores = 1;                // FP64, p a multiple of 64: block updates on the tensor cores (tcgen05)
+  int guards = 0;                      // 1: check every buffer's guard bytes after each solve
   // live per-kernel timing (profile = 1): CUDA events around every launch of an executed iteration
   static constexpr int kKernels = 6;   // K1 op_gram, K4a solve_lambda, K2 update_xr, K4b solve_beta, K3 update_p, K0 residual
   double prof_ms[kKernels] = {0, 0, 0, 0, 0, 0};
@@ -130,6 +135,7 @@ struct bcg_ctx {
   std::vector<cudaEvent_t> ev;         // 2 * 5 * check_every events, reused per batch
   // workspace (owned)
   std::vector<void *> allocs;
+  std::vector<size_t> alloc_bytes;     // requested size of each allocation; 16 guard bytes follow it
   double *R = nullptr, *P = nullptr, *Q = nullptr;           // FP64 iteration vectors
   float *R32 = nullptr, *P32 = nullptr, *Q32 = nullptr, *D32 = nullptr;
   void *vals32 = nullptr;              // FP32 copy of CSR values or faces
@@ -166,12 +172,20 @@ struct bcg_ctx {
       return fail(BCG_ERR_OOM, "cudaMalloc of %zu bytes failed: injected failure (bcg_debug_fail_alloc)",
                   count * sizeof(U));
     void *p_ = nullptr;
-    cudaError_t e = cudaMalloc(&p_, count * sizeof(U) + 16);
+    cudaError_t e = cudaMalloc(&p_, count * sizeof(U) + kGuardBytes);
     if (e != cudaSuccess) {
       cudaGetLastError();
       return fail(BCG_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", count * sizeof(U), cudaGetErrorString(e));
     }
+    // the guard bytes after the buffer (written before the buffer is first used, on the legacy stream)
+    e = cudaMemset(static_cast<unsigned char *>(p_) + count * sizeof(U), kGuardByte, kGuardBytes);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    if (e != cudaSuccess) {
+      cudaFree(p_);
+      return fail(BCG_ERR_CUDA, "guard bytes: %s", cudaGetErrorString(e));
+    }
     allocs.push_back(p_);
+    alloc_bytes.push_back(count * sizeof(U));
     *ptr = static_cast<U *>(p_);
     return BCG_OK;
   }
@@ -486,6 +500,22 @@ bcg_status collect_events(bcg_ctx *h, int executed) {
       h->prof_ms[kk] += ms;
       h->prof_count[kk] += 1;
     }
+  }
+  return BCG_OK;
+}
+
+// Every workspace buffer is followed by kGuardBytes bytes of kGuardByte. A kernel that writes past the end of a
+// buffer changes them; with option "guards" the solves compare them after their work has finished.
+bcg_status check_guards(bcg_ctx *h) {
+  CK(cudaStreamSynchronize(h->stream));
+  unsigned char g[kGuardBytes];
+  for (size_t i = 0; i < h->allocs.size(); ++i) {
+    CK(cudaMemcpy(g, static_cast<unsigned char *>(h->allocs[i]) + h->alloc_bytes[i], kGuardBytes,
+                  cudaMemcpyDeviceToHost));
+    for (int b = 0; b < kGuardBytes; ++b)
+      if (g[b] != kGuardByte)
+        return fail(BCG_ERR_GUARD, "guard byte %d after workspace buffer %zu (%zu bytes) was overwritten", b, i,
+                    h->alloc_bytes[i]);
   }
   return BCG_OK;
 }
@@ -1139,6 +1169,9 @@ bcg_status bcg_set_option(bcg_handle h, const char *key, double value) {
   } else if (!strcmp(key, "tensor_cores")) {
     if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "tensor_cores must be 0 or 1");
     h->tensor_cores = (int)value;
+  } else if (!strcmp(key, "guards")) {
+    if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "guards must be 0 or 1");
+    h->guards = (int)value;
   } else if (!strcmp(key, "graph")) {
     if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "graph must be 0 or 1");
     h->use_graph = (int)value;
@@ -1164,7 +1197,12 @@ bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32
     }
     return h->refine ? solve_replace(h, Bs, Xs, tol, maxit, info) : solve_refine(h, Bs, Xs, tol, maxit, info);
   };
-  if (h->perm == nullptr) return run(B, X);
+  auto guarded = [&](bcg_status st) {
+    if (!h->guards || st == BCG_ERR_INVALID_ARG || st == BCG_ERR_CUDA || st == BCG_ERR_OOM) return st;
+    const bcg_status g = check_guards(h);
+    return g == BCG_OK ? st : g;
+  };
+  if (h->perm == nullptr) return guarded(run(B, X));
   // SELL-C-sigma handle: iterate on the permuted system (Pi A Pi^T)(Pi X) = Pi B
   CK(launch_permute_rows(B, h->perm, h->n, h->k, h->Bp, 0, h->nsm, h->stream));
   CK(launch_permute_rows(X, h->perm, h->n, h->k, h->Xp, 0, h->nsm, h->stream));
@@ -1174,7 +1212,7 @@ bcg_status bcg_solve(bcg_handle h, const double *B, double *X, double tol, int32
   CK(launch_permute_rows(h->Xp, h->perm, h->n, h->k, X, 1, h->nsm, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   g_last_error = msg;
-  return st;
+  return guarded(st);
 }
 
 bcg_status bcg_solve_host(bcg_handle h, const double *B, double *X, double tol, int32_t maxit, bcg_info *info) {
@@ -1410,10 +1448,21 @@ bcg_status bcg_rows_finish(bcg_handle h, bcg_info *info) {
     info->max_rel_res_true = NAN;   // needs the other ranks' rows of X: the caller recomputes it
   }
   h->X_rows = nullptr;
+  if (h->guards) CKS(check_guards(h));
   return st;
 }
 
 const char *bcg_last_error(void) { return g_last_error.c_str(); }
+
+bcg_status bcg_debug_poke_guard(bcg_handle h, int32_t index) {
+  if (h == nullptr) return fail(BCG_ERR_INVALID_ARG, "NULL handle");
+  if (index < 0 || (size_t)index >= h->allocs.size())
+    return fail(BCG_ERR_INVALID_ARG, "index=%d, the handle has %zu workspace buffers", index, h->allocs.size());
+  CK(cudaStreamSynchronize(h->stream));
+  CK(cudaMemset(static_cast<unsigned char *>(h->allocs[index]) + h->alloc_bytes[index], 0, 1));
+  CK(cudaStreamSynchronize(0));
+  return BCG_OK;
+}
 
 bcg_status bcg_debug_fail_alloc(int32_t nth) {
   if (nth < 0) return fail(BCG_ERR_INVALID_ARG, "nth=%d must be >= 0", nth);

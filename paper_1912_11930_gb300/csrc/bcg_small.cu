@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
                                                            int p, int global, const int *__restrict__ active,
                                                            double *__restrict__ lam, double *__restrict__ rho_rec,
                                                            DevStatus *st, double *gws, int alpha_circ,
-                                                           int split, int nparts_r) {
+                                                           int nparts_r) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   const int pp = p * p;
@@ -206,7 +206,6 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_lambda(const double *__restr
     if (threadIdx.x == 0) flag_breakdown(st);
     return;
   }
-  if (split) return;   // k_trsm_cols solves for the columns of lambda from L and rho_rec (both in gws)
   // L Y = rho_rec, then L^T lambda = Y; one thread per right-hand-side column b
   for (int b = threadIdx.x; b < p; b += blockDim.x) {
     for (int a = 0; a < p; ++a) {
@@ -277,11 +276,11 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
     }
     return;
   }
+  if (split) return;        // wide blocks: k_bs_gather, the blocked LU and k_trsm_cols follow
   double *sM = sm;          // rho_rec (row-major), LU-factored in place
   double *sB = sM + pp;     // right-hand sides rho (row-major), become beta
-  double *tmp = sB + pp;    // reduction output, then (split) the pivot rows as ints
+  double *tmp = sB + pp;    // reduction output
   double *scr = tmp + pp;
-  int *pivots = reinterpret_cast<int *>(tmp);
   __shared__ int bad, piv;
   __shared__ double thresh;
   reduce_block(partRho, nparts, k, p, global, jb, tmp, scr);
@@ -317,7 +316,6 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
     }
     if (threadIdx.x == 0) {
       piv = best;
-      if (split) pivots[a] = best;
       if (!(bv > thresh)) bad = 1;
     }
     __syncthreads();
@@ -325,7 +323,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
     if (piv != a) {
       for (int col = threadIdx.x; col < p; col += blockDim.x) {
         double t = sM[a * p + col]; sM[a * p + col] = sM[piv * p + col]; sM[piv * p + col] = t;
-        if (!split) { t = sB[a * p + col]; sB[a * p + col] = sB[piv * p + col]; sB[piv * p + col] = t; }
+        t = sB[a * p + col]; sB[a * p + col] = sB[piv * p + col]; sB[piv * p + col] = t;
       }
     }
     __syncthreads();
@@ -333,7 +331,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
     for (int i = a + 1 + threadIdx.x; i < p; i += blockDim.x) sM[i * p + a] /= ua;   // multipliers
     __syncthreads();
     const int m = p - a - 1;
-    const int w = split ? m : m + p;   // split: the right-hand sides are left to k_trsm_cols
+    const int w = m + p;
     for (int e = threadIdx.x; e < m * w; e += blockDim.x) {
       const int i = a + 1 + e / w, col = e % w;
       const double l = sM[i * p + a];
@@ -344,10 +342,6 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
   }
   if (bad) {
     if (threadIdx.x == 0) flag_breakdown(st);
-    return;
-  }
-  if (split) {   // k_trsm_cols applies the pivots and both substitutions
-    if (threadIdx.x == 0) atomicMax(&st->iter, it);
     return;
   }
   for (int b = threadIdx.x; b < p; b += blockDim.x) {
@@ -371,7 +365,7 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
 }
 
 // Triangular solves of the large-block BSOLVEs, spread over the right-hand-side columns: CTA (jb, g) solves
-// columns [8g, 8g + 8) of block jb. The factors come from k_solve_lambda / k_solve_beta (split mode) in the
+// columns [8g, 8g + 8) of block jb. The factors come from the blocked factorizations (k_chol_* / k_lu_*) in the
 // block's global workspace ws = gws + jb * small_ws_doubles(p): M = ws (p x p row-major), B = ws + p*p
 // (right-hand sides, row-major), pivots (LU) as ints at ws + 2*p*p.
 //   chol = 1: M holds L (lower) of alpha = L L^T; out = L^{-T} L^{-1} B  (lambda)
@@ -474,6 +468,325 @@ __global__ void __launch_bounds__(256) k_trsm_cols(int p, int chol, const double
     if (!isfinite(bs[e])) fin = false;
   }
   if (!__syncthreads_and(fin) && threadIdx.x == 0) flag_breakdown(st);
+}
+
+// ---- Blocked factorizations of the large-block BSOLVEs (p > 32, a multiple of 32) -------------------------
+// A p x p factorization on one CTA is a sequence of p barrier-separated rank-1 steps on one SM's share of the
+// FP64 pipe (at p = 256: 4.2 ms for Cholesky, 6.6 ms for LU). Here the partial sums, the panel solves and the
+// trailing updates are spread over many CTAs in separate launches, panel by panel (width 32, right-looking as in
+// LAPACK's blocked xPOTRF / xGETRF): only the 32-column panel factorization runs on one CTA per block.
+// Block jb's workspace ws = gws + jb * small_ws_doubles(p): M (p x p row-major, factored in place), B (p x p
+// row-major right-hand sides), the LU pivots (p ints) at ws + 2 p^2 and the pivot threshold at ws + 3 p^2.
+constexpr int kPB = 32;   // panel width
+
+__device__ __forceinline__ double *blk_ws(double *gws, int jb, int p) {
+  return gws + (int64_t)jb * small_ws_doubles_dev(p);
+}
+
+// Sum the partial rows of two products of block jb, entry (a, b) of each (partial layout b*p + a): M[a][b] =
+// the first (swapM: stored transposed, M[b][a]), B[a][b] = the second; copyB (optional) receives B row-major,
+// zeroOut (optional) is zeroed for a frozen block. Each thread one entry, partials added in partial-row order.
+__global__ void __launch_bounds__(256) k_bs_gather(const double *__restrict__ partM, int npM,
+                                                   const double *__restrict__ partB, int npB, int k, int p,
+                                                   int global, const int *__restrict__ active, double *gws,
+                                                   double *__restrict__ copyB, double *__restrict__ zeroOut,
+                                                   const double *__restrict__ srcM, const DevStatus *st) {
+  if (st->flags != 0) return;
+  const int jb = blockIdx.x, pp = p * p;
+  const int e = blockIdx.y * blockDim.x + threadIdx.x;   // source index b*p + a
+  if (e >= pp) return;
+  if (!active[jb]) {
+    if (zeroOut) zeroOut[(int64_t)jb * pp + e] = 0.0;
+    return;
+  }
+  const int b = e / p, a = e - b * p;
+  const int64_t E = (int64_t)k * p;
+  const int q = global ? k / p : 1;
+  const int64_t base = global ? 0 : (int64_t)jb * pp;
+  auto sum = [&](const double *part, int np) {
+    double v = 0.0;
+    for (int pi = 0; pi < np; ++pi)
+      for (int j = 0; j < q; ++j) v += part[pi * E + base + (int64_t)j * pp + e];
+    return v;
+  };
+  double *ws = blk_ws(gws, jb, p);
+  if (srcM) ws[e] = srcM[(int64_t)jb * pp + e];           // already row-major (the recomputed rho)
+  else ws[a * p + b] = sum(partM, npM);
+  const double vb = sum(partB, npB);
+  ws[pp + a * p + b] = vb;
+  if (copyB) copyB[(int64_t)jb * pp + a * p + b] = vb;
+}
+
+// Cholesky of the diagonal 32 x 32 block at a0 (lower triangle), after the trailing updates of the earlier
+// panels. At a0 = 0 the pivot threshold 64 eps max|diag| of the unfactored matrix is set first.
+__global__ void __launch_bounds__(256) k_chol_diag(double *gws, int p, int a0, const int *__restrict__ active,
+                                                   DevStatus *st) {
+  if (st->flags != 0) return;
+  const int jb = blockIdx.x;
+  if (!active[jb]) return;
+  double *M = blk_ws(gws, jb, p);
+  double *thr = M + 3 * (int64_t)p * p;
+  __shared__ double L[kPB][kPB + 1];
+  __shared__ int bad;
+  if (a0 == 0) {
+    double m = 0.0;
+    for (int a = threadIdx.x; a < p; a += blockDim.x) m = fmax(m, fabs(M[(int64_t)a * p + a]));
+    m = block_max(m);
+    if (threadIdx.x == 0) thr[0] = kPivotFactor * DBL_EPSILON * m;
+  }
+  for (int e = threadIdx.x; e < kPB * kPB; e += blockDim.x) {
+    const int i = e / kPB, j = e % kPB;
+    L[i][j] = M[(int64_t)(a0 + i) * p + a0 + j];
+  }
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const double thresh = thr[0];
+  for (int a = 0; a < kPB; ++a) {
+    if (threadIdx.x == 0) {
+      const double d = L[a][a];
+      if (!(isfinite(d) && d > thresh)) bad = 1;
+      else L[a][a] = sqrt(d);
+    }
+    __syncthreads();
+    if (bad) break;
+    for (int i = a + 1 + threadIdx.x; i < kPB; i += blockDim.x) L[i][a] /= L[a][a];
+    __syncthreads();
+    const int m = kPB - a - 1;
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      const int i = a + 1 + e / m, j = a + 1 + e % m;
+      if (j <= i) L[i][j] -= L[i][a] * L[j][a];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) flag_breakdown(st);
+    return;
+  }
+  for (int e = threadIdx.x; e < kPB * kPB; e += blockDim.x) {
+    const int i = e / kPB, j = e % kPB;
+    if (j <= i) M[(int64_t)(a0 + i) * p + a0 + j] = L[i][j];
+  }
+}
+
+// The panel below the diagonal block: L21 = A21 L11^{-T}, one row per thread.
+__global__ void __launch_bounds__(128) k_chol_panel(double *gws, int p, int a0, const int *__restrict__ active,
+                                                    DevStatus *st) {
+  if (st->flags != 0) return;
+  const int jb = blockIdx.x;
+  if (!active[jb]) return;
+  double *M = blk_ws(gws, jb, p);
+  __shared__ double L[kPB][kPB + 1];
+  for (int e = threadIdx.x; e < kPB * kPB; e += blockDim.x) {
+    const int i = e / kPB, j = e % kPB;
+    L[i][j] = j <= i ? M[(int64_t)(a0 + i) * p + a0 + j] : 0.0;
+  }
+  __syncthreads();
+  const int r = a0 + kPB + blockIdx.y * blockDim.x + threadIdx.x;
+  if (r >= p) return;
+  double *row = M + (int64_t)r * p + a0;
+  double x[kPB];
+#pragma unroll
+  for (int j = 0; j < kPB; ++j) x[j] = row[j];
+#pragma unroll
+  for (int j = 0; j < kPB; ++j) {
+    double v = x[j];
+#pragma unroll
+    for (int m = 0; m < j; ++m) v -= x[m] * L[j][m];
+    x[j] = v / L[j][j];
+  }
+#pragma unroll
+  for (int j = 0; j < kPB; ++j) row[j] = x[j];
+}
+
+// Trailing update of the lower triangle, A22 -= L21 L21^T, one 32 x 32 tile (ti >= tj) per CTA.
+__global__ void __launch_bounds__(256) k_chol_update(double *gws, int p, int a0, const int *__restrict__ active,
+                                                     DevStatus *st) {
+  if (st->flags != 0) return;
+  const int jb = blockIdx.x;
+  if (!active[jb]) return;
+  double *M = blk_ws(gws, jb, p);
+  const int y = blockIdx.y;
+  int ti = (int)((sqrt(8.0 * y + 1.0) - 1.0) * 0.5);
+  while ((ti + 1) * (ti + 2) / 2 <= y) ++ti;
+  while (ti * (ti + 1) / 2 > y) --ti;
+  const int tj = y - ti * (ti + 1) / 2;
+  const int r0 = a0 + kPB + ti * kPB, c0 = a0 + kPB + tj * kPB;
+  __shared__ double Li[kPB][kPB + 1], Lj[kPB][kPB + 1];
+  for (int e = threadIdx.x; e < kPB * kPB; e += blockDim.x) {
+    const int i = e / kPB, m = e % kPB;
+    Li[i][m] = M[(int64_t)(r0 + i) * p + a0 + m];
+    Lj[i][m] = M[(int64_t)(c0 + i) * p + a0 + m];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kPB * kPB; e += blockDim.x) {
+    const int i = e / kPB, j = e % kPB;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int m = 0; m < kPB; ++m) acc = fma(Li[i][m], Lj[j][m], acc);
+    M[(int64_t)(r0 + i) * p + c0 + j] -= acc;
+  }
+}
+
+// LU with partial pivoting of the panel of columns [a0, a0 + 32), rows a0..p-1, in shared memory; the row
+// interchanges are recorded (global row numbers, factorization order) and applied to the rest of each row. At
+// a0 = 0 the threshold 64 eps max|diag| and the finiteness of the matrix are checked first. After the last panel
+// the iteration counter is raised as the one-CTA factorization does.
+__global__ void __launch_bounds__(256) k_lu_panel(double *gws, int p, int a0, const int *__restrict__ active,
+                                                  DevStatus *st) {
+  if (st->flags != 0) return;
+  const int jb = blockIdx.x;
+  if (!active[jb]) return;
+  double *M = blk_ws(gws, jb, p);
+  const int64_t pp = (int64_t)p * p;
+  int *piv = reinterpret_cast<int *>(M + 2 * pp);
+  double *thr = M + 3 * pp;
+  const int rows = p - a0;
+  extern __shared__ __align__(16) double sm_dyn[];
+  double *Pn = sm_dyn;   // Pn[r * 33 + c] = M[a0 + r][a0 + c]
+  constexpr int LD = kPB + 1;
+  __shared__ int bad, best;
+  if (a0 == 0) {
+    double m = 0.0;
+    bool fin = true;
+    for (int a = threadIdx.x; a < p; a += blockDim.x) m = fmax(m, fabs(M[(int64_t)a * p + a]));
+    for (int64_t e = threadIdx.x; e < pp; e += blockDim.x) fin = fin && isfinite(M[e]);
+    m = block_max(m);
+    fin = __syncthreads_and(fin);
+    if (threadIdx.x == 0) thr[0] = fin ? kPivotFactor * DBL_EPSILON * m : NAN;
+  }
+  for (int e = threadIdx.x; e < rows * kPB; e += blockDim.x) {
+    const int r = e / kPB, c = e % kPB;
+    Pn[r * LD + c] = M[(int64_t)(a0 + r) * p + a0 + c];
+  }
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  const double thresh = thr[0];
+  if (!(thresh >= 0.0)) {   // a non-finite entry
+    if (threadIdx.x == 0) flag_breakdown(st);
+    return;
+  }
+  __shared__ double wv[8];
+  __shared__ int wi[8];
+  for (int a = 0; a < kPB; ++a) {
+    // pivot: the largest |Pn[r][a]|, r >= a, smallest r on ties (NaN counts as infinite)
+    double v = -1.0;
+    int idx = rows;
+    for (int r = a + threadIdx.x; r < rows; r += blockDim.x) {
+      const double x = fabs(Pn[r * LD + a]);
+      const double xv = (x == x) ? x : INFINITY;
+      if (xv > v) { v = xv; idx = r; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ov > v || (ov == v && oi < idx)) { v = ov; idx = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { wv[threadIdx.x >> 5] = v; wi[threadIdx.x >> 5] = idx; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bv = -1.0;
+      int bi = rows;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w)
+        if (wv[w] > bv || (wv[w] == bv && wi[w] < bi)) { bv = wv[w]; bi = wi[w]; }
+      best = bi;
+      piv[a0 + a] = a0 + bi;
+      if (!(bv > thresh)) bad = 1;
+    }
+    __syncthreads();
+    if (bad) break;
+    const int bi = best;
+    if (bi != a && threadIdx.x < kPB) {
+      const double t = Pn[a * LD + threadIdx.x];
+      Pn[a * LD + threadIdx.x] = Pn[bi * LD + threadIdx.x];
+      Pn[bi * LD + threadIdx.x] = t;
+    }
+    __syncthreads();
+    const double ua = Pn[a * LD + a];
+    for (int r = a + 1 + threadIdx.x; r < rows; r += blockDim.x) Pn[r * LD + a] /= ua;
+    __syncthreads();
+    const int w = kPB - a - 1;
+    for (int e = threadIdx.x; e < (rows - a - 1) * w; e += blockDim.x) {
+      const int r = a + 1 + e / w, c = a + 1 + e % w;
+      Pn[r * LD + c] -= Pn[r * LD + a] * Pn[a * LD + c];
+    }
+    __syncthreads();
+  }
+  if (bad) {
+    if (threadIdx.x == 0) flag_breakdown(st);
+    return;
+  }
+  for (int e = threadIdx.x; e < rows * kPB; e += blockDim.x) {
+    const int r = e / kPB, c = e % kPB;
+    M[(int64_t)(a0 + r) * p + a0 + c] = Pn[r * LD + c];
+  }
+  // the panel's interchanges on the columns outside it, in factorization order (each column by one thread)
+  for (int c = threadIdx.x; c < p - kPB; c += blockDim.x) {
+    const int col = c < a0 ? c : c + kPB;
+    for (int a = a0; a < a0 + kPB; ++a) {
+      const int r = piv[a];
+      if (r != a) {
+        const double t = M[(int64_t)a * p + col];
+        M[(int64_t)a * p + col] = M[(int64_t)r * p + col];
+        M[(int64_t)r * p + col] = t;
+      }
+    }
+  }
+  if (a0 + kPB == p && threadIdx.x == 0) atomicMax(&st->iter, st->cur);
+}
+
+// U12 = L11^{-1} A12 (L11 unit lower) for 32 columns right of the panel, one column per thread.
+__global__ void __launch_bounds__(32) k_lu_u12(double *gws, int p, int a0, const int *__restrict__ active,
+                                               DevStatus *st) {
+  if (st->flags != 0) return;
+  const int jb = blockIdx.x;
+  if (!active[jb]) return;
+  double *M = blk_ws(gws, jb, p);
+  __shared__ double L[kPB][kPB + 1];
+  for (int e = threadIdx.x; e < kPB * kPB; e += blockDim.x) {
+    const int i = e / kPB, j = e % kPB;
+    L[i][j] = M[(int64_t)(a0 + i) * p + a0 + j];
+  }
+  __syncthreads();
+  const int c = a0 + kPB + blockIdx.y * kPB + threadIdx.x;
+  if (c >= p) return;
+  double x[kPB];
+#pragma unroll
+  for (int j = 0; j < kPB; ++j) x[j] = M[(int64_t)(a0 + j) * p + c];
+#pragma unroll
+  for (int j = 1; j < kPB; ++j) {
+    double v = x[j];
+#pragma unroll
+    for (int m = 0; m < j; ++m) v -= L[j][m] * x[m];
+    x[j] = v;
+  }
+#pragma unroll
+  for (int j = 0; j < kPB; ++j) M[(int64_t)(a0 + j) * p + c] = x[j];
+}
+
+// Trailing update A22 -= L21 U12, one 32 x 32 tile per CTA.
+__global__ void __launch_bounds__(256) k_lu_update(double *gws, int p, int a0, const int *__restrict__ active,
+                                                   DevStatus *st) {
+  if (st->flags != 0) return;
+  const int jb = blockIdx.x;
+  if (!active[jb]) return;
+  double *M = blk_ws(gws, jb, p);
+  const int t = (p - a0 - kPB) / kPB;
+  const int ti = blockIdx.y / t, tj = blockIdx.y % t;
+  const int r0 = a0 + kPB + ti * kPB, c0 = a0 + kPB + tj * kPB;
+  __shared__ double Ls[kPB][kPB + 1], Us[kPB][kPB + 1];
+  for (int e = threadIdx.x; e < kPB * kPB; e += blockDim.x) {
+    const int i = e / kPB, m = e % kPB;
+    Ls[i][m] = M[(int64_t)(r0 + i) * p + a0 + m];
+    Us[i][m] = M[(int64_t)(a0 + i) * p + c0 + m];
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < kPB * kPB; e += blockDim.x) {
+    const int i = e / kPB, j = e % kPB;
+    double acc = 0.0;
+#pragma unroll 8
+    for (int m = 0; m < kPB; ++m) acc = fma(Ls[i][m], Us[m][j], acc);
+    M[(int64_t)(r0 + i) * p + c0 + j] -= acc;
+  }
 }
 
 // Start of a solve: reduce the initial residual norms, mark zero columns converged, reset the status.
@@ -711,6 +1024,8 @@ static bool small_split(int p) { return p > kMaxP; }
 // 8192 partial entries per block (64^2 Poisson, k = 8: 9.4 -> 7.9 ms per solve), 512 above (128^3, k = 32).
 static int small_threads(int nparts, int p) { return (int64_t)nparts * p * p < 8192 ? 128 : kSmallNT; }
 
+static size_t lu_panel_smem(int p, int a0) { return (size_t)(p - a0) * (kPB + 1) * sizeof(double); }
+
 cudaError_t small_prepare(int p) {
   const size_t sm = small_smem(p);
   if (sm > 48 * 1024) {
@@ -719,8 +1034,15 @@ cudaError_t small_prepare(int p) {
     e = cudaFuncSetAttribute(k_solve_beta, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     if (e != cudaSuccess) return e;
   }
-  if (small_split(p) && trsm_smem(p) > 48 * 1024)
-    return cudaFuncSetAttribute(k_trsm_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem(p));
+  if (small_split(p)) {
+    if (lu_panel_smem(p, 0) > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(k_lu_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)lu_panel_smem(p, 0));
+      if (e != cudaSuccess) return e;
+    }
+    if (trsm_smem(p) > 48 * 1024)
+      return cudaFuncSetAttribute(k_trsm_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)trsm_smem(p));
+  }
   return cudaSuccess;
 }
 
@@ -731,17 +1053,53 @@ static cudaError_t launch_trsm(int p, int nblk, int chol, const double *gws, con
   return cudaGetLastError();
 }
 
+// Wide blocks: the partial sums (k_bs_gather), the blocked factorization panel by panel, then the
+// column-parallel triangular solves.
+static cudaError_t launch_blocked_chol(int p, int nblk, double *gws, const int *active, DevStatus *st,
+                                       cudaStream_t s) {
+  for (int a0 = 0; a0 < p; a0 += kPB) {
+    k_chol_diag<<<nblk, 256, 0, s>>>(gws, p, a0, active, st);
+    const int rows = p - a0 - kPB;
+    if (rows > 0) {
+      k_chol_panel<<<dim3((unsigned)nblk, (unsigned)((rows + 127) / 128)), 128, 0, s>>>(gws, p, a0, active, st);
+      const int t = rows / kPB;
+      k_chol_update<<<dim3((unsigned)nblk, (unsigned)(t * (t + 1) / 2)), 256, 0, s>>>(gws, p, a0, active, st);
+    }
+  }
+  return cudaGetLastError();
+}
+
+static cudaError_t launch_blocked_lu(int p, int nblk, double *gws, const int *active, DevStatus *st,
+                                     cudaStream_t s) {
+  for (int a0 = 0; a0 < p; a0 += kPB) {
+    k_lu_panel<<<nblk, 256, lu_panel_smem(p, a0), s>>>(gws, p, a0, active, st);
+    const int rows = p - a0 - kPB;
+    if (rows > 0) {
+      const int t = rows / kPB;
+      k_lu_u12<<<dim3((unsigned)nblk, (unsigned)t), kPB, 0, s>>>(gws, p, a0, active, st);
+      k_lu_update<<<dim3((unsigned)nblk, (unsigned)(t * t)), 256, 0, s>>>(gws, p, a0, active, st);
+    }
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_solve_lambda(const double *partA, const double *partR, int nparts, int nparts_r, int k, int p,
                                 int global, const int *active, double *lam, double *rho_rec, DevStatus *st,
                                 double *gws, int alpha_circ, cudaStream_t s) {
   const int nblk = global ? 1 : k / p;
   if (small_needs_gws(p) && gws == nullptr) return cudaErrorInvalidValue;
-  const int split = small_split(p) ? 1 : 0;
-  k_solve_lambda<<<nblk, small_threads(std::max(nparts, nparts_r), p), small_smem(p), s>>>(
-      partA, partR, nparts, k, p, global, active, lam, rho_rec, st, small_needs_gws(p) ? gws : nullptr, alpha_circ,
-      split, nparts_r);
+  if (!small_split(p)) {
+    k_solve_lambda<<<nblk, small_threads(std::max(nparts, nparts_r), p), small_smem(p), s>>>(
+        partA, partR, nparts, k, p, global, active, lam, rho_rec, st, small_needs_gws(p) ? gws : nullptr,
+        alpha_circ, nparts_r);
+    return cudaGetLastError();
+  }
+  const int pp = p * p;
+  k_bs_gather<<<dim3((unsigned)nblk, (unsigned)((pp + 255) / 256)), 256, 0, s>>>(
+      partA, nparts, partR, nparts_r, k, p, global, active, gws, rho_rec, lam, nullptr, st);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess || !split) return e;
+  if (e != cudaSuccess) return e;
+  if ((e = launch_blocked_chol(p, nblk, gws, active, st, s)) != cudaSuccess) return e;
   return launch_trsm(p, nblk, 1, gws, active, lam, st, s);
 }
 
@@ -753,11 +1111,17 @@ cudaError_t launch_solve_beta(const double *partRho, const double *partN, int np
   const int nblk = global ? 1 : k / p;
   if (small_needs_gws(p) && gws == nullptr) return cudaErrorInvalidValue;
   const int split = small_split(p) ? 1 : 0;
+  // the column norms, the stopping test and the shifts (wide blocks: only these; the solve follows)
   k_solve_beta<<<nblk, small_threads(nparts, p), small_smem(p), s>>>(
       partRho, partN, nparts, k, p, global, tol2, r0n2, rn2, active, block_iters, rho_rec, beta, st,
       small_needs_gws(p) ? gws : nullptr, rho_circ, nparts_n, split, sc);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !split) return e;
+  const int pp = p * p;
+  k_bs_gather<<<dim3((unsigned)nblk, (unsigned)((pp + 255) / 256)), 256, 0, s>>>(
+      nullptr, 0, partRho, nparts, k, p, global, active, gws, nullptr, nullptr, rho_rec, st);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launch_blocked_lu(p, nblk, gws, active, st, s)) != cudaSuccess) return e;
   return launch_trsm(p, nblk, 0, gws, active, beta, st, s);
 }
 

@@ -117,22 +117,37 @@ def make_plans(M, world: int) -> list:
 
 
 class TorchComm:
-    """Exchanges through torch.distributed (NCCL for device tensors on GPUs, gloo for host tensors)."""
+    """Host-ordered exchanges through torch.distributed (gloo on host tensors, or NCCL): the caller's device
+    work is finished before a collective starts, and the collective is finished when the call returns."""
+
+    on_stream = False
 
     def __init__(self, dist):
         self.dist = dist
         self.rank, self.world = dist.get_rank(), dist.get_world_size()
 
+    @staticmethod
+    def _sync(t):
+        if t is not None and t.is_cuda:
+            import torch
+            torch.cuda.synchronize(t.device)
+
     def allreduce_(self, t):
+        self._sync(t)
         self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+        self._sync(t)
 
     def exchange(self, sends, recvs):
         """sends: {rank: tensor}, recvs: {rank: tensor view to fill}."""
+        for t in sends.values():
+            self._sync(t)
         ops = [self.dist.P2POp(self.dist.isend, t, q) for q, t in sends.items()]
         ops += [self.dist.P2POp(self.dist.irecv, t, q) for q, t in recvs.items()]
         if ops:
             for w in self.dist.batch_isend_irecv(ops):
                 w.wait()
+        for t in recvs.values():
+            self._sync(t)
 
     def all_gather_object(self, obj):
         out = [None] * self.world
@@ -140,9 +155,38 @@ class TorchComm:
         return out
 
 
+class StreamComm(TorchComm):
+    """Exchanges enqueued on one CUDA stream (NCCL): each collective is ordered after the work already on
+    `stream` and before the work enqueued after it, and the host never waits for it, so an iteration's phases
+    and exchanges queue up back to back (and can be captured into one CUDA graph)."""
+
+    on_stream = True
+
+    def __init__(self, dist, stream):
+        super().__init__(dist)
+        self.stream = stream
+
+    def allreduce_(self, t):
+        import torch
+        with torch.cuda.stream(self.stream):
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.SUM)
+
+    def exchange(self, sends, recvs):
+        import torch
+        ops = [self.dist.P2POp(self.dist.isend, t, q) for q, t in sends.items()]
+        ops += [self.dist.P2POp(self.dist.irecv, t, q) for q, t in recvs.items()]
+        if not ops:
+            return
+        with torch.cuda.stream(self.stream):
+            for w in self.dist.batch_isend_irecv(ops):
+                w.wait()   # NCCL: the stream waits, not the host
+
+
 class ThreadComm:
     """`world` ranks as threads of one process (one GPU or the CPU): the exchanges are copies between the
     ranks' tensors, sums in rank order. Each rank's device work is finished before it is read."""
+
+    on_stream = False
 
     class _Shared:
         def __init__(self, world):
@@ -198,16 +242,65 @@ class ThreadComm:
         return out
 
 
+class RowSchedule:
+    """The steps of one row-sharded iteration and their order (Algorithm 1 split over row ranges): BOP needs
+    the halo rows of P, so the owners' rows are packed, exchanged and unpacked first; alpha and the recomputed
+    rho (sums1) are sums over all rows, so they are added over ranks before lambda is solved; rho and the
+    column norms (sums2) likewise before the stopping test and beta.
+
+    `ops` runs one rank's share: pack(q, rows, buf), unpack(), phase(i) and the buffers sums1, sums2, halo;
+    `comm` adds over ranks and exchanges rows (host-ordered, or enqueued on the handle's stream)."""
+
+    def __init__(self, ops, comm, send_rows, send_bufs, recv_views):
+        self.ops, self.comm = ops, comm
+        self.send_rows, self.send_bufs, self.recv_views = send_rows, send_bufs, recv_views
+
+    def halo(self):
+        for q, rows in self.send_rows.items():
+            self.ops.pack(q, rows, self.send_bufs[q])
+        self.comm.exchange(self.send_bufs, self.recv_views)
+        self.ops.unpack()
+
+    def iteration(self):
+        self.halo()
+        self.ops.phase(1)
+        self.comm.allreduce_(self.ops.sums1)
+        self.ops.phase(2)
+        self.comm.allreduce_(self.ops.sums2)
+        self.ops.phase(3)
+
+
+class _HandleOps:
+    """One rank's share through the C ABI (bcg_rows_*): every call enqueues on the handle's stream."""
+
+    def __init__(self, bcg, h, sums1, sums2, halo):
+        self.bcg, self.h, self.sums1, self.sums2, self.halo = bcg, h, sums1, sums2, halo
+
+    def pack(self, q, rows, buf):
+        self.bcg.bcg_rows_pack(self.h, rows, rows.numel(), buf)
+
+    def unpack(self):
+        if self.halo.shape[0]:
+            self.bcg.bcg_rows_unpack(self.h, self.halo, self.halo.shape[0])
+
+    def phase(self, i):
+        self.bcg.bcg_rows_phase(self.h, i)
+
+
 class RowShardedSolver:
     """One rank's share of a row-sharded solve (FP64, CSR): a handle on this rank's rows plus the buffers of
-    its exchanges. `comm` is a TorchComm or a ThreadComm."""
+    its exchanges. `comm` is a StreamComm (NCCL on the handle's stream: no host synchronisation inside a batch
+    of iterations; with `graph`, each batch after the first is one CUDA graph replay), a TorchComm (host-
+    ordered) or a ThreadComm (ranks as threads of one process)."""
 
-    def __init__(self, plan: RowPlan, *, k, p=1, sub="hybrid", comm, device=None, precond=0):
+    def __init__(self, plan: RowPlan, *, k, p=1, sub="hybrid", comm, device=None, precond=0, graph=False):
         import torch
         from . import bcg
         self.torch, self.bcg, self.plan, self.comm = torch, bcg, plan, comm
         self.device = torch.device(device or "cuda")
-        self.stream = torch.cuda.Stream(device=self.device)
+        self.stream = comm.stream if getattr(comm, "on_stream", False) else torch.cuda.Stream(device=self.device)
+        self.graph = bool(graph) and getattr(comm, "on_stream", False)
+        self._graphs, self._warm, self._parity = {}, False, 0
         self.k = k
         self.p = 1 if sub == "parallel" else (k if sub == "classical" else p)
         self.nblk = 1 if sub == "global" else k // self.p
@@ -229,47 +322,58 @@ class RowShardedSolver:
         bcg.bcg_rows_bind(self.h, self.sums1, self.sums2)
         if precond:
             bcg.bcg_set_option(self.h, "precond", precond)
+        self.schedule = RowSchedule(_HandleOps(bcg, self.h, self.sums1, self.sums2, self.halo), comm,
+                                    self.send_rows, self.send_bufs, self.recv_views)
 
-    def _halo(self, X=None):
-        """Refresh the halo rows of P (or of X, when given) from their owners."""
-        bcg, torch = self.bcg, self.torch
-        for q, rows in self.send_rows.items():
-            if X is None:
-                bcg.bcg_rows_pack(self.h, rows, rows.numel(), self.send_bufs[q])
-            else:
-                with torch.cuda.stream(self.stream):
-                    torch.index_select(X[:self.plan.n_local], 0, rows.long(), out=self.send_bufs[q])
-        self.stream.synchronize()
+    def _halo_x(self, X):
+        """The halo rows of X^0 from their owners (once per solve, on the handle's stream)."""
+        torch = self.torch
+        with torch.cuda.stream(self.stream):
+            for q, rows in self.send_rows.items():
+                torch.index_select(X[:self.plan.n_local], 0, rows.long(), out=self.send_bufs[q])
         self.comm.exchange(self.send_bufs, self.recv_views)
-        if X is None:
-            bcg.bcg_rows_unpack(self.h, self.halo, self.halo.shape[0])
-        else:
+        with torch.cuda.stream(self.stream):
             X[self.plan.n_local:].copy_(self.halo)
+
+    def _batch(self, n, X):
+        """n iterations: enqueued eagerly, or (graph) the replay of a graph captured for batches of n. The first
+        batch runs eagerly, so that the communicators and the kernels' first-launch set-up exist before a
+        capture. A graph fixes the host-side arguments of the calls it captured: the solution buffer X (set by
+        bcg_rows_start) and, with blocks wider than 32, which of two buffers holds P (the library swaps P and Q
+        once per iteration) -- so graphs are kept per (n, X, parity of the iterations run on the handle)."""
+        torch = self.torch
+        key = (n, X.data_ptr(), self._parity)
+        g = self._graphs.get(key)
+        if g is None and (not self.graph or not self._warm):
+            for _ in range(n):
+                self.schedule.iteration()
+        else:
+            if g is None:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(g, stream=self.stream):
+                    for _ in range(n):
+                        self.schedule.iteration()
+                self._graphs[key] = g
+            with torch.cuda.stream(self.stream):   # a replay runs on the current stream: the handle's
+                g.replay()
+        self._warm = True
+        self._parity ^= n & 1
 
     def solve(self, B, X, tol=1e-8, maxit=10000, check_every=8):
         """B: n_local x k; X: n_cols x k (rows beyond n_local are scratch for the halo of X^0). Returns the
-        SolveResult of this rank (identical on every rank)."""
+        SolveResult of this rank (identical on every rank). The host waits once per `check_every` iterations
+        (the stopping poll); the exchanges in between follow `comm`'s ordering."""
         bcg, torch = self.bcg, self.torch
         torch.cuda.synchronize(self.device)
-        self._halo(X)
-        torch.cuda.synchronize(self.device)
+        self._halo_x(X)
         bcg.bcg_rows_start(self.h, B, X, tol)
-        self.stream.synchronize()
         self.comm.allreduce_(self.norms)
         bcg.bcg_rows_start_status(self.h)
         done = bcg.bcg_rows_poll(self.h)
         it = 0
         while not done and it < maxit:
             n = min(check_every, maxit - it)
-            for _ in range(n):
-                self._halo()
-                bcg.bcg_rows_phase(self.h, 1)
-                self.stream.synchronize()
-                self.comm.allreduce_(self.sums1)
-                bcg.bcg_rows_phase(self.h, 2)
-                self.stream.synchronize()
-                self.comm.allreduce_(self.sums2)
-                bcg.bcg_rows_phase(self.h, 3)
+            self._batch(n, X)
             it += n
             done = bcg.bcg_rows_poll(self.h)
         st, info = bcg.bcg_rows_finish(self.h)

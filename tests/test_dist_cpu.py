@@ -149,3 +149,101 @@ def test_torch_comm_two_ranks_row_split(tmp_path):
     mp.start_processes(_rows_worker, args=(world, _free_port(), str(tmp_path)), nprocs=world, start_method="spawn")
     for r in range(world):
         assert np.load(tmp_path / f"r{r}.npy").all()
+
+
+# ---- the row-sharded iteration schedule on host tensors (gloo, 2 and 3 ranks) ----
+class _HostRankOps:
+    """One rank's share of Algorithm 1 on its rows, on host tensors, from the oracle's primitives: the
+    interface RowSchedule drives (pack, unpack, phase 1..3, sums1, sums2, halo). Partial block products over
+    the rank's rows go into sums1 / sums2 and are complete only after the schedule has added them over ranks."""
+
+    def __init__(self, plan, B, X0, k, p, sub, torch):
+        import scipy.sparse as sp
+        from oracle import bcg as O
+        self.O, self.torch = O, torch
+        self.kind, self.p = O.canonical_subalgebra(sub, k, p)
+        self.q = k // self.p
+        self.nl = plan.n_local
+        self.A = sp.csr_matrix((plan.vals, plan.colind, plan.rowptr), shape=(plan.n_local, plan.n_cols))
+        nb = self.q if self.kind == "hybrid" else 1
+        self.E = nb * self.p * self.p
+        self.shape = (nb, self.p, self.p)
+        self.sums1 = torch.zeros(2 * self.E, dtype=torch.float64)
+        self.sums2 = torch.zeros(self.E + k, dtype=torch.float64)
+        self.halo = torch.zeros(len(plan.halo_gids), k, dtype=torch.float64)
+        self.X = X0.copy()                          # n_cols x k: own rows, then X^0's halo rows
+        self.R = B - self.A @ self.X
+        self.P = np.zeros_like(self.X)
+        self.P[:self.nl] = self.R
+        self.active = np.ones(nb, dtype=bool)
+
+    def pack(self, q, rows, buf):
+        buf.copy_(self.torch.from_numpy(self.P[rows.numpy().astype(np.int64)]))
+
+    def unpack(self):
+        self.P[self.nl:] = self.halo.numpy()
+
+    def phase(self, i):
+        O, Pl = self.O, self.P[:self.nl]
+        if i == 1:
+            self.Q = self.A @ self.P
+            self.sums1[:self.E] = self.torch.from_numpy(O.block_product(Pl, self.Q, self.p, self.kind).ravel())
+            self.sums1[self.E:] = self.torch.from_numpy(O.block_product(Pl, self.R, self.p, self.kind).ravel())
+        elif i == 2:
+            curv = self.sums1[:self.E].numpy().reshape(self.shape)
+            self.proj = self.sums1[self.E:].numpy().reshape(self.shape).copy()
+            lam, ok = O.bsolve_cholesky(curv, self.proj, self.active)
+            assert ok
+            self.X[:self.nl] = O.baxpy(self.X[:self.nl], Pl, lam, +1.0)
+            self.R = O.baxpy(self.R, self.Q, lam, -1.0)
+            self.sums2[:self.E] = self.torch.from_numpy(O.block_product(self.R, self.R, self.p, self.kind).ravel())
+            self.sums2[self.E:] = self.torch.from_numpy(np.sum(self.R * self.R, axis=0))
+        else:
+            zr = self.sums2[:self.E].numpy().reshape(self.shape)
+            beta, ok = O.bsolve_lu(self.proj, zr, self.active)
+            assert ok
+            self.P[:self.nl] = O.baxpy(self.R, Pl, beta, +1.0)
+
+
+def _schedule_worker(rank, world, port, out, sub, k, p, m):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import torch
+    from paper_1912_11930_gb300 import workloads as W
+    M = W.poisson3d(7, 6, 8)
+    B = W.rhs(M.n, k, seed=11)
+    X0 = 0.01 * W.rhs(M.n, k, seed=12)
+    comm = D.TorchComm(dist)
+    plan = D.local_plan(M.rowptr, M.colind, M.vals, D.row_bounds(M.n, world), rank)
+    D.fill_sends(plan, comm.all_gather_object(plan.requests))
+    r0, r1 = plan.bounds[rank], plan.bounds[rank + 1]
+    ops = _HostRankOps(plan, B[r0:r1], np.vstack([X0[r0:r1], X0[plan.halo_gids]]), k, p, sub, torch)
+    send_rows = {q: torch.from_numpy(rows) for q, rows in plan.send}
+    send_bufs = {q: torch.empty(len(rows), k, dtype=torch.float64) for q, rows in plan.send}
+    recv_views = {q: ops.halo[off:off + cnt] for q, off, cnt in plan.recv}
+    sched = D.RowSchedule(ops, comm, send_rows, send_bufs, recv_views)
+    for _ in range(m):
+        sched.iteration()
+    np.save(os.path.join(out, f"x{rank}.npy"), ops.X[:plan.n_local])
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("world,sub,k,p", [(2, "hybrid", 6, 3), (3, "global", 4, 2), (2, "classical", 4, 4)])
+def test_row_schedule_over_gloo_ranks_matches_the_oracle(tmp_path, world, sub, k, p):
+    """RowSchedule's order of steps (halo of P, phase 1, sum over ranks, phase 2, sum, phase 3), driven over
+    gloo ranks whose shares are written from the oracle's primitives, reproduces the unsharded Algorithm 1:
+    the iterates after m iterations equal the oracle's on the whole matrix up to the rounding of the partial
+    sums' order."""
+    from oracle import bcg as O
+    from paper_1912_11930_gb300 import workloads as W
+    m = 12
+    mp.start_processes(_schedule_worker, args=(world, _free_port(), str(tmp_path), sub, k, p, m), nprocs=world,
+                       start_method="spawn")
+    M = W.poisson3d(7, 6, 8)
+    B = W.rhs(M.n, k, seed=11)
+    X0 = 0.01 * W.rhs(M.n, k, seed=12)
+    ref = O.solve(M.to_scipy(), B, X0=X0, p=p, sub=sub, tol=0.0, maxit=m)
+    X = np.vstack([np.load(tmp_path / f"x{r}.npy") for r in range(world)])
+    err = np.abs(X - ref.X).max(axis=0) / np.abs(ref.X).max(axis=0)
+    assert np.all(err <= 1e-11), err

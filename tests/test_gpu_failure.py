@@ -78,3 +78,47 @@ def test_failure_of_the_host_entry_staging_leaves_the_handle_usable(lib):
 def test_debug_hook_rejects_negative_counts(lib):
     with pytest.raises(bcg.BCGError):
         bcg.bcg_debug_fail_alloc(-1)
+
+
+# ---- guard bytes after every workspace buffer (option "guards") ----
+GUARD_CASES = [  # odd sizes and every form: (matrix, k, p, sub, prec, options)
+    ("p3d_odd", 5, 5, "classical", "fp64", {}), ("p3d_odd", 6, 3, "hybrid", "fp64", {}),
+    ("p3d_odd", 12, 4, "global", "fp64", {}), ("p3d_odd", 7, 1, "parallel", "fp64", {}),
+    ("p3d_odd", 32, 8, "hybrid", "fp32_refine", {}), ("p3d_odd", 32, 8, "hybrid", "fp64_df", {}),
+    ("p3d_odd", 64, 64, "classical", "fp64", {}), ("p3d_odd", 128, 64, "hybrid", "fp64", {"tensor_cores": 0}),
+    ("p3d_odd", 24, 12, "hybrid", "fp64", {"retooled": 1}), ("vc_odd", 16, 4, "hybrid", "fp64", {"precond": 1}),
+]
+
+
+def _guard_mat(name):
+    return {"p3d_odd": lambda: W.poisson3d(13, 11, 7), "vc_odd": lambda: W.varcoef3d(9, 11, 13, seed=2)}[name]()
+
+
+@pytest.mark.parametrize("name,k,p,sub,prec,opts", GUARD_CASES)
+def test_guard_bytes_intact_after_solves(lib, name, k, p, sub, prec, opts):
+    """Odd shapes (n = 1001 and 1287 rows, ragged tails in every kernel's row split) through every form with the
+    guard check on: no kernel writes past the end of any workspace buffer, and the solution still meets the
+    tolerance; then one overwritten guard byte is reported as BCG_ERR_GUARD."""
+    import torch
+    dev = torch.device("cuda:0")
+    M = _guard_mat(name)
+    S = bcg.Solver.from_matrix(M, k=k, p=p, sub=sub, prec=prec, device=dev)
+    S.set_option("guards", 1)
+    for key, v in opts.items():
+        S.set_option(key, v)
+    B = W.rhs(M.n, k, seed=9)
+    Bt = torch.from_numpy(B).to(dev)
+    X, r = S.solve(Bt, tol=1e-8, maxit=3000)
+    assert r.ok, r
+    res = np.linalg.norm(B - M.to_scipy() @ X.cpu().numpy(), axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(res <= 1.5e-8), res
+    Xh = np.zeros_like(B)
+    st, info = bcg.bcg_solve_host(S.h, np.ascontiguousarray(B), Xh, 1e-8, 3000)
+    assert st == bcg.OK
+    bcg.bcg_debug_poke_guard(S.h, 0)
+    with pytest.raises(bcg.BCGError) as ei:
+        S.solve(Bt, tol=1e-8, maxit=3000)
+    assert ei.value.status == bcg.GUARD and "buffer 0" in str(ei.value)
+    with pytest.raises(bcg.BCGError):
+        bcg.bcg_debug_poke_guard(S.h, 100000)
+    S.close()

@@ -120,3 +120,79 @@ def test_rows_handle_rejects_misuse(lib):
     with pytest.raises(bcg.BCGError, match="halo rows"):
         bcg.bcg_rows_unpack(h, X, 3)
     bcg.bcg_destroy(h)
+
+
+@pytest.fixture(scope="module")
+def nccl_world1(lib):
+    """A one-rank NCCL process group in this process (no peer: nothing waits on another GPU)."""
+    import socket
+    import torch
+    import torch.distributed as dist
+    if dist.is_initialized():
+        pytest.skip("a process group already exists in this process")
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    torch.cuda.set_device(0)
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    yield dist
+    dist.destroy_process_group()
+
+
+@pytest.mark.parametrize("sub,k,p,m", [("hybrid", 32, 8, 21), ("global", 16, 4, 17), ("classical", 64, 64, 10)])
+def test_rows_on_stream_nccl_with_graphs(nccl_world1, sub, k, p, m):
+    """The production driver: NCCL collectives enqueued on the handle's stream (StreamComm, no host wait inside
+    a batch), eagerly and with each batch after the first captured into a CUDA graph and replayed. Both give
+    bitwise the same iterate, which matches the oracle at the one-rank bars (1e-9 at equal iterations); a
+    batch count that leaves an odd remainder (m = 21, 17) runs its last batch eagerly."""
+    import torch
+    from paper_1912_11930_gb300 import dist as D
+    dist = nccl_world1
+    dev = torch.device("cuda:0")
+    M = _mat("p3d")
+    B = W.rhs(M.n, k, seed=1)
+    X0 = 0.01 * W.rhs(M.n, k, seed=2)
+    plan = D.make_plans(M, 1)[0]
+    out = {}
+    for graph in (False, True):
+        stream = torch.cuda.Stream(dev)
+        S = D.RowShardedSolver(plan, k=k, p=p, sub=sub, comm=D.StreamComm(dist, stream), device=dev, graph=graph)
+        Bq = torch.from_numpy(B).to(dev)
+        Xq = torch.from_numpy(X0.copy()).to(dev)
+        r = S.solve(Bq, Xq, tol=NEVER, maxit=m, check_every=4)
+        torch.cuda.synchronize(dev)
+        assert r.status == bcg.NOT_CONVERGED and r.iters == m, r
+        assert bool(S._graphs) == graph
+        out[graph] = Xq.cpu().numpy()
+        # a second solve on the same handle replays the graph from its first batch on
+        Xq.copy_(torch.from_numpy(X0))
+        r2 = S.solve(Bq, Xq, tol=NEVER, maxit=m, check_every=4)
+        torch.cuda.synchronize(dev)
+        assert r2.iters == m and np.array_equal(Xq.cpu().numpy(), out[graph])
+        S.close()
+    assert np.array_equal(out[False], out[True])
+    ref = O.solve(M.to_scipy(), B, X0=X0, p=p, sub=sub, tol=0.0, maxit=m)
+    assert_close(out[True], ref.X, 1e-9)
+
+
+def test_rows_on_stream_converges(nccl_world1):
+    import torch
+    from paper_1912_11930_gb300 import dist as D
+    dev = torch.device("cuda:0")
+    M = _mat("vc")
+    A = M.to_scipy()
+    k, p = 16, 4
+    B = W.rhs(M.n, k, seed=3)
+    stream = torch.cuda.Stream(dev)
+    S = D.RowShardedSolver(D.make_plans(M, 1)[0], k=k, p=p, sub="hybrid", comm=D.StreamComm(nccl_world1, stream),
+                           device=dev, graph=True)
+    X = torch.zeros(M.n, k, dtype=torch.float64, device=dev)
+    r = S.solve(torch.from_numpy(B).to(dev), X, tol=1e-8, maxit=3000)
+    S.close()
+    assert r.ok, r
+    ref = O.solve(A, B, p=p, sub="hybrid", tol=1e-8, maxit=3000)
+    assert abs(r.iters - ref.iters) <= 2
+    Xh = X.cpu().numpy()
+    res = np.linalg.norm(B - A @ Xh, axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(res <= 1.5e-8), res
