@@ -314,50 +314,80 @@ def retooled_direction(Q: np.ndarray, S: np.ndarray, psi: np.ndarray) -> np.ndar
 
 
 def solve_retooled(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, sub: str = "hybrid",
-                   tol: float = 1e-8, maxit: int = 1000, record: bool = False) -> Result:
-    """Dubrulle's retooled block CG (Electron. Trans. Numer. Anal. 12, 2001) in the hybrid family of
-    subalgebras, FP64, step by step; M = I. Per iteration, for every block that has not converged:
+                   tol: float = 1e-8, maxit: int = 1000, record: bool = False, precond: str = "none") -> Result:
+    """Dubrulle's retooled block CG (Electron. Trans. Numer. Anal. 12, 2001) in a *-subalgebra S of Section 2,
+    FP64, step by step. The residual is carried as R = Q C with C in S (upper triangular blocks) and Q
+    orthonormal for the product <<Q, M^{-1} Q>> = I; the directions are P = S C. Per iteration, for every
+    block that has not converged:
 
         W = A S;  alpha = <<S, W>>;  xi = alpha^{-1};  X += S (xi C);  T = Q - W xi;
-        gamma = <<T, T>>;  ||R_s||^2 = (C^T gamma C)_ss  (stopping test);
-        gamma = psi^T psi (Cholesky);  C = psi C;  Q = T psi^{-1};  S = Q + S psi^T
+        ||R_s||^2 = (C^T <<T, T>>_Hy C)_ss  (stopping test, per column);
+        gamma = <<T, M^{-1} T>> = psi^T psi (Cholesky);  C = psi C;  Q = T psi^{-1};  S = M^{-1} Q + S psi^T
 
-    starting from R^0 = B - A X^0 = Q C (Cholesky QR) and S = Q. In exact arithmetic X^i is Algorithm 1's
-    iterate (P^i = S^i C^{i-1}, R^i = Q^i C^i)."""
+    starting from <<R^0, M^{-1} R^0>> = C^T C, Q = R^0 C^{-1} and S = M^{-1} Q. These follow from Algorithm 1's
+    recurrences with R^i = Q^i C^i and P^{i+1} = S^{i+1} C^i: lambda = C^{-1} xi C, so P lambda = S xi C; the
+    new residual is (Q - W xi) C; rho = <<R, M^{-1} R>> = C^T gamma C; and beta = (C^T C)^{-1} C_new^T C_new
+    turns P_new = M^{-1} R_new + P beta into S_new C_new with S_new = M^{-1} Q_new + S psi^T. For the global
+    subalgebra the coefficients (C, xi, psi) are one p x p matrix shared by the q column blocks and the
+    products sum over blocks; the column norms still take each block's own <<T_j, T_j>>. In exact arithmetic
+    X^i is Algorithm 1's iterate with the same preconditioner.
+
+    ``precond``: "none" (M = I) or "jacobi" (M = diag(A))."""
     B = np.asarray(B, dtype=np.float64)
     n, k = B.shape
     kind, p = canonical_subalgebra(sub, k, p)
-    if kind != "hybrid":
-        raise ValueError("the retooled form runs in the hybrid, parallel and classical subalgebras")
     q = k // p
+    nb = q if kind == "hybrid" else 1
     X = np.zeros_like(B) if X0 is None else np.array(X0, dtype=np.float64, copy=True)
+    minv = _preconditioner(A, precond)
     hist = {"X": [], "Q": [], "S": [], "C": []} if record else {}
 
     def cols(j):
         return slice(j * p, (j + 1) * p)
 
+    def blk(j):   # which coefficient block serves column block j
+        return j if kind == "hybrid" else 0
+
+    def block_of(j):   # the stopping unit of column block j
+        return j if kind == "hybrid" else 0
+
     R = B - bop(A, X)
-    r0 = np.sqrt(np.sum(R * R, axis=0))
+    r0 = _column_norms(R)
     if not (np.all(np.isfinite(r0)) and np.all(np.isfinite(X))):
-        return Result(X, NUMERIC, 0, np.zeros(q, dtype=np.int64), -1, r0 * np.nan, r0 * np.nan, hist)
+        return Result(X, NUMERIC, 0, np.zeros(nb, dtype=np.int64), -1, r0 * np.nan, r0 * np.nan, hist)
     rn = r0.copy()
-    active = np.array([not np.all(r0[cols(j)] <= tol * r0[cols(j)]) for j in range(q)])
-    block_iters = np.zeros(q, dtype=np.int64)
+    active = ~_converged_blocks(r0, r0, tol, kind, p, q)
+    block_iters = np.zeros(nb, dtype=np.int64)
     status, brk, it = OK, -1, 0
-    # R^0 = Q^0 C^0 (Cholesky QR of every active block), S^1 = Q^0
-    C = np.zeros((q, p, p))
+
+    def chol_qr(G, act):
+        """Per active coefficient block: the lower factor L of G = L L^T (column-relative pivot test); psi = L^T."""
+        Ls = np.zeros((nb, p, p))
+        for b in range(nb):
+            if not act[b]:
+                continue
+            L = cholesky_lower_colrel(G[b])
+            if L is None:
+                return None
+            Ls[b] = L
+        return Ls
+
+    def right_div(Y, L):
+        """Y psi^{-1} = Y L^{-T}, by a triangular solve."""
+        return sla.solve_triangular(L, Y.T, lower=True).T
+
+    # R^0 = Q^0 C^0 with <<Q^0, M^{-1} Q^0>> = I, S^1 = M^{-1} Q^0
+    C = np.zeros((nb, p, p))
     Q = np.zeros_like(B)
-    gamma = block_product(R, R, p, "hybrid")
-    for j in range(q):
-        if not active[j]:
-            continue
-        L = cholesky_lower_colrel(gamma[j])
-        if L is None:
-            status, brk = BREAKDOWN, 1
-            break
-        C[j] = L.T
-        Q[:, cols(j)] = sla.solve_triangular(L, R[:, cols(j)].T, lower=True).T
-    S = Q.copy()
+    Ls = chol_qr(block_product(R, minv(R), p, kind), active)
+    if Ls is None:
+        status, brk = BREAKDOWN, 1
+    else:
+        C = np.transpose(Ls, (0, 2, 1)).copy()
+        for j in range(q):
+            if active[block_of(j)]:
+                Q[:, cols(j)] = right_div(R[:, cols(j)], Ls[blk(j)])
+    S = minv(Q)
     if record and status == OK:
         hist["X"].append(X.copy()); hist["Q"].append(Q.copy()); hist["S"].append(S.copy())
         hist["C"].append(C.copy())
@@ -365,51 +395,52 @@ def solve_retooled(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, s
     while status == OK and np.any(active) and it < maxit:
         it += 1
         block_iters[active] = it
-        # W = A S ; alpha = <<S, W>>
         Wm = bop(A, S)
-        alpha = block_product(S, Wm, p, "hybrid")
-        # xi = alpha^{-1} (Cholesky) ; lambda = xi C
-        xi = np.zeros((q, p, p))
-        lam = np.zeros((q, p, p))
-        for j in range(q):
-            if not active[j]:
+        alpha = block_product(S, Wm, p, kind)
+        xi = np.zeros((nb, p, p))
+        lam = np.zeros((nb, p, p))
+        for b in range(nb):
+            if not active[b]:
                 continue
-            L = cholesky_lower_colrel(alpha[j])
+            L = cholesky_lower_colrel(alpha[b])
             if L is None:
                 status, brk = BREAKDOWN, it
                 break
             Linv = sla.solve_triangular(L, np.eye(p), lower=True)
-            xi[j] = Linv.T @ Linv
-            lam[j] = retooled_solution_coefficient(xi[j], C[j])
+            xi[b] = Linv.T @ Linv
+            lam[b] = retooled_solution_coefficient(xi[b], C[b])
         if status != OK:
             break
-        # X += S lambda ; T = Q - W xi
         X = baxpy(X, S, lam, +1.0)
         T = baxpy(Q, Wm, xi, -1.0)
-        # gamma = <<T, T>> ; ||R_s||^2 = (C^T gamma C)_ss since R = T C
-        gamma = block_product(T, T, p, "hybrid")
+        # column norms of R = T C from each column block's own <<T_j, T_j>>
+        Gh = block_product(T, T, p, "hybrid")
         for j in range(q):
-            if active[j]:
-                rn[cols(j)] = np.sqrt(np.diag(C[j].T @ gamma[j] @ C[j]))
+            if active[block_of(j)]:
+                Cb = C[blk(j)]
+                rn[cols(j)] = np.sqrt(np.diag(Cb.T @ Gh[j] @ Cb))
         if not np.all(np.isfinite(rn)):
             status = NUMERIC
             break
+        active = active & ~_converged_blocks(rn, r0, tol, kind, p, q)
+        # gamma = <<T, M^{-1} T>> = psi^T psi; C = psi C; Q = T psi^{-1}; S = M^{-1} Q + S psi^T
+        Ls = chol_qr(block_product(T, minv(T), p, kind), active)
+        if Ls is None:
+            status, brk = BREAKDOWN, it
+            break
+        Qn = Q.copy()
         for j in range(q):
-            if active[j] and np.all(rn[cols(j)] <= tol * r0[cols(j)]):
-                active[j] = False
-        # T = Q^+ psi (Cholesky QR); C = psi C ; S = Q^+ + S psi^T
+            if active[block_of(j)]:
+                Qn[:, cols(j)] = right_div(T[:, cols(j)], Ls[blk(j)])
+        Zq = minv(Qn)
         for j in range(q):
-            if not active[j]:
-                continue
-            L = cholesky_lower_colrel(gamma[j])
-            if L is None:
-                status, brk = BREAKDOWN, it
-                break
-            psi = L.T
-            C[j] = psi @ C[j]
-            Qj = sla.solve_triangular(L, T[:, cols(j)].T, lower=True).T
-            S[:, cols(j)] = retooled_direction(Qj, S[:, cols(j)], psi)
-            Q[:, cols(j)] = Qj
+            b = block_of(j)
+            if active[b]:
+                S[:, cols(j)] = retooled_direction(Zq[:, cols(j)], S[:, cols(j)], Ls[blk(j)].T)
+                Q[:, cols(j)] = Qn[:, cols(j)]
+        for b in range(nb):
+            if active[b]:
+                C[b] = Ls[b].T @ C[b]
         if record:
             hist["X"].append(X.copy()); hist["Q"].append(Q.copy()); hist["S"].append(S.copy())
             hist["C"].append(C.copy())
@@ -418,7 +449,7 @@ def solve_retooled(A, B: np.ndarray, X0: np.ndarray | None = None, p: int = 1, s
         status = NOT_CONVERGED
     with np.errstate(invalid="ignore", divide="ignore"):
         rel_rec = np.where(r0 > 0, rn / np.where(r0 > 0, r0, 1.0), 0.0)
-        rt = np.sqrt(np.sum((B - bop(A, X)) ** 2, axis=0))
+        rt = _column_norms(B - bop(A, X))
         rel_true = np.where(r0 > 0, rt / np.where(r0 > 0, r0, 1.0), rt)
     return Result(X, status, it, block_iters, brk, rel_rec, rel_true, hist)
 
