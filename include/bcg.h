@@ -196,9 +196,10 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
  *                  R = Q C with Q orthonormal in the S-product (a Cholesky QR per block) and the search
  *                  directions are built from Q; the same iterates in exact arithmetic, but a right-hand side
  *                  whose columns differ in scale by many orders factors like a well-scaled one. Each Cholesky
- *                  pivot is tested against its own diagonal entry. FP64 handles of the hybrid, parallel or
- *                  classical subalgebra with M = I only (INVALID_ARG otherwise, from bcg_set_option or, for
- *                  "precond", from bcg_solve); 0 = Algorithm 1 (default).
+ *                  pivot is tested against its own diagonal entry. Every subalgebra (global: one factor shared
+ *                  by the column blocks) and both preconditioners (Jacobi: Q orthonormal in the product
+ *                  <<Q, M^{-1} Q>>, directions M^{-1} Q + S psi^T). FP64 handles that are not row-sharded
+ *                  only (INVALID_ARG otherwise); 0 = Algorithm 1 (default).
  *   "guards"       1 = after each solve (bcg_solve, bcg_solve_host, bcg_rows_finish) compare the 16 guard
  *                  bytes that follow every workspace buffer of the handle with the pattern written at
  *                  allocation; a change returns BCG_ERR_GUARD naming the buffer. 0 = no check (default).

@@ -279,7 +279,7 @@ bcg_status setup_workspace(bcg_ctx *h) {
     CKS(h->alloc(&h->tc_cexp, (size_t)h->nblk * h->p));
     CKS(h->alloc(&h->tc_ecol, 2 * (size_t)h->k));
   }
-  if (h->prec != BCG_FP32_REFINE && !h->global) {
+  if (h->prec != BCG_FP32_REFINE) {
     CKS(h->alloc(&h->dr_C, pp));
     CKS(h->alloc(&h->dr_xi, pp));
     CKS(h->alloc(&h->dr_psiinv, pp));
@@ -670,7 +670,8 @@ bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int ma
 }
 
 // Dubrulle's retooled block CG (option "retooled"; Electron. Trans. Numer. Anal. 12, 2001, the stability reference
-// of Section 3), FP64, hybrid family, M = I; the kernels and the recurrences are described in bcg_retooled.inc.
+// of Section 3), FP64, every subalgebra, M = I or Jacobi; the kernels and the recurrences are described in
+// bcg_retooled.inc.
 // p <= 32: Algorithm 1's K1 for W = A S and alpha, then two fused streaming updates, all in place (S, W, Q
 // keep their buffers).
 // p > 32: the tiled large-block kernels, unfused, and three n x k buffers rotate: W = A S is dead once
@@ -679,41 +680,45 @@ bcg_status solve_fp64(bcg_ctx *h, const double *B, double *X, double tol, int ma
 // without a base term (a NULL base, or a zeroed output for the tiled update): T + T (psi^{-1} - I) would cancel
 // digits in proportion to the column norms of R^0. Plain launches, a status read every check_every iterations.
 bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, int maxit, bcg_info *info) {
-  if (h->precond) return fail(BCG_ERR_INVALID_ARG, "the retooled form runs with M = I (option precond = 0)");
   cudaStream_t s = h->stream;
   const int64_t n = h->n;
-  const int k = h->k, p = h->p;
+  const int k = h->k, p = h->p, gl = h->global;
   const bool lp = p > kMaxP;
-  const int np_g = lp ? h->g64.op : dr_grid_for(n, k, p, h->nsm, h->nparts);
-  // Gram shifts: R^0 is taken at the scale of its column norms (gamma^0 = <<R^0, R^0>>); afterwards every
-  // operand is of unit scale (Q orthonormal, S built from it) except W = A S (role Q: the operator's offset)
+  const double *dinv = dinv_of<double>(h);
+  const int np_g = lp ? h->g64.op : dr_grid_for(n, k, p, h->nsm, h->nparts, dinv != nullptr);
+  // Gram shifts: R^0 is taken at the scale of its column norms (gamma^0 = <<M^{-1} R^0, R^0>>: M^{-1} R^0 in
+  // the P role); afterwards every operand is of unit scale in the M^{-1} product (Q, S built from it) except
+  // W = A S (role Q: the operator's offset)
   const ShiftCtl sc = shifts_of<double>(h);
   const int *shR = sh_role(sc.sh, k, SH_R), *shP = sh_role(sc.sh, k, SH_P), *shQ = sh_role(sc.sh, k, SH_Q);
-  auto gram = [&](const double *Xv, const double *Yv, double *part, const int *shx, const int *shy) -> cudaError_t {
-    return lp ? launch_lp_gram<double>(Xv, Yv, n, k, p, 0, h->active, part, np_g, h->st, s, nullptr, shx, shy)
-              : launch_dr_gram(Xv, Yv, n, k, p, h->active, part, np_g, h->st, s, shx, shy);
+  // partials of <<X, Y>> per column block; xs: X's rows times xs (the M^{-1} operand)
+  auto gram = [&](const double *Xv, const double *Yv, double *part, const int *shx, const int *shy,
+                  const double *xs) -> cudaError_t {
+    return lp ? launch_lp_gram<double>(Xv, Yv, n, k, p, gl, h->active, part, np_g, h->st, s, xs, shx, shy)
+              : launch_dr_gram(Xv, Yv, n, k, p, h->active, part, np_g, h->st, s, shx, shy, gl, xs);
   };
   // OUT = Y C (no base term)
   auto bmul = [&](double *OUT, const double *Yv, const double *Cm) -> cudaError_t {
-    if (!lp) return launch_dr_baxpy(OUT, nullptr, Yv, Cm, n, k, p, 1.0, h->active, h->st, 0, h->nsm, s);
+    if (!lp) return launch_dr_baxpy(OUT, nullptr, Yv, Cm, n, k, p, 1.0, h->active, h->st, 0, h->nsm, s, gl, nullptr);
     cudaError_t e = cudaMemsetAsync(OUT, 0, sizeof(double) * (size_t)n * k, s);
     if (e != cudaSuccess) return e;
-    return launch_lp_baxpy<double>(OUT, OUT, Yv, Cm, n, k, p, 0, 1.0, h->active, h->st, 0, s, nullptr);
+    return launch_lp_baxpy<double>(OUT, OUT, Yv, Cm, n, k, p, gl, 1.0, h->active, h->st, 0, s, nullptr);
   };
-  auto baxpy = [&](double *OUT, const double *BASE, const double *Yv, const double *Cm, double sign,
-                   int bump) -> cudaError_t {
-    return launch_lp_baxpy<double>(OUT, BASE, Yv, Cm, n, k, p, 0, sign, h->active, h->st, bump, s, nullptr);
+  auto baxpy = [&](double *OUT, const double *BASE, const double *Yv, const double *Cm, double sign, int bump,
+                   const double *bscale) -> cudaError_t {
+    return launch_lp_baxpy<double>(OUT, BASE, Yv, Cm, n, k, p, gl, sign, h->active, h->st, bump, s, bscale);
   };
   double *W = h->R, *S = h->P, *Qb = h->Q;
-  // R^0 = B - A X^0 (in W's buffer) = Q^0 C^0, S^1 = Q^0
+  double *partM = dinv ? h->partR : nullptr;   // <<T, M^{-1} T>> (K1's recomputed-rho partials are unused here)
+  // R^0 = B - A X^0 (in W's buffer) = Q^0 C^0, S^1 = M^{-1} Q^0
   CK(launch_residual<double>(h->A64, X, B, W, nullptr, nullptr, nullptr, n, k, h->partN, h->g64.res, s, nullptr));
-  CK(launch_init_status(h->partN, h->g64.res, k, p, 0, h->r0n2, h->rn2, h->active, h->block_iters, h->lam,
+  CK(launch_init_status(h->partN, h->g64.res, k, p, gl, h->r0n2, h->rn2, h->active, h->block_iters, h->lam,
                         h->beta, h->st, s, sc));
-  CK(gram(W, W, h->partA, shR, shR));
-  CK(launch_dr_start(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_psiinv, h->st, h->gws, s));
+  CK(gram(W, W, h->partA, dinv ? shP : shR, shR, dinv));
+  CK(launch_dr_start(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_psiinv, h->st, h->gws, s, gl));
   CK(launch_fill_shifts(nullptr, k, sc, s));
   CK(bmul(Qb, W, h->dr_psiinv));
-  CK(cudaMemcpyAsync(S, Qb, sizeof(double) * (size_t)n * k, cudaMemcpyDeviceToDevice, s));
+  CK(launch_dr_scale_rows(S, Qb, dinv, n, k, h->nsm, s));
   CKS(set_tol2(h, tol * tol));
   CKS(read_status(h));
   int launched = 0;
@@ -722,27 +727,30 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
     for (int i = 0; i < nb; ++i) {
       if (!lp) {
         // W = A S, alpha (K1; where K1 also forms a recomputed rho, it reads Q and the result is unused) |
-        // xi, lambda | X += S lambda, T = Q - W xi, gamma | stop test, psi | Q = T psi^{-1}, S
-        CK(launch_op_gram<double>(h->A64, S, Qb, W, n, k, p, 0, h->active, h->partA, h->partR, h->st, h->g64.op,
+        // xi, lambda | X += S lambda, T = Q - W xi, <<T, T>> (and <<T, M^{-1} T>>) | stop test, psi |
+        // Q = T psi^{-1}, S = M^{-1} Q + S psi^T
+        CK(launch_op_gram<double>(h->A64, S, Qb, W, n, k, p, gl, h->active, h->partA, h->partR, h->st, h->g64.op,
                                   s, sc.sh));
         CK(launch_dr_xi(h->partA, h->g64.op, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws,
-                        h->g64.alpha_circ, s));
-        CK(launch_dr_update_xt(X, Qb, S, W, n, k, p, h->lam, h->dr_xi, h->active, h->partRho, np_g, h->st, s));
+                        h->g64.alpha_circ, s, gl));
+        CK(launch_dr_update_xt(X, Qb, S, W, n, k, p, h->lam, h->dr_xi, h->active, h->partRho, np_g, h->st, s, gl,
+                               dinv, partM));
         CK(launch_dr_psi(h->partRho, np_g, k, p, h->tol2_dev, h->r0n2, h->rn2, h->active, h->block_iters,
-                         h->dr_C, h->dr_psiinv, h->dr_phi, h->st, h->gws, s));
-        CK(launch_dr_update_qs(Qb, S, n, k, p, h->dr_psiinv, h->dr_phi, h->active, h->st, h->nsm, s));
+                         h->dr_C, h->dr_psiinv, h->dr_phi, h->st, h->gws, s, gl, partM));
+        CK(launch_dr_update_qs(Qb, S, n, k, p, h->dr_psiinv, h->dr_phi, h->active, h->st, h->nsm, s, gl, dinv));
         continue;
       }
       CK(launch_lp_bop<double>(h->A64, S, W, n, k, h->st, h->nsm, s));   // W = A S
-      CK(gram(S, W, h->partA, shP, shQ));                                // alpha = <<S, W>>
-      CK(launch_dr_xi(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws, 0, s));
-      CK(baxpy(X, X, S, h->lam, 1.0, 0));                                // X += S lambda, lambda = xi C
-      CK(baxpy(Qb, Qb, W, h->dr_xi, -1.0, 0));                           // T = Q - W xi
-      CK(gram(Qb, Qb, h->partRho, shR, shR));                            // gamma = <<T, T>>
+      CK(gram(S, W, h->partA, shP, shQ, nullptr));                       // alpha = <<S, W>>
+      CK(launch_dr_xi(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws, 0, s, gl));
+      CK(baxpy(X, X, S, h->lam, 1.0, 0, nullptr));                       // X += S lambda, lambda = xi C
+      CK(baxpy(Qb, Qb, W, h->dr_xi, -1.0, 0, nullptr));                  // T = Q - W xi
+      CK(gram(Qb, Qb, h->partRho, shR, shR, nullptr));                   // <<T, T>> per column block
+      if (dinv) CK(gram(Qb, Qb, partM, shP, shR, dinv));                 // <<M^{-1} T, T>>
       CK(launch_dr_psi(h->partRho, np_g, k, p, h->tol2_dev, h->r0n2, h->rn2, h->active, h->block_iters, h->dr_C,
-                       h->dr_psiinv, h->dr_phi, h->st, h->gws, s));
+                       h->dr_psiinv, h->dr_phi, h->st, h->gws, s, gl, partM));
       CK(bmul(W, Qb, h->dr_psiinv));                                     // Q^+ = T psi^{-1}
-      CK(baxpy(Qb, W, S, h->dr_phi, 1.0, 1));                            // S^+ = Q^+ + S psi^T; the iteration ends
+      CK(baxpy(Qb, W, S, h->dr_phi, 1.0, 1, dinv));                      // S^+ = M^{-1} Q^+ + S psi^T; ends it
       double *old_s = S;
       S = Qb;
       Qb = W;
@@ -1163,8 +1171,8 @@ bcg_status bcg_set_option(bcg_handle h, const char *key, double value) {
     }
   } else if (!strcmp(key, "retooled")) {
     if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "retooled must be 0 or 1");
-    if (value == 1.0 && (h->prec != BCG_FP64 || h->global || h->rows_mode))
-      return fail(BCG_ERR_INVALID_ARG, "the retooled form needs an FP64 handle of the hybrid, parallel or classical subalgebra");
+    if (value == 1.0 && (h->prec != BCG_FP64 || h->rows_mode))
+      return fail(BCG_ERR_INVALID_ARG, "the retooled form needs an FP64 handle (not row-sharded)");
     h->retooled = (int)value;
   } else if (!strcmp(key, "tensor_cores")) {
     if (value != 0.0 && value != 1.0) return fail(BCG_ERR_INVALID_ARG, "tensor_cores must be 0 or 1");

@@ -149,31 +149,40 @@ cudaError_t launch_grad_values(const int32_t *rowidx, const int32_t *colind, con
                                int64_t nnz, int k, double *grad, int nsm, cudaStream_t s);
 cudaError_t launch_row_index(const int64_t *rowptr, int64_t n, int32_t *rowidx, int nsm, cudaStream_t s);
 
-// Retooled block CG (bcg_retooled.inc), FP64, hybrid family: streaming kernels for p <= 32 (the large-block
-// path uses launch_lp_*), and the per-block Cholesky QR kernels. Cf (C), xi, lam, psiinv (psi^{-1}) and
-// phi (psi^T) hold one row-major p x p matrix per block. launch_dr_baxpy: BASE may be NULL (zero).
+// Retooled block CG (bcg_retooled.inc), FP64, every subalgebra, M = I or Jacobi (dinv = 1 / diag(A), NULL: I):
+// streaming kernels for p <= 32 (the large-block path uses launch_lp_*), and the Cholesky QR kernels. Cf (C),
+// xi, lam, psiinv (psi^{-1}) and phi (psi^T) hold one row-major p x p matrix per coefficient block (q of them,
+// or one for the global subalgebra). launch_dr_baxpy: BASE may be NULL (zero), rscale a row scale (or NULL).
 // partial-row count of the gamma products of the streaming retooled path (<= cap, the partial buffers' rows)
-int dr_grid_for(int64_t n, int k, int p, int nsm, int cap);
+int dr_grid_for(int64_t n, int k, int p, int nsm, int cap, int jac);
+// partials of <<M^{-1} X, Y>> per column block (dinv NULL: <<X, Y>>)
 cudaError_t launch_dr_gram(const double *X, const double *Y, int64_t n, int k, int p, const int *active,
                            double *part, int grid, const DevStatus *st, cudaStream_t s, const int *shX,
-                           const int *shY);
-// X += S lambda, Qb = Qb - W xi (= T), partials of <<T, T>>_S
+                           const int *shY, int global, const double *dinv);
+// X += S lambda, Qb = Qb - W xi (= T), partials of <<T, T>> per column block, and (dinv) of <<T, M^{-1} T>>
 cudaError_t launch_dr_update_xt(double *X, double *Qb, const double *S, const double *W, int64_t n, int k, int p,
                                 const double *lam, const double *xi, const int *active, double *part, int grid,
-                                const DevStatus *st, cudaStream_t s);
-// Qb = Qb psiinv, S = Qb + S phi (in place); advances the iteration counter
+                                const DevStatus *st, cudaStream_t s, int global, const double *dinv,
+                                double *partM);
+// Qb = Qb psiinv, S = M^{-1} Qb + S phi (in place); advances the iteration counter
 cudaError_t launch_dr_update_qs(double *Qb, double *S, int64_t n, int k, int p, const double *psiinv,
-                                const double *phi, const int *active, DevStatus *st, int nsm, cudaStream_t s);
+                                const double *phi, const int *active, DevStatus *st, int nsm, cudaStream_t s,
+                                int global, const double *dinv);
 cudaError_t launch_dr_baxpy(double *OUT, const double *BASE, const double *Y, const double *C, int64_t n, int k,
                             int p, double sign, const int *active, DevStatus *st, int bump, int nsm,
-                            cudaStream_t s);
+                            cudaStream_t s, int global, const double *rscale);
+cudaError_t launch_dr_scale_rows(double *OUT, const double *IN, const double *rs, int64_t n, int k, int nsm,
+                                 cudaStream_t s);
 cudaError_t launch_dr_start(const double *partG, int nparts, int k, int p, const int *active, double *Cf,
-                            double *psiinv, DevStatus *st, double *gws, cudaStream_t s);
+                            double *psiinv, DevStatus *st, double *gws, cudaStream_t s, int global);
 // alpha_circ: the alpha partials are K1's circulant-diagonal storage
 cudaError_t launch_dr_xi(const double *partA, int nparts, int k, int p, const int *active, const double *Cf,
-                         double *xi, double *lam, DevStatus *st, double *gws, int alpha_circ, cudaStream_t s);
+                         double *xi, double *lam, DevStatus *st, double *gws, int alpha_circ, cudaStream_t s,
+                         int global);
+// stopping test from the per-column-block partials of <<T, T>> (partG); gamma from partGM (M^{-1} product) or,
+// without it, from partG (summed over the column blocks for the global subalgebra)
 cudaError_t launch_dr_psi(const double *partG, int nparts, int k, int p, const double *tol2, const double *r0n2,
                           double *rn2, int *active, int *block_iters, double *Cf, double *psiinv, double *phi,
-                          DevStatus *st, double *gws, cudaStream_t s);
+                          DevStatus *st, double *gws, cudaStream_t s, int global, const double *partGM);
 
 }  // namespace bcgk

@@ -130,15 +130,16 @@ def test_mixed_scaled_reaches_fp64_accuracy(torch_dev, sub, k, p, sb, sa, refine
 
 
 @pytest.mark.parametrize("sb,sa", [(1e-30, 1.0), (1e30, 1.0), (1e-20, 1e10), (1e20, 1e-10)])
-@pytest.mark.parametrize("k,p", [(8, 4), (64, 64)])
-def test_retooled_scaled_equal_iterations(torch_dev, k, p, sb, sa):
-    """Dubrulle's form: gamma^0 = <<R^0, R^0>> at the residual's scale, W = A S at the operator's."""
+@pytest.mark.parametrize("sub,k,p,jac", [("hybrid", 8, 4, 0), ("hybrid", 64, 64, 0), ("global", 16, 4, 0),
+                                         ("hybrid", 8, 4, 1), ("global", 128, 64, 1)])
+def test_retooled_scaled_equal_iterations(torch_dev, sub, k, p, jac, sb, sa):
+    """Dubrulle's form: gamma^0 = <<M^{-1} R^0, R^0>> at the residual's scale, W = A S at the operator's."""
     M = scaled(base("p3d_14"), sa)
     B = sb * W.rhs(M.n, k, seed=15)
     m = 10 if p == 64 else 20
-    Xg, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub="hybrid", maxit=m, opts={"retooled": 1})
+    Xg, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, maxit=m, opts={"retooled": 1, "precond": jac})
     assert r.status == bcg.NOT_CONVERGED and r.iters == m, r
-    ref = O.solve_retooled(M.to_scipy(), B, p=p, sub="hybrid", tol=0.0, maxit=m)
+    ref = O.solve_retooled(M.to_scipy(), B, p=p, sub=sub, tol=0.0, maxit=m, precond="jacobi" if jac else "none")
     assert_close(Xg, ref.X, 1e-9)
 
 

@@ -41,11 +41,12 @@ def mat(name):
     return _MATS[name]
 
 
-def gpu_solve(torch_dev, M, B, *, k, p, sub, form="csr", tol=NEVER, maxit=30, X0=None, retooled=1):
+def gpu_solve(torch_dev, M, B, *, k, p, sub, form="csr", tol=NEVER, maxit=30, X0=None, retooled=1, precond=0):
     torch, dev = torch_dev
     from paper_1912_11930_gb300 import bcg
     S = bcg.Solver.from_matrix(M, k=k, p=p, sub=sub, prec="fp64", form=form, device=dev)
     S.set_option("retooled", retooled)
+    S.set_option("precond", precond)
     Bt = torch.from_numpy(np.ascontiguousarray(B)).to(dev)
     Xt = None if X0 is None else torch.from_numpy(np.ascontiguousarray(X0)).to(dev)
     X, r = S.solve(Bt, Xt, tol=tol, maxit=maxit)
@@ -149,22 +150,13 @@ def test_retooled_degenerate_cases_and_arguments(torch_dev):
     for Bd in (np.hstack([B[:, :2], B[:, :2]]), np.hstack([B[:, :3], np.zeros((M.n, 1))])):
         X, r = gpu_solve(torch_dev, M, Bd, k=4, p=4, sub="classical", tol=1e-10, maxit=50)
         assert r.status == bcg.BREAKDOWN and r.breakdown_iter == 1 and r.iters == 0
-    # argument checks: FP64 handles of the hybrid family with M = I only
-    S = bcg.Solver.from_matrix(M, k=8, p=4, sub="global", prec="fp64", device=dev)
-    with pytest.raises(bcg.BCGError, match="retooled"):
-        S.set_option("retooled", 1)
-    S.close()
+    # argument checks: FP64 handles only
     S = bcg.Solver.from_matrix(M, k=8, p=4, sub="hybrid", prec="fp32_refine", device=dev)
     with pytest.raises(bcg.BCGError, match="retooled"):
         S.set_option("retooled", 1)
     S.close()
-    S = bcg.Solver.from_matrix(M, k=8, p=4, sub="hybrid", prec="fp64", device=dev)
-    S.set_option("retooled", 1)
-    S.set_option("precond", 1)
-    with pytest.raises(bcg.BCGError, match="retooled"):
-        S.solve(torch.from_numpy(B).to(dev), tol=1e-8, maxit=10)
     # switching back to Algorithm 1 on the same handle
-    S.set_option("precond", 0)
+    S = bcg.Solver.from_matrix(M, k=8, p=4, sub="hybrid", prec="fp64", device=dev)
     S.set_option("retooled", 0)
     X1, r1 = S.solve(torch.from_numpy(B).to(dev), tol=1e-8, maxit=500)
     S.set_option("retooled", 1)
@@ -189,3 +181,65 @@ def test_retooled_full_size_against_oracle(torch_dev):
     assert r.status == bcg.NOT_CONVERGED and r.iters == m
     ref = O.solve_retooled(M.to_scipy(), B, p=p, sub="hybrid", tol=0.0, maxit=m)
     assert_close(X.cpu().numpy(), ref.X, 1e-9)
+
+
+# ---- the global subalgebra and the Jacobi preconditioner ----
+# (matrix, form, sub, k, p, iterations, Jacobi): the streaming kernels (p <= 32; global with one shared factor
+# for all column blocks, Jacobi with the second Gram <<T, M^{-1} T>>) and the tiled large-block path
+GJ_FIXED = [
+    ("p2d_37x29", "csr", "global", 8, 4, 25, 0), ("p3d_30", "csr", "global", 32, 8, 20, 0),
+    ("p3d_30", "stencil", "global", 12, 4, 20, 0), ("p3d_30", "csr", "global", 6, 3, 20, 0),
+    ("vc_20", "csr", "hybrid", 16, 4, 8, 1), ("vc_20", "stencil", "hybrid", 32, 8, 8, 1),
+    ("vc_20", "csr", "global", 16, 4, 8, 1), ("vc_20", "csr", "parallel", 8, 1, 10, 1),
+    ("vc_20", "csr", "classical", 16, 16, 8, 1), ("s27_15", "csr", "hybrid", 32, 32, 8, 1),
+    ("p3d_17", "csr", "global", 128, 64, 4, 0), ("p3d_17", "csr", "hybrid", 64, 64, 5, 1),
+    ("p3d_17", "csr", "global", 128, 64, 4, 1),
+]
+
+
+@pytest.mark.parametrize("name,form,sub,k,p,m,jac", GJ_FIXED)
+def test_retooled_global_and_jacobi_equal_iterations(torch_dev, name, form, sub, k, p, m, jac):
+    M = mat(name)
+    B = W.rhs(M.n, k, seed=1)
+    X0 = 0.01 * W.rhs(M.n, k, seed=2)
+    Xg, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, form=form, maxit=m, X0=X0, precond=jac)
+    assert r.status == bcg.NOT_CONVERGED and r.iters == m, r
+    ref = O.solve_retooled(M.to_scipy(), B, X0=X0, p=p, sub=sub, tol=0.0, maxit=m,
+                           precond="jacobi" if jac else "none")
+    assert_close(Xg, ref.X, 1e-9)
+
+
+@pytest.mark.parametrize("name,sub,k,p,jac", [("p3d_30", "global", 32, 8, 0), ("vc_20", "hybrid", 16, 4, 1),
+                                             ("vc_20", "global", 16, 8, 1), ("p3d_17", "global", 128, 64, 1)])
+def test_retooled_global_and_jacobi_converge(torch_dev, name, sub, k, p, jac):
+    """Converged counts within the oracle's spread (+2) of the oracle's retooled form with the same
+    preconditioner, and the true residual at the tolerance."""
+    M = mat(name)
+    A = M.to_scipy()
+    B = W.rhs(M.n, k, seed=3)
+    tol = 1e-8
+    pre = "jacobi" if jac else "none"
+    X, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, tol=tol, maxit=3000, precond=jac)
+    assert r.ok, r
+    ref = O.solve_retooled(A, B, p=p, sub=sub, tol=tol, maxit=3000, precond=pre)
+    spread = [O.solve_retooled(A, B * (1 + 1e-16 * np.random.default_rng(s).standard_normal(B.shape)), p=p,
+                               sub=sub, tol=tol, maxit=3000, precond=pre).iters for s in range(2)]
+    allow = 2 + max(spread + [ref.iters]) - min(spread + [ref.iters])
+    assert abs(r.iters - ref.iters) <= allow, (r.iters, ref.iters, spread)
+    res = np.linalg.norm(B - A @ X, axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(res <= 1.5 * tol), res
+
+
+def test_retooled_global_shared_column_scaling(torch_dev):
+    """Global subalgebra, columns scaled 1e-8 .. 1e8 by one diagonal shared by the column blocks: the retooled
+    form converges like the unscaled system (X scales with B), where Algorithm 1 breaks down."""
+    M = mat("p3d_30")
+    k, p = 16, 4
+    B = W.rhs(M.n, k, seed=12)
+    d = np.tile(10.0 ** np.linspace(-8, 8, p), k // p)
+    X1, r1 = gpu_solve(torch_dev, M, B, k=k, p=p, sub="global", tol=1e-8, maxit=2000)
+    X2, r2 = gpu_solve(torch_dev, M, B * d, k=k, p=p, sub="global", tol=1e-8, maxit=2000)
+    assert r1.ok and r2.ok and abs(r1.iters - r2.iters) <= 1, (r1, r2)
+    assert_close(X2 / d, X1, 1e-7)
+    _, ra = gpu_solve(torch_dev, M, B * d, k=k, p=p, sub="global", tol=1e-8, maxit=2000, retooled=0)
+    assert ra.status == bcg.BREAKDOWN
