@@ -152,6 +152,8 @@ struct bcg_ctx {
   uint16_t *tc_cs = nullptr;           // tensor-core block updates: bf16 digit images of lambda or beta
   int *tc_cexp = nullptr;              // their column exponents
   int *tc_ecol = nullptr;              // tensor-core block products: the operands' column exponent fields (2 k)
+  unsigned char *tc_img[4] = {nullptr, nullptr, nullptr, nullptr};   // digit images: 2 column, 2 row images
+  int *tc_erow = nullptr;              // row exponents of the two row images (2 ceil(n / 128) 128 (k / p))
   double *dinv64 = nullptr;            // 1 / diag(A) (Jacobi preconditioner)
   double *dr_C = nullptr, *dr_xi = nullptr, *dr_psiinv = nullptr, *dr_phi = nullptr;   // retooled form, p x p per block
   float *dinv32 = nullptr;             // its FP32 copy for the mixed form's inner solve
@@ -278,6 +280,10 @@ bcg_status setup_workspace(bcg_ctx *h) {
     CKS(h->alloc(&h->tc_cs, tc_workspace_bytes(h->nblk, h->p) / sizeof(uint16_t)));
     CKS(h->alloc(&h->tc_cexp, (size_t)h->nblk * h->p));
     CKS(h->alloc(&h->tc_ecol, 2 * (size_t)h->k));
+    // digit images of the large-block iteration (16 bytes per value each, 4 of them: about 64 n k bytes)
+    const size_t ib = std::max(tc_row_image_size(h->n, h->k), tc_col_image_size(h->n, h->k));
+    for (int i = 0; i < 4; ++i) CKS(h->alloc(&h->tc_img[i], ib));
+    CKS(h->alloc(&h->tc_erow, 2 * (size_t)((h->n + 127) / 128) * 128 * (h->k / h->p)));
   }
   if (h->prec != BCG_FP32_REFINE) {
     CKS(h->alloc(&h->dr_C, pp));
@@ -417,46 +423,78 @@ bcg_status launch_iteration(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q,
   return BCG_OK;
 }
 
-// One large-block update OUT = BASE (x bscale per row) + sign Y C: on the tensor cores where the handle allows it
-// (FP64 data, p a multiple of 64, option "tensor_cores"), else the tiled FMA kernel. `sliced` tells whether C's
-// bf16 digit images are already in the handle's workspace (lambda serves two updates).
+// One large-block update OUT = BASE (x bscale per row) + sign Y C with the tiled FMA kernel.
 template <typename T>
 bcg_status lp_update(bcg_ctx *h, T *OUT, const T *BASE, const T *Y, const double *C, double sign, int bump,
-                     const T *bscale, bool &sliced) {
-  if constexpr (sizeof(T) == 8) {
-    if (h->tensor_cores && h->tc_cs != nullptr) {
-      if (!sliced) {
-        CK(launch_tc_slice(C, h->nblk, h->p, h->tc_cs, h->tc_cexp, h->stream));
-        sliced = true;
-      }
-      CK(launch_tc_baxpy(OUT, BASE, Y, h->tc_cs, h->tc_cexp, h->n, h->k, h->p, h->global, sign, h->active, h->st,
-                         bump, h->stream, bscale, h->nsm));
-      return BCG_OK;
-    }
-  }
+                     const T *bscale) {
   CK(launch_lp_baxpy<T>(OUT, BASE, Y, C, h->n, h->k, h->p, h->global, sign, h->active, h->st, bump, h->stream,
                         bscale));
   return BCG_OK;
 }
 
-// Partials of a large-block product <<X, Y>>_S (X's rows times xscale if given) into `chunks` partial rows: on the
-// tensor cores where the handle allows it (as lp_update), else the tiled Dot2 kernel.
+// Partials of a large-block product <<X, Y>>_S (X's rows times xscale if given) into `chunks` partial rows with the
+// tiled Dot2 kernel.
 template <typename T>
 bcg_status lp_gram(bcg_ctx *h, const T *X, const T *Y, double *part, int chunks, const T *xscale, const int *shX,
                    const int *shY) {
-  if constexpr (sizeof(T) == 8) {
-    if (h->tensor_cores && h->tc_ecol != nullptr) {
-      CK(launch_tc_gram(X, Y, xscale, h->n, h->k, h->p, h->global, h->active, part, chunks, h->tc_ecol, h->st,
-                        h->stream, h->nsm));
-      return BCG_OK;
-    }
-  }
   CK(launch_lp_gram<T>(X, Y, h->n, h->k, h->p, h->global, h->active, part, chunks, h->st, h->stream, xscale, shX,
                        shY));
   return BCG_OK;
 }
 
-// One iteration with large blocks (p > 32): tiled products. The direction update cannot run in place across
+// One FP64 iteration with large blocks on the tensor cores, from digit images (p a multiple of 64): every operand is
+// cut once per use into images that the MMA kernels copy into shared memory whole (P twice: column images for the
+// Grams, row images for the updates, the latter serving both X += P lambda and P = Z + P beta). The new P is
+// written into Q's buffer; the caller swaps P and Q.
+bcg_status launch_iteration_tcimg(bcg_ctx *h, const OpDesc &A, double *X, double *R, double *P, double *Q,
+                                  const StreamGrids &g) {
+  cudaStream_t s = h->stream;
+  const int64_t n = h->n;
+  const int k = h->k, p = h->p, gl = h->global, ch = g.op, nsm = h->nsm;
+  const ShiftCtl sc = shifts_of<double>(h);
+  const double *dinv = dinv_of<double>(h);
+  unsigned char *G1 = h->tc_img[0], *G2 = h->tc_img[1], *RP = h->tc_img[2], *RQ = h->tc_img[3];
+  int *ec1 = h->tc_ecol, *ec2 = h->tc_ecol + k;
+  int *erP = h->tc_erow, *erQ = h->tc_erow + (size_t)((n + 127) / 128) * 128 * (k / p);
+  CK(launch_lp_bop<double>(A, P, Q, n, k, h->st, nsm, s));
+  // alpha = <<P, Q>> and the recomputed rho = <<P, R>> (P's column images serve both)
+  CK(launch_tc_col_exp(P, nullptr, n, k, ec1, nsm, s));
+  CK(launch_tc_cut_cols(P, nullptr, n, k, ec1, G1, nsm, s));
+  CK(launch_tc_col_exp(Q, nullptr, n, k, ec2, nsm, s));
+  CK(launch_tc_cut_cols(Q, nullptr, n, k, ec2, G2, nsm, s));
+  CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partA, ch, ec1, ec2, h->st, s));
+  CK(launch_tc_col_exp(R, nullptr, n, k, ec2, nsm, s));   // stream order: after the alpha kernel read ec2 and G2
+  CK(launch_tc_cut_cols(R, nullptr, n, k, ec2, G2, nsm, s));
+  CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partR, ch, ec1, ec2, h->st, s));
+  CK(launch_solve_lambda(h->partA, h->partR, ch, ch, k, p, gl, h->active, h->lam, h->rho_rec, h->st, h->gws, 0, s));
+  // X += P lambda, R -= Q lambda
+  CK(launch_tc_slice(h->lam, h->nblk, p, h->tc_cs, h->tc_cexp, s));
+  CK(launch_tc_cut_rows(P, n, k, p, RP, erP, s));
+  CK(launch_tc_cut_rows(Q, n, k, p, RQ, erQ, s));
+  CK(launch_tc_baxpy_img(X, X, RP, erP, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 0, s, nullptr, nsm));
+  CK(launch_tc_baxpy_img(R, R, RQ, erQ, h->tc_cs, h->tc_cexp, n, k, p, gl, -1.0, h->active, h->st, 0, s, nullptr,
+                         nsm));
+  // rho = <<Z, R>>, Z = M^{-1} R formed in the cut
+  CK(launch_tc_col_exp(R, dinv, n, k, ec1, nsm, s));
+  CK(launch_tc_cut_cols(R, dinv, n, k, ec1, G1, nsm, s));
+  if (dinv) {
+    CK(launch_tc_col_exp(R, nullptr, n, k, ec2, nsm, s));
+    CK(launch_tc_cut_cols(R, nullptr, n, k, ec2, G2, nsm, s));
+    CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partRho, ch, ec1, ec2, h->st, s));
+  } else {
+    CK(launch_tc_gram_img(G1, G1, n, k, p, gl, h->active, h->partRho, ch, ec1, ec1, h->st, s));
+  }
+  CK(launch_lp_colnorm<double>(R, n, k, h->partN, g.res, h->st, s, sh_role(sc.sh, k, SH_R)));
+  CK(launch_solve_beta(h->partRho, h->partN, ch, g.res, k, p, gl, h->tol2_dev, h->r0n2, h->rn2, h->active,
+                       h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s, sc));
+  // P = Z + P beta into Q's buffer (P's row images are still those of this iteration's P)
+  CK(launch_tc_slice(h->beta, h->nblk, p, h->tc_cs, h->tc_cexp, s));
+  CK(launch_tc_baxpy_img(Q, R, RP, erP, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 1, s, dinv, nsm));
+  return BCG_OK;
+}
+
+// One iteration with large blocks (p > 32): tiled FMA / Dot2 products (the mixed form's FP32 process, and FP64
+// with option "tensor_cores" 0). The direction update cannot run in place across
 // column tiles, so it writes into the Q buffer (free at that point) and the caller swaps P and Q.
 template <typename T>
 bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g) {
@@ -469,16 +507,15 @@ bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T 
   CKS(lp_gram<T>(h, P, R, h->partR, ch, nullptr, shP, shR));
   CK(launch_solve_lambda(h->partA, h->partR, ch, ch, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
                          h->gws, 0, s));
-  bool lam_sliced = false, beta_sliced = false;
-  CKS(lp_update<T>(h, X, X, P, h->lam, 1.0, 0, nullptr, lam_sliced));
-  CKS(lp_update<T>(h, R, R, Q, h->lam, -1.0, 0, nullptr, lam_sliced));
+  CKS(lp_update<T>(h, X, X, P, h->lam, 1.0, 0, nullptr));
+  CKS(lp_update<T>(h, R, R, Q, h->lam, -1.0, 0, nullptr));
   // rho = <<Z, R>> with Z = M^{-1} R formed on the fly
   CKS(lp_gram<T>(h, R, R, h->partRho, ch, dinv_of<T>(h), shP, shR));
   CK(launch_lp_colnorm<T>(R, h->n, h->k, h->partN, g.res, h->st, s, shR));   // a full-GPU grid, like K0's
   CK(launch_solve_beta(h->partRho, h->partN, ch, g.res, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
                        h->active,
                        h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s, sc));
-  CKS(lp_update<T>(h, Q, R, P, h->beta, 1.0, 1, dinv_of<T>(h), beta_sliced));
+  CKS(lp_update<T>(h, Q, R, P, h->beta, 1.0, 1, dinv_of<T>(h)));
   return BCG_OK;
 }
 
@@ -539,7 +576,12 @@ bcg_status run_iterations(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, c
     while (h->h_st->flags == 0 && launched < maxit) {
       const int nb = std::min(batch, maxit - launched);
       for (int i = 0; i < nb; ++i) {
-        CKS(launch_iteration_lp<T>(h, A, X, R, P, Q, g));
+        if constexpr (sizeof(T) == 8) {
+          if (h->tensor_cores && h->tc_img[0] != nullptr) CKS(launch_iteration_tcimg(h, A, X, R, P, Q, g));
+          else CKS(launch_iteration_lp<T>(h, A, X, R, P, Q, g));
+        } else {
+          CKS(launch_iteration_lp<T>(h, A, X, R, P, Q, g));
+        }
         std::swap(P, Q);
       }
       launched += nb;

@@ -1,6 +1,6 @@
 // Tensor-core (tcgen05) block products and block updates for wide blocks, FP64-accurate:
-//   kt_baxpy  OUT_j = BASE_j + sign * Y_j C_j          (Section 3's BAXPY, omega = 2 n p^2 per block)
-//   kt_gram   partials of gamma_j = X_j^T Y_j           (Section 2's block product, the BDOT of Section 3)
+//   kt_baxpy_img  OUT_j = BASE_j + sign * Y_j C_j          (Section 3's BAXPY, omega = 2 n p^2 per block)
+//   kt_gram_img   partials of gamma_j = X_j^T Y_j           (Section 2's block product, the BDOT of Section 3)
 // for 64 <= p <= 256, p a multiple of 64.
 //
 // Exact slicing (the Ozaki scheme: K. Ozaki, T. Ogita, S. Oishi, S. M. Rump, "Error-free transformations of
@@ -17,18 +17,20 @@
 // sharing an exponent are of one magnitude, about 2^-44 of sum_k |u_k v_k|), the dropped pairs (i + j > 7) about
 // 2^-45 of sum_k |u_k v_k|. FP64 FMAs give about K 2^-53 of sum_k |u_k v_k|.
 //
-//   kt_baxpy: u = Y[r][.] with one exponent per row (over the block's p columns), v = C[.][b] with one per column;
-//             output tiles of 128 rows x 64 columns of one block; C is cut once per launch (kt_slice_cmat).
-//   kt_gram:  u = X[.][a], v = Y[.][b] with one exponent per column over all rows (kt_col_exp); output tiles of
-//             128 x 64 entries of one block (rows of the tile beyond p are zero), partial sums over a range of rows,
-//             read out every 512 rows into float pairs.
+// The operands are cut once per use into digit images in global memory that are byte for byte the kernels'
+// shared-memory stages (kt_cut_rows, kt_cut_cols, kt_slice_cmat; see "Digit images" below):
+//   BAXPY: u = Y[r][.] with one exponent per row (over the block's p columns), v = C[.][b] with one per column;
+//          output tiles of 128 rows x 64 columns of one block.
+//   Gram:  u = X[.][a], v = Y[.][b] with one exponent per column over all rows (kt_col_exp); output tiles of
+//          128 x 64 entries of one block (rows of the tile beyond p are zero), partial sums over a range of rows,
+//          read out every 512 rows into float pairs.
 // Work: one CTA per SM (256 threads, ~200 KB of shared memory, the whole 512-column TMEM: 8 accumulators of 64
-// FP32 columns x 128 lanes). The contraction runs in chunks of 32 staged in two shared-memory buffers: while the
-// tensor cores multiply one chunk (one thread issues the 2 x 36 MMAs, M = 128, N = 64, K = 16, and commits them to
-// the buffer's mbarrier), all threads cut the next chunk into the other buffer's 8 + 8 digit tiles (K-major core
-// matrices of 8 rows x 16 bytes, no swizzle). Every wait on an mbarrier is bounded: ST_TIMEOUT if it never
-// completes. Accumulators are read back with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4) .. +31, 8 columns at a
-// time).
+// FP32 columns x 128 lanes). The contraction runs in chunks of 16 through four shared-memory stages: one thread
+// fills a stage with bulk copies of the images, issues the chunk's 36 MMAs (M = 128, N = 64, K = 16) when the
+// copies are in and commits them to the stage's "empty" mbarrier, so the copies of the next three chunks overlap
+// the MMAs of this one (K-major core matrices of 8 rows x 16 bytes, no swizzle). Every wait on an mbarrier is bounded:
+// ST_TIMEOUT if it never completes. The CTA reads the accumulators back with tcgen05.ld (warp w: TMEM lanes
+// 32 (w mod 4) .. +31, 8 columns at a time).
 #pragma once
 
 #include <cstdint>
@@ -39,17 +41,18 @@ namespace bcgk {
 
 constexpr int kTcRows = 128;      // M: rows of an output tile (TMEM lanes)
 constexpr int kTcCols = 64;       // N: columns of an output tile
-constexpr int kTcK = 32;          // contraction chunk of one shared-memory stage
+constexpr int kTcK = 16;          // contraction chunk of one shared-memory stage (one K step of the MMA)
+constexpr int kTcStages = 4;      // shared-memory stages in flight (bulk copies run up to 3 chunks ahead)
 constexpr int kTcSlices = 8;      // 6-bit digits per value (48 bits)
 constexpr int kTcDigitBits = 6;
 constexpr int kTcThreads = 256;
 constexpr int kTcWindow = 512;    // contraction terms an accumulator takes before it is read out (exactness)
-constexpr uint32_t kTcSliceBytesA = kTcRows * kTcK * 2;          // 8 KB: one digit slice of an M x K chunk
-constexpr uint32_t kTcSliceBytesB = kTcCols * kTcK * 2;          // 4 KB: one digit slice of an N x K chunk
-constexpr uint32_t kTcStageBytesA = kTcSlices * kTcSliceBytesA;  // 64 KB
-constexpr uint32_t kTcStageBytesB = kTcSlices * kTcSliceBytesB;  // 32 KB: also the pre-sliced image of a C chunk
+constexpr uint32_t kTcSliceBytesA = kTcRows * kTcK * 2;          // 4 KB: one digit slice of an M x K chunk
+constexpr uint32_t kTcSliceBytesB = kTcCols * kTcK * 2;          // 2 KB: one digit slice of an N x K chunk
+constexpr uint32_t kTcStageBytesA = kTcSlices * kTcSliceBytesA;  // 32 KB
+constexpr uint32_t kTcStageBytesB = kTcSlices * kTcSliceBytesB;  // 16 KB: also the pre-sliced image of a C chunk
 constexpr uint32_t kTcSbo = (kTcK / 8) * 128;                    // bytes between 8-row core-matrix groups
-constexpr size_t kTcSmemOps = 2 * (size_t)(kTcStageBytesA + kTcStageBytesB);   // 192 KB
+constexpr size_t kTcSmemOps = kTcStages * (size_t)(kTcStageBytesA + kTcStageBytesB);   // 192 KB
 constexpr size_t kTcSmemMisc = 4096;
 constexpr size_t kTcSmem = kTcSmemOps + kTcSmemMisc + 1024;       // + alignment slack
 constexpr long long kTcWaitLimit = 1ll << 24;                     // mbarrier polls before ST_TIMEOUT
@@ -110,6 +113,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
     if (done) return true;
   }
   return false;
+}
+
+// Bulk copies (global -> this CTA's shared memory) tracked by an mbarrier's transaction count: the issuing thread
+// arrives once and announces the bytes; the phase completes when the arrival and all bytes are in.
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+// dst, src 16-byte aligned, bytes a multiple of 16
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
 }
 
 // TMEM: 512 columns for the whole CTA (one warp allocates and frees)
@@ -178,20 +193,21 @@ __device__ __forceinline__ void tc_store8(unsigned char *stage, uint32_t slice_b
     *reinterpret_cast<uint4 *>(stage + i * slice_bytes + off) = make_uint4(w[i][0], w[i][1], w[i][2], w[i][3]);
 }
 
-// The 2 x 36 MMAs of one chunk (digit pairs i + j <= 7 into accumulator s = i + j, 64 TMEM columns each).
-// fresh: the first chunk since the accumulators were read out (its first MMA into each accumulator overwrites it).
+// The 36 MMAs of one chunk (digit pairs i + j <= 7 into accumulator s = i + j, 64 TMEM columns each), fully
+// unrolled: the descriptors of the slices are the stage's descriptor plus constant offsets (the start-address
+// field holds address >> 4 in its low bits, and stage addresses stay below 256 KB, so the addition never carries
+// into the next field). fresh: the first chunk since the accumulators were read out (its first MMA into each
+// accumulator overwrites it).
 __device__ __forceinline__ void tc_issue_chunk(uint32_t tbase, uint32_t aStage, uint32_t bStage, bool fresh) {
-  const uint32_t idesc = tc_idesc_bf16(kTcRows, kTcCols);
-#pragma unroll 1
-  for (int ks = 0; ks < kTcK / 16; ++ks)
-#pragma unroll 1
-    for (int sacc = 0; sacc < kTcSlices; ++sacc)
-#pragma unroll 1
-      for (int i = 0; i <= sacc; ++i) {
-        const uint64_t ad = tc_smem_desc(aStage + i * kTcSliceBytesA + ks * 256, 128, kTcSbo);
-        const uint64_t bd = tc_smem_desc(bStage + (sacc - i) * kTcSliceBytesB + ks * 256, 128, kTcSbo);
-        tc_mma(tbase + (uint32_t)(sacc * kTcCols), ad, bd, idesc, !(fresh && ks == 0 && i == 0));
-      }
+  static_assert(kTcK == 16, "one K step of kind::f16 per chunk");
+  constexpr uint32_t idesc = tc_idesc_bf16(kTcRows, kTcCols);
+  const uint64_t a0 = tc_smem_desc(aStage, 128, kTcSbo), b0 = tc_smem_desc(bStage, 128, kTcSbo);
+#pragma unroll
+  for (int sacc = 0; sacc < kTcSlices; ++sacc)
+#pragma unroll
+    for (int i = 0; i <= sacc; ++i)
+      tc_mma(tbase + (uint32_t)(sacc * kTcCols), a0 + (uint64_t)((i * kTcSliceBytesA) >> 4),
+             b0 + (uint64_t)(((sacc - i) * kTcSliceBytesB) >> 4), idesc, i != 0 || !fresh);
 }
 
 // Read back 8 columns (col .. col + 7) of all 8 accumulators for this warp's 32 lanes and combine them:
@@ -211,42 +227,13 @@ __device__ __forceinline__ void tc_read8(uint32_t tbase, int q, int col, float (
   }
 }
 
-// Two-stage pipeline state: one mbarrier per shared-memory stage, its phase parity, and whether a commit on it is
-// still to be waited for. Every commit is waited for exactly once.
-struct TcPipe {
-  uint32_t mbar[2];
-  uint32_t ph[2];
-  int pending[2];
-  // Wait for the MMAs that read stage st (if any). Returns false on timeout (the same in every thread).
-  __device__ __forceinline__ bool acquire(int st) {
-    bool ok = true;
-    if (pending[st]) {
-      ok = mbar_wait(mbar[st], ph[st]);
-      ph[st] ^= 1u;
-      pending[st] = 0;
-    }
-    return !__syncthreads_or(!ok);
-  }
-  __device__ __forceinline__ bool drain() { return acquire(0) && acquire(1); }
-};
-
-// Common start of the tensor-core kernels: 1024-byte aligned shared memory for the two stages, TMEM (512 columns,
-// allocated by warp 0), the two mbarriers. Returns the TMEM base address.
-__device__ __forceinline__ uint32_t tc_setup(unsigned char *raw, unsigned char *&ops, unsigned char *&misc, TcPipe &pipe) {
+// Common start of the tensor-core kernels: 1024-byte aligned shared memory for the two stages and TMEM (512
+// columns, allocated by warp 0). Returns the TMEM base address.
+__device__ __forceinline__ uint32_t tc_setup(unsigned char *raw, unsigned char *&ops, unsigned char *&misc) {
   ops = raw + ((1024u - (smem_u32(raw) & 1023u)) & 1023u);
   misc = ops + kTcSmemOps;
-  uint64_t *bars = reinterpret_cast<uint64_t *>(misc);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(bars + 2);
+  uint32_t *tslot = reinterpret_cast<uint32_t *>(misc);
   if ((threadIdx.x >> 5) == 0) tmem_alloc(smem_u32(tslot), 512);
-  pipe.mbar[0] = smem_u32(bars);
-  pipe.mbar[1] = smem_u32(bars + 1);
-  pipe.ph[0] = pipe.ph[1] = 0;
-  pipe.pending[0] = pipe.pending[1] = 0;
-  if (threadIdx.x == 0) {
-    mbar_init(pipe.mbar[0], 1);
-    mbar_init(pipe.mbar[1], 1);
-    fence_mbar_init();
-  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -263,7 +250,7 @@ __device__ __forceinline__ void tc_teardown(uint32_t tbase, bool timeout, DevSta
 // shared-memory stage addresses
 __device__ __forceinline__ unsigned char *tc_stage_a(unsigned char *ops, int st) { return ops + st * kTcStageBytesA; }
 __device__ __forceinline__ unsigned char *tc_stage_b(unsigned char *ops, int st) {
-  return ops + 2 * kTcStageBytesA + st * kTcStageBytesB;
+  return ops + kTcStages * kTcStageBytesA + st * kTcStageBytesB;
 }
 
 // ---- BAXPY ------------------------------------------------------------------------------------------------------
@@ -295,151 +282,6 @@ __global__ void kt_slice_cmat(const double *__restrict__ C, int nblkC, int p, ui
   }
 }
 
-// OUT_j = BASE_j (times bscale[r] per row, if given) + sign * Y_j C_j over every block j (global: C_0 for all), with
-// C pre-sliced by kt_slice_cmat. OUT may equal BASE; Y must not alias OUT. Frozen blocks (active[j] = 0) get
-// OUT = BASE (scaled), as in kl_baxpy. bump: CTA 0 advances the iteration counter (the P update's role).
-// Persistent: CTA c takes output tiles c, c + gridDim.x, ...; a row's exponent E_r is the largest exponent field
-// of its p values in the block (integer maxima, no FP64 instruction).
-__global__ void __launch_bounds__(kTcThreads, 1) kt_baxpy(double *OUT, const double *BASE, const double *__restrict__ Y,
-                                                          const uint16_t *__restrict__ Cs, const int *__restrict__ Cexp,
-                                                          int64_t n, int k, int p, int global, double sign,
-                                                          const int *__restrict__ active, DevStatus *__restrict__ st,
-                                                          int bump, const double *__restrict__ bscale) {
-  if (st->flags != 0) return;
-  if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->cur += 1;
-  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
-  unsigned char *ops, *misc;
-  TcPipe pipe;
-  const uint32_t tbase = tc_setup(tc_smem_raw, ops, misc, pipe);
-  int *sE = reinterpret_cast<int *>(misc + 64);   // 128 row exponents
-  int *sBad = sE + kTcRows;                       // 128 row flags (a non-finite entry)
-  int *sF = sBad + kTcRows;                       // 64 column exponents of C
-  int *sX = sF + kTcCols;                         // 256 partial maxima of the exponent fields
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nt = p / kTcCols, nc = p / kTcK;
-  const int ntn = k / kTcCols;
-  const int64_t ntiles = ((n + kTcRows - 1) / kTcRows) * ntn;
-  bool timeout = false;
-  for (int64_t tile = blockIdx.x; tile < ntiles && !timeout; tile += gridDim.x) {
-    const int tn = (int)(tile % ntn);
-    const int64_t r0 = (tile / ntn) * kTcRows;
-    const int c0 = tn * kTcCols;            // first output column
-    const int j = c0 / p, b0 = c0 - j * p;  // block and column offset inside it
-    const int jc = global ? 0 : j;
-    if (!block_active(active, global, j)) {   // block-uniform: every thread of the CTA takes this branch
-      for (int it = tid; it < kTcRows * (kTcCols / 8); it += kTcThreads) {
-        const int rl = it & (kTcRows - 1), cg = it >> 7;
-        const int64_t r = r0 + rl;
-        if (r >= n) continue;
-        const double s = bscale ? bscale[r] : 1.0;
-        for (int e = 0; e < 8; ++e) OUT[r * k + c0 + cg * 8 + e] = BASE[r * k + c0 + cg * 8 + e] * s;
-      }
-      continue;
-    }
-    {   // row exponents: two threads per row, half of the block's columns each
-      const int rl = tid & (kTcRows - 1), half = tid >> 7;
-      const int64_t r = r0 + rl;
-      int em = 0;
-      if (r < n) {
-        const int2 *src = reinterpret_cast<const int2 *>(Y + r * k + (int64_t)j * p + half * (p / 2));
-#pragma unroll 8
-        for (int q = 0; q < p / 2; ++q) em = max(em, (__ldg(src + q).y >> 20) & 0x7FF);
-      }
-      sX[tid] = em;
-      __syncthreads();
-      if (tid < kTcRows) {
-        const int e2 = max(sX[tid], sX[tid + kTcRows]);
-        sE[tid] = e2 > 0 ? e2 - 1023 : -1023;
-        sBad[tid] = e2 == 0x7FF;
-      }
-      if (tid < kTcCols) sF[tid] = Cexp[jc * p + b0 + tid];
-      __syncthreads();
-    }
-    for (int kc = 0; kc < nc; ++kc) {
-      const int stg = kc & 1;
-      if (!pipe.acquire(stg)) {
-        timeout = true;
-        break;
-      }
-      unsigned char *sa = tc_stage_a(ops, stg), *sb = tc_stage_b(ops, stg);
-      // cut the chunk of Y: item (row rl, k-group kg), 2 per thread, loads first
-      double v[2][8];
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int it = tid + u * kTcThreads, rl = it & (kTcRows - 1), kg = it >> 7;
-        const int64_t r = r0 + rl;
-        if (r < n) {
-          const double2 *src = reinterpret_cast<const double2 *>(Y + r * k + (int64_t)j * p + kc * kTcK + kg * 8);
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const double2 t2 = __ldg(src + q);
-            v[u][2 * q] = t2.x;
-            v[u][2 * q + 1] = t2.y;
-          }
-        } else {
-#pragma unroll
-          for (int e = 0; e < 8; ++e) v[u][e] = 0.0;
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 2; ++u) {
-        const int it = tid + u * kTcThreads, rl = it & (kTcRows - 1), kg = it >> 7;
-        uint32_t w[kTcSlices][4];
-        tc_pack8(v[u], sE[rl], w);
-        tc_store8(sa, kTcSliceBytesA, rl, kg, w);
-      }
-      {   // the pre-sliced chunk of C^T
-        const uint4 *src = reinterpret_cast<const uint4 *>(
-            reinterpret_cast<const unsigned char *>(Cs) + ((size_t)(jc * nt + b0 / kTcCols) * nc + kc) * kTcStageBytesB);
-        uint4 *dst = reinterpret_cast<uint4 *>(sb);
-#pragma unroll
-        for (int q = 0; q < (int)(kTcStageBytesB / 16 / kTcThreads); ++q) dst[tid + q * kTcThreads] = __ldg(src + tid + q * kTcThreads);
-      }
-      fence_async_smem();
-      __syncthreads();
-      if (tid == 0) {
-        tc_fence_after();
-        tc_issue_chunk(tbase, smem_u32(sa), smem_u32(sb), kc == 0);
-        tc_commit(pipe.mbar[stg]);
-      }
-      pipe.pending[stg] = 1;
-    }
-    if (timeout || !pipe.drain()) {
-      timeout = true;
-      break;
-    }
-    tc_fence_after();
-    {   // read back: warp w holds rows 32 (w mod 4) .. +31, columns 32 (w / 4) .. +31 of the tile
-      const int q = warp & 3, h = warp >> 2;
-      const int rl = q * 32 + lane;
-      const int64_t r = r0 + rl;
-      const int E = sE[rl];
-      const bool bad = sBad[rl] != 0;
-      const double bs = (r < n && bscale) ? bscale[r] : 1.0;
-#pragma unroll 1
-      for (int cg = 0; cg < 4; ++cg) {
-        float hi[8], lo[8];
-        const int cb = h * 32 + cg * 8;
-        tc_read8(tbase, q, cb, hi, lo);
-        if (r < n) {
-          double *o = OUT + r * k + c0 + cb;
-          const double *bp = BASE + r * k + c0 + cb;
-#pragma unroll
-          for (int e = 0; e < 8; ++e) {
-            const int t = E + sF[cb + e] - 10;
-            const double base = bscale ? bp[e] * bs : bp[e];
-            const double res = (base + sign * f2d_scaled(hi[e], t)) + sign * f2d_scaled(lo[e], t);
-            o[e] = bad ? __longlong_as_double(0x7FF8000000000000ll) : res;
-          }
-        }
-      }
-    }
-    tc_fence_before();
-    __syncthreads();
-  }
-  tc_teardown(tbase, timeout, st);
-}
-
 // ---- Gram ------------------------------------------------------------------------------------------------------
 // Column exponent fields for the Gram slicing: ecol[c] = max over rows of the biased exponent of X[r][c] (times
 // xscale[r] if given), by integer maxima (the caller zeroes ecol). Thread (g, c) covers rows g, g + rows per CTA
@@ -457,16 +299,324 @@ __global__ void __launch_bounds__(kNT) kt_col_exp(const double *__restrict__ X, 
   atomicMax(ecol + c, em);
 }
 
-// Partials of gamma_j = X_j^T Y_j (X's rows times xscale[r] if given): CTA (tile, chunk) takes the 128 x 64 entries
-// (a in [128 ta, 128 ta + 128), b in [64 tb, 64 tb + 64)) of block j over the rows of chunk blockIdx.y, and writes them
-// into partial row blockIdx.y in the layout of kl_gram (entry (a, b) of block j at j p p + b p + a); rows of the tile
-// with a >= p are zero and not written. ecx, ecy: column exponent fields of X and Y (kt_col_exp). Frozen blocks get
-// zero partials. The accumulators are read out into float pairs every kTcWindow rows.
-__global__ void __launch_bounds__(kTcThreads, 1) kt_gram(const double *__restrict__ X, const double *__restrict__ Y,
-                                                         const double *__restrict__ xscale, int64_t n, int k, int p,
-                                                         int global, const int *__restrict__ active,
-                                                         double *__restrict__ part, const int *__restrict__ ecx,
-                                                         const int *__restrict__ ecy, DevStatus *__restrict__ st) {
+// ---- Digit images in global memory ------------------------------------------------------------------------------
+// Cutting the operands inside the MMA kernels (one CTA per output tile) would cut an operand feeding several
+// output tiles once per tile (4 times for the Gram's X at p = 256), on the integer pipe, while the tensor pipe
+// waits. So every operand is cut once per use into HBM images that are byte-for-byte shared-memory stages, and the
+// MMA kernels fill their stages with bulk copies (cp.async.bulk, completion counted on an mbarrier); one thread
+// produces the stages and issues the MMAs, and the whole CTA only reads the accumulators out.
+//   row images (BAXPY's Y, one exponent per row of a block): 64 KB per (128-row tile rt, 32-column chunk kc of
+//     k), the A stage of kt_baxpy: image (rt, kc) at (rt (k/32) + kc) 64 KB; erow[j * nrows + r] = E_r of block j
+//     (kTcBadRow: a non-finite value in the row).
+//   column images (the Gram's operands, one exponent per column over all rows): 32 KB per (64-column tile ct,
+//     32-row chunk rc), the B stage of kt_gram; image (ct, rc) at (ct nrc + rc) 32 KB, nrc = ceil(n / 32). An A
+//     stage of 128 columns is the two 64-column images side by side in every 8 KB slice.
+constexpr int kTcBadRow = 0x7FFFFFFF;
+constexpr uint32_t kTcImgRow = kTcStageBytesA;   // 64 KB
+constexpr uint32_t kTcImgCol = kTcStageBytesB;   // 32 KB
+
+__host__ __device__ constexpr size_t tc_row_image_bytes(int64_t n, int k) {
+  return (size_t)((n + kTcRows - 1) / kTcRows) * (k / kTcK) * kTcImgRow;
+}
+__host__ __device__ constexpr size_t tc_col_image_bytes(int64_t n, int k) {
+  return (size_t)((n + kTcK - 1) / kTcK) * (k / kTcCols) * kTcImgCol;
+}
+
+// Row images of Y for every block j: CTA (rt, j) computes the 128 row exponents of its rows over the block's p
+// columns (integer maxima of the exponent fields) and cuts the p / 32 chunks.
+__global__ void __launch_bounds__(kTcThreads) kt_cut_rows(const double *__restrict__ Y, int64_t n, int k, int p,
+                                                          unsigned char *__restrict__ img, int *__restrict__ erow) {
+  __shared__ int sX[kTcThreads];
+  __shared__ int sE[kTcRows];
+  const int tid = threadIdx.x;
+  const int64_t rt = blockIdx.x;
+  const int j = blockIdx.y;
+  const int64_t r0 = rt * kTcRows;
+  const int64_t nrows = ((n + kTcRows - 1) / kTcRows) * kTcRows;
+  {
+    const int rl = tid & (kTcRows - 1), half = tid >> 7;
+    const int64_t r = r0 + rl;
+    int em = 0;
+    if (r < n) {
+      const int2 *src = reinterpret_cast<const int2 *>(Y + r * k + (int64_t)j * p + half * (p / 2));
+#pragma unroll 8
+      for (int q = 0; q < p / 2; ++q) em = max(em, (__ldg(src + q).y >> 20) & 0x7FF);
+    }
+    sX[tid] = em;
+    __syncthreads();
+    if (tid < kTcRows) {
+      const int e2 = max(sX[tid], sX[tid + kTcRows]);
+      const int E = e2 > 0 ? e2 - 1023 : -1023;
+      sE[tid] = E;
+      erow[(int64_t)j * nrows + r0 + tid] = e2 == 0x7FF ? kTcBadRow : E;
+    }
+    __syncthreads();
+  }
+  constexpr int kItems = kTcRows * (kTcK / 8);   // (row, 8-value k-group) items of a chunk
+  for (int kc = 0; kc < p / kTcK; ++kc) {
+    unsigned char *dst = img + ((size_t)rt * (k / kTcK) + (size_t)j * (p / kTcK) + kc) * kTcImgRow;
+#pragma unroll
+    for (int u = 0; u < (kItems + kTcThreads - 1) / kTcThreads; ++u) {
+      const int it = tid + u * kTcThreads, rl = it & (kTcRows - 1), kg = it >> 7;
+      if (it >= kItems) break;
+      const int64_t r = r0 + rl;
+      double v[8];
+      if (r < n) {
+        const double2 *src = reinterpret_cast<const double2 *>(Y + r * k + (int64_t)j * p + kc * kTcK + kg * 8);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const double2 t2 = __ldg(src + q);
+          v[2 * q] = t2.x;
+          v[2 * q + 1] = t2.y;
+        }
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) v[e] = 0.0;
+      }
+      uint32_t w[kTcSlices][4];
+      tc_pack8(v, sE[rl], w);
+      tc_store8(dst, kTcSliceBytesA, rl, kg, w);
+    }
+  }
+}
+
+// Column images of X (rows times xscale[r] if given) with the column exponent fields ecol (kt_col_exp): CTA
+// (ct, y) cuts the 64 columns of tile ct over the row chunks y, y + gridDim.y, ...
+__global__ void __launch_bounds__(kTcThreads) kt_cut_cols(const double *__restrict__ X, const double *__restrict__ xscale,
+                                                          int64_t n, int k, const int *__restrict__ ecol,
+                                                          unsigned char *__restrict__ img) {
+  const int tid = threadIdx.x;
+  const int ct = blockIdx.x;
+  constexpr int kItems = kTcCols * (kTcK / 8);   // (column, 8-row k-group) items of a chunk
+  constexpr int kPer = kTcThreads / kItems;      // chunks per pass of the CTA
+  const int item = tid % kItems, sub = tid / kItems;
+  const int col = item & (kTcCols - 1), kg = item >> 6;
+  const int c = ct * kTcCols + col;
+  const int E = (ecol[c] > 0 ? ecol[c] : 1) - 1023;
+  const int64_t nrc = (n + kTcK - 1) / kTcK;
+  for (int64_t rc = (int64_t)blockIdx.y * kPer + sub; rc < nrc; rc += (int64_t)gridDim.y * kPer) {
+    double v[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int64_t r = rc * kTcK + kg * 8 + e;
+      v[e] = r < n ? (xscale ? X[r * k + c] * xscale[r] : X[r * k + c]) : 0.0;
+    }
+    uint32_t w[kTcSlices][4];
+    tc_pack8(v, E, w);
+    tc_store8(img + ((size_t)ct * nrc + rc) * kTcImgCol, kTcSliceBytesB, col, kg, w);
+  }
+}
+
+// Roles in the image kernels: thread 32 (warp 1, lane 0) is the producer -- it fills the kTcStages shared-memory
+// stages with bulk copies of the images; thread 0 issues the MMAs. Chunk g (counted over the whole launch) uses
+// stage g mod kTcStages, and its "full" mbarrier (copies in) and "empty" mbarrier (its MMAs complete, by
+// tcgen05.commit) complete for the (g / kTcStages)-th time, so the parity of every wait follows from g alone. The
+// producer refills a stage once the MMAs of the chunk kTcStages before have completed, so copies run up to
+// kTcStages chunks ahead of the tensor cores; a "done" mbarrier (one commit after the last chunk of a tile or
+// window) tells thread 0 that the accumulators are complete. Every wait is bounded (kTcWaitLimit polls); a
+// timeout sets a flag that ends the kernel for the whole CTA after both roles have waited (bounded) for their own
+// copies and MMAs in flight.
+constexpr int kTcProducer = 32;
+
+struct TcBars {
+  uint32_t full[kTcStages], empty[kTcStages], done;
+};
+__device__ __forceinline__ TcBars tc_bars_setup(unsigned char *misc) {
+  uint64_t *bars = reinterpret_cast<uint64_t *>(misc + 256);
+  TcBars b;
+  for (int s = 0; s < kTcStages; ++s) {
+    b.full[s] = smem_u32(bars + s);
+    b.empty[s] = smem_u32(bars + kTcStages + s);
+  }
+  b.done = smem_u32(bars + 2 * kTcStages);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      mbar_init(b.full[s], 1);
+      mbar_init(b.empty[s], 1);
+    }
+    mbar_init(b.done, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  return b;
+}
+__device__ __forceinline__ uint32_t tc_par(int64_t g) { return (uint32_t)((g / kTcStages) & 1); }
+
+// kt_baxpy with Y's row images (kt_cut_rows) and C's images (kt_slice_cmat): the same tiles, readout and arguments.
+// The producer also prefetches the first chunks of the CTA's next tile while the current tile is read out.
+__global__ void __launch_bounds__(kTcThreads, 1) kt_baxpy_img(double *OUT, const double *BASE,
+                                                              const unsigned char *__restrict__ imgY,
+                                                              const int *__restrict__ erow,
+                                                              const uint16_t *__restrict__ Cs,
+                                                              const int *__restrict__ Cexp, int64_t n, int k, int p,
+                                                              int global, double sign, const int *__restrict__ active,
+                                                              DevStatus *__restrict__ st, int bump,
+                                                              const double *__restrict__ bscale) {
+  if (st->flags != 0) return;
+  if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->cur += 1;
+  extern __shared__ __align__(16) unsigned char tc_smem_raw[];
+  unsigned char *ops, *misc;
+  const uint32_t tbase = tc_setup(tc_smem_raw, ops, misc);
+  const TcBars bars = tc_bars_setup(misc);
+  int *sE = reinterpret_cast<int *>(misc + 512);   // 128 row exponents (kTcBadRow: NaN row)
+  int *sF = sE + kTcRows;                          // 64 column exponents of C
+  int *sFlag = sF + kTcCols;                       // [0]: a wait timed out
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nt = p / kTcCols, nc = p / kTcK;
+  const int ntn = k / kTcCols;
+  const int64_t nrt = (n + kTcRows - 1) / kTcRows;
+  const int64_t nrows = nrt * kTcRows;
+  const int64_t ntiles = nrt * ntn;
+  if (tid == 0) sFlag[0] = 0;
+  __syncthreads();
+  auto tile_active = [&](int64_t t) { return block_active(active, global, (int)(t % ntn) * kTcCols / p); };
+  // producer state: chunks produced over the launch, and which tile / chunk comes next
+  int64_t gprod = 0, ptile = blockIdx.x;
+  int pc = 0;
+  auto next_active = [&](int64_t t) {
+    while (t < ntiles && !tile_active(t)) t += gridDim.x;
+    return t;
+  };
+  // produce chunks of tile ptile from pc up to (not including) chunk `upto` of tile `limit_tile` (and its
+  // predecessors); returns false on a timeout
+  auto produce_until = [&](int64_t limit_tile, int upto) -> bool {
+    while (ptile < ntiles && (ptile < limit_tile || (ptile == limit_tile && pc < upto))) {
+      const int s = (int)(gprod % kTcStages);
+      if (gprod >= kTcStages && !mbar_wait(bars.empty[s], tc_par(gprod - kTcStages))) return false;
+      const int tn = (int)(ptile % ntn);
+      const int64_t rt = ptile / ntn;
+      const int c0 = tn * kTcCols, j = c0 / p, b0 = c0 - j * p, jc = global ? 0 : j;
+      const unsigned char *cimg =
+          reinterpret_cast<const unsigned char *>(Cs) + ((size_t)(jc * nt + b0 / kTcCols) * nc + pc) * kTcStageBytesB;
+      const unsigned char *yimg = imgY + ((size_t)rt * (k / kTcK) + (size_t)j * nc + pc) * kTcImgRow;
+      mbar_arrive_expect_tx(bars.full[s], kTcImgRow + kTcStageBytesB);
+      bulk_g2s(smem_u32(tc_stage_a(ops, s)), yimg, kTcImgRow, bars.full[s]);
+      bulk_g2s(smem_u32(tc_stage_b(ops, s)), cimg, kTcStageBytesB, bars.full[s]);
+      ++gprod;
+      if (++pc == nc) {
+        pc = 0;
+        ptile = next_active(ptile + gridDim.x);
+      }
+    }
+    return true;
+  };
+  int64_t gcons = 0, ndone = 0;   // MMA thread: chunks consumed, tiles completed
+  if (tid == kTcProducer) {
+    ptile = next_active(ptile);
+    if (!produce_until(ptile, min(nc, kTcStages))) sFlag[0] = 1;
+  }
+  bool timeout = false;
+  for (int64_t tile = blockIdx.x; tile < ntiles && !timeout; tile += gridDim.x) {
+    const int tn = (int)(tile % ntn);
+    const int64_t r0 = (tile / ntn) * kTcRows;
+    const int c0 = tn * kTcCols;
+    const int j = c0 / p, b0 = c0 - j * p;
+    const int jc = global ? 0 : j;
+    if (!block_active(active, global, j)) {
+      for (int it = tid; it < kTcRows * (kTcCols / 8); it += kTcThreads) {
+        const int rl = it & (kTcRows - 1), cg = it >> 7;
+        const int64_t r = r0 + rl;
+        if (r >= n) continue;
+        const double s = bscale ? bscale[r] : 1.0;
+        for (int e = 0; e < 8; ++e) OUT[r * k + c0 + cg * 8 + e] = BASE[r * k + c0 + cg * 8 + e] * s;
+      }
+      continue;
+    }
+    if (tid < kTcRows) sE[tid] = erow[(int64_t)j * nrows + r0 + tid];
+    if (tid < kTcCols) sF[tid] = Cexp[jc * p + b0 + tid];
+    // this thread's 32 outputs: row rl = 32 (w mod 4) + lane, columns 32 (w / 4) .. +31 of the tile; their BASE
+    // values are loaded now, while the MMAs run (16-byte loads; consumed after the barrier)
+    const int q = warp & 3, h = warp >> 2;
+    const int rl = q * 32 + lane;
+    const int64_t r = r0 + rl;
+    double2 bv[16];
+    if (r < n) {
+      const double2 *bp = reinterpret_cast<const double2 *>(BASE + r * k + c0 + h * 32);
+#pragma unroll
+      for (int e = 0; e < 16; ++e) bv[e] = bp[e];
+    }
+    const double bs = (r < n && bscale) ? bscale[r] : 1.0;
+    if (tid == kTcProducer && !sFlag[0]) {   // the rest of this tile, then the next tile's first stages
+      const int64_t nxt = next_active(tile + gridDim.x);
+      const bool ok = nxt < ntiles ? produce_until(nxt, min(nc, kTcStages)) : produce_until(tile, nc);
+      if (!ok) sFlag[0] = 1;
+    }
+    if (tid == 0) {
+      bool ok = true;
+      for (int c = 0; c < nc && ok; ++c, ++gcons) {
+        const int s = (int)(gcons % kTcStages);
+        ok = mbar_wait(bars.full[s], tc_par(gcons)) && !*(volatile int *)sFlag;
+        if (!ok) break;
+        tc_fence_after();
+        tc_issue_chunk(tbase, smem_u32(tc_stage_a(ops, s)), smem_u32(tc_stage_b(ops, s)), c == 0);
+        tc_commit(bars.empty[s]);
+      }
+      if (ok) {
+        tc_commit(bars.done);
+        ok = mbar_wait(bars.done, (uint32_t)(ndone & 1));
+        ++ndone;
+      }
+      if (!ok) sFlag[0] = 1;
+    }
+    __syncthreads();
+    if (sFlag[0]) {
+      timeout = true;
+      break;
+    }
+    tc_fence_after();
+    {   // read back: warp w holds rows 32 (w mod 4) .. +31, columns 32 (w / 4) .. +31 of the tile
+      const int E = sE[rl];
+      const bool bad = E == kTcBadRow;
+#pragma unroll
+      for (int cg = 0; cg < 4; ++cg) {
+        float hi[8], lo[8];
+        const int cb = h * 32 + cg * 8;
+        tc_read8(tbase, q, cb, hi, lo);
+        if (r < n) {
+          double2 *o = reinterpret_cast<double2 *>(OUT + r * k + c0 + cb);
+#pragma unroll
+          for (int e2 = 0; e2 < 4; ++e2) {
+            double res[2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+              const int e = 2 * e2 + u;
+              const int t = E + sF[cb + e] - 10;
+              const double b = u ? bv[cg * 4 + e2].y : bv[cg * 4 + e2].x;
+              const double base = bscale ? b * bs : b;
+              // (s + c) 2^t as one double (integer operations), one FP64 addition
+              const double v = base + sign * df_pair_to_double(hi[e], lo[e], t);
+              res[u] = bad ? __longlong_as_double(0x7FF8000000000000ll) : v;
+            }
+            o[e2] = make_double2(res[0], res[1]);
+          }
+        }
+      }
+    }
+    tc_fence_before();
+    __syncthreads();
+  }
+  if (timeout) {   // both roles wait (bounded) for what they started
+    __shared__ long long sCons;
+    if (tid == 0) sCons = gcons;
+    __syncthreads();
+    if (tid == kTcProducer)
+      for (int64_t g = sCons; g < gprod; ++g) (void)mbar_wait(bars.full[g % kTcStages], tc_par(g));
+    if (tid == 0 && gcons > 0) (void)mbar_wait(bars.empty[(gcons - 1) % kTcStages], tc_par(gcons - 1));
+  }
+  tc_teardown(tbase, timeout, st);
+}
+
+// kt_gram with the column images of X and Y (kt_cut_cols; the same image may serve both): CTA (tile, y) covers the
+// 128 x 64 entries (a in [128 ta, 128 ta + 128), b in [64 tb, 64 tb + 64)) of block j over the 16-row chunks of
+// partial row y, and writes them into partial row y in the layout of kl_gram (entry (a, b) of block j at
+// j p p + b p + a); rows of the tile with a >= p are zero and not written. ecx, ecy: the column exponent fields
+// the images were cut with. Frozen blocks get zero partials. The accumulators are read out into float pairs every
+// kTcWindow rows.
+__global__ void __launch_bounds__(kTcThreads, 1) kt_gram_img(const unsigned char *__restrict__ imgX,
+                                                             const unsigned char *__restrict__ imgY, int64_t n, int k,
+                                                             int p, int global, const int *__restrict__ active,
+                                                             double *__restrict__ part, const int *__restrict__ ecx,
+                                                             const int *__restrict__ ecy, DevStatus *__restrict__ st) {
   if (st != nullptr && st->flags != 0) return;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int ta_n = (p + kTcRows - 1) / kTcRows, tb_n = p / kTcCols;
@@ -474,7 +624,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) kt_gram(const double *__restric
   const int a0 = ta * kTcRows, b0 = tb * kTcCols;
   double *out = part + (size_t)blockIdx.y * k * p + (size_t)j * p * p;
   const int q = warp & 3, h = warp >> 2;
-  const int al = q * 32 + lane;   // this thread's tile row in the read-out
+  const int al = q * 32 + lane;
   if (!block_active(active, global, j)) {
     if (a0 + al < p)
       for (int e = 0; e < 32; ++e) out[(size_t)(b0 + h * 32 + e) * p + a0 + al] = 0.0;
@@ -482,82 +632,94 @@ __global__ void __launch_bounds__(kTcThreads, 1) kt_gram(const double *__restric
   }
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];
   unsigned char *ops, *misc;
-  TcPipe pipe;
-  const uint32_t tbase = tc_setup(tc_smem_raw, ops, misc, pipe);
-  const int64_t chunk = (n + gridDim.y - 1) / gridDim.y;
-  const int64_t r_begin = (int64_t)blockIdx.y * chunk, r_end = min(n, r_begin + chunk);
-  // cutting items: A (X^T) -- column a = items & 127 of the tile, k-group rg; B (Y) -- column b = tid & 63, k-group
-  const int colA[2] = {tid & (kTcRows - 1), tid & (kTcRows - 1)};
-  const int rgA[2] = {tid >> 7, (tid + kTcThreads) >> 7};
-  const int cA = j * p + a0 + colA[0];
-  const bool validA = a0 + colA[0] < p;
-  const int EA = validA ? ((ecx[cA] > 0 ? ecx[cA] : 1) - 1023) : 0;
-  const int bB = tid & (kTcCols - 1), rgB = tid >> 6;
-  const int cB = j * p + b0 + bB;
-  const int EB = (ecy[cB] > 0 ? ecy[cB] : 1) - 1023;
-  float rs[32], rc[32];   // running float pairs of this thread's 32 read-out entries
+  const uint32_t tbase = tc_setup(tc_smem_raw, ops, misc);
+  const bool two = a0 + kTcCols < p;   // the A stage's second 64 columns exist (else they stay zero)
+  if (!two) {   // zero the upper halves of all A stages once; the bulk copies never write them
+    for (int s2 = 0; s2 < kTcStages; ++s2)
+      for (int i = 0; i < kTcSlices; ++i) {
+        uint4 *z = reinterpret_cast<uint4 *>(tc_stage_a(ops, s2) + i * kTcSliceBytesA + kTcSliceBytesB);
+        for (int e = tid; e < (int)(kTcSliceBytesB / 16); e += kTcThreads) z[e] = make_uint4(0, 0, 0, 0);
+      }
+    fence_async_smem();
+  }
+  const TcBars bars = tc_bars_setup(misc);
+  int *sFlag = reinterpret_cast<int *>(misc + 512);
+  if (tid == 0) sFlag[0] = 0;
+  __syncthreads();
+  const int64_t nrc = (n + kTcK - 1) / kTcK;
+  const int64_t per = (nrc + gridDim.y - 1) / gridDim.y;
+  const int64_t rc_begin = (int64_t)blockIdx.y * per, rc_end = min(nrc, rc_begin + per);
+  const int64_t nch = rc_end > rc_begin ? rc_end - rc_begin : 0;
+  const int ctA = (j * p + a0) / kTcCols, ctB = (j * p + b0) / kTcCols;
+  const uint32_t bytesA = (two ? 2u : 1u) * kTcSlices * kTcSliceBytesB;
+  float rs[32], rc[32];
 #pragma unroll
   for (int e = 0; e < 32; ++e) rs[e] = rc[e] = 0.0f;
   bool timeout = false;
-  const int64_t nchunks = (r_end - r_begin + kTcK - 1) / kTcK;
-  for (int64_t cc = 0; cc < nchunks && !timeout; ++cc) {
-    const int stg = (int)(cc & 1);
-    if (!pipe.acquire(stg)) {
+  constexpr int kWin = kTcWindow / kTcK;   // chunks per accumulator window
+  int64_t gprod = 0, gcons = 0, ndone = 0;
+  auto produce_until = [&](int64_t upto) -> bool {   // producer: chunks gprod .. upto - 1
+    for (; gprod < upto; ++gprod) {
+      const int s = (int)(gprod % kTcStages);
+      if (gprod >= kTcStages && !mbar_wait(bars.empty[s], tc_par(gprod - kTcStages))) return false;
+      const int64_t r = rc_begin + gprod;
+      mbar_arrive_expect_tx(bars.full[s], bytesA + kTcImgCol);
+      const unsigned char *xa = imgX + ((size_t)ctA * nrc + r) * kTcImgCol;
+      const unsigned char *xb = imgX + ((size_t)(ctA + 1) * nrc + r) * kTcImgCol;
+      const uint32_t sa = smem_u32(tc_stage_a(ops, s));
+#pragma unroll
+      for (int i = 0; i < kTcSlices; ++i) {
+        bulk_g2s(sa + i * kTcSliceBytesA, xa + i * kTcSliceBytesB, kTcSliceBytesB, bars.full[s]);
+        if (two) bulk_g2s(sa + i * kTcSliceBytesA + kTcSliceBytesB, xb + i * kTcSliceBytesB, kTcSliceBytesB, bars.full[s]);
+      }
+      bulk_g2s(smem_u32(tc_stage_b(ops, s)), imgY + ((size_t)ctB * nrc + r) * kTcImgCol, kTcImgCol, bars.full[s]);
+    }
+    return true;
+  };
+  for (int64_t c0 = 0; c0 < nch && !timeout; c0 += kWin) {   // one accumulator window per pass
+    const int64_t c1 = min(nch, c0 + kWin);
+    // the producer may run kTcStages chunks past the window: those wait only for MMAs of this window
+    if (tid == kTcProducer && !sFlag[0] && !produce_until(min(nch, c1 + kTcStages))) sFlag[0] = 1;
+    if (tid == 0) {
+      bool ok = true;
+      for (; gcons < c1 && ok; ++gcons) {
+        const int s = (int)(gcons % kTcStages);
+        ok = mbar_wait(bars.full[s], tc_par(gcons)) && !*(volatile int *)sFlag;
+        if (!ok) break;
+        tc_fence_after();
+        tc_issue_chunk(tbase, smem_u32(tc_stage_a(ops, s)), smem_u32(tc_stage_b(ops, s)), gcons == c0);
+        tc_commit(bars.empty[s]);
+      }
+      if (ok) {
+        tc_commit(bars.done);
+        ok = mbar_wait(bars.done, (uint32_t)(ndone & 1));
+        ++ndone;
+      }
+      if (!ok) sFlag[0] = 1;
+    }
+    __syncthreads();
+    if (sFlag[0]) {
       timeout = true;
       break;
     }
-    unsigned char *sa = tc_stage_a(ops, stg), *sb = tc_stage_b(ops, stg);
-    const int64_t rbase = r_begin + cc * kTcK;
-    double va[2][8], vb[8];
+    tc_fence_after();
 #pragma unroll
-    for (int u = 0; u < 2; ++u)
+    for (int cg = 0; cg < 4; ++cg) {
+      float hi[8], lo[8];
+      tc_read8(tbase, q, h * 32 + cg * 8, hi, lo);
 #pragma unroll
-      for (int e = 0; e < 8; ++e) {
-        const int64_t r = rbase + rgA[u] * 8 + e;
-        va[u][e] = (validA && r < r_end) ? (xscale ? X[r * k + cA] * xscale[r] : X[r * k + cA]) : 0.0;
-      }
-#pragma unroll
-    for (int e = 0; e < 8; ++e) {
-      const int64_t r = rbase + rgB * 8 + e;
-      vb[e] = r < r_end ? Y[r * k + cB] : 0.0;
+      for (int e = 0; e < 8; ++e) two_sum_acc(rs[cg * 8 + e], rc[cg * 8 + e], hi[e], lo[e]);
     }
-#pragma unroll
-    for (int u = 0; u < 2; ++u) {
-      uint32_t w[kTcSlices][4];
-      tc_pack8(va[u], EA, w);
-      tc_store8(sa, kTcSliceBytesA, colA[u], rgA[u], w);
-    }
-    {
-      uint32_t w[kTcSlices][4];
-      tc_pack8(vb, EB, w);
-      tc_store8(sb, kTcSliceBytesB, bB, rgB, w);
-    }
-    fence_async_smem();
+    tc_fence_before();
     __syncthreads();
-    const bool fresh = (cc % (kTcWindow / kTcK)) == 0;
-    if (tid == 0) {
-      tc_fence_after();
-      tc_issue_chunk(tbase, smem_u32(sa), smem_u32(sb), fresh);
-      tc_commit(pipe.mbar[stg]);
-    }
-    pipe.pending[stg] = 1;
-    const bool window_end = ((cc + 1) % (kTcWindow / kTcK)) == 0 || cc + 1 == nchunks;
-    if (window_end) {   // read the accumulators out into the running float pairs
-      if (!pipe.drain()) {
-        timeout = true;
-        break;
-      }
-      tc_fence_after();
-#pragma unroll
-      for (int cg = 0; cg < 4; ++cg) {
-        float hi[8], lo[8];
-        tc_read8(tbase, q, h * 32 + cg * 8, hi, lo);
-#pragma unroll
-        for (int e = 0; e < 8; ++e) two_sum_acc(rs[cg * 8 + e], rc[cg * 8 + e], hi[e], lo[e]);
-      }
-      tc_fence_before();
-      __syncthreads();
-    }
+  }
+  if (timeout) {   // both roles wait (bounded) for what they started
+    __shared__ long long sCons;
+    if (tid == 0) sCons = gcons;
+    __syncthreads();
+    if (tid == kTcProducer)
+      for (int64_t g = sCons; g < gprod; ++g) (void)mbar_wait(bars.full[g % kTcStages], tc_par(g));
+    if (tid == 0 && gcons > 0) (void)mbar_wait(bars.empty[(gcons - 1) % kTcStages], tc_par(gcons - 1));
   }
   if (!timeout && a0 + al < p) {
     const int ca = j * p + a0 + al;

@@ -89,21 +89,32 @@ template <typename T>
 cudaError_t launch_lp_colnorm(const T *R, int64_t n, int k, double *partN, int grid, const DevStatus *st,
                               cudaStream_t s, const int *shR);
 
-// Tensor-core large-block BAXPY (bcg_kernels_tc.cuh; FP64 data, p a multiple of 64 up to 256): the p x p matrices
-// are first cut into bf16 digit images (launch_tc_slice: C row-major per distinct block, Cs of
-// tc_workspace_bytes(nblkC, p) bytes, Cexp nblkC * p ints), then OUT_j = BASE_j (x bscale) + sign Y_j C_j.
+// Tensor-core large-block products and updates (bcg_kernels_tc.cuh; FP64 data, p a multiple of 64 up to 256).
+// Every operand is first cut into bf16 digit images that are byte for byte the kernels' shared-memory stages:
+// the p x p matrices with launch_tc_slice (C row-major per distinct block, Cs of tc_workspace_bytes(nblkC, p)
+// bytes, Cexp nblkC * p ints); the Gram's operands into column images (an exponent per column:
+// launch_tc_col_exp, then launch_tc_cut_cols; X times xscale per row if given); the BAXPY's Y into row images (an
+// exponent per row of a block, written to erow: ceil(n / 128) * 128 * (k / p) ints). Then launch_tc_gram_img
+// writes the partials of <<X, Y>>_S into `chunks` partial rows in the layout of launch_lp_gram, and
+// launch_tc_baxpy_img forms OUT_j = BASE_j (x bscale) + sign Y_j C_j.
 bool tc_ok(int k, int p);
 size_t tc_workspace_bytes(int nblkC, int p);
 cudaError_t launch_tc_slice(const double *C, int nblkC, int p, uint16_t *Cs, int *Cexp, cudaStream_t s);
-cudaError_t launch_tc_baxpy(double *OUT, const double *BASE, const double *Y, const uint16_t *Cs, const int *Cexp,
-                            int64_t n, int k, int p, int global, double sign, const int *active, DevStatus *st,
-                            int bump, cudaStream_t s, const double *bscale, int nsm);
-// Tensor-core partials of <<X, Y>>_S (X's rows times xscale[r] if given) into `chunks` partial rows in the layout
-// of launch_lp_gram; ecol: 2 k ints of workspace (the columns' exponent fields).
-cudaError_t launch_tc_gram(const double *X, const double *Y, const double *xscale, int64_t n, int k, int p,
-                           int global, const int *active, double *part, int chunks, int *ecol, DevStatus *st,
-                           cudaStream_t s, int nsm);
-
+size_t tc_row_image_size(int64_t n, int k);
+size_t tc_col_image_size(int64_t n, int k);
+cudaError_t launch_tc_col_exp(const double *X, const double *xscale, int64_t n, int k, int *ecol, int nsm,
+                              cudaStream_t s);
+cudaError_t launch_tc_cut_cols(const double *X, const double *xscale, int64_t n, int k, const int *ecol,
+                               unsigned char *img, int nsm, cudaStream_t s);
+cudaError_t launch_tc_cut_rows(const double *Y, int64_t n, int k, int p, unsigned char *img, int *erow,
+                               cudaStream_t s);
+cudaError_t launch_tc_gram_img(const unsigned char *imgX, const unsigned char *imgY, int64_t n, int k, int p,
+                               int global, const int *active, double *part, int chunks, const int *ecx,
+                               const int *ecy, DevStatus *st, cudaStream_t s);
+cudaError_t launch_tc_baxpy_img(double *OUT, const double *BASE, const unsigned char *imgY, const int *erow,
+                                const uint16_t *Cs, const int *Cexp, int64_t n, int k, int p, int global,
+                                double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
+                                const double *bscale, int nsm);
 // doubles of per-block workspace of the p x p solves; kept in global memory (gws) when too big for shared
 size_t small_ws_doubles(int p);
 bool small_needs_gws(int p);

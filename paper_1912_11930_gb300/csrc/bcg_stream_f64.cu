@@ -14,33 +14,59 @@ cudaError_t launch_tc_slice(const double *C, int nblkC, int p, uint16_t *Cs, int
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_gram(const double *X, const double *Y, const double *xscale, int64_t n, int k, int p,
-                           int global, const int *active, double *part, int chunks, int *ecol, DevStatus *st,
-                           cudaStream_t s, int nsm) {
-  if (!tc_layout_ok(k, p)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaMemsetAsync(ecol, 0, 2 * sizeof(int) * (size_t)k, s);
+size_t tc_row_image_size(int64_t n, int k) { return tc_row_image_bytes(n, k); }
+size_t tc_col_image_size(int64_t n, int k) { return tc_col_image_bytes(n, k); }
+
+cudaError_t launch_tc_col_exp(const double *X, const double *xscale, int64_t n, int k, int *ecol, int nsm,
+                              cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(ecol, 0, sizeof(int) * (size_t)k, s);
   if (e != cudaSuccess) return e;
   const int ge = (int)std::min<int64_t>((n * k + kNT - 1) / kNT, (int64_t)nsm * 8);
   kt_col_exp<<<ge, kNT, 0, s>>>(X, xscale, n, k, ecol);
-  kt_col_exp<<<ge, kNT, 0, s>>>(Y, nullptr, n, k, ecol + k);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if ((e = cudaFuncSetAttribute(kt_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem)) != cudaSuccess)
-    return e;
-  const int tiles = (k / p) * ((p + kTcRows - 1) / kTcRows) * (p / kTcCols);
-  dim3 grid((unsigned)tiles, (unsigned)chunks);
-  kt_gram<<<grid, kTcThreads, kTcSmem, s>>>(X, Y, xscale, n, k, p, global, active, part, ecol, ecol + k, st);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_baxpy(double *OUT, const double *BASE, const double *Y, const uint16_t *Cs, const int *Cexp,
-                            int64_t n, int k, int p, int global, double sign, const int *active, DevStatus *st,
-                            int bump, cudaStream_t s, const double *bscale, int nsm) {
+cudaError_t launch_tc_cut_cols(const double *X, const double *xscale, int64_t n, int k, const int *ecol,
+                               unsigned char *img, int nsm, cudaStream_t s) {
+  if (k % kTcCols) return cudaErrorInvalidValue;
+  const int64_t nrc = (n + kTcK - 1) / kTcK;
+  const int cts = k / kTcCols;
+  const int gy = (int)std::max<int64_t>(1, std::min<int64_t>(nrc, ((int64_t)nsm * 8 + cts - 1) / cts));
+  kt_cut_cols<<<dim3((unsigned)cts, (unsigned)gy), kTcThreads, 0, s>>>(X, xscale, n, k, ecol, img);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_cut_rows(const double *Y, int64_t n, int k, int p, unsigned char *img, int *erow,
+                               cudaStream_t s) {
   if (!tc_layout_ok(k, p)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(kt_baxpy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  const int64_t nrt = (n + kTcRows - 1) / kTcRows;
+  kt_cut_rows<<<dim3((unsigned)nrt, (unsigned)(k / p)), kTcThreads, 0, s>>>(Y, n, k, p, img, erow);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_gram_img(const unsigned char *imgX, const unsigned char *imgY, int64_t n, int k, int p,
+                               int global, const int *active, double *part, int chunks, const int *ecx,
+                               const int *ecy, DevStatus *st, cudaStream_t s) {
+  if (!tc_layout_ok(k, p)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kt_gram_img, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  if (e != cudaSuccess) return e;
+  const int tiles = (k / p) * ((p + kTcRows - 1) / kTcRows) * (p / kTcCols);
+  kt_gram_img<<<dim3((unsigned)tiles, (unsigned)chunks), kTcThreads, kTcSmem, s>>>(imgX, imgY, n, k, p, global,
+                                                                                   active, part, ecx, ecy, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tc_baxpy_img(double *OUT, const double *BASE, const unsigned char *imgY, const int *erow,
+                                const uint16_t *Cs, const int *Cexp, int64_t n, int k, int p, int global,
+                                double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
+                                const double *bscale, int nsm) {
+  if (!tc_layout_ok(k, p)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(kt_baxpy_img, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = ((n + kTcRows - 1) / kTcRows) * (k / kTcCols);
   const int grid = (int)std::min<int64_t>(ntiles, nsm);
-  kt_baxpy<<<grid, kTcThreads, kTcSmem, s>>>(OUT, BASE, Y, Cs, Cexp, n, k, p, global, sign, active, st, bump, bscale);
+  kt_baxpy_img<<<grid, kTcThreads, kTcSmem, s>>>(OUT, BASE, imgY, erow, Cs, Cexp, n, k, p, global, sign, active, st,
+                                                 bump, bscale);
   return cudaGetLastError();
 }
 
