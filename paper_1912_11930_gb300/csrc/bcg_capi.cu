@@ -276,7 +276,7 @@ bcg_status setup_workspace(bcg_ctx *h) {
   CKS(h->alloc(&h->bdot_sh, 2 * (size_t)h->k));
   if (h->prec == BCG_FP32_REFINE) CKS(h->alloc(&h->msig, h->k));
   if (small_needs_gws(h->p)) CKS(h->alloc(&h->gws, (size_t)h->nblk * small_ws_doubles(h->p)));
-  if (h->prec != BCG_FP32_REFINE && tc_ok(h->k, h->p)) {
+  if (tc_ok(h->k, h->p)) {   // FP64 products and updates; the mixed form's FP32 process uses the products
     CKS(h->alloc(&h->tc_cs, tc_workspace_bytes(h->nblk, h->p) / sizeof(uint16_t)));
     CKS(h->alloc(&h->tc_cexp, (size_t)h->nblk * h->p));
     CKS(h->alloc(&h->tc_ecol, 2 * (size_t)h->k));
@@ -458,13 +458,13 @@ bcg_status launch_iteration_tcimg(bcg_ctx *h, const OpDesc &A, double *X, double
   int *erP = h->tc_erow, *erQ = h->tc_erow + (size_t)((n + 127) / 128) * 128 * (k / p);
   CK(launch_lp_bop<double>(A, P, Q, n, k, h->st, nsm, s));
   // alpha = <<P, Q>> and the recomputed rho = <<P, R>> (P's column images serve both)
-  CK(launch_tc_col_exp(P, nullptr, n, k, ec1, nsm, s));
-  CK(launch_tc_cut_cols(P, nullptr, n, k, ec1, G1, nsm, s));
-  CK(launch_tc_col_exp(Q, nullptr, n, k, ec2, nsm, s));
-  CK(launch_tc_cut_cols(Q, nullptr, n, k, ec2, G2, nsm, s));
+  CK(launch_tc_col_exp<double>(P, nullptr, n, k, ec1, nsm, s));
+  CK(launch_tc_cut_cols<double>(P, nullptr, n, k, ec1, G1, nsm, s));
+  CK(launch_tc_col_exp<double>(Q, nullptr, n, k, ec2, nsm, s));
+  CK(launch_tc_cut_cols<double>(Q, nullptr, n, k, ec2, G2, nsm, s));
   CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partA, ch, ec1, ec2, h->st, s));
-  CK(launch_tc_col_exp(R, nullptr, n, k, ec2, nsm, s));   // stream order: after the alpha kernel read ec2 and G2
-  CK(launch_tc_cut_cols(R, nullptr, n, k, ec2, G2, nsm, s));
+  CK(launch_tc_col_exp<double>(R, nullptr, n, k, ec2, nsm, s));   // stream order: after the alpha kernel read ec2 and G2
+  CK(launch_tc_cut_cols<double>(R, nullptr, n, k, ec2, G2, nsm, s));
   CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partR, ch, ec1, ec2, h->st, s));
   CK(launch_solve_lambda(h->partA, h->partR, ch, ch, k, p, gl, h->active, h->lam, h->rho_rec, h->st, h->gws, 0, s));
   // X += P lambda, R -= Q lambda
@@ -475,11 +475,11 @@ bcg_status launch_iteration_tcimg(bcg_ctx *h, const OpDesc &A, double *X, double
   CK(launch_tc_baxpy_img(R, R, RQ, erQ, h->tc_cs, h->tc_cexp, n, k, p, gl, -1.0, h->active, h->st, 0, s, nullptr,
                          nsm));
   // rho = <<Z, R>>, Z = M^{-1} R formed in the cut
-  CK(launch_tc_col_exp(R, dinv, n, k, ec1, nsm, s));
-  CK(launch_tc_cut_cols(R, dinv, n, k, ec1, G1, nsm, s));
+  CK(launch_tc_col_exp<double>(R, dinv, n, k, ec1, nsm, s));
+  CK(launch_tc_cut_cols<double>(R, dinv, n, k, ec1, G1, nsm, s));
   if (dinv) {
-    CK(launch_tc_col_exp(R, nullptr, n, k, ec2, nsm, s));
-    CK(launch_tc_cut_cols(R, nullptr, n, k, ec2, G2, nsm, s));
+    CK(launch_tc_col_exp<double>(R, nullptr, n, k, ec2, nsm, s));
+    CK(launch_tc_cut_cols<double>(R, nullptr, n, k, ec2, G2, nsm, s));
     CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partRho, ch, ec1, ec2, h->st, s));
   } else {
     CK(launch_tc_gram_img(G1, G1, n, k, p, gl, h->active, h->partRho, ch, ec1, ec1, h->st, s));
@@ -493,24 +493,56 @@ bcg_status launch_iteration_tcimg(bcg_ctx *h, const OpDesc &A, double *X, double
   return BCG_OK;
 }
 
-// One iteration with large blocks (p > 32): tiled FMA / Dot2 products (the mixed form's FP32 process, and FP64
-// with option "tensor_cores" 0). The direction update cannot run in place across
+// One iteration with large blocks (p > 32): tiled FMA kernels for BOP and the block updates; the block products on
+// the tensor cores where the handle has digit images (the mixed form's FP32 process), else the tiled Dot2 kernel
+// (and FP64 with option "tensor_cores" 0). The direction update cannot run in place across
 // column tiles, so it writes into the Q buffer (free at that point) and the caller swaps P and Q.
 template <typename T>
 bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g) {
   cudaStream_t s = h->stream;
   const int ch = g.op;
+  const int64_t n = h->n;
+  const int k = h->k, p = h->p, gl = h->global, nsm = h->nsm;
   const ShiftCtl sc = shifts_of<T>(h);
   const int *shR = sh_role(sc.sh, h->k, SH_R), *shP = sh_role(sc.sh, h->k, SH_P), *shQ = sh_role(sc.sh, h->k, SH_Q);
+  // the block products on the tensor cores from digit images where the handle has them (the mixed form's FP32
+  // process; the FP64 form has launch_iteration_tcimg)
+  const bool tc = h->tensor_cores && h->tc_img[0] != nullptr;
+  unsigned char *G1 = h->tc_img[0], *G2 = h->tc_img[1];
+  int *ec1 = h->tc_ecol, *ec2 = h->tc_ecol + k;
   CK(launch_lp_bop<T>(A, P, Q, h->n, h->k, h->st, h->nsm, s));
-  CKS(lp_gram<T>(h, P, Q, h->partA, ch, nullptr, shP, shQ));
-  CKS(lp_gram<T>(h, P, R, h->partR, ch, nullptr, shP, shR));
+  if (tc) {   // alpha = <<P, Q>>, the recomputed rho = <<P, R>> (P's images serve both)
+    CK(launch_tc_col_exp<T>(P, nullptr, n, k, ec1, nsm, s));
+    CK(launch_tc_cut_cols<T>(P, nullptr, n, k, ec1, G1, nsm, s));
+    CK(launch_tc_col_exp<T>(Q, nullptr, n, k, ec2, nsm, s));
+    CK(launch_tc_cut_cols<T>(Q, nullptr, n, k, ec2, G2, nsm, s));
+    CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partA, ch, ec1, ec2, h->st, s));
+    CK(launch_tc_col_exp<T>(R, nullptr, n, k, ec2, nsm, s));
+    CK(launch_tc_cut_cols<T>(R, nullptr, n, k, ec2, G2, nsm, s));
+    CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partR, ch, ec1, ec2, h->st, s));
+  } else {
+    CKS(lp_gram<T>(h, P, Q, h->partA, ch, nullptr, shP, shQ));
+    CKS(lp_gram<T>(h, P, R, h->partR, ch, nullptr, shP, shR));
+  }
   CK(launch_solve_lambda(h->partA, h->partR, ch, ch, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
                          h->gws, 0, s));
   CKS(lp_update<T>(h, X, X, P, h->lam, 1.0, 0, nullptr));
   CKS(lp_update<T>(h, R, R, Q, h->lam, -1.0, 0, nullptr));
   // rho = <<Z, R>> with Z = M^{-1} R formed on the fly
-  CKS(lp_gram<T>(h, R, R, h->partRho, ch, dinv_of<T>(h), shP, shR));
+  if (tc) {
+    const T *dv = dinv_of<T>(h);
+    CK(launch_tc_col_exp<T>(R, dv, n, k, ec1, nsm, s));
+    CK(launch_tc_cut_cols<T>(R, dv, n, k, ec1, G1, nsm, s));
+    if (dv) {
+      CK(launch_tc_col_exp<T>(R, nullptr, n, k, ec2, nsm, s));
+      CK(launch_tc_cut_cols<T>(R, nullptr, n, k, ec2, G2, nsm, s));
+      CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partRho, ch, ec1, ec2, h->st, s));
+    } else {
+      CK(launch_tc_gram_img(G1, G1, n, k, p, gl, h->active, h->partRho, ch, ec1, ec1, h->st, s));
+    }
+  } else {
+    CKS(lp_gram<T>(h, R, R, h->partRho, ch, dinv_of<T>(h), shP, shR));
+  }
   CK(launch_lp_colnorm<T>(R, h->n, h->k, h->partN, g.res, h->st, s, shR));   // a full-GPU grid, like K0's
   CK(launch_solve_beta(h->partRho, h->partN, ch, g.res, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
                        h->active,

@@ -159,6 +159,23 @@ __device__ __forceinline__ unsigned long long tc_fixed48(double x, int E) {
   const int sft = 1028 + E - e;   // >= 5 since e - 1023 <= E
   return (e == 0 || e == 0x7FF || sft >= 64) ? 0ull : (m >> (sft < 5 ? 5 : sft));
 }
+// the same for an FP32 value (all 24 bits of its mantissa fit the window when its exponent is within 24 of E; zero,
+// subnormal or non-finite x: 0)
+__device__ __forceinline__ unsigned long long tc_fixed48(float x, int E) {
+  const uint32_t u = __float_as_uint(x);
+  const int ef = (int)((u >> 23) & 0xFFu);
+  const unsigned long long m = (u & 0x7FFFFFu) | 0x800000u;
+  const int sft = ef - 103 - E;   // |x| 2^(47 - E) = m 2^sft, below 2^48 since |x| < 2^(E+1)
+  if (ef == 0 || ef == 0xFF || sft <= -64) return 0ull;
+  return sft >= 0 ? (m << sft) : (m >> -sft);
+}
+// biased FP64 exponent field of x (a float's normal exponent moved to the FP64 bias; zero or subnormal: 0)
+__device__ __forceinline__ int tc_exp_field(double x) { return (__double2hiint(x) >> 20) & 0x7FF; }
+__device__ __forceinline__ int tc_exp_field(float x) {
+  const int ef = (int)((__float_as_uint(x) >> 23) & 0xFFu);
+  return ef == 0 ? 0 : (ef == 0xFF ? 0x7FF : ef + 896);
+}
+
 // bf16 bit pattern of sign * d for an integer 0 <= d < 64 (exact: 6 significant bits)
 __device__ __forceinline__ uint32_t tc_bf16_digit(uint32_t d, uint32_t sign16) {
   const float f = __uint_as_float(0x4B000000u | d) - 8388608.0f;
@@ -171,7 +188,8 @@ __device__ __forceinline__ uint32_t tc_digit(unsigned long long v, int i) {
 
 // Digits of 8 values sharing the exponent E (consecutive along the contraction): w[i] = the 16-byte core-matrix
 // row of slice i (8 bf16, the first value in the low half of w[i][0]).
-__device__ __forceinline__ void tc_pack8(const double (&v)[8], int E, uint32_t (&w)[kTcSlices][4]) {
+template <typename T>
+__device__ __forceinline__ void tc_pack8(const T (&v)[8], int E, uint32_t (&w)[kTcSlices][4]) {
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     const unsigned long long fx = tc_fixed48(v[e], E);
@@ -286,15 +304,17 @@ __global__ void kt_slice_cmat(const double *__restrict__ C, int nblkC, int p, ui
 // Column exponent fields for the Gram slicing: ecol[c] = max over rows of the biased exponent of X[r][c] (times
 // xscale[r] if given), by integer maxima (the caller zeroes ecol). Thread (g, c) covers rows g, g + rows per CTA
 // pass, ... of column c.
-__global__ void __launch_bounds__(kNT) kt_col_exp(const double *__restrict__ X, const double *__restrict__ xscale,
+// (FP32 data, the mixed form's process: the exponent fields in FP64's bias, so the same images and kernels serve.)
+template <typename T>
+__global__ void __launch_bounds__(kNT) kt_col_exp(const T *__restrict__ X, const T *__restrict__ xscale,
                                                   int64_t n, int k, int *__restrict__ ecol) {
   const int rpp = kNT / k;
   const int g = threadIdx.x / k, c = threadIdx.x - g * k;
   if (g >= rpp) return;
   int em = 0;
   for (int64_t r = (int64_t)blockIdx.x * rpp + g; r < n; r += (int64_t)gridDim.x * rpp) {
-    const double v = xscale ? X[r * k + c] * xscale[r] : X[r * k + c];
-    em = max(em, (__double2hiint(v) >> 20) & 0x7FF);
+    const T v = xscale ? X[r * k + c] * xscale[r] : X[r * k + c];
+    em = max(em, tc_exp_field(v));
   }
   atomicMax(ecol + c, em);
 }
@@ -382,7 +402,8 @@ __global__ void __launch_bounds__(kTcThreads) kt_cut_rows(const double *__restri
 
 // Column images of X (rows times xscale[r] if given) with the column exponent fields ecol (kt_col_exp): CTA
 // (ct, y) cuts the 64 columns of tile ct over the row chunks y, y + gridDim.y, ...
-__global__ void __launch_bounds__(kTcThreads) kt_cut_cols(const double *__restrict__ X, const double *__restrict__ xscale,
+template <typename T>
+__global__ void __launch_bounds__(kTcThreads) kt_cut_cols(const T *__restrict__ X, const T *__restrict__ xscale,
                                                           int64_t n, int k, const int *__restrict__ ecol,
                                                           unsigned char *__restrict__ img) {
   const int tid = threadIdx.x;
@@ -395,11 +416,11 @@ __global__ void __launch_bounds__(kTcThreads) kt_cut_cols(const double *__restri
   const int E = (ecol[c] > 0 ? ecol[c] : 1) - 1023;
   const int64_t nrc = (n + kTcK - 1) / kTcK;
   for (int64_t rc = (int64_t)blockIdx.y * kPer + sub; rc < nrc; rc += (int64_t)gridDim.y * kPer) {
-    double v[8];
+    T v[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
       const int64_t r = rc * kTcK + kg * 8 + e;
-      v[e] = r < n ? (xscale ? X[r * k + c] * xscale[r] : X[r * k + c]) : 0.0;
+      v[e] = r < n ? (xscale ? X[r * k + c] * xscale[r] : X[r * k + c]) : T(0);
     }
     uint32_t w[kTcSlices][4];
     tc_pack8(v, E, w);

@@ -102,10 +102,12 @@ size_t tc_workspace_bytes(int nblkC, int p);
 cudaError_t launch_tc_slice(const double *C, int nblkC, int p, uint16_t *Cs, int *Cexp, cudaStream_t s);
 size_t tc_row_image_size(int64_t n, int k);
 size_t tc_col_image_size(int64_t n, int k);
-cudaError_t launch_tc_col_exp(const double *X, const double *xscale, int64_t n, int k, int *ecol, int nsm,
-                              cudaStream_t s);
-cudaError_t launch_tc_cut_cols(const double *X, const double *xscale, int64_t n, int k, const int *ecol,
-                               unsigned char *img, int nsm, cudaStream_t s);
+// T = double or float (the mixed form's FP32 process: FP32 values are exact in the 48-bit cut)
+template <typename T>
+cudaError_t launch_tc_col_exp(const T *X, const T *xscale, int64_t n, int k, int *ecol, int nsm, cudaStream_t s);
+template <typename T>
+cudaError_t launch_tc_cut_cols(const T *X, const T *xscale, int64_t n, int k, const int *ecol, unsigned char *img,
+                               int nsm, cudaStream_t s);
 cudaError_t launch_tc_cut_rows(const double *Y, int64_t n, int k, int p, unsigned char *img, int *erow,
                                cudaStream_t s);
 cudaError_t launch_tc_gram_img(const unsigned char *imgX, const unsigned char *imgY, int64_t n, int k, int p,

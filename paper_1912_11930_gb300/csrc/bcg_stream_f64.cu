@@ -17,24 +17,31 @@ cudaError_t launch_tc_slice(const double *C, int nblkC, int p, uint16_t *Cs, int
 size_t tc_row_image_size(int64_t n, int k) { return tc_row_image_bytes(n, k); }
 size_t tc_col_image_size(int64_t n, int k) { return tc_col_image_bytes(n, k); }
 
-cudaError_t launch_tc_col_exp(const double *X, const double *xscale, int64_t n, int k, int *ecol, int nsm,
-                              cudaStream_t s) {
+template <typename T>
+cudaError_t launch_tc_col_exp(const T *X, const T *xscale, int64_t n, int k, int *ecol, int nsm, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(ecol, 0, sizeof(int) * (size_t)k, s);
   if (e != cudaSuccess) return e;
   const int ge = (int)std::min<int64_t>((n * k + kNT - 1) / kNT, (int64_t)nsm * 8);
-  kt_col_exp<<<ge, kNT, 0, s>>>(X, xscale, n, k, ecol);
+  kt_col_exp<T><<<ge, kNT, 0, s>>>(X, xscale, n, k, ecol);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_cut_cols(const double *X, const double *xscale, int64_t n, int k, const int *ecol,
-                               unsigned char *img, int nsm, cudaStream_t s) {
+template <typename T>
+cudaError_t launch_tc_cut_cols(const T *X, const T *xscale, int64_t n, int k, const int *ecol, unsigned char *img,
+                               int nsm, cudaStream_t s) {
   if (k % kTcCols) return cudaErrorInvalidValue;
   const int64_t nrc = (n + kTcK - 1) / kTcK;
   const int cts = k / kTcCols;
   const int gy = (int)std::max<int64_t>(1, std::min<int64_t>(nrc, ((int64_t)nsm * 8 + cts - 1) / cts));
-  kt_cut_cols<<<dim3((unsigned)cts, (unsigned)gy), kTcThreads, 0, s>>>(X, xscale, n, k, ecol, img);
+  kt_cut_cols<T><<<dim3((unsigned)cts, (unsigned)gy), kTcThreads, 0, s>>>(X, xscale, n, k, ecol, img);
   return cudaGetLastError();
 }
+template cudaError_t launch_tc_col_exp<double>(const double *, const double *, int64_t, int, int *, int, cudaStream_t);
+template cudaError_t launch_tc_col_exp<float>(const float *, const float *, int64_t, int, int *, int, cudaStream_t);
+template cudaError_t launch_tc_cut_cols<double>(const double *, const double *, int64_t, int, const int *,
+                                                unsigned char *, int, cudaStream_t);
+template cudaError_t launch_tc_cut_cols<float>(const float *, const float *, int64_t, int, const int *,
+                                               unsigned char *, int, cudaStream_t);
 
 cudaError_t launch_tc_cut_rows(const double *Y, int64_t n, int k, int p, unsigned char *img, int *erow,
                                cudaStream_t s) {

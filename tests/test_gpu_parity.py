@@ -36,6 +36,7 @@ def mat(name):
             "vc_20": lambda: W.varcoef3d(20, 17, 23, seed=4),
             "s27_15": lambda: W.stencil27(15, 14, 13, seed=5),
             "spd_200": lambda: W.dense_to_csr(W.random_spd_dense(200, seed=6, cond=40.0)),
+            "p3d_17": lambda: W.poisson3d(17, 19, 16),
         }[name]()
     return _MATS[name]
 
@@ -562,3 +563,26 @@ def test_large_p_tensor_cores_match_fma(torch_dev, name, sub, k, p, m):
         assert_close(a, b, 1e-10, f"tensor cores against FMA kernels (Jacobi {jac})")
         ref = O.solve(M.to_scipy(), B, p=p, sub=sub, tol=0.0, maxit=m, precond="jacobi" if jac else "none")
         assert_close(a, ref.X, 1e-9, f"tensor cores against the oracle (Jacobi {jac})")
+
+
+@pytest.mark.parametrize("name,sub,k,p,jac", [("p3d_17", "classical", 64, 64, 0), ("p3d_17", "hybrid", 128, 64, 1),
+                                              ("p3d_17", "global", 128, 64, 0), ("p3d_17", "classical", 128, 128, 1)])
+def test_mixed_large_blocks_tensor_core_products(torch_dev, name, sub, k, p, jac):
+    """The mixed form's FP32 process with wide blocks takes its block products on the tensor cores (FP32 values cut
+    into the same 48-bit digit images): refined to 1e-10 it reaches the FP64 oracle's solution within 1e-8, at
+    FP64's iteration count within a few, and agrees with the same solve on the Dot2 kernels."""
+    M = mat(name)
+    A = M.to_scipy()
+    B = W.rhs(M.n, k, seed=44)
+    pre = "jacobi" if jac else "none"
+    a, ra = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, prec="fp32_refine", tol=1e-10, maxit=5000,
+                      opts={"tensor_cores": 1, "precond": jac})
+    b, rb = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, prec="fp32_refine", tol=1e-10, maxit=5000,
+                      opts={"tensor_cores": 0, "precond": jac})
+    assert ra.ok and rb.ok, (ra, rb)
+    assert abs(ra.iters - rb.iters) <= max(4, rb.iters // 20), (ra.iters, rb.iters)
+    true = np.linalg.norm(B - A @ a, axis=0) / np.linalg.norm(B, axis=0)
+    assert np.all(true <= 1.5e-10), true
+    ref = O.solve(A, B, p=p, sub=sub, tol=1e-12, maxit=5000, precond=pre)
+    assert_close(a, ref.X, 1e-8, "tensor-core products against the oracle")
+    assert_close(a, b, 1e-8, "tensor-core products against the Dot2 products")
