@@ -784,6 +784,11 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
   };
   double *W = h->R, *S = h->P, *Qb = h->Q;
   double *partM = dinv ? h->partR : nullptr;   // <<T, M^{-1} T>> (K1's recomputed-rho partials are unused here)
+  // wide blocks on the tensor cores (digit images) where the handle has them
+  const bool tc = lp && h->tensor_cores && h->tc_img[0] != nullptr;
+  unsigned char *G1 = h->tc_img[0], *G2 = h->tc_img[1], *RS = h->tc_img[2], *RT = h->tc_img[3];
+  int *ec1 = h->tc_ecol, *ec2 = h->tc_ecol + k;
+  int *erS = h->tc_erow, *erT = h->tc_erow + (size_t)((n + 127) / 128) * 128 * (k / p);
   // R^0 = B - A X^0 (in W's buffer) = Q^0 C^0, S^1 = M^{-1} Q^0
   CK(launch_residual<double>(h->A64, X, B, W, nullptr, nullptr, nullptr, n, k, h->partN, h->g64.res, s, nullptr));
   CK(launch_init_status(h->partN, h->g64.res, k, p, gl, h->r0n2, h->rn2, h->active, h->block_iters, h->lam,
@@ -812,6 +817,45 @@ bcg_status solve_retooled(bcg_ctx *h, const double *B, double *X, double tol, in
         CK(launch_dr_psi(h->partRho, np_g, k, p, h->tol2_dev, h->r0n2, h->rn2, h->active, h->block_iters,
                          h->dr_C, h->dr_psiinv, h->dr_phi, h->st, h->gws, s, gl, partM));
         CK(launch_dr_update_qs(Qb, S, n, k, p, h->dr_psiinv, h->dr_phi, h->active, h->st, h->nsm, s, gl, dinv));
+        continue;
+      }
+      if (tc) {   // the same steps on the tensor cores, from digit images
+        CK(launch_lp_bop<double>(h->A64, S, W, n, k, h->st, h->nsm, s));                       // W = A S
+        CK(launch_tc_col_exp<double>(S, nullptr, n, k, ec1, h->nsm, s));                       // alpha = <<S, W>>
+        CK(launch_tc_cut_cols<double>(S, nullptr, n, k, ec1, G1, h->nsm, s));
+        CK(launch_tc_col_exp<double>(W, nullptr, n, k, ec2, h->nsm, s));
+        CK(launch_tc_cut_cols<double>(W, nullptr, n, k, ec2, G2, h->nsm, s));
+        CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partA, np_g, ec1, ec2, h->st, s));
+        CK(launch_dr_xi(h->partA, np_g, k, p, h->active, h->dr_C, h->dr_xi, h->lam, h->st, h->gws, 0, s, gl));
+        CK(launch_tc_slice(h->lam, h->nblk, p, h->tc_cs, h->tc_cexp, s));                     // X += S lambda
+        CK(launch_tc_cut_rows(S, n, k, p, RS, erS, s));
+        CK(launch_tc_baxpy_img(X, X, RS, erS, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 0, s, nullptr,
+                               h->nsm));
+        CK(launch_tc_slice(h->dr_xi, h->nblk, p, h->tc_cs, h->tc_cexp, s));                   // T = Q - W xi
+        CK(launch_tc_cut_rows(W, n, k, p, RT, erT, s));
+        CK(launch_tc_baxpy_img(Qb, Qb, RT, erT, h->tc_cs, h->tc_cexp, n, k, p, gl, -1.0, h->active, h->st, 0, s,
+                               nullptr, h->nsm));
+        CK(launch_tc_col_exp<double>(Qb, nullptr, n, k, ec1, h->nsm, s));                      // <<T, T>> per block
+        CK(launch_tc_cut_cols<double>(Qb, nullptr, n, k, ec1, G1, h->nsm, s));
+        CK(launch_tc_gram_img(G1, G1, n, k, p, gl, h->active, h->partRho, np_g, ec1, ec1, h->st, s));
+        if (dinv) {                                                                             // <<M^{-1} T, T>>
+          CK(launch_tc_col_exp<double>(Qb, dinv, n, k, ec2, h->nsm, s));
+          CK(launch_tc_cut_cols<double>(Qb, dinv, n, k, ec2, G2, h->nsm, s));
+          CK(launch_tc_gram_img(G2, G1, n, k, p, gl, h->active, partM, np_g, ec2, ec1, h->st, s));
+        }
+        CK(launch_dr_psi(h->partRho, np_g, k, p, h->tol2_dev, h->r0n2, h->rn2, h->active, h->block_iters, h->dr_C,
+                         h->dr_psiinv, h->dr_phi, h->st, h->gws, s, gl, partM));
+        CK(launch_tc_slice(h->dr_psiinv, h->nblk, p, h->tc_cs, h->tc_cexp, s));               // Q^+ = T psi^{-1}
+        CK(launch_tc_cut_rows(Qb, n, k, p, RT, erT, s));
+        CK(launch_tc_baxpy_img(W, nullptr, RT, erT, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 0, s,
+                               nullptr, h->nsm));
+        CK(launch_tc_slice(h->dr_phi, h->nblk, p, h->tc_cs, h->tc_cexp, s));                  // S^+ = M^{-1} Q^+ + S psi^T
+        CK(launch_tc_baxpy_img(Qb, W, RS, erS, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 1, s, dinv,
+                               h->nsm));
+        double *old_s = S;
+        S = Qb;
+        Qb = W;
+        W = old_s;
         continue;
       }
       CK(launch_lp_bop<double>(h->A64, S, W, n, k, h->st, h->nsm, s));   // W = A S

@@ -463,8 +463,11 @@ __device__ __forceinline__ TcBars tc_bars_setup(unsigned char *misc) {
 }
 __device__ __forceinline__ uint32_t tc_par(int64_t g) { return (uint32_t)((g / kTcStages) & 1); }
 
-// kt_baxpy with Y's row images (kt_cut_rows) and C's images (kt_slice_cmat): the same tiles, readout and arguments.
-// The producer also prefetches the first chunks of the CTA's next tile while the current tile is read out.
+// OUT_j = BASE_j (times bscale[r] per row, if given; BASE NULL: zero) + sign * Y_j C_j over every block j (global: C_0
+// for all), from Y's row images (kt_cut_rows) and C's images (kt_slice_cmat). OUT may equal BASE. Frozen blocks
+// (active[j] = 0) get OUT = BASE (scaled). bump: CTA 0 advances the iteration counter (the P update's role).
+// Persistent over 128 x 64 output tiles; the producer also prefetches the first chunks of the CTA's next tile while
+// the current tile is read out.
 __global__ void __launch_bounds__(kTcThreads, 1) kt_baxpy_img(double *OUT, const double *BASE,
                                                               const unsigned char *__restrict__ imgY,
                                                               const int *__restrict__ erow,
@@ -539,7 +542,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) kt_baxpy_img(double *OUT, const
         const int64_t r = r0 + rl;
         if (r >= n) continue;
         const double s = bscale ? bscale[r] : 1.0;
-        for (int e = 0; e < 8; ++e) OUT[r * k + c0 + cg * 8 + e] = BASE[r * k + c0 + cg * 8 + e] * s;
+        for (int e = 0; e < 8; ++e) OUT[r * k + c0 + cg * 8 + e] = BASE ? BASE[r * k + c0 + cg * 8 + e] * s : 0.0;
       }
       continue;
     }
@@ -551,10 +554,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) kt_baxpy_img(double *OUT, const
     const int rl = q * 32 + lane;
     const int64_t r = r0 + rl;
     double2 bv[16];
-    if (r < n) {
+    if (r < n && BASE) {
       const double2 *bp = reinterpret_cast<const double2 *>(BASE + r * k + c0 + h * 32);
 #pragma unroll
       for (int e = 0; e < 16; ++e) bv[e] = bp[e];
+    } else {
+#pragma unroll
+      for (int e = 0; e < 16; ++e) bv[e] = make_double2(0.0, 0.0);
     }
     const double bs = (r < n && bscale) ? bscale[r] : 1.0;
     if (tid == kTcProducer && !sFlag[0]) {   // the rest of this tile, then the next tile's first stages
