@@ -364,7 +364,8 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
   if (threadIdx.x == 0) atomicMax(&st->iter, it);
 }
 
-// Triangular solves of the large-block BSOLVEs, spread over the right-hand-side columns: CTA (jb, g) solves
+// Triangular solves of the large-block BSOLVEs (chol = 2: the backward solve with L^T alone), spread over the
+// right-hand-side columns: CTA (jb, g) solves
 // columns [8g, 8g + 8) of block jb. The factors come from the blocked factorizations (k_chol_* / k_lu_*) in the
 // block's global workspace ws = gws + jb * small_ws_doubles(p): M = ws (p x p row-major), B = ws + p*p
 // (right-hand sides, row-major), pivots (LU) as ints at ws + 2*p*p.
@@ -411,8 +412,8 @@ __global__ void __launch_bounds__(256) k_trsm_cols(int p, int chol, const double
       }
     __syncthreads();
   }
-  // forward: column panels pan[(i - a0) * 32 + j] = M[i][a0 + j], rows i >= a0
-  for (int a0 = 0; a0 < p; a0 += kTrsmPanel) {
+  // forward: column panels pan[(i - a0) * 32 + j] = M[i][a0 + j], rows i >= a0 (chol = 2: L^T X = B alone)
+  for (int a0 = 0; a0 < p && chol != 2; a0 += kTrsmPanel) {
     const int rows = p - a0;
     for (int e = threadIdx.x; e < rows * kTrsmPanel; e += NT) {
       const int r = e / kTrsmPanel, j = e % kTrsmPanel;
@@ -519,18 +520,25 @@ __global__ void __launch_bounds__(256) k_bs_gather(const double *__restrict__ pa
 
 // Cholesky of the diagonal 32 x 32 block at a0 (lower triangle), after the trailing updates of the earlier
 // panels. At a0 = 0 the pivot threshold 64 eps max|diag| of the unfactored matrix is set first.
+// colrel: the pivot test of the retooled form (each pivot against 64 eps times its own original diagonal entry,
+// kept at ws + 3 p^2 + 8 .. + p), else Algorithm 1's (against 64 eps max|diag|).
 __global__ void __launch_bounds__(256) k_chol_diag(double *gws, int p, int a0, const int *__restrict__ active,
-                                                   DevStatus *st) {
+                                                   DevStatus *st, int colrel) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   if (!active[jb]) return;
   double *M = blk_ws(gws, jb, p);
   double *thr = M + 3 * (int64_t)p * p;
+  double *dg = thr + 8;
   __shared__ double L[kPB][kPB + 1];
   __shared__ int bad;
   if (a0 == 0) {
     double m = 0.0;
-    for (int a = threadIdx.x; a < p; a += blockDim.x) m = fmax(m, fabs(M[(int64_t)a * p + a]));
+    for (int a = threadIdx.x; a < p; a += blockDim.x) {
+      const double d = M[(int64_t)a * p + a];
+      m = fmax(m, fabs(d));
+      if (colrel) dg[a] = d;
+    }
     m = block_max(m);
     if (threadIdx.x == 0) thr[0] = kPivotFactor * DBL_EPSILON * m;
   }
@@ -540,10 +548,10 @@ __global__ void __launch_bounds__(256) k_chol_diag(double *gws, int p, int a0, c
   }
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
-  const double thresh = thr[0];
   for (int a = 0; a < kPB; ++a) {
     if (threadIdx.x == 0) {
       const double d = L[a][a];
+      const double thresh = colrel ? kPivotFactor * DBL_EPSILON * dg[a0 + a] : thr[0];
       if (!(isfinite(d) && d > thresh)) bad = 1;
       else L[a][a] = sqrt(d);
     }
@@ -1056,9 +1064,9 @@ static cudaError_t launch_trsm(int p, int nblk, int chol, const double *gws, con
 // Wide blocks: the partial sums (k_bs_gather), the blocked factorization panel by panel, then the
 // column-parallel triangular solves.
 static cudaError_t launch_blocked_chol(int p, int nblk, double *gws, const int *active, DevStatus *st,
-                                       cudaStream_t s) {
+                                       cudaStream_t s, int colrel = 0) {
   for (int a0 = 0; a0 < p; a0 += kPB) {
-    k_chol_diag<<<nblk, 256, 0, s>>>(gws, p, a0, active, st);
+    k_chol_diag<<<nblk, 256, 0, s>>>(gws, p, a0, active, st, colrel);
     const int rows = p - a0 - kPB;
     if (rows > 0) {
       k_chol_panel<<<dim3((unsigned)nblk, (unsigned)((rows + 127) / 128)), 128, 0, s>>>(gws, p, a0, active, st);
