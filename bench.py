@@ -303,9 +303,33 @@ def run_extra(name, args):
             rows.append(dict(prec=prec, tensor_cores=tc, s=t, iterations=r.iters, status=bcg.STATUS_NAMES[r.status],
                              ms_per_iteration=t * 1e3 / max(r.iters, 1)))
             print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        # the tensor-core kernels alone (option "profile": each launch bracketed by CUDA events), 6 iterations, and
+        # their throughput against the measured dense bf16 peak: each launch does 2 n p^2 FP64-accurate products
+        # per block as 36 bf16 digit-pair products
+        S = bcg.Solver.from_matrix(M, k=k, p=k, sub="classical", prec="fp64", device=dev)
+        S.set_option("profile", 1)
+        X = torch.zeros_like(B)
+        S.solve(B, X, tol=1e-300, maxit=6)
+        prof = S.profile()
+        S.close()
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+                bf16 = float(json.load(fh)["bf16_tflops"])
+            src = "measured burst"
+        except Exception:
+            bf16, src = 1900.0, "fallback"
+        flop = 2.0 * M.n * k * k * 36
+        tc = {}
+        for name in ("tc_gram", "tc_baxpy"):
+            tot, cnt = prof[name]
+            if cnt:
+                avg = tot / cnt
+                tc[name] = {"avg_ms": avg, "launches": cnt, "bf16_tflops": flop / (avg * 1e-3) / 1e12,
+                            "frac_of_bf16_peak": flop / (avg * 1e-3) / 1e12 / bf16, "bf16_peak": bf16,
+                            "peak_source": src}
         out.update(value=rows[0]["s"], dtype="f64 (and f32 with f64 residual replacement)",
                    config={"workload": "poisson3d_64_csr_k256_classical_24_iterations", "n": M.n, "k": k, "p": k},
-                   results=rows)
+                   results=rows, tensor_core_kernels=tc)
     elif name == "retooled_128_k32":
         # Dubrulle's retooled block CG against Algorithm 1 (FP64): the 128^3 Poisson solve to 1e-8, the same with
         # the right-hand side's columns scaled from 1e-6 to 1e6 inside every block of 8 (Algorithm 1 breaks down

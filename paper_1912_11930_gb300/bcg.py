@@ -235,15 +235,16 @@ def bcg_bdot_noalloc(n, k, p, sub, X, Y, gamma, stream=None):
                                    _stream(stream)))
 
 
-KERNEL_NAMES = ["op_gram", "solve_lambda", "update_xr", "solve_beta", "update_p", "residual"]
+KERNEL_NAMES = ["op_gram", "solve_lambda", "update_xr", "solve_beta", "update_p", "residual", "tc_gram", "tc_baxpy"]
 
 
 def bcg_profile(h):
     """{kernel: (total_ms, launches)} of the profiled iterations since profiling was enabled."""
-    ms = (ctypes.c_double * 6)()
-    cnt = (ctypes.c_int64 * 6)()
-    _check(load().bcg_profile(h, ms, cnt, 6))
-    return {KERNEL_NAMES[i]: (ms[i], cnt[i]) for i in range(6)}
+    nk = len(KERNEL_NAMES)
+    ms = (ctypes.c_double * nk)()
+    cnt = (ctypes.c_int64 * nk)()
+    _check(load().bcg_profile(h, ms, cnt, nk))
+    return {KERNEL_NAMES[i]: (ms[i], cnt[i]) for i in range(nk)}
 
 
 def bcg_destroy(h):

@@ -129,9 +129,11 @@ struct bcg_ctx {
   int tensor_cores = 1;                // FP64, p a multiple of 64: block updates on the tensor cores (tcgen05)
   int guards = 0;                      // 1: check every buffer's guard bytes after each solve
   // live per-kernel timing (profile = 1): CUDA events around every launch of an executed iteration
-  static constexpr int kKernels = 6;   // K1 op_gram, K4a solve_lambda, K2 update_xr, K4b solve_beta, K3 update_p, K0 residual
-  double prof_ms[kKernels] = {0, 0, 0, 0, 0, 0};
-  int64_t prof_count[kKernels] = {0, 0, 0, 0, 0, 0};
+  // K1 op_gram, K4a solve_lambda, K2 update_xr, K4b solve_beta, K3 update_p, K0 residual, and the tensor-core
+  // block products and block updates of wide blocks (kt_gram_img, kt_baxpy_img)
+  static constexpr int kKernels = 8;
+  double prof_ms[kKernels] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int64_t prof_count[kKernels] = {0, 0, 0, 0, 0, 0, 0, 0};
   std::vector<cudaEvent_t> ev;         // 2 * 5 * check_every events, reused per batch
   // workspace (owned)
   std::vector<void *> allocs;
@@ -446,6 +448,28 @@ bcg_status lp_gram(bcg_ctx *h, const T *X, const T *Y, double *part, int chunks,
 // cut once per use into images that the MMA kernels copy into shared memory whole (P twice: column images for the
 // Grams, row images for the updates, the latter serving both X += P lambda and P = Z + P beta). The new P is
 // written into Q's buffer; the caller swaps P and Q.
+bcg_status ensure_events(bcg_ctx *h, int count);
+
+// With option "profile": one tensor-core launch bracketed by CUDA events and read back at once (slot 6: block
+// products, 7: block updates).
+template <typename F>
+bcg_status tc_timed(bcg_ctx *h, int slot, F &&launch) {
+  if (!h->profile) {
+    CK(launch());
+    return BCG_OK;
+  }
+  CKS(ensure_events(h, 2));
+  CK(cudaEventRecord(h->ev[0], h->stream));
+  CK(launch());
+  CK(cudaEventRecord(h->ev[1], h->stream));
+  CK(cudaEventSynchronize(h->ev[1]));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, h->ev[0], h->ev[1]));
+  h->prof_ms[slot] += ms;
+  h->prof_count[slot] += 1;
+  return BCG_OK;
+}
+
 bcg_status launch_iteration_tcimg(bcg_ctx *h, const OpDesc &A, double *X, double *R, double *P, double *Q,
                                   const StreamGrids &g) {
   cudaStream_t s = h->stream;
@@ -462,34 +486,40 @@ bcg_status launch_iteration_tcimg(bcg_ctx *h, const OpDesc &A, double *X, double
   CK(launch_tc_cut_cols<double>(P, nullptr, n, k, ec1, G1, nsm, s));
   CK(launch_tc_col_exp<double>(Q, nullptr, n, k, ec2, nsm, s));
   CK(launch_tc_cut_cols<double>(Q, nullptr, n, k, ec2, G2, nsm, s));
-  CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partA, ch, ec1, ec2, h->st, s));
+  CKS(tc_timed(h, 6, [&] { return launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partA, ch, ec1, ec2, h->st, s); }));
   CK(launch_tc_col_exp<double>(R, nullptr, n, k, ec2, nsm, s));   // stream order: after the alpha kernel read ec2 and G2
   CK(launch_tc_cut_cols<double>(R, nullptr, n, k, ec2, G2, nsm, s));
-  CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partR, ch, ec1, ec2, h->st, s));
+  CKS(tc_timed(h, 6, [&] { return launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partR, ch, ec1, ec2, h->st, s); }));
   CK(launch_solve_lambda(h->partA, h->partR, ch, ch, k, p, gl, h->active, h->lam, h->rho_rec, h->st, h->gws, 0, s));
   // X += P lambda, R -= Q lambda
   CK(launch_tc_slice(h->lam, h->nblk, p, h->tc_cs, h->tc_cexp, s));
   CK(launch_tc_cut_rows(P, n, k, p, RP, erP, s));
   CK(launch_tc_cut_rows(Q, n, k, p, RQ, erQ, s));
-  CK(launch_tc_baxpy_img(X, X, RP, erP, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 0, s, nullptr, nsm));
-  CK(launch_tc_baxpy_img(R, R, RQ, erQ, h->tc_cs, h->tc_cexp, n, k, p, gl, -1.0, h->active, h->st, 0, s, nullptr,
-                         nsm));
+  CKS(tc_timed(h, 7, [&] {
+    return launch_tc_baxpy_img(X, X, RP, erP, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 0, s, nullptr, nsm);
+  }));
+  CKS(tc_timed(h, 7, [&] {
+    return launch_tc_baxpy_img(R, R, RQ, erQ, h->tc_cs, h->tc_cexp, n, k, p, gl, -1.0, h->active, h->st, 0, s, nullptr,
+                               nsm);
+  }));
   // rho = <<Z, R>>, Z = M^{-1} R formed in the cut
   CK(launch_tc_col_exp<double>(R, dinv, n, k, ec1, nsm, s));
   CK(launch_tc_cut_cols<double>(R, dinv, n, k, ec1, G1, nsm, s));
   if (dinv) {
     CK(launch_tc_col_exp<double>(R, nullptr, n, k, ec2, nsm, s));
     CK(launch_tc_cut_cols<double>(R, nullptr, n, k, ec2, G2, nsm, s));
-    CK(launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partRho, ch, ec1, ec2, h->st, s));
+    CKS(tc_timed(h, 6, [&] { return launch_tc_gram_img(G1, G2, n, k, p, gl, h->active, h->partRho, ch, ec1, ec2, h->st, s); }));
   } else {
-    CK(launch_tc_gram_img(G1, G1, n, k, p, gl, h->active, h->partRho, ch, ec1, ec1, h->st, s));
+    CKS(tc_timed(h, 6, [&] { return launch_tc_gram_img(G1, G1, n, k, p, gl, h->active, h->partRho, ch, ec1, ec1, h->st, s); }));
   }
   CK(launch_lp_colnorm<double>(R, n, k, h->partN, g.res, h->st, s, sh_role(sc.sh, k, SH_R)));
   CK(launch_solve_beta(h->partRho, h->partN, ch, g.res, k, p, gl, h->tol2_dev, h->r0n2, h->rn2, h->active,
                        h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s, sc));
   // P = Z + P beta into Q's buffer (P's row images are still those of this iteration's P)
   CK(launch_tc_slice(h->beta, h->nblk, p, h->tc_cs, h->tc_cexp, s));
-  CK(launch_tc_baxpy_img(Q, R, RP, erP, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 1, s, dinv, nsm));
+  CKS(tc_timed(h, 7, [&] {
+    return launch_tc_baxpy_img(Q, R, RP, erP, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 1, s, dinv, nsm);
+  }));
   return BCG_OK;
 }
 
