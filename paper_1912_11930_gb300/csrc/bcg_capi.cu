@@ -523,9 +523,9 @@ bcg_status launch_iteration_tcimg(bcg_ctx *h, const OpDesc &A, double *X, double
   return BCG_OK;
 }
 
-// One iteration with large blocks (p > 32): tiled FMA kernels for BOP and the block updates; the block products on
-// the tensor cores where the handle has digit images (the mixed form's FP32 process), else the tiled Dot2 kernel
-// (and FP64 with option "tensor_cores" 0). The direction update cannot run in place across
+// One iteration with large blocks (p > 32): the tiled FMA kernel for BOP; the block products and updates on the
+// tensor cores where the handle has digit images (the mixed form's FP32 process), else the tiled Dot2 products and
+// FMA updates (and FP64 with option "tensor_cores" 0). The direction update cannot run in place across
 // column tiles, so it writes into the Q buffer (free at that point) and the caller swaps P and Q.
 template <typename T>
 bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, const StreamGrids &g) {
@@ -556,8 +556,25 @@ bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T 
   }
   CK(launch_solve_lambda(h->partA, h->partR, ch, ch, h->k, h->p, h->global, h->active, h->lam, h->rho_rec, h->st,
                          h->gws, 0, s));
-  CKS(lp_update<T>(h, X, X, P, h->lam, 1.0, 0, nullptr));
-  CKS(lp_update<T>(h, R, R, Q, h->lam, -1.0, 0, nullptr));
+  // X += P lambda, R -= Q lambda (tensor cores: from the row images of P and Q; P's also serve P = Z + P beta)
+  unsigned char *RP = h->tc_img[2], *RQ = h->tc_img[3];
+  int *erP = h->tc_erow, *erQ = h->tc_erow + (size_t)((n + 127) / 128) * 128 * (k / p);
+  if (tc) {
+    CK(launch_tc_slice(h->lam, h->nblk, p, h->tc_cs, h->tc_cexp, s));
+    CK(launch_tc_cut_rows<T>(P, n, k, p, RP, erP, s));
+    CK(launch_tc_cut_rows<T>(Q, n, k, p, RQ, erQ, s));
+    CKS(tc_timed(h, 7, [&] {
+      return launch_tc_baxpy_img<T>(X, X, RP, erP, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 0, s,
+                                    nullptr, nsm);
+    }));
+    CKS(tc_timed(h, 7, [&] {
+      return launch_tc_baxpy_img<T>(R, R, RQ, erQ, h->tc_cs, h->tc_cexp, n, k, p, gl, -1.0, h->active, h->st, 0, s,
+                                    nullptr, nsm);
+    }));
+  } else {
+    CKS(lp_update<T>(h, X, X, P, h->lam, 1.0, 0, nullptr));
+    CKS(lp_update<T>(h, R, R, Q, h->lam, -1.0, 0, nullptr));
+  }
   // rho = <<Z, R>> with Z = M^{-1} R formed on the fly
   if (tc) {
     const T *dv = dinv_of<T>(h);
@@ -577,7 +594,15 @@ bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T 
   CK(launch_solve_beta(h->partRho, h->partN, ch, g.res, h->k, h->p, h->global, h->tol2_dev, h->r0n2, h->rn2,
                        h->active,
                        h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s, sc));
-  CKS(lp_update<T>(h, Q, R, P, h->beta, 1.0, 1, dinv_of<T>(h)));
+  if (tc) {
+    CK(launch_tc_slice(h->beta, h->nblk, p, h->tc_cs, h->tc_cexp, s));
+    CKS(tc_timed(h, 7, [&] {
+      return launch_tc_baxpy_img<T>(Q, R, RP, erP, h->tc_cs, h->tc_cexp, n, k, p, gl, 1.0, h->active, h->st, 1, s,
+                                    dinv_of<T>(h), nsm);
+    }));
+  } else {
+    CKS(lp_update<T>(h, Q, R, P, h->beta, 1.0, 1, dinv_of<T>(h)));
+  }
   return BCG_OK;
 }
 

@@ -100,19 +100,33 @@ __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
 }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t phase) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(done)
+      : "r"(mbar), "r"(phase)
+      : "memory");
+  return done != 0;
+}
 // true once the phase with parity `phase` has completed; gives up after kTcWaitLimit polls
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
+  for (long long i = 0; i < kTcWaitLimit; ++i)
+    if (mbar_try(mbar, phase)) return true;
+  return false;
+}
+// the same, also giving up once *flag is set (another role of the CTA gave up)
+__device__ __forceinline__ bool mbar_wait_flag(uint32_t mbar, uint32_t phase, const volatile int *flag) {
   for (long long i = 0; i < kTcWaitLimit; ++i) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(phase)
-        : "memory");
-    if (done) return true;
+    if (mbar_try(mbar, phase)) return true;
+    if ((i & 255) == 255 && *flag != 0) return false;
   }
   return false;
+}
+// one of the barrier's expected arrivals, without a transaction count
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
 }
 
 // Bulk copies (global -> this CTA's shared memory) tracked by an mbarrier's transaction count: the issuing thread
@@ -342,9 +356,33 @@ __host__ __device__ constexpr size_t tc_col_image_bytes(int64_t n, int k) {
   return (size_t)((n + kTcK - 1) / kTcK) * (k / kTcCols) * kTcImgCol;
 }
 
+// 8 consecutive values (16-byte aligned) as T
+__device__ __forceinline__ void tc_load8(const double *src, double (&v)[8]) {
+  const double2 *q = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const double2 t = __ldg(q + e);
+    v[2 * e] = t.x;
+    v[2 * e + 1] = t.y;
+  }
+}
+__device__ __forceinline__ void tc_load8(const float *src, float (&v)[8]) {
+  const float4 *q = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+  for (int e = 0; e < 2; ++e) {
+    const float4 t = __ldg(q + e);
+    v[4 * e] = t.x;
+    v[4 * e + 1] = t.y;
+    v[4 * e + 2] = t.z;
+    v[4 * e + 3] = t.w;
+  }
+}
+
 // Row images of Y for every block j: CTA (rt, j) computes the 128 row exponents of its rows over the block's p
-// columns (integer maxima of the exponent fields) and cuts the p / 32 chunks.
-__global__ void __launch_bounds__(kTcThreads) kt_cut_rows(const double *__restrict__ Y, int64_t n, int k, int p,
+// columns (integer maxima of the exponent fields) and cuts the p / 16 chunks. T = double, or float (the mixed
+// form's FP32 process; its values are exact in the 48-bit window where a row's exponents span at most 24).
+template <typename T>
+__global__ void __launch_bounds__(kTcThreads) kt_cut_rows(const T *__restrict__ Y, int64_t n, int k, int p,
                                                           unsigned char *__restrict__ img, int *__restrict__ erow) {
   __shared__ int sX[kTcThreads];
   __shared__ int sE[kTcRows];
@@ -358,9 +396,9 @@ __global__ void __launch_bounds__(kTcThreads) kt_cut_rows(const double *__restri
     const int64_t r = r0 + rl;
     int em = 0;
     if (r < n) {
-      const int2 *src = reinterpret_cast<const int2 *>(Y + r * k + (int64_t)j * p + half * (p / 2));
+      const T *src = Y + r * k + (int64_t)j * p + half * (p / 2);
 #pragma unroll 8
-      for (int q = 0; q < p / 2; ++q) em = max(em, (__ldg(src + q).y >> 20) & 0x7FF);
+      for (int q = 0; q < p / 2; ++q) em = max(em, tc_exp_field(__ldg(src + q)));
     }
     sX[tid] = em;
     __syncthreads();
@@ -380,18 +418,12 @@ __global__ void __launch_bounds__(kTcThreads) kt_cut_rows(const double *__restri
       const int it = tid + u * kTcThreads, rl = it & (kTcRows - 1), kg = it >> 7;
       if (it >= kItems) break;
       const int64_t r = r0 + rl;
-      double v[8];
+      T v[8];
       if (r < n) {
-        const double2 *src = reinterpret_cast<const double2 *>(Y + r * k + (int64_t)j * p + kc * kTcK + kg * 8);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          const double2 t2 = __ldg(src + q);
-          v[2 * q] = t2.x;
-          v[2 * q + 1] = t2.y;
-        }
+        tc_load8(Y + r * k + (int64_t)j * p + kc * kTcK + kg * 8, v);
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) v[e] = 0.0;
+        for (int e = 0; e < 8; ++e) v[e] = T(0);
       }
       uint32_t w[kTcSlices][4];
       tc_pack8(v, sE[rl], w);
@@ -463,172 +495,204 @@ __device__ __forceinline__ TcBars tc_bars_setup(unsigned char *misc) {
 }
 __device__ __forceinline__ uint32_t tc_par(int64_t g) { return (uint32_t)((g / kTcStages) & 1); }
 
+// Roles in kt_baxpy_img: warps 0-7 read the accumulators out (warp w: TMEM lanes 32 (w mod 4) .. +31, the tile's
+// rows, and the tile's columns 32 (w / 4) .. +31), lane 0 of warp 8 issues the MMAs, lane 0 of warp 9 issues the
+// bulk copies. TMEM holds the 8 accumulators of one tile: the readout warps fold them into float pairs in registers
+// and release TMEM (the "free" mbarrier, one arrival per readout warp) before they turn the pairs into doubles, add
+// BASE and store, so that this part of the readout overlaps the next tile's MMAs.
+constexpr int kTcOutWarps = 8;
+constexpr int kTcBaxThreads = (kTcOutWarps + 2) * 32;
+constexpr int kTcBaxMma = kTcOutWarps * 32;
+constexpr int kTcBaxProducer = kTcBaxMma + 32;
+
+// 16 consecutive values (16-byte aligned) of OUT / BASE, widened to double, and back
+__device__ __forceinline__ void tc_load16(const double *src, double (&v)[16]) {
+  const double2 *q = reinterpret_cast<const double2 *>(src);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) {
+    const double2 t = q[e];
+    v[2 * e] = t.x;
+    v[2 * e + 1] = t.y;
+  }
+}
+__device__ __forceinline__ void tc_load16(const float *src, double (&v)[16]) {
+  const float4 *q = reinterpret_cast<const float4 *>(src);
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const float4 t = q[e];
+    v[4 * e] = t.x;
+    v[4 * e + 1] = t.y;
+    v[4 * e + 2] = t.z;
+    v[4 * e + 3] = t.w;
+  }
+}
+__device__ __forceinline__ void tc_store16(double *dst, const double (&v)[16]) {
+  double2 *q = reinterpret_cast<double2 *>(dst);
+#pragma unroll
+  for (int e = 0; e < 8; ++e) q[e] = make_double2(v[2 * e], v[2 * e + 1]);
+}
+__device__ __forceinline__ void tc_store16(float *dst, const double (&v)[16]) {
+  float4 *q = reinterpret_cast<float4 *>(dst);
+#pragma unroll
+  for (int e = 0; e < 4; ++e)
+    q[e] = make_float4((float)v[4 * e], (float)v[4 * e + 1], (float)v[4 * e + 2], (float)v[4 * e + 3]);
+}
+
 // OUT_j = BASE_j (times bscale[r] per row, if given; BASE NULL: zero) + sign * Y_j C_j over every block j (global: C_0
-// for all), from Y's row images (kt_cut_rows) and C's images (kt_slice_cmat). OUT may equal BASE. Frozen blocks
+// for all), from Y's row images (kt_cut_rows) and C's images (kt_slice_cmat). OUT may equal BASE. T = double, or
+// float (the mixed form's FP32 process: the sum is formed in FP64 and rounded once). Frozen blocks
 // (active[j] = 0) get OUT = BASE (scaled). bump: CTA 0 advances the iteration counter (the P update's role).
-// Persistent over 128 x 64 output tiles; the producer also prefetches the first chunks of the CTA's next tile while
-// the current tile is read out.
-__global__ void __launch_bounds__(kTcThreads, 1) kt_baxpy_img(double *OUT, const double *BASE,
-                                                              const unsigned char *__restrict__ imgY,
-                                                              const int *__restrict__ erow,
-                                                              const uint16_t *__restrict__ Cs,
-                                                              const int *__restrict__ Cexp, int64_t n, int k, int p,
-                                                              int global, double sign, const int *__restrict__ active,
-                                                              DevStatus *__restrict__ st, int bump,
-                                                              const double *__restrict__ bscale) {
+// Persistent over 128 x 64 output tiles (tile t: row tile t / (k / 64), column tile t mod (k / 64)); every role
+// walks the CTA's tiles in the same order, the issuing roles skipping frozen blocks.
+template <typename T>
+__global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T *BASE,
+                                                                 const unsigned char *__restrict__ imgY,
+                                                                 const int *__restrict__ erow,
+                                                                 const uint16_t *__restrict__ Cs,
+                                                                 const int *__restrict__ Cexp, int64_t n, int k,
+                                                                 int p, int global, double sign,
+                                                                 const int *__restrict__ active,
+                                                                 DevStatus *__restrict__ st, int bump,
+                                                                 const T *__restrict__ bscale) {
   if (st->flags != 0) return;
   if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->cur += 1;
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];
   unsigned char *ops, *misc;
   const uint32_t tbase = tc_setup(tc_smem_raw, ops, misc);
   const TcBars bars = tc_bars_setup(misc);
-  int *sE = reinterpret_cast<int *>(misc + 512);   // 128 row exponents (kTcBadRow: NaN row)
-  int *sF = sE + kTcRows;                          // 64 column exponents of C
-  int *sFlag = sF + kTcCols;                       // [0]: a wait timed out
+  const uint32_t tfree = smem_u32(reinterpret_cast<uint64_t *>(misc + 256) + 2 * kTcStages + 1);
+  volatile int *sFlag = reinterpret_cast<volatile int *>(misc + 512);   // [0]: a wait gave up
+  long long *sCount = reinterpret_cast<long long *>(misc + 576);       // chunks copied [0] and consumed [1]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nt = p / kTcCols, nc = p / kTcK;
   const int ntn = k / kTcCols;
   const int64_t nrt = (n + kTcRows - 1) / kTcRows;
   const int64_t nrows = nrt * kTcRows;
   const int64_t ntiles = nrt * ntn;
-  if (tid == 0) sFlag[0] = 0;
+  if (tid == 0) {
+    mbar_init(tfree, kTcOutWarps);
+    fence_mbar_init();
+    sFlag[0] = 0;
+    sCount[0] = sCount[1] = 0;
+  }
   __syncthreads();
   auto tile_active = [&](int64_t t) { return block_active(active, global, (int)(t % ntn) * kTcCols / p); };
-  // producer state: chunks produced over the launch, and which tile / chunk comes next
-  int64_t gprod = 0, ptile = blockIdx.x;
-  int pc = 0;
   auto next_active = [&](int64_t t) {
     while (t < ntiles && !tile_active(t)) t += gridDim.x;
     return t;
   };
-  // produce chunks of tile ptile from pc up to (not including) chunk `upto` of tile `limit_tile` (and its
-  // predecessors); returns false on a timeout
-  auto produce_until = [&](int64_t limit_tile, int upto) -> bool {
-    while (ptile < ntiles && (ptile < limit_tile || (ptile == limit_tile && pc < upto))) {
-      const int s = (int)(gprod % kTcStages);
-      if (gprod >= kTcStages && !mbar_wait(bars.empty[s], tc_par(gprod - kTcStages))) return false;
-      const int tn = (int)(ptile % ntn);
-      const int64_t rt = ptile / ntn;
-      const int c0 = tn * kTcCols, j = c0 / p, b0 = c0 - j * p, jc = global ? 0 : j;
+  if (tid == kTcBaxProducer) {   // chunk g of the launch into stage g mod kTcStages, once its last MMAs are done
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t tile = next_active(blockIdx.x); tile < ntiles && ok; tile = next_active(tile + gridDim.x)) {
+      const int c0 = (int)(tile % ntn) * kTcCols, j = c0 / p, b0 = c0 - j * p, jc = global ? 0 : j;
       const unsigned char *cimg =
-          reinterpret_cast<const unsigned char *>(Cs) + ((size_t)(jc * nt + b0 / kTcCols) * nc + pc) * kTcStageBytesB;
-      const unsigned char *yimg = imgY + ((size_t)rt * (k / kTcK) + (size_t)j * nc + pc) * kTcImgRow;
-      mbar_arrive_expect_tx(bars.full[s], kTcImgRow + kTcStageBytesB);
-      bulk_g2s(smem_u32(tc_stage_a(ops, s)), yimg, kTcImgRow, bars.full[s]);
-      bulk_g2s(smem_u32(tc_stage_b(ops, s)), cimg, kTcStageBytesB, bars.full[s]);
-      ++gprod;
-      if (++pc == nc) {
-        pc = 0;
-        ptile = next_active(ptile + gridDim.x);
+          reinterpret_cast<const unsigned char *>(Cs) + (size_t)(jc * nt + b0 / kTcCols) * nc * kTcStageBytesB;
+      const unsigned char *yimg = imgY + ((size_t)(tile / ntn) * (k / kTcK) + (size_t)j * nc) * kTcImgRow;
+      for (int c = 0; c < nc; ++c, ++g) {
+        const int s = (int)(g % kTcStages);
+        if (g >= kTcStages && !mbar_wait_flag(bars.empty[s], tc_par(g - kTcStages), sFlag)) {
+          ok = false;
+          break;
+        }
+        mbar_arrive_expect_tx(bars.full[s], kTcImgRow + kTcStageBytesB);
+        bulk_g2s(smem_u32(tc_stage_a(ops, s)), yimg + (size_t)c * kTcImgRow, kTcImgRow, bars.full[s]);
+        bulk_g2s(smem_u32(tc_stage_b(ops, s)), cimg + (size_t)c * kTcStageBytesB, kTcStageBytesB, bars.full[s]);
       }
     }
-    return true;
-  };
-  int64_t gcons = 0, ndone = 0;   // MMA thread: chunks consumed, tiles completed
-  if (tid == kTcProducer) {
-    ptile = next_active(ptile);
-    if (!produce_until(ptile, min(nc, kTcStages))) sFlag[0] = 1;
-  }
-  bool timeout = false;
-  for (int64_t tile = blockIdx.x; tile < ntiles && !timeout; tile += gridDim.x) {
-    const int tn = (int)(tile % ntn);
-    const int64_t r0 = (tile / ntn) * kTcRows;
-    const int c0 = tn * kTcCols;
-    const int j = c0 / p, b0 = c0 - j * p;
-    const int jc = global ? 0 : j;
-    if (!block_active(active, global, j)) {
-      for (int it = tid; it < kTcRows * (kTcCols / 8); it += kTcThreads) {
-        const int rl = it & (kTcRows - 1), cg = it >> 7;
-        const int64_t r = r0 + rl;
-        if (r >= n) continue;
-        const double s = bscale ? bscale[r] : 1.0;
-        for (int e = 0; e < 8; ++e) OUT[r * k + c0 + cg * 8 + e] = BASE ? BASE[r * k + c0 + cg * 8 + e] * s : 0.0;
+    if (!ok) sFlag[0] = 1;
+    sCount[0] = g;
+  } else if (tid == kTcBaxMma) {   // a tile's MMAs once the previous tile's accumulators are folded
+    int64_t g = 0, i = 0;
+    bool ok = true;
+    for (int64_t tile = next_active(blockIdx.x); tile < ntiles && ok; tile = next_active(tile + gridDim.x), ++i) {
+      if (i > 0 && !mbar_wait_flag(tfree, (uint32_t)((i - 1) & 1), sFlag)) {
+        ok = false;
+        break;
       }
-      continue;
-    }
-    if (tid < kTcRows) sE[tid] = erow[(int64_t)j * nrows + r0 + tid];
-    if (tid < kTcCols) sF[tid] = Cexp[jc * p + b0 + tid];
-    // this thread's 32 outputs: row rl = 32 (w mod 4) + lane, columns 32 (w / 4) .. +31 of the tile; their BASE
-    // values are loaded now, while the MMAs run (16-byte loads; consumed after the barrier)
-    const int q = warp & 3, h = warp >> 2;
-    const int rl = q * 32 + lane;
-    const int64_t r = r0 + rl;
-    double2 bv[16];
-    if (r < n && BASE) {
-      const double2 *bp = reinterpret_cast<const double2 *>(BASE + r * k + c0 + h * 32);
-#pragma unroll
-      for (int e = 0; e < 16; ++e) bv[e] = bp[e];
-    } else {
-#pragma unroll
-      for (int e = 0; e < 16; ++e) bv[e] = make_double2(0.0, 0.0);
-    }
-    const double bs = (r < n && bscale) ? bscale[r] : 1.0;
-    if (tid == kTcProducer && !sFlag[0]) {   // the rest of this tile, then the next tile's first stages
-      const int64_t nxt = next_active(tile + gridDim.x);
-      const bool ok = nxt < ntiles ? produce_until(nxt, min(nc, kTcStages)) : produce_until(tile, nc);
-      if (!ok) sFlag[0] = 1;
-    }
-    if (tid == 0) {
-      bool ok = true;
-      for (int c = 0; c < nc && ok; ++c, ++gcons) {
-        const int s = (int)(gcons % kTcStages);
-        ok = mbar_wait(bars.full[s], tc_par(gcons)) && !*(volatile int *)sFlag;
-        if (!ok) break;
+      tc_fence_after();
+      for (int c = 0; c < nc; ++c, ++g) {
+        const int s = (int)(g % kTcStages);
+        if (!mbar_wait_flag(bars.full[s], tc_par(g), sFlag)) {
+          ok = false;
+          break;
+        }
         tc_fence_after();
         tc_issue_chunk(tbase, smem_u32(tc_stage_a(ops, s)), smem_u32(tc_stage_b(ops, s)), c == 0);
         tc_commit(bars.empty[s]);
       }
-      if (ok) {
-        tc_commit(bars.done);
-        ok = mbar_wait(bars.done, (uint32_t)(ndone & 1));
-        ++ndone;
-      }
-      if (!ok) sFlag[0] = 1;
+      if (ok) tc_commit(bars.done);
     }
-    __syncthreads();
-    if (sFlag[0]) {
-      timeout = true;
-      break;
-    }
-    tc_fence_after();
-    {   // read back: warp w holds rows 32 (w mod 4) .. +31, columns 32 (w / 4) .. +31 of the tile
-      const int E = sE[rl];
-      const bool bad = E == kTcBadRow;
-#pragma unroll
-      for (int cg = 0; cg < 4; ++cg) {
-        float hi[8], lo[8];
-        const int cb = h * 32 + cg * 8;
-        tc_read8(tbase, q, cb, hi, lo);
+    if (!ok) sFlag[0] = 1;
+    sCount[1] = g;
+  } else if (warp < kTcOutWarps) {
+    const int q = warp & 3, cb0 = (warp >> 2) * 32;   // TMEM lane quadrant; first of the thread's 32 columns
+    const int rl = q * 32 + lane;
+    int64_t i = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+      const int c0 = (int)(tile % ntn) * kTcCols, j = c0 / p, b0 = c0 - j * p, jc = global ? 0 : j;
+      const int64_t r = (tile / ntn) * kTcRows + rl;
+      if (!block_active(active, global, j)) {   // frozen block: OUT = BASE (scaled)
         if (r < n) {
-          double2 *o = reinterpret_cast<double2 *>(OUT + r * k + c0 + cb);
+          const T s = bscale ? bscale[r] : T(1);
+          for (int e = 0; e < 32; ++e) OUT[r * k + c0 + cb0 + e] = BASE ? BASE[r * k + c0 + cb0 + e] * s : T(0);
+        }
+        continue;
+      }
+      // lane 0 waits for the tile's MMAs; the warp follows it (the TMEM loads are warp-collective)
+      bool ok = lane == 0 ? mbar_wait_flag(bars.done, (uint32_t)(i & 1), sFlag) : true;
+      ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+      if (!ok) {
+        if (lane == 0) sFlag[0] = 1;
+        break;
+      }
+      ++i;
+      tc_fence_after();
+      float hi[4][8], lo[4][8];
 #pragma unroll
-          for (int e2 = 0; e2 < 4; ++e2) {
-            double res[2];
+      for (int cg = 0; cg < 4; ++cg) tc_read8(tbase, q, cb0 + cg * 8, hi[cg], lo[cg]);
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(tfree);
+      if (r >= n) continue;
+      // (s + c) 2^t as one double (integer operations), one FP64 addition; 16 columns at a time, their BASE
+      // values loaded before any store (OUT may be BASE)
+      const int E = erow[(int64_t)j * nrows + r];
+      const bool bad = E == kTcBadRow;
+      const double bs = bscale ? (double)bscale[r] : 1.0;
+      const int4 *F4 = reinterpret_cast<const int4 *>(Cexp + jc * p + b0 + cb0);
 #pragma unroll
-            for (int u = 0; u < 2; ++u) {
-              const int e = 2 * e2 + u;
-              const int t = E + sF[cb + e] - 10;
-              const double b = u ? bv[cg * 4 + e2].y : bv[cg * 4 + e2].x;
-              const double base = bscale ? b * bs : b;
-              // (s + c) 2^t as one double (integer operations), one FP64 addition
-              const double v = base + sign * df_pair_to_double(hi[e], lo[e], t);
-              res[u] = bad ? __longlong_as_double(0x7FF8000000000000ll) : v;
-            }
-            o[e2] = make_double2(res[0], res[1]);
+      for (int half = 0; half < 2; ++half) {
+        double v[16];
+        if (BASE) {
+          tc_load16(BASE + r * k + c0 + cb0 + half * 16, v);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] = 0.0;
+        }
+#pragma unroll
+        for (int cg2 = 0; cg2 < 2; ++cg2) {
+          const int cg = half * 2 + cg2;
+          const int4 fa = __ldg(F4 + 2 * cg), fb = __ldg(F4 + 2 * cg + 1);
+          const int F[8] = {fa.x, fa.y, fa.z, fa.w, fb.x, fb.y, fb.z, fb.w};
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const double base = bscale ? v[cg2 * 8 + e] * bs : v[cg2 * 8 + e];
+            const double x = base + sign * df_pair_to_double(hi[cg][e], lo[cg][e], E + F[e] - 10);
+            v[cg2 * 8 + e] = bad ? __longlong_as_double(0x7FF8000000000000ll) : x;
           }
         }
+        tc_store16(OUT + r * k + c0 + cb0 + half * 16, v);
       }
     }
-    tc_fence_before();
-    __syncthreads();
   }
-  if (timeout) {   // both roles wait (bounded) for what they started
-    __shared__ long long sCons;
-    if (tid == 0) sCons = gcons;
-    __syncthreads();
-    if (tid == kTcProducer)
-      for (int64_t g = sCons; g < gprod; ++g) (void)mbar_wait(bars.full[g % kTcStages], tc_par(g));
-    if (tid == 0 && gcons > 0) (void)mbar_wait(bars.empty[(gcons - 1) % kTcStages], tc_par(gcons - 1));
+  __syncthreads();
+  const bool timeout = sFlag[0] != 0;
+  if (timeout) {   // both issuing roles wait (bounded) for what they started
+    if (tid == kTcBaxProducer)
+      for (int64_t g = sCount[1]; g < sCount[0]; ++g) (void)mbar_wait(bars.full[g % kTcStages], tc_par(g));
+    if (tid == kTcBaxMma && sCount[1] > 0)
+      (void)mbar_wait(bars.empty[(sCount[1] - 1) % kTcStages], tc_par(sCount[1] - 1));
   }
   tc_teardown(tbase, timeout, st);
 }

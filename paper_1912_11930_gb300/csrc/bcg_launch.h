@@ -89,7 +89,8 @@ template <typename T>
 cudaError_t launch_lp_colnorm(const T *R, int64_t n, int k, double *partN, int grid, const DevStatus *st,
                               cudaStream_t s, const int *shR);
 
-// Tensor-core large-block products and updates (bcg_kernels_tc.cuh; FP64 data, p a multiple of 64 up to 256).
+// Tensor-core large-block products and updates (bcg_kernels_tc.cuh; FP64 data, or the mixed form's FP32 data; p a
+// multiple of 64 up to 256).
 // Every operand is first cut into bf16 digit images that are byte for byte the kernels' shared-memory stages:
 // the p x p matrices with launch_tc_slice (C row-major per distinct block, Cs of tc_workspace_bytes(nblkC, p)
 // bytes, Cexp nblkC * p ints); the Gram's operands into column images (an exponent per column:
@@ -108,15 +109,21 @@ cudaError_t launch_tc_col_exp(const T *X, const T *xscale, int64_t n, int k, int
 template <typename T>
 cudaError_t launch_tc_cut_cols(const T *X, const T *xscale, int64_t n, int k, const int *ecol, unsigned char *img,
                                int nsm, cudaStream_t s);
-cudaError_t launch_tc_cut_rows(const double *Y, int64_t n, int k, int p, unsigned char *img, int *erow,
-                               cudaStream_t s);
+template <typename T>
+cudaError_t launch_tc_cut_rows(const T *Y, int64_t n, int k, int p, unsigned char *img, int *erow, cudaStream_t s);
 cudaError_t launch_tc_gram_img(const unsigned char *imgX, const unsigned char *imgY, int64_t n, int k, int p,
                                int global, const int *active, double *part, int chunks, const int *ecx,
                                const int *ecy, DevStatus *st, cudaStream_t s);
-cudaError_t launch_tc_baxpy_img(double *OUT, const double *BASE, const unsigned char *imgY, const int *erow,
-                                const uint16_t *Cs, const int *Cexp, int64_t n, int k, int p, int global,
-                                double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
-                                const double *bscale, int nsm);
+// T is deduced from OUT alone (BASE and bscale may be NULL)
+template <typename T>
+struct TcId {
+  using type = T;
+};
+template <typename T>
+cudaError_t launch_tc_baxpy_img(T *OUT, const typename TcId<T>::type *BASE, const unsigned char *imgY,
+                                const int *erow, const uint16_t *Cs, const int *Cexp, int64_t n, int k, int p,
+                                int global, double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
+                                const typename TcId<T>::type *bscale, int nsm);
 // doubles of per-block workspace of the p x p solves; kept in global memory (gws) when too big for shared
 size_t small_ws_doubles(int p);
 bool small_needs_gws(int p);

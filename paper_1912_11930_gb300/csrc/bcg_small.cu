@@ -365,24 +365,92 @@ __global__ void __launch_bounds__(kSmallNT) k_solve_beta(const double *__restric
 }
 
 // Triangular solves of the large-block BSOLVEs (chol = 2: the backward solve with L^T alone), spread over the
-// right-hand-side columns: CTA (jb, g) solves
-// columns [8g, 8g + 8) of block jb. The factors come from the blocked factorizations (k_chol_* / k_lu_*) in the
-// block's global workspace ws = gws + jb * small_ws_doubles(p): M = ws (p x p row-major), B = ws + p*p
-// (right-hand sides, row-major), pivots (LU) as ints at ws + 2*p*p.
+// right-hand-side columns: CTA (jb, g) solves columns [2g, 2g + 2) of block jb, one column per warp. The factors
+// come from the blocked factorizations (k_chol_* / k_lu_*) in the block's global workspace
+// ws = gws + jb * small_ws_doubles(p): M = ws (p x p row-major), B = ws + p*p (right-hand sides, row-major),
+// pivots (LU) as ints at ws + 2*p*p.
 //   chol = 1: M holds L (lower) of alpha = L L^T; out = L^{-T} L^{-1} B  (lambda)
 //   chol = 0: M holds P rho_rec = L U (unit L below the diagonal, U on and above it) with the row
 //             interchanges `pivots`; out = U^{-1} L^{-1} P B  (beta)
-// Each substitution is column oriented (B[i] -= M[i][a] B[a] after B[a] is final) and walks the factor in
-// panels of 32 columns (or rows) staged in shared memory with coalesced loads.
-constexpr int kTrsmCols = 8;
+// Each substitution is column oriented (B[i] -= M[i][a] B[a] once B[a] is final). A warp keeps its column in
+// registers (lane l: rows l, l + 32, ..., p <= 256), so a step is a shuffle of the final B[a] and one FMA per row
+// the lane holds, with no block barrier. The factor is staged in shared memory 32 columns (or rows) at a time,
+// double-buffered: the asynchronous copies of the next panel run while the warps work on this one. A diagonal
+// entry d enters as a product with 1 / d (as LAPACK's unblocked LU scales by a reciprocal), by division only
+// where 1 / d would overflow.
+constexpr int kTrsmCols = 2;
 constexpr int kTrsmPanel = 32;
+constexpr int kTrsmLd = kTrsmPanel + 1;
+constexpr int kTrsmSlots = 8;   // rows per lane: p <= 256
 __host__ __device__ inline size_t trsm_smem(int p) {
-  return ((size_t)p * kTrsmPanel + (size_t)p * kTrsmCols) * sizeof(double);
+  return 2 * (size_t)p * kTrsmLd * sizeof(double) + 2 * (size_t)p * sizeof(int);
 }
 
-__global__ void __launch_bounds__(256) k_trsm_cols(int p, int chol, const double *__restrict__ gws,
-                                                   const int *__restrict__ active, double *__restrict__ out,
-                                                   DevStatus *st) {
+__device__ __forceinline__ void cp_async8(double *dst, const double *src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Copies of panel `s0` into pan: forward, rows a0 .. p-1 of columns a0 .. a0+31 (pan[r ld + j] = M[a0 + r][a0 + j]);
+// backward, rows 0 .. a0+31 of the upper factor's columns a0 .. a0+31 (pan[i ld + j] = U[i][a0 + j], with
+// U = L^T for chol: M[a0 + j][i]).
+__device__ __forceinline__ void trsm_issue(double *pan, const double *M, int p, int s0, bool fwd, bool lt) {
+  const int a0 = s0 * kTrsmPanel, NT = blockDim.x;
+  if (fwd) {
+    const int n = (p - a0) * kTrsmPanel;
+    for (int e = threadIdx.x; e < n; e += NT)
+      cp_async8(pan + (e >> 5) * kTrsmLd + (e & 31), M + (int64_t)(a0 + (e >> 5)) * p + a0 + (e & 31));
+  } else if (lt) {
+    const int a1 = a0 + kTrsmPanel;
+    for (int e = threadIdx.x; e < kTrsmPanel * a1; e += NT) {
+      const int j = e / a1, i = e - j * a1;
+      cp_async8(pan + i * kTrsmLd + j, M + (int64_t)(a0 + j) * p + i);
+    }
+  } else {
+    const int n = (a0 + kTrsmPanel) * kTrsmPanel;
+    for (int e = threadIdx.x; e < n; e += NT)
+      cp_async8(pan + (e >> 5) * kTrsmLd + (e & 31), M + (int64_t)(e >> 5) * p + a0 + (e & 31));
+  }
+}
+
+// The 32 steps of panel S0 on this warp's column b (forward: rows a0 + jl final in order jl = 0..31, rows below
+// updated; backward: jl = 31..0, rows above updated). unit: the forward factor has a unit diagonal (LU).
+template <int S0>
+__device__ __forceinline__ void trsm_steps(double (&b)[kTrsmSlots], const double *pan, int ns, bool fwd, bool unit,
+                                           int lane) {
+  constexpr unsigned kAll = 0xffffffffu;
+  // this lane's diagonal entry of the panel (row a0 + lane, column a0 + lane)
+  const double d = fwd ? pan[lane * kTrsmLd + lane] : pan[(S0 * kTrsmPanel + lane) * kTrsmLd + lane];
+  const bool scale = !(fwd && unit);
+  const double rd = 1.0 / d;
+  const bool rec = fabs(d) >= DBL_MIN;
+  if (fwd) {
+    for (int jl = 0; jl < kTrsmPanel; ++jl) {
+      const double own = scale ? (rec ? b[S0] * rd : b[S0] / d) : b[S0];
+      const double x = __shfl_sync(kAll, own, jl);
+      if (lane == jl) b[S0] = x;
+      else if (lane > jl) b[S0] = fma(-pan[lane * kTrsmLd + jl], x, b[S0]);
+#pragma unroll
+      for (int s = S0 + 1; s < kTrsmSlots; ++s)
+        if (s < ns) b[s] = fma(-pan[((s - S0) * kTrsmPanel + lane) * kTrsmLd + jl], x, b[s]);
+    }
+  } else {
+    for (int jl = kTrsmPanel - 1; jl >= 0; --jl) {
+      const double own = rec ? b[S0] * rd : b[S0] / d;
+      const double x = __shfl_sync(kAll, own, jl);
+      if (lane == jl) b[S0] = x;
+      else if (lane < jl) b[S0] = fma(-pan[(S0 * kTrsmPanel + lane) * kTrsmLd + jl], x, b[S0]);
+#pragma unroll
+      for (int s = 0; s < S0; ++s) b[s] = fma(-pan[(s * kTrsmPanel + lane) * kTrsmLd + jl], x, b[s]);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kTrsmCols * 32) k_trsm_cols(int p, int chol, const double *__restrict__ gws,
+                                                              const int *__restrict__ active,
+                                                              double *__restrict__ out, DevStatus *st) {
   if (st->flags != 0) return;
   const int jb = blockIdx.x;
   if (!active[jb]) return;   // frozen block: its lambda / beta were zeroed by the factorization kernel
@@ -390,84 +458,69 @@ __global__ void __launch_bounds__(256) k_trsm_cols(int p, int chol, const double
   const double *M = gws + (int64_t)jb * small_ws_doubles_dev(p);
   const double *Bg = M + pp;
   const int *pivots = reinterpret_cast<const int *>(M + 2 * pp);
-  const int c0 = blockIdx.y * kTrsmCols;
+  const int lane = threadIdx.x & 31;
+  const int c = blockIdx.y * kTrsmCols + (threadIdx.x >> 5);   // this warp's column
+  const int ns = p / kTrsmPanel;
   extern __shared__ __align__(16) double sm_dyn[];
-  double *pan = sm_dyn;                          // panel: up to p x 32
-  double *bs = pan + (size_t)p * kTrsmPanel;     // bs[i * 8 + cc] = B[i][c0 + cc]
-  const int NT = blockDim.x;
-  for (int e = threadIdx.x; e < p * kTrsmCols; e += NT) {
-    const int i = e / kTrsmCols, cc = e % kTrsmCols;
-    bs[e] = Bg[(int64_t)i * p + c0 + cc];
-  }
-  __syncthreads();
-  if (!chol) {   // row interchanges in factorization order
-    if (threadIdx.x < kTrsmCols)
+  double *pan0 = sm_dyn, *pan1 = sm_dyn + (size_t)p * kTrsmLd;
+  int *perm = reinterpret_cast<int *>(pan1 + (size_t)p * kTrsmLd);
+  // panel sequence: forward panels 0 .. ns-1 (not for chol = 2), then backward panels ns-1 .. 0
+  const int nfwd = chol == 2 ? 0 : ns, npan = nfwd + ns;
+  auto panel_of = [&](int t) { return t < nfwd ? t : nfwd + ns - 1 - t; };
+  trsm_issue(pan0, M, p, panel_of(0), nfwd > 0, chol != 0);
+  cp_async_commit();
+  // LU: row i of P B is row perm[i] of B (the interchanges applied in factorization order)
+  if (!chol) {
+    int *pv = perm + p;
+    for (int i = threadIdx.x; i < p; i += blockDim.x) {
+      perm[i] = i;
+      pv[i] = pivots[i];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
       for (int a = 0; a < p; ++a) {
-        const int r = pivots[a];
+        const int r = pv[a];
         if (r != a) {
-          const double t = bs[a * kTrsmCols + threadIdx.x];
-          bs[a * kTrsmCols + threadIdx.x] = bs[r * kTrsmCols + threadIdx.x];
-          bs[r * kTrsmCols + threadIdx.x] = t;
+          const int t = perm[a];
+          perm[a] = perm[r];
+          perm[r] = t;
         }
       }
     __syncthreads();
   }
-  // forward: column panels pan[(i - a0) * 32 + j] = M[i][a0 + j], rows i >= a0 (chol = 2: L^T X = B alone)
-  for (int a0 = 0; a0 < p && chol != 2; a0 += kTrsmPanel) {
-    const int rows = p - a0;
-    for (int e = threadIdx.x; e < rows * kTrsmPanel; e += NT) {
-      const int r = e / kTrsmPanel, j = e % kTrsmPanel;
-      pan[e] = M[(int64_t)(a0 + r) * p + a0 + j];
-    }
-    __syncthreads();
-    for (int j = 0; j < kTrsmPanel; ++j) {
-      const int a = a0 + j;
-      if (chol) {
-        if (threadIdx.x < kTrsmCols) bs[a * kTrsmCols + threadIdx.x] /= pan[j * kTrsmPanel + j];
-        __syncthreads();
-      }
-      for (int e = threadIdx.x; e < (p - a - 1) * kTrsmCols; e += NT) {
-        const int i = a + 1 + e / kTrsmCols, cc = e % kTrsmCols;
-        bs[i * kTrsmCols + cc] -= pan[(i - a0) * kTrsmPanel + j] * bs[a * kTrsmCols + cc];
-      }
-      __syncthreads();
-    }
+  double b[kTrsmSlots];
+#pragma unroll
+  for (int s = 0; s < kTrsmSlots; ++s) {
+    const int i = s * kTrsmPanel + lane;
+    b[s] = s < ns ? Bg[(int64_t)(chol ? i : perm[i]) * p + c] : 0.0;
   }
-  // backward, a = p-1 .. 0
-  for (int a1 = p; a1 > 0; a1 -= kTrsmPanel) {
-    const int a0 = a1 - kTrsmPanel;
-    if (chol) {   // row panel of L: pan[j * a1 + i] = L[a0 + j][i], i < a1 (L^T[i][a] = L[a][i])
-      for (int e = threadIdx.x; e < kTrsmPanel * a1; e += NT) {
-        const int j = e / a1, i = e % a1;
-        pan[e] = M[(int64_t)(a0 + j) * p + i];
-      }
-    } else {      // column panel of U: pan[i * 32 + j] = U[i][a0 + j], i < a1
-      for (int e = threadIdx.x; e < a1 * kTrsmPanel; e += NT) {
-        const int i = e / kTrsmPanel, j = e % kTrsmPanel;
-        pan[e] = M[(int64_t)i * p + a0 + j];
-      }
+  for (int t = 0; t < npan; ++t) {
+    const double *cur = (t & 1) ? pan1 : pan0;
+    if (t + 1 < npan) trsm_issue((t & 1) ? pan0 : pan1, M, p, panel_of(t + 1), t + 1 < nfwd, chol != 0);
+    cp_async_commit();
+    cp_async_wait1();   // this thread's copies of panel t are in
+    __syncthreads();    // and everyone's
+    const bool fwd = t < nfwd, unit = chol == 0;
+    switch (panel_of(t)) {
+      case 0: trsm_steps<0>(b, cur, ns, fwd, unit, lane); break;
+      case 1: trsm_steps<1>(b, cur, ns, fwd, unit, lane); break;
+      case 2: trsm_steps<2>(b, cur, ns, fwd, unit, lane); break;
+      case 3: trsm_steps<3>(b, cur, ns, fwd, unit, lane); break;
+      case 4: trsm_steps<4>(b, cur, ns, fwd, unit, lane); break;
+      case 5: trsm_steps<5>(b, cur, ns, fwd, unit, lane); break;
+      case 6: trsm_steps<6>(b, cur, ns, fwd, unit, lane); break;
+      default: trsm_steps<7>(b, cur, ns, fwd, unit, lane); break;
     }
-    __syncthreads();
-    for (int j = kTrsmPanel - 1; j >= 0; --j) {
-      const int a = a0 + j;
-      const double d = chol ? pan[j * a1 + a] : pan[a * kTrsmPanel + j];
-      if (threadIdx.x < kTrsmCols) bs[a * kTrsmCols + threadIdx.x] /= d;
-      __syncthreads();
-      for (int e = threadIdx.x; e < a * kTrsmCols; e += NT) {
-        const int i = e / kTrsmCols, cc = e % kTrsmCols;
-        const double m = chol ? pan[j * a1 + i] : pan[i * kTrsmPanel + j];
-        bs[i * kTrsmCols + cc] -= m * bs[a * kTrsmCols + cc];
-      }
-      __syncthreads();
-    }
+    __syncthreads();    // panel t's buffer is refilled in step t + 1
   }
   bool fin = true;
   double *oj = out + (int64_t)jb * pp;
-  for (int e = threadIdx.x; e < p * kTrsmCols; e += NT) {
-    const int i = e / kTrsmCols, cc = e % kTrsmCols;
-    oj[(int64_t)i * p + c0 + cc] = bs[e];
-    if (!isfinite(bs[e])) fin = false;
-  }
+#pragma unroll
+  for (int s = 0; s < kTrsmSlots; ++s)
+    if (s < ns) {
+      oj[(int64_t)(s * kTrsmPanel + lane) * p + c] = b[s];
+      fin = fin && isfinite(b[s]);
+    }
   if (!__syncthreads_and(fin) && threadIdx.x == 0) flag_breakdown(st);
 }
 
@@ -653,6 +706,7 @@ __global__ void __launch_bounds__(256) k_lu_panel(double *gws, int p, int a0, co
   double *Pn = sm_dyn;   // Pn[r * 33 + c] = M[a0 + r][a0 + c]
   constexpr int LD = kPB + 1;
   __shared__ int bad, best;
+  __shared__ double srec;
   if (a0 == 0) {
     double m = 0.0;
     bool fin = true;
@@ -699,6 +753,7 @@ __global__ void __launch_bounds__(256) k_lu_panel(double *gws, int p, int a0, co
       best = bi;
       piv[a0 + a] = a0 + bi;
       if (!(bv > thresh)) bad = 1;
+      else srec = 1.0 / Pn[bi * LD + a];   // the pivot's reciprocal, used while it stays finite
     }
     __syncthreads();
     if (bad) break;
@@ -709,8 +764,10 @@ __global__ void __launch_bounds__(256) k_lu_panel(double *gws, int p, int a0, co
       Pn[bi * LD + threadIdx.x] = t;
     }
     __syncthreads();
-    const double ua = Pn[a * LD + a];
-    for (int r = a + 1 + threadIdx.x; r < rows; r += blockDim.x) Pn[r * LD + a] /= ua;
+    const double ua = Pn[a * LD + a], ru = srec;
+    const bool rec = fabs(ua) >= DBL_MIN;
+    for (int r = a + 1 + threadIdx.x; r < rows; r += blockDim.x)
+      Pn[r * LD + a] = rec ? Pn[r * LD + a] * ru : Pn[r * LD + a] / ua;
     __syncthreads();
     const int w = kPB - a - 1;
     for (int e = threadIdx.x; e < (rows - a - 1) * w; e += blockDim.x) {
@@ -727,17 +784,42 @@ __global__ void __launch_bounds__(256) k_lu_panel(double *gws, int p, int a0, co
     const int r = e / kPB, c = e % kPB;
     M[(int64_t)(a0 + r) * p + a0 + c] = Pn[r * LD + c];
   }
-  // the panel's interchanges on the columns outside it, in factorization order (each column by one thread)
-  for (int c = threadIdx.x; c < p - kPB; c += blockDim.x) {
-    const int col = c < a0 ? c : c + kPB;
-    for (int a = a0; a < a0 + kPB; ++a) {
-      const int r = piv[a];
+  // the panel's interchanges on the columns outside it: composed into "row dst[q] receives row src[q]" (at most
+  // 2 x 32 rows move), then each column reads all its moving entries before writing any (one column per thread)
+  __shared__ int mv_dst[2 * kPB], mv_src[2 * kPB], nmv;
+  int *rowmap = reinterpret_cast<int *>(Pn);   // the panel is in M again: its buffer holds the row map of rows a0..
+  __syncthreads();
+  for (int i = threadIdx.x; i < rows; i += blockDim.x) rowmap[i] = a0 + i;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int a = 0; a < kPB; ++a) {
+      const int r = piv[a0 + a] - a0;
       if (r != a) {
-        const double t = M[(int64_t)a * p + col];
-        M[(int64_t)a * p + col] = M[(int64_t)r * p + col];
-        M[(int64_t)r * p + col] = t;
+        const int t = rowmap[a];
+        rowmap[a] = rowmap[r];
+        rowmap[r] = t;
       }
     }
+    int m = 0;
+    for (int i = 0; i < rows; ++i)
+      if (rowmap[i] != a0 + i) {
+        mv_dst[m] = a0 + i;
+        mv_src[m] = rowmap[i];
+        ++m;
+      }
+    nmv = m;
+  }
+  __syncthreads();
+  const int nm = nmv;
+  for (int c = threadIdx.x; c < p - kPB; c += blockDim.x) {
+    const int col = c < a0 ? c : c + kPB;
+    double v[2 * kPB];
+#pragma unroll
+    for (int q = 0; q < 2 * kPB; ++q)
+      if (q < nm) v[q] = M[(int64_t)mv_src[q] * p + col];
+#pragma unroll
+    for (int q = 0; q < 2 * kPB; ++q)
+      if (q < nm) M[(int64_t)mv_dst[q] * p + col] = v[q];
   }
   if (a0 + kPB == p && threadIdx.x == 0) atomicMax(&st->iter, st->cur);
 }
@@ -1057,7 +1139,7 @@ cudaError_t small_prepare(int p) {
 static cudaError_t launch_trsm(int p, int nblk, int chol, const double *gws, const int *active, double *out,
                                DevStatus *st, cudaStream_t s) {
   dim3 grid((unsigned)nblk, (unsigned)(p / kTrsmCols));
-  k_trsm_cols<<<grid, 256, trsm_smem(p), s>>>(p, chol, gws, active, out, st);
+  k_trsm_cols<<<grid, kTrsmCols * 32, trsm_smem(p), s>>>(p, chol, gws, active, out, st);
   return cudaGetLastError();
 }
 

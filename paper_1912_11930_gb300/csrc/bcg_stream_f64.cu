@@ -43,13 +43,17 @@ template cudaError_t launch_tc_cut_cols<double>(const double *, const double *, 
 template cudaError_t launch_tc_cut_cols<float>(const float *, const float *, int64_t, int, const int *,
                                                unsigned char *, int, cudaStream_t);
 
-cudaError_t launch_tc_cut_rows(const double *Y, int64_t n, int k, int p, unsigned char *img, int *erow,
-                               cudaStream_t s) {
+template <typename T>
+cudaError_t launch_tc_cut_rows(const T *Y, int64_t n, int k, int p, unsigned char *img, int *erow, cudaStream_t s) {
   if (!tc_layout_ok(k, p)) return cudaErrorInvalidValue;
   const int64_t nrt = (n + kTcRows - 1) / kTcRows;
-  kt_cut_rows<<<dim3((unsigned)nrt, (unsigned)(k / p)), kTcThreads, 0, s>>>(Y, n, k, p, img, erow);
+  kt_cut_rows<T><<<dim3((unsigned)nrt, (unsigned)(k / p)), kTcThreads, 0, s>>>(Y, n, k, p, img, erow);
   return cudaGetLastError();
 }
+template cudaError_t launch_tc_cut_rows<double>(const double *, int64_t, int, int, unsigned char *, int *,
+                                                cudaStream_t);
+template cudaError_t launch_tc_cut_rows<float>(const float *, int64_t, int, int, unsigned char *, int *,
+                                               cudaStream_t);
 
 cudaError_t launch_tc_gram_img(const unsigned char *imgX, const unsigned char *imgY, int64_t n, int k, int p,
                                int global, const int *active, double *part, int chunks, const int *ecx,
@@ -63,19 +67,26 @@ cudaError_t launch_tc_gram_img(const unsigned char *imgX, const unsigned char *i
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_baxpy_img(double *OUT, const double *BASE, const unsigned char *imgY, const int *erow,
-                                const uint16_t *Cs, const int *Cexp, int64_t n, int k, int p, int global,
-                                double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
-                                const double *bscale, int nsm) {
+template <typename T>
+cudaError_t launch_tc_baxpy_img(T *OUT, const typename TcId<T>::type *BASE, const unsigned char *imgY,
+                                const int *erow, const uint16_t *Cs, const int *Cexp, int64_t n, int k, int p,
+                                int global, double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
+                                const typename TcId<T>::type *bscale, int nsm) {
   if (!tc_layout_ok(k, p)) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(kt_baxpy_img, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  cudaError_t e = cudaFuncSetAttribute(kt_baxpy_img<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = ((n + kTcRows - 1) / kTcRows) * (k / kTcCols);
   const int grid = (int)std::min<int64_t>(ntiles, nsm);
-  kt_baxpy_img<<<grid, kTcThreads, kTcSmem, s>>>(OUT, BASE, imgY, erow, Cs, Cexp, n, k, p, global, sign, active, st,
-                                                 bump, bscale);
+  kt_baxpy_img<T><<<grid, kTcBaxThreads, kTcSmem, s>>>(OUT, BASE, imgY, erow, Cs, Cexp, n, k, p, global, sign, active,
+                                                       st, bump, bscale);
   return cudaGetLastError();
 }
+template cudaError_t launch_tc_baxpy_img<double>(double *, const double *, const unsigned char *, const int *,
+                                                 const uint16_t *, const int *, int64_t, int, int, int, double,
+                                                 const int *, DevStatus *, int, cudaStream_t, const double *, int);
+template cudaError_t launch_tc_baxpy_img<float>(float *, const float *, const unsigned char *, const int *,
+                                                const uint16_t *, const int *, int64_t, int, int, int, double,
+                                                const int *, DevStatus *, int, cudaStream_t, const float *, int);
 
 cudaError_t launch_inv_diag(const OpDesc &A, int64_t n, double *dinv, double *opmax, int nsm, cudaStream_t s) {
   if (opmax) {
