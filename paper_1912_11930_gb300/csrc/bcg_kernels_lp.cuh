@@ -214,9 +214,29 @@ __global__ void __launch_bounds__(kNT) kl_colnorm(const T *__restrict__ R, int64
   double d = 0.0;
   int pass = 0;
   if (slot) {
-    for (int64_t r = (int64_t)blockIdx.x * rpp + g; r < n; r += (int64_t)gridDim.x * rpp) {
-      const BT v = G::conv(R[r * k + c], sR);
-      G::add(s, cc, v, v);
+    // rows r, r + stride, ... in order; 8 loads in flight per thread (the flushes fall every kFlushPasses rows
+    // as in a one-row loop, a multiple of 8)
+    static_assert(kFlushPasses % 8 == 0, "flush cadence");
+    const int64_t stride = (int64_t)gridDim.x * rpp;
+    int64_t r = (int64_t)blockIdx.x * rpp + g;
+    for (; r + 7 * stride < n; r += 8 * stride) {
+      T v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = R[(r + u * stride) * k + c];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const BT b = G::conv(v[u], sR);
+        G::add(s, cc, b, b);
+      }
+      pass += 8;
+      if (pass == kFlushPasses) {
+        pass = 0;
+        norm_flush<T>(d, s, cc, sR);
+      }
+    }
+    for (; r < n; r += stride) {
+      const BT b = G::conv(R[r * k + c], sR);
+      G::add(s, cc, b, b);
       if (++pass == kFlushPasses) {
         pass = 0;
         norm_flush<T>(d, s, cc, sR);

@@ -384,29 +384,29 @@ __device__ __forceinline__ void tc_load8(const float *src, float (&v)[8]) {
 template <typename T>
 __global__ void __launch_bounds__(kTcThreads) kt_cut_rows(const T *__restrict__ Y, int64_t n, int k, int p,
                                                           unsigned char *__restrict__ img, int *__restrict__ erow) {
-  __shared__ int sX[kTcThreads];
   __shared__ int sE[kTcRows];
   const int tid = threadIdx.x;
   const int64_t rt = blockIdx.x;
   const int j = blockIdx.y;
   const int64_t r0 = rt * kTcRows;
   const int64_t nrows = ((n + kTcRows - 1) / kTcRows) * kTcRows;
-  {
-    const int rl = tid & (kTcRows - 1), half = tid >> 7;
-    const int64_t r = r0 + rl;
-    int em = 0;
-    if (r < n) {
-      const T *src = Y + r * k + (int64_t)j * p + half * (p / 2);
+  {   // row exponents: warp w takes rows w, w + 8, ..., each read whole by the warp (coalesced), max by shuffles
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int rl = warp; rl < kTcRows; rl += kTcThreads / 32) {
+      const int64_t r = r0 + rl;
+      int em = 0;
+      if (r < n) {
+        const T *src = Y + r * k + (int64_t)j * p;
 #pragma unroll 8
-      for (int q = 0; q < p / 2; ++q) em = max(em, tc_exp_field(__ldg(src + q)));
-    }
-    sX[tid] = em;
-    __syncthreads();
-    if (tid < kTcRows) {
-      const int e2 = max(sX[tid], sX[tid + kTcRows]);
-      const int E = e2 > 0 ? e2 - 1023 : -1023;
-      sE[tid] = E;
-      erow[(int64_t)j * nrows + r0 + tid] = e2 == 0x7FF ? kTcBadRow : E;
+        for (int q = lane; q < p; q += 32) em = max(em, tc_exp_field(__ldg(src + q)));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) em = max(em, __shfl_xor_sync(0xffffffffu, em, o));
+      if (lane == 0) {
+        const int E = em > 0 ? em - 1023 : -1023;
+        sE[rl] = E;
+        erow[(int64_t)j * nrows + r] = em == 0x7FF ? kTcBadRow : E;
+      }
     }
     __syncthreads();
   }

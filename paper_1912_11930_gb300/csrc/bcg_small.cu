@@ -769,10 +769,22 @@ __global__ void __launch_bounds__(256) k_lu_panel(double *gws, int p, int a0, co
     for (int r = a + 1 + threadIdx.x; r < rows; r += blockDim.x)
       Pn[r * LD + a] = rec ? Pn[r * LD + a] * ru : Pn[r * LD + a] / ua;
     __syncthreads();
+    // rank-1 update of the entries (r, c), r, c > a, taken in row-major order e = (r - a - 1) w + (c - a - 1);
+    // thread t takes e = t, t + T, ... with (r, c) advanced incrementally (one division per step)
     const int w = kPB - a - 1;
-    for (int e = threadIdx.x; e < (rows - a - 1) * w; e += blockDim.x) {
-      const int r = a + 1 + e / w, c = a + 1 + e % w;
-      Pn[r * LD + c] -= Pn[r * LD + a] * Pn[a * LD + c];
+    if (w > 0) {
+      const int T = blockDim.x, dq = T / w, dr = T - dq * w;
+      int rr = threadIdx.x / w, cc = threadIdx.x - rr * w;
+      for (int r = a + 1 + rr; r < rows;) {
+        const int c = a + 1 + cc;
+        Pn[r * LD + c] -= Pn[r * LD + a] * Pn[a * LD + c];
+        r += dq;
+        cc += dr;
+        if (cc >= w) {
+          cc -= w;
+          ++r;
+        }
+      }
     }
     __syncthreads();
   }
