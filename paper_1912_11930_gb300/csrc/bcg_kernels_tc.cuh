@@ -60,6 +60,10 @@ constexpr long long kTcWaitLimit = 1ll << 24;                     // mbarrier po
 __host__ __device__ constexpr bool tc_layout_ok(int k, int p) {
   return p >= 64 && p <= 256 && p % 64 == 0 && k % p == 0 && k <= 256;
 }
+// blocks of 16 or 32 columns paired into 64-column tiles (block-diagonal C images)
+__host__ __device__ constexpr bool tc_pair_layout_ok(int k, int p) {
+  return (p == 16 || p == 32) && k % 64 == 0 && k <= 256;
+}
 // bf16 digits of the pre-sliced C^T for nblkC distinct blocks: (p / 64) (p / 32) chunk images of 32 KB per block
 __host__ __device__ constexpr size_t tc_cmat_bytes(int nblkC, int p) {
   return (size_t)nblkC * (p / kTcCols) * (p / kTcK) * kTcStageBytesB;
@@ -314,6 +318,22 @@ __global__ void kt_slice_cmat(const double *__restrict__ C, int nblkC, int p, ui
   }
 }
 
+// Block-diagonal 64 x 64 matrices from p x p blocks (p = 16 or 32): out block o (row-major) holds blocks
+// o (64 / p) .. o (64 / p) + 64 / p - 1 of C on its diagonal (global: block 0 of C in every position) and zeros
+// elsewhere, so that 64 / p blocks of columns are updated by one 64-column tile. One thread per entry.
+__global__ void kt_pair_cmat(const double *__restrict__ C, int nout, int p, int global, double *__restrict__ out) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nout * 64 * 64) return;
+  const int o = idx >> 12, a = (idx >> 6) & 63, b = idx & 63;
+  const int ba = a / p, bb = b / p;
+  double v = 0.0;
+  if (ba == bb) {
+    const int jc = global ? 0 : o * (64 / p) + ba;
+    v = C[(size_t)jc * p * p + (size_t)(a - ba * p) * p + (b - bb * p)];
+  }
+  out[idx] = v;
+}
+
 // ---- Gram ------------------------------------------------------------------------------------------------------
 // Column exponent fields for the Gram slicing: ecol[c] = max over rows of the biased exponent of X[r][c] (times
 // xscale[r] if given), by integer maxima (the caller zeroes ecol). Thread (g, c) covers rows g, g + rows per CTA
@@ -540,7 +560,9 @@ __device__ __forceinline__ void tc_store16(float *dst, const double (&v)[16]) {
 
 // OUT_j = BASE_j (times bscale[r] per row, if given; BASE NULL: zero) + sign * Y_j C_j over every block j (global: C_0
 // for all), from Y's row images (kt_cut_rows) and C's images (kt_slice_cmat). OUT may equal BASE. T = double, or
-// float (the mixed form's FP32 process: the sum is formed in FP64 and rounded once). Frozen blocks
+// float (the mixed form's FP32 process: the sum is formed in FP64 and rounded once). pe: the width of the column
+// blocks that own a row exponent (p; or 16 or 32 where blocks of that width are paired into 64-column tiles with
+// block-diagonal C images, kt_pair_cmat: each output column then sums over its own block's digits only). Frozen blocks
 // (active[j] = 0) get OUT = BASE (scaled). bump: CTA 0 advances the iteration counter (the P update's role).
 // Persistent over 128 x 64 output tiles (tile t: row tile t / (k / 64), column tile t mod (k / 64)); every role
 // walks the CTA's tiles in the same order, the issuing roles skipping frozen blocks.
@@ -553,7 +575,7 @@ __global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T
                                                                  int p, int global, double sign,
                                                                  const int *__restrict__ active,
                                                                  DevStatus *__restrict__ st, int bump,
-                                                                 const T *__restrict__ bscale) {
+                                                                 const T *__restrict__ bscale, int pe) {
   if (st->flags != 0) return;
   if (bump && blockIdx.x == 0 && threadIdx.x == 0) st->cur += 1;
   extern __shared__ __align__(16) unsigned char tc_smem_raw[];
@@ -656,13 +678,15 @@ __global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T
       if (lane == 0) mbar_arrive(tfree);
       if (r >= n) continue;
       // (s + c) 2^t as one double (integer operations), one FP64 addition; 16 columns at a time, their BASE
-      // values loaded before any store (OUT may be BASE)
-      const int E = erow[(int64_t)j * nrows + r];
-      const bool bad = E == kTcBadRow;
+      // values loaded before any store (OUT may be BASE). Row exponents per pe columns: columns cb0 .. +15 take
+      // Eh[0], cb0 + 16 .. +31 take Eh[1] (the same value unless pe = 16).
+      const int Eh[2] = {erow[(int64_t)((c0 + cb0) / pe) * nrows + r], erow[(int64_t)((c0 + cb0 + 16) / pe) * nrows + r]};
       const double bs = bscale ? (double)bscale[r] : 1.0;
       const int4 *F4 = reinterpret_cast<const int4 *>(Cexp + jc * p + b0 + cb0);
 #pragma unroll
       for (int half = 0; half < 2; ++half) {
+        const int E = Eh[half];
+        const bool bad = E == kTcBadRow;
         double v[16];
         if (BASE) {
           tc_load16(BASE + r * k + c0 + cb0 + half * 16, v);

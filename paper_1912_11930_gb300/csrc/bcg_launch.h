@@ -99,6 +99,12 @@ cudaError_t launch_lp_colnorm(const T *R, int64_t n, int k, double *partN, int g
 // writes the partials of <<X, Y>>_S into `chunks` partial rows in the layout of launch_lp_gram, and
 // launch_tc_baxpy_img forms OUT_j = BASE_j (x bscale) + sign Y_j C_j.
 bool tc_ok(int k, int p);
+// Blocks of 32 columns (k a multiple of 64) on the same kernels: launch_tc_pair_cmat writes the block-diagonal
+// 64 x 64 matrices pairing consecutive blocks (k / 64 of them, one if global; 64 x 64 doubles each, row-major),
+// which launch_tc_slice cuts with p = 64; launch_tc_cut_rows takes p = 32 (one exponent per row of each block);
+// launch_tc_baxpy_img takes p = 64 and pe = 32.
+bool tc_pair_ok(int k, int p);
+cudaError_t launch_tc_pair_cmat(const double *C, int k, int p, int global, double *out, cudaStream_t s);
 size_t tc_workspace_bytes(int nblkC, int p);
 cudaError_t launch_tc_slice(const double *C, int nblkC, int p, uint16_t *Cs, int *Cexp, cudaStream_t s);
 size_t tc_row_image_size(int64_t n, int k);
@@ -123,7 +129,7 @@ template <typename T>
 cudaError_t launch_tc_baxpy_img(T *OUT, const typename TcId<T>::type *BASE, const unsigned char *imgY,
                                 const int *erow, const uint16_t *Cs, const int *Cexp, int64_t n, int k, int p,
                                 int global, double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
-                                const typename TcId<T>::type *bscale, int nsm);
+                                const typename TcId<T>::type *bscale, int nsm, int pe = 0);
 // doubles of per-block workspace of the p x p solves; kept in global memory (gws) when too big for shared
 size_t small_ws_doubles(int p);
 bool small_needs_gws(int p);

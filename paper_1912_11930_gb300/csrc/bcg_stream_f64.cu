@@ -6,6 +6,14 @@
 
 namespace bcgk {
 bool tc_ok(int k, int p) { return tc_layout_ok(k, p); }
+bool tc_pair_ok(int k, int p) { return tc_pair_layout_ok(k, p); }
+
+cudaError_t launch_tc_pair_cmat(const double *C, int k, int p, int global, double *out, cudaStream_t s) {
+  if (!tc_pair_layout_ok(k, p)) return cudaErrorInvalidValue;
+  const int nout = global ? 1 : k / 64;
+  kt_pair_cmat<<<(nout * 4096 + 255) / 256, 256, 0, s>>>(C, nout, p, global, out);
+  return cudaGetLastError();
+}
 size_t tc_workspace_bytes(int nblkC, int p) { return tc_cmat_bytes(nblkC, p); }
 
 cudaError_t launch_tc_slice(const double *C, int nblkC, int p, uint16_t *Cs, int *Cexp, cudaStream_t s) {
@@ -45,7 +53,7 @@ template cudaError_t launch_tc_cut_cols<float>(const float *, const float *, int
 
 template <typename T>
 cudaError_t launch_tc_cut_rows(const T *Y, int64_t n, int k, int p, unsigned char *img, int *erow, cudaStream_t s) {
-  if (!tc_layout_ok(k, p)) return cudaErrorInvalidValue;
+  if (!tc_layout_ok(k, p) && !tc_pair_layout_ok(k, p)) return cudaErrorInvalidValue;
   const int64_t nrt = (n + kTcRows - 1) / kTcRows;
   kt_cut_rows<T><<<dim3((unsigned)nrt, (unsigned)(k / p)), kTcThreads, 0, s>>>(Y, n, k, p, img, erow);
   return cudaGetLastError();
@@ -71,22 +79,25 @@ template <typename T>
 cudaError_t launch_tc_baxpy_img(T *OUT, const typename TcId<T>::type *BASE, const unsigned char *imgY,
                                 const int *erow, const uint16_t *Cs, const int *Cexp, int64_t n, int k, int p,
                                 int global, double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
-                                const typename TcId<T>::type *bscale, int nsm) {
-  if (!tc_layout_ok(k, p)) return cudaErrorInvalidValue;
+                                const typename TcId<T>::type *bscale, int nsm, int pe) {
+  if (pe == 0) pe = p;
+  if (!tc_layout_ok(k, p) || !(pe == p || (p == 64 && tc_pair_layout_ok(k, pe)))) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(kt_baxpy_img<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
   const int64_t ntiles = ((n + kTcRows - 1) / kTcRows) * (k / kTcCols);
   const int grid = (int)std::min<int64_t>(ntiles, nsm);
   kt_baxpy_img<T><<<grid, kTcBaxThreads, kTcSmem, s>>>(OUT, BASE, imgY, erow, Cs, Cexp, n, k, p, global, sign, active,
-                                                       st, bump, bscale);
+                                                       st, bump, bscale, pe);
   return cudaGetLastError();
 }
 template cudaError_t launch_tc_baxpy_img<double>(double *, const double *, const unsigned char *, const int *,
                                                  const uint16_t *, const int *, int64_t, int, int, int, double,
-                                                 const int *, DevStatus *, int, cudaStream_t, const double *, int);
+                                                 const int *, DevStatus *, int, cudaStream_t, const double *, int,
+                                                 int);
 template cudaError_t launch_tc_baxpy_img<float>(float *, const float *, const unsigned char *, const int *,
                                                 const uint16_t *, const int *, int64_t, int, int, int, double,
-                                                const int *, DevStatus *, int, cudaStream_t, const float *, int);
+                                                const int *, DevStatus *, int, cudaStream_t, const float *, int,
+                                                int);
 
 cudaError_t launch_inv_diag(const OpDesc &A, int64_t n, double *dinv, double *opmax, int nsm, cudaStream_t s) {
   if (opmax) {

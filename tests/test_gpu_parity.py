@@ -565,6 +565,45 @@ def test_large_p_tensor_cores_match_fma(torch_dev, name, sub, k, p, m):
         assert_close(a, ref.X, 1e-9, f"tensor cores against the oracle (Jacobi {jac})")
 
 
+@pytest.mark.parametrize("name,sub,k,p,m", [("p3d_30", "hybrid", 64, 32, 6), ("p3d_30", "hybrid", 128, 32, 5),
+                                            ("s27_15", "global", 128, 32, 5), ("vc_20", "hybrid", 256, 32, 4)])
+def test_pairs_of_32_tensor_cores_match_fma(torch_dev, name, sub, k, p, m):
+    """FP64 blocks of 32 columns with k a multiple of 64 take their block updates on the tensor cores, two blocks per
+    64-column tile (block-diagonal coefficient images, row exponents per block of 32): against the warp-chunk FMA
+    kernels (option "tensor_cores" 0) and the oracle at equal iteration counts, with and without Jacobi. The row
+    counts (26,970, 2,730, 7,820) leave ragged last tiles."""
+    M = mat(name)
+    B = W.rhs(M.n, k, seed=37)
+    for jac in (0, 1):
+        a, ra = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, maxit=m, opts={"tensor_cores": 1, "precond": jac})
+        b, rb = gpu_solve(torch_dev, M, B, k=k, p=p, sub=sub, maxit=m, opts={"tensor_cores": 0, "precond": jac})
+        assert ra.status == rb.status == bcg.NOT_CONVERGED and ra.iters == rb.iters == m
+        assert_close(a, b, 1e-10, f"tensor cores against FMA kernels (Jacobi {jac})")
+        ref = O.solve(M.to_scipy(), B, p=p, sub=sub, tol=0.0, maxit=m, precond="jacobi" if jac else "none")
+        assert_close(a, ref.X, 1e-9, f"tensor cores against the oracle (Jacobi {jac})")
+
+
+def test_pairs_of_32_frozen_and_converged(torch_dev):
+    """Blocks of 32 on the tensor cores to the stopping rule: a zero block shares its 64-column tile with a block that
+    iterates, and stays exactly zero; a block scaled by 1e-3 converges like the others; the counts are within +-2
+    of the oracle's and the true residual is at the tolerance."""
+    M = mat("p3d_30")
+    A = M.to_scipy()
+    k, p, tol = 128, 32, 1e-8
+    B = W.rhs(M.n, k, seed=61)
+    B[:, 32:64] = 0.0
+    B[:, 96:128] *= 1e-3
+    X, r = gpu_solve(torch_dev, M, B, k=k, p=p, sub="hybrid", tol=tol, maxit=2000)
+    assert r.ok, r
+    assert r.block_iters[1] == 0 and np.all(X[:, 32:64] == 0.0)
+    live = np.r_[0:32, 64:128]
+    res = np.linalg.norm(B[:, live] - A @ X[:, live], axis=0) / np.linalg.norm(B[:, live], axis=0)
+    assert np.all(res <= 1.5 * tol)
+    ref = O.solve(A, B, p=p, sub="hybrid", tol=tol, maxit=2000)
+    assert abs(r.iters - ref.iters) <= 2
+    assert np.all(np.abs(np.asarray(r.block_iters) - ref.block_iters) <= 2), (r.block_iters, ref.block_iters)
+
+
 @pytest.mark.parametrize("name,sub,k,p,jac", [("p3d_17", "classical", 64, 64, 0), ("p3d_17", "hybrid", 128, 64, 1),
                                               ("p3d_17", "global", 128, 64, 0), ("p3d_17", "classical", 128, 128, 1)])
 def test_mixed_large_blocks_tensor_core_products(torch_dev, name, sub, k, p, jac):
