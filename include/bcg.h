@@ -27,7 +27,7 @@
  *
  * Arithmetic of the FP64 form (BCG_FP64):
  *  - BOP (Y = A X), the block updates (BAXPY) and the p x p Cholesky/LU solves (BSOLVE) are IEEE FP64
- *    operations (fused multiply-adds).
+ *    operations (fused multiply-adds), except for the block updates that the tensor-core path below forms.
  *  - Block products (BDOT: alpha, the recomputed rho, rho, the column norms of the stopping test) are not
  *    summed with FP64 operations. Each FP64 operand column c is first scaled by an exact power of two 2^-s_c
  *    (s_c from the column's latest 2-norm in the solver, from its largest entry in bcg_bdot), then every value
@@ -42,6 +42,17 @@
  *  - Range: any FP64 operands whose products and sums are finite in FP64 (tested with entries from 1e-300 to
  *    1e300 and exact zeros, and with B scaled by 1e+-30 and A by 1e+-10); within the solver a column may
  *    grow by about 2^50 or shrink by about 2^49 between two norm updates without loss.
+ *  - Tensor cores (option "tensor_cores", on by default): with p a multiple of 64 (up to 256) the block products
+ *    and block updates, and with p = 32 and k a multiple of 64 the block updates, are formed on the tensor
+ *    cores instead (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012). Every operand value is truncated
+ *    to 48 bits below an exponent shared along the contraction (per row of a block for the updated block Y,
+ *    per column for lambda / beta and for the operands of the products) and cut into eight 6-bit digits held
+ *    exactly in bf16. The 36 digit pairs of weight at least 2^-42 are multiplied and summed exactly in FP32
+ *    (at most 512 terms before each read-out). The eight partial sums are combined with error-free float
+ *    additions, and an update adds the result to its base with one FP64 addition. Error per entry: about
+ *    2^-44 sum |u v| (truncation where the values sharing an exponent are of one magnitude; at most
+ *    2^-47 max|u| sum|v| + 2^-47 max|v| sum|u|), plus about 2^-45 sum |u v| (the dropped pairs); FP64 FMAs
+ *    give about K 2^-53 of it. Range: as the block products above (exponents are taken per row or column).
  */
 #ifndef BCG_H
 #define BCG_H
@@ -200,6 +211,11 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
  *                  by the column blocks) and both preconditioners (Jacobi: Q orthonormal in the product
  *                  <<Q, M^{-1} Q>>, directions M^{-1} Q + S psi^T). FP64 handles that are not row-sharded
  *                  only (INVALID_ARG otherwise); 0 = Algorithm 1 (default).
+ *   "tensor_cores" 1 (default) = the tcgen05 path described under "Arithmetic of the FP64 form": FP64 handles
+ *                  with p a multiple of 64 take their block products and updates there, FP64 handles with
+ *                  p = 32 and k a multiple of 64 their block updates (two blocks per 64-column tile); the
+ *                  mixed form's FP32 process with p a multiple of 64 takes both (its updates summed in FP64
+ *                  and rounded once to FP32). 0 = FP64 FMA updates and Dot2 products everywhere.
  *   "guards"       1 = after each solve (bcg_solve, bcg_solve_host, bcg_rows_finish) compare the 16 guard
  *                  bytes that follow every workspace buffer of the handle with the pattern written at
  *                  allocation; a change returns BCG_ERR_GUARD naming the buffer. 0 = no check (default).
