@@ -288,7 +288,7 @@ bcg_status setup_workspace(bcg_ctx *h) {
     for (int i = 0; i < 4; ++i) CKS(h->alloc(&h->tc_img[i], ib));
     CKS(h->alloc(&h->tc_erow, 2 * (size_t)((h->n + 127) / 128) * 128 * (h->k / h->p)));
   }
-  if (h->prec == BCG_FP64 && tc_pair_ok(h->k, h->p) && h->p == 32) {
+  if (h->prec == BCG_FP64 && tc_pair_ok(h->k, h->p)) {
     // blocks of 32 paired into 64-column tiles: the block updates' row images of P and Q (16 bytes per value each)
     const int nout = h->global ? 1 : h->k / 64;
     CKS(h->alloc(&h->tc_pair, (size_t)nout * 64 * 64));

@@ -6,7 +6,9 @@
 
 namespace bcgk {
 bool tc_ok(int k, int p) { return tc_layout_ok(k, p); }
-bool tc_pair_ok(int k, int p) { return tc_pair_layout_ok(k, p); }
+// blocks of 16 fit the kernels too, but measured slower than their fused FMA path: K1 must then form the recomputed
+// rho (K3 does at p <= 16), and rho and the norms need passes of their own (160^3, k = 64: 44.7 s against 40.3 s)
+bool tc_pair_ok(int k, int p) { return p == 32 && tc_pair_layout_ok(k, p); }
 
 cudaError_t launch_tc_pair_cmat(const double *C, int k, int p, int global, double *out, cudaStream_t s) {
   if (!tc_pair_layout_ok(k, p)) return cudaErrorInvalidValue;
