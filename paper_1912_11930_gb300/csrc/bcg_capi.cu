@@ -126,7 +126,7 @@ struct bcg_ctx {
   int precond = 0;                     // 0: M = I; 1: Jacobi, M = diag(A)
   int refine = 1;                      // FP32_REFINE: 1 residual replacement, 0 restarted refinement
   int retooled = 0;                    // FP64: 1 Dubrulle's retooled block CG instead of Algorithm 1's recurrences
-  int tensor_cores = 1;                // FP64, p a multiple of 64 (or 32 with k a multiple of 64): tcgen05 kernels
+  int tensor_cores = 1;                // FP64, p a multiple of 64 or p = 32: tcgen05 kernels
   int guards = 0;                      // 1: check every buffer's guard bytes after each solve
   // live per-kernel timing (profile = 1): CUDA events around every launch of an executed iteration
   // K1 op_gram, K4a solve_lambda, K2 update_xr, K4b solve_beta, K3 update_p, K0 residual, and the tensor-core
@@ -156,7 +156,8 @@ struct bcg_ctx {
   int *tc_ecol = nullptr;              // tensor-core block products: the operands' column exponent fields (2 k)
   unsigned char *tc_img[4] = {nullptr, nullptr, nullptr, nullptr};   // digit images: 2 column, 2 row images
   int *tc_erow = nullptr;              // row exponents of the two row images (2 ceil(n / 128) 128 (k / p))
-  double *tc_pair = nullptr;           // blocks of 32 on the tensor cores: the paired block-diagonal 64 x 64 lambda / beta
+  int tc_small = 0;                    // FP64 blocks of 32 with their block updates on the tensor cores
+  double *tc_pair = nullptr;           // the paired block-diagonal 64 x 64 lambda / beta of those (64 | k)
   double *dinv64 = nullptr;            // 1 / diag(A) (Jacobi preconditioner)
   double *dr_C = nullptr, *dr_xi = nullptr, *dr_psiinv = nullptr, *dr_phi = nullptr;   // retooled form, p x p per block
   float *dinv32 = nullptr;             // its FP32 copy for the mixed form's inner solve
@@ -288,12 +289,19 @@ bcg_status setup_workspace(bcg_ctx *h) {
     for (int i = 0; i < 4; ++i) CKS(h->alloc(&h->tc_img[i], ib));
     CKS(h->alloc(&h->tc_erow, 2 * (size_t)((h->n + 127) / 128) * 128 * (h->k / h->p)));
   }
-  if (h->prec == BCG_FP64 && tc_pair_ok(h->k, h->p)) {
-    // blocks of 32 paired into 64-column tiles: the block updates' row images of P and Q (16 bytes per value each)
-    const int nout = h->global ? 1 : h->k / 64;
-    CKS(h->alloc(&h->tc_pair, (size_t)nout * 64 * 64));
-    CKS(h->alloc(&h->tc_cs, tc_workspace_bytes(nout, 64) / sizeof(uint16_t)));
-    CKS(h->alloc(&h->tc_cexp, (size_t)nout * 64));
+  if (h->prec == BCG_FP64 && (tc_pair_ok(h->k, h->p) || tc_b32_ok(h->k, h->p))) {
+    // blocks of 32, paired into 64-column tiles where 64 divides k, else in 32-column tiles: the block updates'
+    // row images of P and Q (16 bytes per value each) and the digit images of lambda / beta
+    h->tc_small = 1;
+    if (tc_pair_ok(h->k, h->p)) {
+      const int nout = h->global ? 1 : h->k / 64;
+      CKS(h->alloc(&h->tc_pair, (size_t)nout * 64 * 64));
+      CKS(h->alloc(&h->tc_cs, tc_workspace_bytes(nout, 64) / sizeof(uint16_t)));
+      CKS(h->alloc(&h->tc_cexp, (size_t)nout * 64));
+    } else {
+      CKS(h->alloc(&h->tc_cs, tc_workspace_bytes(h->nblk, h->p) / sizeof(uint16_t)));
+      CKS(h->alloc(&h->tc_cexp, (size_t)h->nblk * h->p));
+    }
     for (int i = 2; i < 4; ++i) CKS(h->alloc(&h->tc_img[i], tc_row_image_size(h->n, h->k)));
     CKS(h->alloc(&h->tc_erow, 2 * (size_t)((h->n + 127) / 128) * 128 * (h->k / h->p)));
   }
@@ -616,10 +624,11 @@ bcg_status launch_iteration_lp(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T 
   return BCG_OK;
 }
 
-// One FP64 iteration with blocks of 32 columns (k a multiple of 64) whose block updates run on the tensor cores:
-// K1 as in the fused path (BOP, alpha and the recomputed rho); X += P lambda and R -= Q lambda from row images of P
-// and Q with two blocks paired into each 64-column tile (block-diagonal coefficient images, row exponents per block
-// of 32); rho = <<Z, R>> and the column norms in passes of their own (the tiled Dot2 product and norm kernels);
+// One FP64 iteration with blocks of 32 columns whose block updates run on the tensor cores: K1 as in the fused path
+// (BOP, alpha and the recomputed rho); X += P lambda and R -= Q lambda from row images of P and Q, with two blocks
+// paired into each 64-column tile where 64 divides k (block-diagonal coefficient images, row exponents per block of
+// 32), else in 32-column tiles; rho = <<Z, R>> and the column norms in passes of their own (the tiled Dot2 product
+// and norm kernels);
 // P = Z + P beta into Q's buffer (the caller swaps P and Q). Frozen blocks have lambda = beta = 0, so their X and R
 // keep their values and their P becomes Z, as the warp-chunk kernels leave them.
 bcg_status launch_iteration_tcpair(bcg_ctx *h, const OpDesc &A, double *X, double *R, double *P, double *Q,
@@ -632,30 +641,34 @@ bcg_status launch_iteration_tcpair(bcg_ctx *h, const OpDesc &A, double *X, doubl
   const int *shP = sh_role(sc.sh, k, SH_P), *shR = sh_role(sc.sh, k, SH_R);
   unsigned char *RP = h->tc_img[2], *RQ = h->tc_img[3];
   int *erP = h->tc_erow, *erQ = h->tc_erow + (size_t)((n + 127) / 128) * 128 * (k / p);
-  const int nout = gl ? 1 : k / 64;
+  const bool paired = h->tc_pair != nullptr;
+  const int nout = gl ? 1 : k / 64, pt = paired ? 64 : p;   // pt: the block width of the update kernel's images
+  auto coef = [&](const double *C) -> cudaError_t {   // digit images of lambda or beta
+    if (!paired) return launch_tc_slice(C, h->nblk, p, h->tc_cs, h->tc_cexp, s);
+    const cudaError_t e = launch_tc_pair_cmat(C, k, p, gl, h->tc_pair, s);
+    return e != cudaSuccess ? e : launch_tc_slice(h->tc_pair, nout, 64, h->tc_cs, h->tc_cexp, s);
+  };
   CK(launch_op_gram<double>(A, P, R, Q, n, k, p, gl, h->active, h->partA, h->partR, h->st, g.op, s, sc.sh));
   CK(launch_solve_lambda(h->partA, h->partR, g.op, g.op, k, p, gl, h->active, h->lam, h->rho_rec, h->st, h->gws,
                          g.alpha_circ, s));
-  CK(launch_tc_pair_cmat(h->lam, k, p, gl, h->tc_pair, s));
-  CK(launch_tc_slice(h->tc_pair, nout, 64, h->tc_cs, h->tc_cexp, s));
+  CK(coef(h->lam));
   CK(launch_tc_cut_rows<double>(P, n, k, p, RP, erP, s));
   CK(launch_tc_cut_rows<double>(Q, n, k, p, RQ, erQ, s));
   CKS(tc_timed(h, 7, [&] {
-    return launch_tc_baxpy_img<double>(X, X, RP, erP, h->tc_cs, h->tc_cexp, n, k, 64, gl, 1.0, nullptr, h->st, 0, s,
+    return launch_tc_baxpy_img<double>(X, X, RP, erP, h->tc_cs, h->tc_cexp, n, k, pt, gl, 1.0, nullptr, h->st, 0, s,
                                        nullptr, nsm, p);
   }));
   CKS(tc_timed(h, 7, [&] {
-    return launch_tc_baxpy_img<double>(R, R, RQ, erQ, h->tc_cs, h->tc_cexp, n, k, 64, gl, -1.0, nullptr, h->st, 0, s,
+    return launch_tc_baxpy_img<double>(R, R, RQ, erQ, h->tc_cs, h->tc_cexp, n, k, pt, gl, -1.0, nullptr, h->st, 0, s,
                                        nullptr, nsm, p);
   }));
   CK(launch_lp_gram<double>(R, R, n, k, p, gl, h->active, h->partRho, g.op, h->st, s, dinv, shP, shR));
   CK(launch_lp_colnorm<double>(R, n, k, h->partN, g.res, h->st, s, shR));
   CK(launch_solve_beta(h->partRho, h->partN, g.op, g.res, k, p, gl, h->tol2_dev, h->r0n2, h->rn2, h->active,
                        h->block_iters, h->rho_rec, h->beta, h->st, h->gws, 0, s, sc));
-  CK(launch_tc_pair_cmat(h->beta, k, p, gl, h->tc_pair, s));
-  CK(launch_tc_slice(h->tc_pair, nout, 64, h->tc_cs, h->tc_cexp, s));
+  CK(coef(h->beta));
   CKS(tc_timed(h, 7, [&] {
-    return launch_tc_baxpy_img<double>(Q, R, RP, erP, h->tc_cs, h->tc_cexp, n, k, 64, gl, 1.0, nullptr, h->st, 1, s,
+    return launch_tc_baxpy_img<double>(Q, R, RP, erP, h->tc_cs, h->tc_cexp, n, k, pt, gl, 1.0, nullptr, h->st, 1, s,
                                        dinv, nsm, p);
   }));
   return BCG_OK;
@@ -715,7 +728,7 @@ bcg_status run_iterations(bcg_ctx *h, const OpDesc &A, T *X, T *R, T *P, T *Q, c
   int launched = 0;
   const int batch = h->check_every;
   bool pair = false;   // FP64 blocks of 32 with their block updates on the tensor cores
-  if constexpr (sizeof(T) == 8) pair = h->tensor_cores && h->tc_pair != nullptr && h->prec == BCG_FP64;
+  if constexpr (sizeof(T) == 8) pair = h->tensor_cores && h->tc_small && h->prec == BCG_FP64;
   if (pair) {   // plain launches, P and Q swap every iteration
     while (h->h_st->flags == 0 && launched < maxit) {
       const int nb = std::min(batch, maxit - launched);

@@ -64,10 +64,16 @@ __host__ __device__ constexpr bool tc_layout_ok(int k, int p) {
 __host__ __device__ constexpr bool tc_pair_layout_ok(int k, int p) {
   return (p == 16 || p == 32) && k % 64 == 0 && k <= 256;
 }
-// bf16 digits of the pre-sliced C^T for nblkC distinct blocks: (p / 64) (p / 32) chunk images of 32 KB per block
+// bf16 digits of the pre-sliced C^T for nblkC distinct blocks: 8 digits of 2 bytes per entry (p / NC column tiles
+// of p / 16 chunk images of 8 NC K-major rows of 16 entries each)
 __host__ __device__ constexpr size_t tc_cmat_bytes(int nblkC, int p) {
-  return (size_t)nblkC * (p / kTcCols) * (p / kTcK) * kTcStageBytesB;
+  return (size_t)nblkC * p * p * kTcSlices * 2;
 }
+// digit slice and stage of an N x 16 chunk for output tiles of NC columns (64; 32 for blocks of 32 columns)
+template <int NC>
+__host__ __device__ constexpr uint32_t tc_slice_b() { return (uint32_t)NC * kTcK * 2; }
+template <int NC>
+__host__ __device__ constexpr uint32_t tc_stage_b() { return kTcSlices * tc_slice_b<NC>(); }
 
 // ---- PTX wrappers (tcgen05, mbarrier) --------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -234,25 +240,28 @@ __device__ __forceinline__ void tc_store8(unsigned char *stage, uint32_t slice_b
 // field holds address >> 4 in its low bits, and stage addresses stay below 256 KB, so the addition never carries
 // into the next field). fresh: the first chunk since the accumulators were read out (its first MMA into each
 // accumulator overwrites it).
+template <int NC = kTcCols>
 __device__ __forceinline__ void tc_issue_chunk(uint32_t tbase, uint32_t aStage, uint32_t bStage, bool fresh) {
   static_assert(kTcK == 16, "one K step of kind::f16 per chunk");
-  constexpr uint32_t idesc = tc_idesc_bf16(kTcRows, kTcCols);
+  static_assert(NC == 64 || NC == 32, "N = 64 or 32");
+  constexpr uint32_t idesc = tc_idesc_bf16(kTcRows, NC);
   const uint64_t a0 = tc_smem_desc(aStage, 128, kTcSbo), b0 = tc_smem_desc(bStage, 128, kTcSbo);
 #pragma unroll
   for (int sacc = 0; sacc < kTcSlices; ++sacc)
 #pragma unroll
     for (int i = 0; i <= sacc; ++i)
-      tc_mma(tbase + (uint32_t)(sacc * kTcCols), a0 + (uint64_t)((i * kTcSliceBytesA) >> 4),
-             b0 + (uint64_t)(((sacc - i) * kTcSliceBytesB) >> 4), idesc, i != 0 || !fresh);
+      tc_mma(tbase + (uint32_t)(sacc * NC), a0 + (uint64_t)((i * kTcSliceBytesA) >> 4),
+             b0 + (uint64_t)(((sacc - i) * tc_slice_b<NC>()) >> 4), idesc, i != 0 || !fresh);
 }
 
 // Read back 8 columns (col .. col + 7) of all 8 accumulators for this warp's 32 lanes and combine them:
 // hi[e] + lo[e] = sum_s 2^(-6 s) acc_s (column col + e, this thread's lane), a float pair.
+template <int NC = kTcCols>
 __device__ __forceinline__ void tc_read8(uint32_t tbase, int q, int col, float (&hi)[8], float (&lo)[8]) {
   float acc[kTcSlices][8];
 #pragma unroll
   for (int sacc = 0; sacc < kTcSlices; ++sacc)
-    tmem_ld8(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(sacc * kTcCols + col), acc[sacc]);
+    tmem_ld8(tbase + ((uint32_t)(q * 32) << 16) + (uint32_t)(sacc * NC + col), acc[sacc]);
 #pragma unroll
   for (int e = 0; e < 8; ++e) {
     hi[e] = acc[kTcSlices - 1][e] * 0x1p-42f;
@@ -291,9 +300,11 @@ __device__ __forceinline__ unsigned char *tc_stage_b(unsigned char *ops, int st)
 
 // ---- BAXPY ------------------------------------------------------------------------------------------------------
 // Pre-slicing of the p x p matrices C_jc (row-major, entry (a, b) at jc p p + a p + b) into the bf16 digit images that
-// kt_baxpy copies into a shared-memory B stage: for block jc, N-tile t = b / 64 and chunk c = a / 32, a 32 KB image
-// at ((jc (p/64) + t) (p/32) + c) * 32 KB of 8 slices of 4 KB, entry (b, a) at the core-matrix position of tc_store8
-// (row b mod 64, k-group (a mod 32) / 8, element a mod 8). Cexp[jc p + b] = F_b. One thread per column (jc, b).
+// kt_baxpy copies into a shared-memory B stage: for block jc, N-tile t = b / NC and chunk c = a / 16, an image of
+// tc_stage_b<NC>() bytes at ((jc (p/NC) + t) (p/16) + c) of 8 slices, entry (b, a) at the core-matrix position of
+// tc_store8 (row b mod NC, k-group (a mod 16) / 8, element a mod 8). Cexp[jc p + b] = F_b. One thread per column
+// (jc, b).
+template <int NC>
 __global__ void kt_slice_cmat(const double *__restrict__ C, int nblkC, int p, uint16_t *__restrict__ Cs,
                               int *__restrict__ Cexp) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -304,17 +315,17 @@ __global__ void kt_slice_cmat(const double *__restrict__ C, int nblkC, int p, ui
   for (int a = 0; a < p; ++a) m = fmax(m, fabs(Cj[(size_t)a * p + b]));
   const int F = exponent_of(m);
   Cexp[idx] = F;
-  const int nt = p / kTcCols, nc = p / kTcK, t = b / kTcCols, bl = b % kTcCols;
+  const int nt = p / NC, nc = p / kTcK, t = b / NC, bl = b % NC;
   for (int a = 0; a < p; ++a) {
     const double v = Cj[(size_t)a * p + b];
     const unsigned long long fx = tc_fixed48(v, F);
     const uint32_t sg = signbit(v) ? 0x8000u : 0u;
     const int c = a / kTcK, al = a % kTcK;
-    const size_t img = ((size_t)(jc * nt + t) * nc + c) * kTcStageBytesB;
+    const size_t img = ((size_t)(jc * nt + t) * nc + c) * tc_stage_b<NC>();
     const size_t in_slice = (size_t)((bl >> 3) * (kTcK / 8) + (al >> 3)) * 128 + (bl & 7) * 16 + (al & 7) * 2;
 #pragma unroll
     for (int i = 0; i < kTcSlices; ++i)
-      Cs[(img + (size_t)i * kTcSliceBytesB + in_slice) / 2] = (uint16_t)tc_bf16_digit(tc_digit(fx, i), sg);
+      Cs[(img + (size_t)i * tc_slice_b<NC>() + in_slice) / 2] = (uint16_t)tc_bf16_digit(tc_digit(fx, i), sg);
   }
 }
 
@@ -564,9 +575,10 @@ __device__ __forceinline__ void tc_store16(float *dst, const double (&v)[16]) {
 // blocks that own a row exponent (p; or 16 or 32 where blocks of that width are paired into 64-column tiles with
 // block-diagonal C images, kt_pair_cmat: each output column then sums over its own block's digits only). Frozen blocks
 // (active[j] = 0) get OUT = BASE (scaled). bump: CTA 0 advances the iteration counter (the P update's role).
-// Persistent over 128 x 64 output tiles (tile t: row tile t / (k / 64), column tile t mod (k / 64)); every role
-// walks the CTA's tiles in the same order, the issuing roles skipping frozen blocks.
-template <typename T>
+// Persistent over 128 x NC output tiles (tile t: row tile t / (k / NC), column tile t mod (k / NC); NC = 64, or 32
+// for blocks of 32 columns that are not paired); every role walks the CTA's tiles in the same order, the issuing
+// roles skipping frozen blocks.
+template <typename T, int NC>
 __global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T *BASE,
                                                                  const unsigned char *__restrict__ imgY,
                                                                  const int *__restrict__ erow,
@@ -586,8 +598,9 @@ __global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T
   volatile int *sFlag = reinterpret_cast<volatile int *>(misc + 512);   // [0]: a wait gave up
   long long *sCount = reinterpret_cast<long long *>(misc + 576);       // chunks copied [0] and consumed [1]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nt = p / kTcCols, nc = p / kTcK;
-  const int ntn = k / kTcCols;
+  constexpr int CPT = NC / 2;   // columns per readout thread (two warps per TMEM lane quadrant)
+  const int nt = p / NC, nc = p / kTcK;
+  const int ntn = k / NC;
   const int64_t nrt = (n + kTcRows - 1) / kTcRows;
   const int64_t nrows = nrt * kTcRows;
   const int64_t ntiles = nrt * ntn;
@@ -598,7 +611,7 @@ __global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T
     sCount[0] = sCount[1] = 0;
   }
   __syncthreads();
-  auto tile_active = [&](int64_t t) { return block_active(active, global, (int)(t % ntn) * kTcCols / p); };
+  auto tile_active = [&](int64_t t) { return block_active(active, global, (int)(t % ntn) * NC / p); };
   auto next_active = [&](int64_t t) {
     while (t < ntiles && !tile_active(t)) t += gridDim.x;
     return t;
@@ -607,9 +620,9 @@ __global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T
     int64_t g = 0;
     bool ok = true;
     for (int64_t tile = next_active(blockIdx.x); tile < ntiles && ok; tile = next_active(tile + gridDim.x)) {
-      const int c0 = (int)(tile % ntn) * kTcCols, j = c0 / p, b0 = c0 - j * p, jc = global ? 0 : j;
+      const int c0 = (int)(tile % ntn) * NC, j = c0 / p, b0 = c0 - j * p, jc = global ? 0 : j;
       const unsigned char *cimg =
-          reinterpret_cast<const unsigned char *>(Cs) + (size_t)(jc * nt + b0 / kTcCols) * nc * kTcStageBytesB;
+          reinterpret_cast<const unsigned char *>(Cs) + (size_t)(jc * nt + b0 / NC) * nc * tc_stage_b<NC>();
       const unsigned char *yimg = imgY + ((size_t)(tile / ntn) * (k / kTcK) + (size_t)j * nc) * kTcImgRow;
       for (int c = 0; c < nc; ++c, ++g) {
         const int s = (int)(g % kTcStages);
@@ -617,9 +630,9 @@ __global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T
           ok = false;
           break;
         }
-        mbar_arrive_expect_tx(bars.full[s], kTcImgRow + kTcStageBytesB);
+        mbar_arrive_expect_tx(bars.full[s], kTcImgRow + tc_stage_b<NC>());
         bulk_g2s(smem_u32(tc_stage_a(ops, s)), yimg + (size_t)c * kTcImgRow, kTcImgRow, bars.full[s]);
-        bulk_g2s(smem_u32(tc_stage_b(ops, s)), cimg + (size_t)c * kTcStageBytesB, kTcStageBytesB, bars.full[s]);
+        bulk_g2s(smem_u32(tc_stage_b(ops, s)), cimg + (size_t)c * tc_stage_b<NC>(), tc_stage_b<NC>(), bars.full[s]);
       }
     }
     if (!ok) sFlag[0] = 1;
@@ -640,7 +653,7 @@ __global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T
           break;
         }
         tc_fence_after();
-        tc_issue_chunk(tbase, smem_u32(tc_stage_a(ops, s)), smem_u32(tc_stage_b(ops, s)), c == 0);
+        tc_issue_chunk<NC>(tbase, smem_u32(tc_stage_a(ops, s)), smem_u32(tc_stage_b(ops, s)), c == 0);
         tc_commit(bars.empty[s]);
       }
       if (ok) tc_commit(bars.done);
@@ -648,16 +661,16 @@ __global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T
     if (!ok) sFlag[0] = 1;
     sCount[1] = g;
   } else if (warp < kTcOutWarps) {
-    const int q = warp & 3, cb0 = (warp >> 2) * 32;   // TMEM lane quadrant; first of the thread's 32 columns
+    const int q = warp & 3, cb0 = (warp >> 2) * CPT;   // TMEM lane quadrant; first of the thread's CPT columns
     const int rl = q * 32 + lane;
     int64_t i = 0;
     for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-      const int c0 = (int)(tile % ntn) * kTcCols, j = c0 / p, b0 = c0 - j * p, jc = global ? 0 : j;
+      const int c0 = (int)(tile % ntn) * NC, j = c0 / p, b0 = c0 - j * p, jc = global ? 0 : j;
       const int64_t r = (tile / ntn) * kTcRows + rl;
       if (!block_active(active, global, j)) {   // frozen block: OUT = BASE (scaled)
         if (r < n) {
           const T s = bscale ? bscale[r] : T(1);
-          for (int e = 0; e < 32; ++e) OUT[r * k + c0 + cb0 + e] = BASE ? BASE[r * k + c0 + cb0 + e] * s : T(0);
+          for (int e = 0; e < CPT; ++e) OUT[r * k + c0 + cb0 + e] = BASE ? BASE[r * k + c0 + cb0 + e] * s : T(0);
         }
         continue;
       }
@@ -670,21 +683,22 @@ __global__ void __launch_bounds__(kTcBaxThreads, 1) kt_baxpy_img(T *OUT, const T
       }
       ++i;
       tc_fence_after();
-      float hi[4][8], lo[4][8];
+      float hi[CPT / 8][8], lo[CPT / 8][8];
 #pragma unroll
-      for (int cg = 0; cg < 4; ++cg) tc_read8(tbase, q, cb0 + cg * 8, hi[cg], lo[cg]);
+      for (int cg = 0; cg < CPT / 8; ++cg) tc_read8<NC>(tbase, q, cb0 + cg * 8, hi[cg], lo[cg]);
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(tfree);
       if (r >= n) continue;
       // (s + c) 2^t as one double (integer operations), one FP64 addition; 16 columns at a time, their BASE
       // values loaded before any store (OUT may be BASE). Row exponents per pe columns: columns cb0 .. +15 take
-      // Eh[0], cb0 + 16 .. +31 take Eh[1] (the same value unless pe = 16).
-      const int Eh[2] = {erow[(int64_t)((c0 + cb0) / pe) * nrows + r], erow[(int64_t)((c0 + cb0 + 16) / pe) * nrows + r]};
+      // Eh[0], cb0 + 16 .. +31 (CPT = 32) take Eh[1] (the same value unless pe = 16).
+      const int e0 = erow[(int64_t)((c0 + cb0) / pe) * nrows + r];
+      const int Eh[2] = {e0, CPT > 16 ? erow[(int64_t)((c0 + cb0 + 16) / pe) * nrows + r] : e0};
       const double bs = bscale ? (double)bscale[r] : 1.0;
       const int4 *F4 = reinterpret_cast<const int4 *>(Cexp + jc * p + b0 + cb0);
 #pragma unroll
-      for (int half = 0; half < 2; ++half) {
+      for (int half = 0; half < CPT / 16; ++half) {
         const int E = Eh[half];
         const bool bad = E == kTcBadRow;
         double v[16];

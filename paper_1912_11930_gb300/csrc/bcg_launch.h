@@ -104,6 +104,8 @@ bool tc_ok(int k, int p);
 // which launch_tc_slice cuts with p = 64; launch_tc_cut_rows takes p = 32 (one exponent per row of each block);
 // launch_tc_baxpy_img takes p = 64 and pe = 32.
 bool tc_pair_ok(int k, int p);
+// Blocks of 32 where 64 does not divide k: 32-column tiles (launch_tc_slice and launch_tc_baxpy_img with p = 32)
+bool tc_b32_ok(int k, int p);
 cudaError_t launch_tc_pair_cmat(const double *C, int k, int p, int global, double *out, cudaStream_t s);
 size_t tc_workspace_bytes(int nblkC, int p);
 cudaError_t launch_tc_slice(const double *C, int nblkC, int p, uint16_t *Cs, int *Cexp, cudaStream_t s);

@@ -9,6 +9,8 @@ bool tc_ok(int k, int p) { return tc_layout_ok(k, p); }
 // blocks of 16 fit the kernels too, but measured slower than their fused FMA path: K1 must then form the recomputed
 // rho (K3 does at p <= 16), and rho and the norms need passes of their own (160^3, k = 64: 44.7 s against 40.3 s)
 bool tc_pair_ok(int k, int p) { return p == 32 && tc_pair_layout_ok(k, p); }
+// blocks of 32 in 32-column tiles (k a multiple of 32 that 64 does not divide)
+bool tc_b32_ok(int k, int p) { return p == 32 && k % 32 == 0 && k <= 256 && k % 64 != 0; }
 
 cudaError_t launch_tc_pair_cmat(const double *C, int k, int p, int global, double *out, cudaStream_t s) {
   if (!tc_pair_layout_ok(k, p)) return cudaErrorInvalidValue;
@@ -20,7 +22,9 @@ size_t tc_workspace_bytes(int nblkC, int p) { return tc_cmat_bytes(nblkC, p); }
 
 cudaError_t launch_tc_slice(const double *C, int nblkC, int p, uint16_t *Cs, int *Cexp, cudaStream_t s) {
   const int nthr = nblkC * p;
-  kt_slice_cmat<<<(nthr + 127) / 128, 128, 0, s>>>(C, nblkC, p, Cs, Cexp);
+  if (p % 64 == 0) kt_slice_cmat<64><<<(nthr + 127) / 128, 128, 0, s>>>(C, nblkC, p, Cs, Cexp);
+  else if (p == 32) kt_slice_cmat<32><<<(nthr + 127) / 128, 128, 0, s>>>(C, nblkC, p, Cs, Cexp);
+  else return cudaErrorInvalidValue;
   return cudaGetLastError();
 }
 
@@ -55,7 +59,7 @@ template cudaError_t launch_tc_cut_cols<float>(const float *, const float *, int
 
 template <typename T>
 cudaError_t launch_tc_cut_rows(const T *Y, int64_t n, int k, int p, unsigned char *img, int *erow, cudaStream_t s) {
-  if (!tc_layout_ok(k, p) && !tc_pair_layout_ok(k, p)) return cudaErrorInvalidValue;
+  if (!tc_layout_ok(k, p) && !tc_pair_layout_ok(k, p) && !tc_b32_ok(k, p)) return cudaErrorInvalidValue;
   const int64_t nrt = (n + kTcRows - 1) / kTcRows;
   kt_cut_rows<T><<<dim3((unsigned)nrt, (unsigned)(k / p)), kTcThreads, 0, s>>>(Y, n, k, p, img, erow);
   return cudaGetLastError();
@@ -83,13 +87,16 @@ cudaError_t launch_tc_baxpy_img(T *OUT, const typename TcId<T>::type *BASE, cons
                                 int global, double sign, const int *active, DevStatus *st, int bump, cudaStream_t s,
                                 const typename TcId<T>::type *bscale, int nsm, int pe) {
   if (pe == 0) pe = p;
-  if (!tc_layout_ok(k, p) || !(pe == p || (p == 64 && tc_pair_layout_ok(k, pe)))) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(kt_baxpy_img<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+  const bool b32 = tc_b32_ok(k, p) && pe == p;   // 32-column tiles
+  if (!b32 && (!tc_layout_ok(k, p) || !(pe == p || (p == 64 && tc_pair_layout_ok(k, pe)))))
+    return cudaErrorInvalidValue;
+  auto kern = b32 ? kt_baxpy_img<T, 32> : kt_baxpy_img<T, 64>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
   if (e != cudaSuccess) return e;
-  const int64_t ntiles = ((n + kTcRows - 1) / kTcRows) * (k / kTcCols);
+  const int64_t ntiles = ((n + kTcRows - 1) / kTcRows) * (k / (b32 ? 32 : 64));
   const int grid = (int)std::min<int64_t>(ntiles, nsm);
-  kt_baxpy_img<T><<<grid, kTcBaxThreads, kTcSmem, s>>>(OUT, BASE, imgY, erow, Cs, Cexp, n, k, p, global, sign, active,
-                                                       st, bump, bscale, pe);
+  kern<<<grid, kTcBaxThreads, kTcSmem, s>>>(OUT, BASE, imgY, erow, Cs, Cexp, n, k, p, global, sign, active, st, bump,
+                                            bscale, pe);
   return cudaGetLastError();
 }
 template cudaError_t launch_tc_baxpy_img<double>(double *, const double *, const unsigned char *, const int *,

@@ -566,12 +566,14 @@ def test_large_p_tensor_cores_match_fma(torch_dev, name, sub, k, p, m):
 
 
 @pytest.mark.parametrize("name,sub,k,p,m", [("p3d_30", "hybrid", 64, 32, 6), ("p3d_30", "hybrid", 128, 32, 5),
-                                            ("s27_15", "global", 128, 32, 5), ("vc_20", "hybrid", 256, 32, 4)])
+                                            ("s27_15", "global", 128, 32, 5), ("vc_20", "hybrid", 256, 32, 4),
+                                            ("p3d_30", "classical", 32, 32, 6), ("vc_20", "hybrid", 96, 32, 5),
+                                            ("s27_15", "global", 96, 32, 5)])
 def test_pairs_of_32_tensor_cores_match_fma(torch_dev, name, sub, k, p, m):
-    """FP64 blocks of 32 columns with k a multiple of 64 take their block updates on the tensor cores, two blocks per
-    64-column tile (block-diagonal coefficient images, row exponents per block of 32): against the warp-chunk FMA
-    kernels (option "tensor_cores" 0) and the oracle at equal iteration counts, with and without Jacobi. The row
-    counts (26,970, 2,730, 7,820) leave ragged last tiles."""
+    """FP64 blocks of 32 columns take their block updates on the tensor cores: two blocks per 64-column tile where 64
+    divides k (block-diagonal coefficient images, row exponents per block of 32), else 32-column tiles (k = 32, 96).
+    Against the FMA kernels (option "tensor_cores" 0) and the oracle at equal iteration counts, with and without
+    Jacobi. The row counts (26,970, 2,730, 7,820) leave ragged last tiles."""
     M = mat(name)
     B = W.rhs(M.n, k, seed=37)
     for jac in (0, 1):

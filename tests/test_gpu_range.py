@@ -65,7 +65,8 @@ def gpu_solve(torch_dev, M, B, *, k, p, sub, prec="fp64", form="csr", tol=NEVER,
 # (sub, k, p, operator form): the streaming kernels (per-element and warp-chunk layouts), the matrix-free
 # stencil and the tiled large-block path
 ALG1 = [("hybrid", 8, 4, "csr"), ("global", 8, 4, "csr"), ("parallel", 8, 1, "csr"), ("hybrid", 32, 8, "csr"),
-        ("hybrid", 6, 3, "csr"), ("hybrid", 8, 4, "stencil"), ("classical", 64, 64, "csr"), ("hybrid", 64, 32, "csr")]
+        ("hybrid", 6, 3, "csr"), ("hybrid", 8, 4, "stencil"), ("classical", 64, 64, "csr"), ("hybrid", 64, 32, "csr"),
+        ("classical", 32, 32, "csr")]
 
 
 @pytest.mark.parametrize("sb,sa", SCALES)
