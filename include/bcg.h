@@ -43,7 +43,7 @@
  *    1e300 and exact zeros, and with B scaled by 1e+-30 and A by 1e+-10); within the solver a column may
  *    grow by about 2^50 or shrink by about 2^49 between two norm updates without loss.
  *  - Tensor cores (option "tensor_cores", on by default): with p a multiple of 64 (up to 256) the block products
- *    and block updates, and with p = 32 and k a multiple of 64 the block updates, are formed on the tensor
+ *    and block updates, and with p = 32 the block updates, are formed on the tensor
  *    cores instead (Ozaki, Ogita, Oishi & Rump, Numer. Algorithms 59, 2012). Every operand value is truncated
  *    to 48 bits below an exponent shared along the contraction (per row of a block for the updated block Y,
  *    per column for lambda / beta and for the operands of the products) and cut into eight 6-bit digits held
@@ -213,7 +213,7 @@ bcg_status bcg_create_stencil(bcg_handle *h, int32_t kind, int32_t nx, int32_t n
  *                  only (INVALID_ARG otherwise); 0 = Algorithm 1 (default).
  *   "tensor_cores" 1 (default) = the tcgen05 path described under "Arithmetic of the FP64 form": FP64 handles
  *                  with p a multiple of 64 take their block products and updates there, FP64 handles with
- *                  p = 32 and k a multiple of 64 their block updates (two blocks per 64-column tile); the
+ *                  p = 32 their block updates (two blocks per 64-column tile where 64 divides k); the
  *                  mixed form's FP32 process with p a multiple of 64 takes both (its updates summed in FP64
  *                  and rounded once to FP32). 0 = FP64 FMA updates and Dot2 products everywhere.
  *   "guards"       1 = after each solve (bcg_solve, bcg_solve_host, bcg_rows_finish) compare the 16 guard
