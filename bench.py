@@ -189,8 +189,8 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------------------------------------------
 # Other workloads (not the default line): measured with `python bench.py --workload NAME`
 EXTRA_WORKLOADS = ("poisson2d_64_k8", "varcoef3d_160_k64_mixed", "varcoef3d_160_k64_jacobi", "stencil27_100_k16_autograd",
-                   "poisson3d_96_sweep", "sell_vs_csr", "large_blocks_64_k256", "retooled_128_k32",
-                   "repetitions_varcoef2d_512_128rhs")
+                   "poisson3d_96_sweep", "sell_vs_csr", "large_blocks_64_k256", "blocks32_96_k256",
+                   "retooled_128_k32", "repetitions_varcoef2d_512_128rhs")
 
 
 def time_solve(bcg, torch, M, B, *, k, p, sub, prec, form="csr", tol=1e-8, reps=2, dev=None, opts=None, warm=True,
@@ -330,6 +330,22 @@ def run_extra(name, args):
         out.update(value=rows[0]["s"], dtype="f64 (and f32 with f64 residual replacement)",
                    config={"workload": "poisson3d_64_csr_k256_classical_24_iterations", "n": M.n, "k": k, "p": k},
                    results=rows, tensor_core_kernels=tc)
+    elif name == "blocks32_96_k256":
+        # hybrid blocks of 32 at k = 256 (FP64): 24 iterations with the block updates on the tensor cores (two blocks
+        # per 64-column tile) and 24 on the warp-chunk FMA kernels, for the launch profile of that path
+        M = W.poisson3d(96)
+        k, p = 256, 32
+        B = torch.from_numpy(W.rhs(M.n, k, seed=0)).to(dev)
+        rows = []
+        for tc in (1, 0):
+            t, r, _ = time_solve(bcg, torch, M, B, k=k, p=p, sub="hybrid", prec="fp64", tol=1e-300, reps=1, dev=dev,
+                                 warm=False, maxit=24, opts={"tensor_cores": tc})
+            rows.append(dict(prec="fp64", tensor_cores=tc, s=t, iterations=r.iters, status=bcg.STATUS_NAMES[r.status],
+                             ms_per_iteration=t * 1e3 / max(r.iters, 1)))
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        out.update(value=rows[0]["s"], dtype="f64",
+                   config={"workload": "poisson3d_96_csr_k256_hybrid_p32_24_iterations", "n": M.n, "k": k, "p": p},
+                   results=rows)
     elif name == "retooled_128_k32":
         # Dubrulle's retooled block CG against Algorithm 1 (FP64): the 128^3 Poisson solve to 1e-8, the same with
         # the right-hand side's columns scaled from 1e-6 to 1e6 inside every block of 8 (Algorithm 1 breaks down
