@@ -20,17 +20,17 @@
 // The operands are cut once per use into digit images in global memory that are byte for byte the kernels'
 // shared-memory stages (kt_cut_rows, kt_cut_cols, kt_slice_cmat; see "Digit images" below):
 //   BAXPY: u = Y[r][.] with one exponent per row (over the block's p columns), v = C[.][b] with one per column;
-//          output tiles of 128 rows x 64 columns of one block.
+//          output tiles of 128 rows x 64 columns (x 32 for blocks of 32 that 64-column tiles cannot pair).
 //   Gram:  u = X[.][a], v = Y[.][b] with one exponent per column over all rows (kt_col_exp); output tiles of
 //          128 x 64 entries of one block (rows of the tile beyond p are zero), partial sums over a range of rows,
 //          read out every 512 rows into float pairs.
-// Work: one CTA per SM (256 threads, ~200 KB of shared memory, the whole 512-column TMEM: 8 accumulators of 64
-// FP32 columns x 128 lanes). The contraction runs in chunks of 16 through four shared-memory stages: one thread
-// fills a stage with bulk copies of the images, issues the chunk's 36 MMAs (M = 128, N = 64, K = 16) when the
-// copies are in and commits them to the stage's "empty" mbarrier, so the copies of the next three chunks overlap
-// the MMAs of this one (K-major core matrices of 8 rows x 16 bytes, no swizzle). Every wait on an mbarrier is bounded:
-// ST_TIMEOUT if it never completes. The CTA reads the accumulators back with tcgen05.ld (warp w: TMEM lanes
-// 32 (w mod 4) .. +31, 8 columns at a time).
+// Work: one CTA per SM (256 threads for the products, 320 for the updates; ~200 KB of shared memory; the whole
+// 512-column TMEM: 8 accumulators of 64 FP32 columns x 128 lanes). The contraction runs in chunks of 16 through four
+// shared-memory stages: a producer thread fills a stage with bulk copies of the images, an MMA thread issues the
+// chunk's 36 MMAs (M = 128, N = 64, K = 16) when the copies are in and commits them to the stage's "empty"
+// mbarrier, so the copies of the next three chunks overlap the MMAs of this one (K-major core matrices of 8 rows x
+// 16 bytes, no swizzle). Every wait on an mbarrier is bounded: ST_TIMEOUT if it never completes. The accumulators
+// are read back with tcgen05.ld (warp w: TMEM lanes 32 (w mod 4) .. +31, 8 columns at a time).
 #pragma once
 
 #include <cstdint>
@@ -368,17 +368,16 @@ __global__ void __launch_bounds__(kNT) kt_col_exp(const T *__restrict__ X, const
 // Cutting the operands inside the MMA kernels (one CTA per output tile) would cut an operand feeding several
 // output tiles once per tile (4 times for the Gram's X at p = 256), on the integer pipe, while the tensor pipe
 // waits. So every operand is cut once per use into HBM images that are byte-for-byte shared-memory stages, and the
-// MMA kernels fill their stages with bulk copies (cp.async.bulk, completion counted on an mbarrier); one thread
-// produces the stages and issues the MMAs, and the whole CTA only reads the accumulators out.
-//   row images (BAXPY's Y, one exponent per row of a block): 64 KB per (128-row tile rt, 32-column chunk kc of
-//     k), the A stage of kt_baxpy: image (rt, kc) at (rt (k/32) + kc) 64 KB; erow[j * nrows + r] = E_r of block j
-//     (kTcBadRow: a non-finite value in the row).
-//   column images (the Gram's operands, one exponent per column over all rows): 32 KB per (64-column tile ct,
-//     32-row chunk rc), the B stage of kt_gram; image (ct, rc) at (ct nrc + rc) 32 KB, nrc = ceil(n / 32). An A
-//     stage of 128 columns is the two 64-column images side by side in every 8 KB slice.
+// MMA kernels fill their stages with bulk copies (cp.async.bulk, completion counted on an mbarrier).
+//   row images (BAXPY's Y, one exponent per row of a block): 32 KB per (128-row tile rt, 16-column chunk kc of
+//     k), the A stage of kt_baxpy_img: image (rt, kc) at (rt (k/16) + kc) 32 KB; erow[j * nrows + r] = E_r of
+//     block j (kTcBadRow: a non-finite value in the row).
+//   column images (the Gram's operands, one exponent per column over all rows): 16 KB per (64-column tile ct,
+//     16-row chunk rc), the B stage of kt_gram_img; image (ct, rc) at (ct nrc + rc) 16 KB, nrc = ceil(n / 16). An
+//     A stage of 128 columns is the two 64-column images side by side in every 4 KB slice.
 constexpr int kTcBadRow = 0x7FFFFFFF;
-constexpr uint32_t kTcImgRow = kTcStageBytesA;   // 64 KB
-constexpr uint32_t kTcImgCol = kTcStageBytesB;   // 32 KB
+constexpr uint32_t kTcImgRow = kTcStageBytesA;   // 32 KB
+constexpr uint32_t kTcImgCol = kTcStageBytesB;   // 16 KB
 
 __host__ __device__ constexpr size_t tc_row_image_bytes(int64_t n, int k) {
   return (size_t)((n + kTcRows - 1) / kTcRows) * (k / kTcK) * kTcImgRow;
