@@ -330,7 +330,7 @@ bcg_status bcg_bop(bcg_handle h, const double *X, double *Y);
  * stream (plain launches, no graph replay), counting only iterations that executed. Fills, for
  *   0 K1 (BOP + alpha + recomputed rho), 1 K4a (Cholesky solve), 2 K2 (X, R update + rho + norms),
  *   3 K4b (stopping test + LU solve), 4 K3 (P update), 5 reserved, 6 the tensor-core block products and
- *   7 the tensor-core block updates of wide FP64 blocks (each launch timed alone, the host waiting for it),
+ *   7 the tensor-core block updates (FP64 blocks of 32 and wider; each launch timed alone, the host waiting for it),
  * the total milliseconds ms[i] and the launch count count[i]. ms, count: host arrays of cap >= 8.
  * Timing instrumentation, not part of the paper's method.
  */
